@@ -1,0 +1,309 @@
+/*
+ * splat.h -- C ABI of the GB300 (sm_103a) hybrid 3D-4D Gaussian rasterizer.
+ *
+ * The library renders a mixed set of static 3D Gaussians and dynamic 4D
+ * Gaussians ("Hybrid 3D-4D Gaussian Splatting for Fast Dynamic Scene
+ * Representation", Sec. 4.3 and Alg. 1 "GPU Rasterization of 3D&4D
+ * Gaussians") and differentiates the result with respect to every Gaussian
+ * parameter.  One call of each stage handles a batch of V views (cameras and
+ * timestamps, resolutions may differ).  Stages, in order:
+ *
+ *   splat_slice_project     Alg. 1 CullGaussian, ProjGaussian4D, ProjGaussian3D
+ *   splat_bin_sort          Alg. 1 CreateTiles, DuplicateWithKeys, SortByKeys,
+ *                           IdentifyTileRanges
+ *   splat_composite_fwd     Alg. 1 BlendInOrder (Eq. 3)
+ *   splat_composite_bwd     reverse mode of all of the above
+ *   splat_convert_4d_to_3d  Sec. 4.1 static/dynamic identification and
+ *                           Sec. 4.2 conversion (Eq. 9)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every pointer inside the structs below is DEVICE memory owned by the
+ *    caller, unless a comment says "host".  The library never allocates; its
+ *    scratch memory is a caller-supplied workspace of splat_workspace_size()
+ *    bytes (256-byte aligned).  Pointers are borrowed for the call only.
+ *  - Calls are asynchronous on the caller's CUDA stream (`stream`, a
+ *    cudaStream_t; NULL = legacy default stream) and may be captured into a
+ *    CUDA graph: no entry point synchronises or reads device memory on the
+ *    host.
+ *  - The return value reports argument errors found on the host
+ *    (SPLAT_ERR_INVALID_ARG) and launch failures (SPLAT_ERR_CUDA).  Errors
+ *    found on the device are written to `status`, a device int32[4]:
+ *      status[0]  first error code (0 = OK), never overwritten once set
+ *      status[1]  stage that set it (SPLAT_STAGE_*)
+ *      status[2]  low 32 bits of an auxiliary value (CAPACITY: required count)
+ *      status[3]  high 32 bits of it
+ *    splat_slice_project clears status at its start; later stages skip their
+ *    work while status[0] != 0.  Kernels never trap: bounded waits that run
+ *    out set SPLAT_ERR_TIMEOUT and return.
+ *  - Gaussian parameters are raw, before activation: log-scales, opacity
+ *    logits, quaternions that need not be normalised, quaternion order
+ *    (w,x,y,z) for 3D and (a,b,c,d) / (p,q,r,s) for the 4D left / right
+ *    quaternions of Eq. 4.  4D coordinates are (x,y,z,t).  All fields of one
+ *    set share one storage dtype (SPLAT_F32, SPLAT_BF16, SPLAT_F16); all
+ *    arithmetic is FP32, gradients are always FP32.
+ *  - Merged index: inside one view, Gaussian i in [0, N4) is the i-th 4D
+ *    Gaussian and i in [N4, N4+N3) the (i-N4)-th 3D Gaussian (Alg. 1 fills M'
+ *    with the 4D Gaussians first, then appends the 3D ones).  Projected rows
+ *    are indexed r = v*N + i with N = N4 + N3.
+ *  - Tiles are 16x16 pixels.  View v has TX = ceil(W/16) by TY = ceil(H/16)
+ *    tiles; tiles of all views are numbered consecutively, view by view, row
+ *    major inside a view.  Pixel (u, y) of a view is evaluated at the point
+ *    (u, y) of the image plane, where a camera-space point (x, y, z) lands at
+ *    (fx x/z + cx, fy y/z + cy).
+ *  - Images of all views are stored back to back: view v starts at pixel
+ *    offset P_v = sum_{w<v} W_w H_w; rgb is planar per view, [3][H][W]
+ *    starting at float offset 3 P_v; final_T and last start at offset P_v.
+ */
+#ifndef SPLAT_H
+#define SPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPLAT_OK = 0,
+    SPLAT_ERR_INVALID_ARG = 1, /* host-side argument check failed                */
+    SPLAT_ERR_CAPACITY = 2,    /* a caller buffer is too small; see status[2..3] */
+    SPLAT_ERR_TIMEOUT = 3,     /* a bounded device-side wait ran out             */
+    SPLAT_ERR_NONFINITE = 4,   /* a projected quantity was NaN or infinite        */
+    SPLAT_ERR_CUDA = 5         /* a CUDA runtime call or launch failed            */
+} splat_status;
+
+typedef enum { SPLAT_F32 = 0, SPLAT_BF16 = 1, SPLAT_F16 = 2 } splat_dtype;
+
+enum {
+    SPLAT_STAGE_SLICE_PROJECT = 1,
+    SPLAT_STAGE_DEPTH_SORT = 2,
+    SPLAT_STAGE_SCAN = 3,
+    SPLAT_STAGE_DUPLICATE = 4,
+    SPLAT_STAGE_TILE_SORT = 5,
+    SPLAT_STAGE_COMPOSITE_FWD = 6,
+    SPLAT_STAGE_COMPOSITE_BWD = 7,
+    SPLAT_STAGE_ADJOINT = 8,
+    SPLAT_STAGE_CONVERT = 9
+};
+
+#define SPLAT_MAX_VIEWS 16
+#define SPLAT_TILE 16
+#define SPLAT_SH_COEFFS 16           /* degree 3, 3 channels each              */
+#define SPLAT_MAX_INSTANCES (1 << 30) /* upper bound of splat_bins.capacity    */
+
+/* Static 3D Gaussians (Eq. 1, Eq. 2). */
+typedef struct {
+    int64_t n;        /* N3                                                     */
+    int64_t capacity; /* rows allocated in every field (>= n); convert appends  */
+    int32_t dtype;    /* splat_dtype of every field                             */
+    int32_t reserved;
+    void *mean;       /* [capacity][3] world position                           */
+    void *log_scale;  /* [capacity][3] s, scale = exp(s)                        */
+    void *quat;       /* [capacity][4] (w,x,y,z)                                */
+    void *opacity;    /* [capacity]    logit, opacity = sigmoid(o)              */
+    void *sh;         /* [capacity][16][3] SH coefficients, degree 3            */
+} splat_g3;
+
+/* Dynamic 4D Gaussians (Eq. 4 - Eq. 6). */
+typedef struct {
+    int64_t n;        /* N4                                                     */
+    int32_t dtype;
+    int32_t reserved;
+    void *mean;       /* [n][4] (x,y,z,t)                                       */
+    void *log_scale;  /* [n][4] (s_x,s_y,s_z,s_t)                               */
+    void *ql;         /* [n][4] left quaternion (a,b,c,d)                       */
+    void *qr;         /* [n][4] right quaternion (p,q,r,s)                      */
+    void *opacity;    /* [n]                                                    */
+    void *sh;         /* [n][16][3]                                             */
+} splat_g4;
+
+/* One camera and timestamp (host memory; the library copies it into kernel
+ * parameters).  x_cam = R x_world + T, R row major. */
+typedef struct {
+    float R[9];
+    float T[3];
+    float fx, fy, cx, cy;
+    int32_t W, H;     /* image size in pixels, each in [1, 16384]               */
+    float t;          /* timestamp the 4D Gaussians are sliced at (Eq. 5/6)     */
+    float z_near;     /* Gaussians with camera depth <= z_near are culled       */
+    float bg[3];      /* background colour added with the final transmittance   */
+    float reserved;
+} splat_view;
+
+/* Projected Gaussians (Alg. 1 M'), one row per (view, merged Gaussian). */
+typedef struct {
+    int64_t n;             /* N = N4 + N3 rows per view                         */
+    int32_t views;         /* V                                                 */
+    int32_t reserved;
+    float *xy;             /* [V*N][2]  projected mean (px, py)                  */
+    float *conic_opacity;  /* [V*N][4]  (a, b, c, alpha_max): inverse 2D covariance
+                              [[a,b],[b,c]] and the peak opacity                 */
+    float *rgb_depth;      /* [V*N][4]  (r, g, b, camera depth)                  */
+    int32_t *rect;         /* [V*N][4]  tile rectangle x0,y0,x1,y1 (half open)   */
+    int32_t *radius;       /* [V*N]     support radius in pixels, 0 = culled     */
+    uint32_t *n_tiles;     /* [V*N]     tiles in the rectangle, 0 = culled        */
+} splat_proj;
+
+/* Per-tile sorted instance lists (Alg. 1 L, K and R). */
+typedef struct {
+    int64_t capacity;      /* entries allocated in keys / vals, <= 2^30          */
+    uint32_t *keys;        /* [capacity] global tile index, ascending             */
+    uint32_t *vals;        /* [capacity] projected row v*N + i                    */
+    uint32_t *ranges;      /* [total_tiles][2] [start, end) of each tile in vals  */
+    int64_t *n_instances;  /* [1] K, the number of (tile, Gaussian) instances;
+                              on SPLAT_ERR_CAPACITY the count that was needed    */
+} splat_bins;
+
+/* Rendered images and the per-pixel state the backward pass replays. */
+typedef struct {
+    float *rgb;            /* [sum_v 3 W_v H_v] planar per view                  */
+    float *final_T;        /* [sum_v W_v H_v] transmittance after the last blend */
+    int32_t *last;         /* [sum_v W_v H_v] list entries walked up to and
+                              including the last contributing Gaussian          */
+} splat_image;
+
+/* FP32 gradients, same shapes as splat_g3 / splat_g4 (first n rows). */
+typedef struct {
+    float *mean, *log_scale, *quat, *opacity, *sh;
+} splat_grads3;
+
+typedef struct {
+    float *mean, *log_scale, *ql, *qr, *opacity, *sh;
+} splat_grads4;
+
+/* Workspace selectors for splat_workspace_size. */
+enum {
+    SPLAT_OP_BIN_SORT = 1,
+    SPLAT_OP_COMPOSITE_BWD = 2,
+    SPLAT_OP_CONVERT = 3,
+    SPLAT_OP_ALL = 4       /* one workspace good for every entry point           */
+};
+
+/* splat_composite_bwd flags */
+#define SPLAT_BWD_STOP_2D 1u /* stop after the 2D gradients (dproj), skip the adjoint */
+
+/*
+ * Bytes of workspace an entry point needs.  N3, N4: Gaussian counts (for
+ * CONVERT, N4 is the 4D count); V views of sizes W[v] x H[v] (host arrays);
+ * capacity: splat_bins.capacity.  Returns 0 on invalid arguments.
+ */
+size_t splat_workspace_size(int op, int64_t N3, int64_t N4, int V, const int32_t *W, const int32_t *H,
+                            int64_t capacity);
+
+/* Total number of tiles of V views (host arrays W, H): the length of
+ * splat_bins.ranges / 2. */
+int64_t splat_total_tiles(int V, const int32_t *W, const int32_t *H);
+
+/*
+ * Alg. 1 CullGaussian + ProjGaussian4D + ProjGaussian3D, for every view.
+ * 4D Gaussians are sliced at the view's t: conditional mean (Eq. 5) and
+ * Schur-complement covariance (Eq. 6) of Sigma_4D = R S S^T R^T with R from
+ * Eq. 4, and opacity scaled by exp(-(t-mu_t)^2 / (2 Sigma_tt)).  Every Gaussian
+ * is culled when its camera depth is <= z_near or its peak opacity is below
+ * 1/255, EWA-projected (Jacobian at the mean with x/z, y/z clamped to
+ * +-1.3 W/(2 fx), +-1.3 H/(2 fy); 0.3 px^2 added to the 2D covariance
+ * diagonal), given the radius ceil(3 sqrt(lambda_max)), the tile rectangle
+ * [floor((px-r)/16), ceil((px+r)/16)) x [...] clipped to the image's tiles, and
+ * the colour max(0, 0.5 + sum_k sh_k Y_k(d)) of the degree-3 real SH at the
+ * unit direction d from the camera centre to the (sliced) mean.
+ * g3 / g4 may be NULL or have n == 0.  out->n must be N4 + N3 and
+ * out->views == V.  Clears status[] first.
+ */
+splat_status splat_slice_project(const splat_g3 *g3, const splat_g4 *g4, const splat_view *views, int V,
+                                 splat_proj *out, int32_t *status, void *stream);
+
+/*
+ * Alg. 1 CreateTiles + DuplicateWithKeys + SortByKeys + IdentifyTileRanges.
+ * Every visible row emits one instance per tile of its rectangle, keyed by
+ * (global tile index, camera depth); the instances are sorted by that key,
+ * stably, ties in emission order (row r ascending, tiles row major).  Because
+ * the depth part of the key is the same for every instance of a row, the
+ * depth digits of this LSD radix sort are sorted once per row before the
+ * duplication, then the tile digits after it; the resulting order is the
+ * same.  Writes bins->keys/vals (first K entries), bins->ranges (every tile,
+ * [0,0) when empty) and *bins->n_instances = K.  K > capacity sets
+ * SPLAT_ERR_CAPACITY with the required K in status[2..3] and n_instances.
+ */
+splat_status splat_bin_sort(const splat_proj *proj, const splat_view *views, int V, splat_bins *bins,
+                            int32_t *status, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Alg. 1 BlendInOrder, Eq. 3 front to back per pixel over its tile's list:
+ * power = -(a dx^2 + c dy^2)/2 - b dx dy with (dx, dy) = mean - pixel; skip
+ * when power > 0; alpha = min(0.99, alpha_max exp(power)); skip when
+ * alpha < 1/255; stop (without blending) when T (1 - alpha) < 1e-4;
+ * otherwise C += rgb alpha T, T *= 1 - alpha.  Finally C += T bg.
+ */
+splat_status splat_composite_fwd(const splat_proj *proj, const splat_bins *bins, const splat_view *views, int V,
+                                 splat_image *img, int32_t *status, void *stream);
+
+/*
+ * Reverse mode of the forward pipeline for a loss with pixel gradient
+ * dL_drgb (same layout as img->rgb).  Replays each pixel back to front from
+ * its stored final_T and last (T_i = T_{i+1} / (1 - alpha_i)); no per-splat
+ * state is stored by the forward.  Writes the 2D gradients to dproj (caller
+ * memory [V*N][12] f32, or workspace when dproj is NULL): per row
+ * (dpx, dpy, da, db, dc, dalpha_max, dr, dg, db, 0, 0, 0), then chains them
+ * through the colour, EWA, slicing and covariance of every Gaussian and
+ * OVERWRITES dg3 / dg4 with the gradient summed over the V views.  With
+ * SPLAT_BWD_STOP_2D only dproj is written.  g3, g4 must be the parameters the
+ * forward used.
+ */
+splat_status splat_composite_bwd(const splat_proj *proj, const splat_bins *bins, const splat_view *views, int V,
+                                 const splat_image *img, const float *dL_drgb, const splat_g3 *g3,
+                                 const splat_g4 *g4, splat_grads3 *dg3, splat_grads4 *dg4, float *dproj,
+                                 uint32_t flags, int32_t *status, void *workspace, size_t workspace_bytes,
+                                 void *stream);
+
+/*
+ * Sec. 4.1 + Sec. 4.2: every 4D Gaussian with exp(s_t) > tau is static.  Its
+ * (mu_x, q_3D, s_x, s_y, s_z, opacity, SH) is appended to g3 in increasing 4D
+ * index order, where q_3D comes from the top-left 3x3 block of R_4D by Eq. 9
+ * (the largest-diagonal branch of Shepperd's method when 1 + tr < 1e-2),
+ * normalised with w >= 0; mu_t and s_t are dropped.  The remaining 4D
+ * Gaussians are compacted in place, order kept.  *n_moved_dev receives the
+ * number moved; g3->n and g4->n are NOT updated (the host reads n_moved and
+ * updates them).  g3 and g4 must share one dtype.  If g3->n + moved exceeds
+ * g3->capacity nothing is changed and status reports SPLAT_ERR_CAPACITY.
+ * Does not clear status.
+ */
+splat_status splat_convert_4d_to_3d(splat_g4 *g4, splat_g3 *g3, float tau, int64_t *n_moved_dev, int32_t *status,
+                                    void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * L1 photometric loss of a training step (Sec. 4.3 trains the rendered
+ * images against the captured frames): *loss = sum_i |img_i - target_i|
+ * (device float, overwritten), dL_dimg_i = scale * sign(img_i - target_i).
+ * n floats, all three arrays 16-byte aligned (any layout, e.g. img->rgb).
+ */
+splat_status splat_l1_loss(const float *img, const float *target, int64_t n, float scale, float *dL_dimg,
+                           float *loss, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *splat_status_string(int32_t code);
+
+/*
+ * Test knob: maximum polling iterations of every bounded device-side wait
+ * (decoupled look-back of the scans and sorts).  0 gives up at the first
+ * not-yet-published predecessor.  Default 1 << 22.  Host-side global.
+ */
+void splat_set_spin_limit(int64_t iterations);
+
+/*
+ * Tuning knob of the compositing kernels: pixels each lane owns (1, 2, 4 or
+ * 8; one warp covers 32 x that many pixels of a 16x16 tile).  Other values
+ * are ignored.  Default 8 / 8.  Host-side global; the results do not depend
+ * on it beyond floating-point summation order of the gradients.
+ */
+void splat_set_pixels_per_lane(int fwd, int bwd);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+int32_t splat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPLAT_H */

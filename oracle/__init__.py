@@ -47,7 +47,7 @@ PROJ_DTYPE = np.dtype([
     ("px", "f8"), ("py", "f8"), ("depth", "f8"), ("conic", "f8", 3), ("alpha", "f8"), ("rgb", "f8", 3),
     ("margin_fwd", "f8"), ("margin_grad", "f8"),
     ("radius", "i4"), ("rect", "i4", 4), ("visible", "i4"), ("n_tiles", "i4"), ("pad", "i4"),
-    ("rect_hull", "i4", 4),
+    ("r3", "f8"), ("margin_cull", "f8"),
 ], align=True)
 
 

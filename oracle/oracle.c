@@ -87,7 +87,8 @@ typedef struct {
     int32_t visible;     /* not culled and the rectangle is not empty        */
     int32_t n_tiles;
     int32_t pad;
-    int32_t rect_hull[4];/* tiles whose membership a fragile decision could flip */
+    double r3;           /* 3 sqrt(lambda_max) before the ceil               */
+    double margin_cull;  /* min relative margin of the near-plane and alpha cull */
 } oproj;
 
 /* reading D5: thresholds inherited from the 3DGS rasterizer */
@@ -331,6 +332,10 @@ static int grid_tiles(int n) { return (n + TILE - 1) / TILE; }
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* floor / ceil to int, saturating far outside the image */
+static int ifloor(double q) { return (int)floor(fmax(-1e9, fmin(1e9, q))); }
+static int iceil(double q) { return (int)ceil(fmax(-1e9, fmin(1e9, q))); }
+
 /* world mean/covariance of merged Gaussian i at the view's time (Eq. 2 or Eq. 5/6) */
 static void gaussian_world(const og3 *g3, const og4 *g4, int64_t i, double t,
                            double mu[3], double cov[9], double *alpha_max, const double **sh)
@@ -369,8 +374,8 @@ static void project_one(const double mu[3], const double cov[9], double alpha_ma
     double z = xc[2];
     o->depth = z;
     double m_fwd = INFINITY, m_grad = INFINITY;
-    m_fwd = dmin(m_fwd, fabs(z - v->z_near) / v->z_near);
-    m_fwd = dmin(m_fwd, fabs(alpha_max - ALPHA_MIN) / ALPHA_MIN);
+    o->margin_cull = dmin(fabs(z - v->z_near) / v->z_near, fabs(alpha_max - ALPHA_MIN) / ALPHA_MIN);
+    m_fwd = dmin(m_fwd, o->margin_cull);
     o->alpha = alpha_max;
     int culled = (z <= v->z_near) || (alpha_max < ALPHA_MIN);
     if (z <= 0.0) {  /* no projection exists behind the camera */
@@ -400,6 +405,7 @@ static void project_one(const double mu[3], const double cov[9], double alpha_ma
     double mid = 0.5 * (S2[0] + S2[3]);
     double lam = mid + sqrt(fmax(0.1, mid * mid - det));
     double r3 = 3.0 * sqrt(lam);
+    o->r3 = r3;
     m_fwd = dmin(m_fwd, int_margin(r3));
     int radius = (int)ceil(r3);
     double px = v->fx * xc[0] / z + v->cx, py = v->fy * xc[1] / z + v->cy;
@@ -407,15 +413,10 @@ static void project_one(const double mu[3], const double cov[9], double alpha_ma
     o->py = py;
     double qx0 = (px - radius) / TILE, qx1 = (px + radius) / TILE;
     double qy0 = (py - radius) / TILE, qy1 = (py + radius) / TILE;
-    int x0 = clampi((int)floor(qx0), 0, TX), x1 = clampi((int)ceil(qx1), 0, TX);
-    int y0 = clampi((int)floor(qy0), 0, TY), y1 = clampi((int)ceil(qy1), 0, TY);
+    int x0 = clampi(ifloor(qx0), 0, TX), x1 = clampi(iceil(qx1), 0, TX);
+    int y0 = clampi(ifloor(qy0), 0, TY), y1 = clampi(iceil(qy1), 0, TY);
     double m_rect = dmin(dmin(int_margin(qx0), int_margin(qx1)), dmin(int_margin(qy0), int_margin(qy1)));
     m_fwd = dmin(m_fwd, m_rect);
-    /* the tiles a decision within its margin could add: one more radius step and one tile each side */
-    o->rect_hull[0] = clampi((int)floor((px - radius - 1) / TILE) - 1, 0, TX);
-    o->rect_hull[1] = clampi((int)floor((py - radius - 1) / TILE) - 1, 0, TY);
-    o->rect_hull[2] = clampi((int)ceil((px + radius + 1) / TILE) + 1, 0, TX);
-    o->rect_hull[3] = clampi((int)ceil((py + radius + 1) / TILE) + 1, 0, TY);
     /* colour: degree-3 SH at the viewing direction (reading D8) */
     double cc[3], d[3], Y[16];
     camera_centre(v, cc);
@@ -501,6 +502,7 @@ static int64_t blend_pixel(const oproj *P, const dkey *list, int64_t m, int u, i
     double mf = INFINITY, mg = INFINITY;
     int32_t last = 0;
     int64_t nt = 0;
+    double prev_depth = -1.0;  /* depth of the previous Gaussian that touched the pixel */
     for (int64_t j = 0; j < m; ++j) {
         const oproj *o = &P[list[j].idx];
         double dx = o->px - u, dy = o->py - vpix;
@@ -513,6 +515,11 @@ static int64_t blend_pixel(const oproj *P, const dkey *list, int64_t m, int u, i
         double raw = o->alpha * G;
         mf = dmin(mf, fabs(raw - ALPHA_MIN) / ALPHA_MIN);
         mg = dmin(mg, fabs(raw - ALPHA_MAX_CLAMP) / ALPHA_MAX_CLAMP);
+        if (raw >= ALPHA_MIN) {
+            /* two touching Gaussians at (nearly) equal depth: their order is a decision too */
+            if (prev_depth > 0.0) mf = dmin(mf, fabs(o->depth - prev_depth) / o->depth);
+            prev_depth = o->depth;
+        }
         double alpha = raw < ALPHA_MAX_CLAMP ? raw : ALPHA_MAX_CLAMP;
         if (alpha < ALPHA_MIN) continue;
         double test_T = T * (1.0 - alpha);

@@ -1,0 +1,187 @@
+"""ctypes binding of libsplat (include/splat.h): struct mirrors and the entry
+points under the same names.  Argument marshalling only -- every step of the
+rasterizer runs in the CUDA library.  Importing this module fails loudly when
+the library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsplat.so")
+
+SPLAT_OK = 0
+SPLAT_ERR_INVALID_ARG = 1
+SPLAT_ERR_CAPACITY = 2
+SPLAT_ERR_TIMEOUT = 3
+SPLAT_ERR_NONFINITE = 4
+SPLAT_ERR_CUDA = 5
+
+SPLAT_F32, SPLAT_BF16, SPLAT_F16 = 0, 1, 2
+SPLAT_OP_BIN_SORT, SPLAT_OP_COMPOSITE_BWD, SPLAT_OP_CONVERT, SPLAT_OP_ALL = 1, 2, 3, 4
+SPLAT_BWD_STOP_2D = 1
+SPLAT_MAX_VIEWS = 16
+SPLAT_MAX_INSTANCES = 1 << 30
+
+STAGES = {1: "slice_project", 2: "depth_sort", 3: "scan", 4: "duplicate", 5: "tile_sort",
+          6: "composite_fwd", 7: "composite_bwd", 8: "adjoint", 9: "convert"}
+
+
+class splat_g3(C.Structure):
+    _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("dtype", C.c_int32), ("reserved", C.c_int32),
+                ("mean", C.c_void_p), ("log_scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
+                ("sh", C.c_void_p)]
+
+
+class splat_g4(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dtype", C.c_int32), ("reserved", C.c_int32),
+                ("mean", C.c_void_p), ("log_scale", C.c_void_p), ("ql", C.c_void_p), ("qr", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class splat_view(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("T", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("W", C.c_int32), ("H", C.c_int32), ("t", C.c_float),
+                ("z_near", C.c_float), ("bg", C.c_float * 3), ("reserved", C.c_float)]
+
+
+class splat_proj(C.Structure):
+    _fields_ = [("n", C.c_int64), ("views", C.c_int32), ("reserved", C.c_int32),
+                ("xy", C.c_void_p), ("conic_opacity", C.c_void_p), ("rgb_depth", C.c_void_p),
+                ("rect", C.c_void_p), ("radius", C.c_void_p), ("n_tiles", C.c_void_p)]
+
+
+class splat_bins(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("keys", C.c_void_p), ("vals", C.c_void_p), ("ranges", C.c_void_p),
+                ("n_instances", C.c_void_p)]
+
+
+class splat_image(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("final_T", C.c_void_p), ("last", C.c_void_p)]
+
+
+class splat_grads3(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
+                ("sh", C.c_void_p)]
+
+
+class splat_grads4(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("ql", C.c_void_p), ("qr", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p)]
+
+
+_P = C.POINTER
+EXPORTS = {
+    "splat_version": (C.c_int32, []),
+    "splat_set_spin_limit": (None, [C.c_int64]),
+    "splat_set_pixels_per_lane": (None, [C.c_int, C.c_int]),
+    "splat_status_string": (C.c_char_p, [C.c_int32]),
+    "splat_total_tiles": (C.c_int64, [C.c_int, _P(C.c_int32), _P(C.c_int32)]),
+    "splat_workspace_size": (C.c_size_t, [C.c_int, C.c_int64, C.c_int64, C.c_int, _P(C.c_int32), _P(C.c_int32),
+                                          C.c_int64]),
+    "splat_slice_project": (C.c_int, [_P(splat_g3), _P(splat_g4), _P(splat_view), C.c_int, _P(splat_proj),
+                                      C.c_void_p, C.c_void_p]),
+    "splat_bin_sort": (C.c_int, [_P(splat_proj), _P(splat_view), C.c_int, _P(splat_bins), C.c_void_p, C.c_void_p,
+                                 C.c_size_t, C.c_void_p]),
+    "splat_composite_fwd": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int, _P(splat_image),
+                                      C.c_void_p, C.c_void_p]),
+    "splat_composite_bwd": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int, _P(splat_image),
+                                      C.c_void_p, _P(splat_g3), _P(splat_g4), _P(splat_grads3), _P(splat_grads4),
+                                      C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "splat_convert_4d_to_3d": (C.c_int, [_P(splat_g4), _P(splat_g3), C.c_float, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_size_t, C.c_void_p]),
+    "splat_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_void_p,
+                                C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libsplat (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsplat is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SplatError(RuntimeError):
+    def __init__(self, code, where="", stage=0, aux=0):
+        self.code, self.stage, self.aux = int(code), int(stage), int(aux)
+        msg = "%s: %s" % (where, status_string(code))
+        if stage:
+            msg += " (stage %s, aux %d)" % (STAGES.get(stage, stage), aux)
+        super().__init__(msg)
+
+
+def status_string(code) -> str:
+    return lib().splat_status_string(int(code)).decode()
+
+
+def splat_status_string(code) -> str:
+    return status_string(code)
+
+
+def check(code, where):
+    if code != SPLAT_OK:
+        raise SplatError(code, where)
+
+
+# --- entry points, same names as the C ABI ---------------------------------
+
+def splat_version():
+    return lib().splat_version()
+
+
+def splat_set_spin_limit(n):
+    lib().splat_set_spin_limit(int(n))
+
+
+def splat_set_pixels_per_lane(fwd, bwd):
+    lib().splat_set_pixels_per_lane(int(fwd), int(bwd))
+
+
+def _i32arr(vals):
+    a = (C.c_int32 * max(1, len(vals)))(*[int(x) for x in vals])
+    return a
+
+
+def splat_total_tiles(W, H):
+    return lib().splat_total_tiles(len(W), _i32arr(W), _i32arr(H))
+
+
+def splat_workspace_size(op, N3, N4, W, H, capacity):
+    return lib().splat_workspace_size(int(op), int(N3), int(N4), len(W), _i32arr(W), _i32arr(H), int(capacity))
+
+
+def splat_slice_project(g3, g4, views, V, proj, status, stream):
+    return lib().splat_slice_project(g3, g4, views, V, proj, status, stream)
+
+
+def splat_bin_sort(proj, views, V, bins, status, ws, ws_bytes, stream):
+    return lib().splat_bin_sort(proj, views, V, bins, status, ws, ws_bytes, stream)
+
+
+def splat_composite_fwd(proj, bins, views, V, img, status, stream):
+    return lib().splat_composite_fwd(proj, bins, views, V, img, status, stream)
+
+
+def splat_composite_bwd(proj, bins, views, V, img, dL, g3, g4, dg3, dg4, dproj, flags, status, ws, ws_bytes, stream):
+    return lib().splat_composite_bwd(proj, bins, views, V, img, dL, g3, g4, dg3, dg4, dproj, flags, status, ws,
+                                     ws_bytes, stream)
+
+
+def splat_convert_4d_to_3d(g4, g3, tau, n_moved, status, ws, ws_bytes, stream):
+    return lib().splat_convert_4d_to_3d(g4, g3, tau, n_moved, status, ws, ws_bytes, stream)
+
+
+def splat_l1_loss(img, target, n, scale, dL, loss, stream):
+    return lib().splat_l1_loss(img, target, n, scale, dL, loss, stream)

@@ -1,0 +1,320 @@
+// api.cu -- the extern "C" entry points declared in include/splat.h:
+// host-side argument checks, per-view parameter packing, workspace carving
+// and kernel launches.  No entry point synchronises the stream or reads
+// device memory.
+#include <atomic>
+#include <cmath>
+
+#include "splat_internal.cuh"
+
+namespace splat {
+
+cudaError_t launch_slice_project(const splat_g3&, const splat_g4&, const ViewBatch&, const splat_proj&, int32_t*, int,
+                                 const LaunchCtx&);
+cudaError_t launch_adjoint(const splat_g3&, const splat_g4&, const ViewBatch&, const splat_proj&, const float*,
+                           const splat_grads3&, const splat_grads4&, int32_t*, int, const LaunchCtx&);
+cudaError_t launch_bin_sort(const splat_proj&, const ViewBatch&, const splat_bins&, int32_t*, void*, const LaunchCtx&);
+size_t bin_sort_workspace(int64_t n_rows, int64_t capacity);
+cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&, int32_t*,
+                                 int, const LaunchCtx&);
+cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
+                                 const float*, float*, int32_t*, int, const LaunchCtx&);
+cudaError_t launch_convert(const splat_g4&, const splat_g3&, float, int64_t*, int32_t*, void*, const LaunchCtx&);
+size_t convert_workspace(int64_t n4, int dtype_bytes);
+cudaError_t launch_l1_loss(const float*, const float*, int64_t, float, float*, float*, const LaunchCtx&);
+
+static std::atomic<int64_t> g_spin_limit{1ll << 22};
+static std::atomic<int> g_ppl_fwd{8}, g_ppl_bwd{8};
+static int g_num_sms[64];
+
+LaunchCtx launch_ctx(void* stream)
+{
+    LaunchCtx c;
+    c.stream = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (g_num_sms[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        g_num_sms[dev] = n;
+    }
+    c.num_sms = g_num_sms[dev];
+    c.spin_limit = g_spin_limit.load();
+    return c;
+}
+
+static bool valid_views(const splat_view* views, int V)
+{
+    if (!views || V < 1 || V > SPLAT_MAX_VIEWS) return false;
+    for (int v = 0; v < V; ++v) {
+        const splat_view& s = views[v];
+        if (s.W < 1 || s.H < 1 || s.W > 16384 || s.H > 16384) return false;
+        if (!(s.fx > 0.f) || !(s.fy > 0.f) || !std::isfinite(s.cx) || !std::isfinite(s.cy)) return false;
+        if (!(s.z_near > 0.f) || !std::isfinite(s.t)) return false;
+    }
+    return true;
+}
+
+static ViewBatch make_batch(const splat_view* views, int V)
+{
+    ViewBatch b{};
+    b.V = V;
+    int tiles = 0;
+    int64_t pix = 0;
+    for (int v = 0; v < V; ++v) {
+        const splat_view& s = views[v];
+        ViewParams& p = b.v[v];
+        for (int k = 0; k < 9; ++k) p.R[k] = s.R[k];
+        for (int k = 0; k < 3; ++k) p.T[k] = s.T[k];
+        for (int k = 0; k < 3; ++k) p.cam[k] = -(s.R[0 * 3 + k] * s.T[0] + s.R[1 * 3 + k] * s.T[1] + s.R[2 * 3 + k] * s.T[2]);
+        p.fx = s.fx; p.fy = s.fy; p.cx = s.cx; p.cy = s.cy;
+        p.limx = kFovClamp * (0.5f * (float)s.W / s.fx);
+        p.limy = kFovClamp * (0.5f * (float)s.H / s.fy);
+        p.t = s.t;
+        p.z_near = s.z_near;
+        for (int k = 0; k < 3; ++k) p.bg[k] = s.bg[k];
+        p.W = s.W; p.H = s.H;
+        p.TX = (s.W + kTile - 1) / kTile;
+        p.TY = (s.H + kTile - 1) / kTile;
+        p.tile_base = tiles;
+        p.pix_base = pix;
+        tiles += p.TX * p.TY;
+        pix += (int64_t)s.W * s.H;
+    }
+    b.total_tiles = tiles;
+    return b;
+}
+
+static splat_g3 g3_or_empty(const splat_g3* g)
+{
+    if (g) return *g;
+    splat_g3 e{};
+    return e;
+}
+
+static splat_g4 g4_or_empty(const splat_g4* g)
+{
+    if (g) return *g;
+    splat_g4 e{};
+    return e;
+}
+
+static bool valid_g3(const splat_g3& g)
+{
+    if (g.n < 0) return false;
+    if (g.n == 0) return true;
+    if (g.dtype < SPLAT_F32 || g.dtype > SPLAT_F16) return false;
+    return g.mean && g.log_scale && g.quat && g.opacity && g.sh && g.capacity >= g.n;
+}
+
+static bool valid_g4(const splat_g4& g)
+{
+    if (g.n < 0) return false;
+    if (g.n == 0) return true;
+    if (g.dtype < SPLAT_F32 || g.dtype > SPLAT_F16) return false;
+    return g.mean && g.log_scale && g.ql && g.qr && g.opacity && g.sh;
+}
+
+static int common_dtype(const splat_g3& g3, const splat_g4& g4, bool* ok)
+{
+    *ok = true;
+    if (g3.n > 0 && g4.n > 0 && g3.dtype != g4.dtype) *ok = false;
+    return g4.n > 0 ? g4.dtype : (g3.n > 0 ? g3.dtype : SPLAT_F32);
+}
+
+static bool valid_proj(const splat_proj* p, int V)
+{
+    return p && p->views == V && p->n >= 0 && (p->n == 0 || (p->xy && p->conic_opacity && p->rgb_depth && p->rect &&
+                                                              p->radius && p->n_tiles)) &&
+           (int64_t)V * p->n < (1ll << 32);
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static splat_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SPLAT_OK : SPLAT_ERR_CUDA; }
+
+}  // namespace splat
+
+using namespace splat;
+
+extern "C" {
+
+int32_t splat_version(void) { return 0x000100; }
+
+void splat_set_spin_limit(int64_t iterations) { g_spin_limit.store(iterations < 0 ? 0 : iterations); }
+
+void splat_set_pixels_per_lane(int fwd, int bwd)
+{
+    auto ok = [](int p) { return p == 1 || p == 2 || p == 4 || p == 8; };
+    if (ok(fwd)) g_ppl_fwd.store(fwd);
+    if (ok(bwd)) g_ppl_bwd.store(bwd);
+}
+
+const char* splat_status_string(int32_t code)
+{
+    switch (code) {
+    case SPLAT_OK: return "ok";
+    case SPLAT_ERR_INVALID_ARG: return "invalid argument";
+    case SPLAT_ERR_CAPACITY: return "buffer capacity exceeded";
+    case SPLAT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SPLAT_ERR_NONFINITE: return "non-finite projected value";
+    case SPLAT_ERR_CUDA: return "CUDA error";
+    default: return "unknown status";
+    }
+}
+
+int64_t splat_total_tiles(int V, const int32_t* W, const int32_t* H)
+{
+    if (!W || !H || V < 0) return -1;
+    int64_t t = 0;
+    for (int v = 0; v < V; ++v) {
+        if (W[v] < 1 || H[v] < 1) return -1;
+        t += (int64_t)((W[v] + kTile - 1) / kTile) * ((H[v] + kTile - 1) / kTile);
+    }
+    return t;
+}
+
+size_t splat_workspace_size(int op, int64_t N3, int64_t N4, int V, const int32_t* W, const int32_t* H,
+                            int64_t capacity)
+{
+    if (N3 < 0 || N4 < 0 || capacity < 0 || capacity > SPLAT_MAX_INSTANCES) return 0;
+    const int64_t N = N3 + N4;
+    size_t sort_b = 0, bwd_b = 0, conv_b = 0;
+    if (op == SPLAT_OP_BIN_SORT || op == SPLAT_OP_ALL || op == SPLAT_OP_COMPOSITE_BWD) {
+        if (V < 1 || V > SPLAT_MAX_VIEWS || splat_total_tiles(V, W, H) < 0) return 0;
+    }
+    if (op == SPLAT_OP_BIN_SORT || op == SPLAT_OP_ALL) sort_b = bin_sort_workspace(N * V, capacity);
+    if (op == SPLAT_OP_COMPOSITE_BWD || op == SPLAT_OP_ALL) bwd_b = ((size_t)N * V * 48 + 255) & ~(size_t)255;
+    if (op == SPLAT_OP_CONVERT || op == SPLAT_OP_ALL) conv_b = convert_workspace(N4, 4);
+    if (op < SPLAT_OP_BIN_SORT || op > SPLAT_OP_ALL) return 0;
+    size_t m = sort_b;
+    if (bwd_b > m) m = bwd_b;
+    if (conv_b > m) m = conv_b;
+    return m < 256 ? 256 : m;
+}
+
+splat_status splat_slice_project(const splat_g3* g3p, const splat_g4* g4p, const splat_view* views, int V,
+                                 splat_proj* out, int32_t* status, void* stream)
+{
+    const splat_g3 g3 = g3_or_empty(g3p);
+    const splat_g4 g4 = g4_or_empty(g4p);
+    bool same = true;
+    const int dt = common_dtype(g3, g4, &same);
+    if (!same || !valid_g3(g3) || !valid_g4(g4) || !valid_views(views, V) || !valid_proj(out, V) || !status)
+        return SPLAT_ERR_INVALID_ARG;
+    if (out->n != g3.n + g4.n) return SPLAT_ERR_INVALID_ARG;
+    if (!aligned(out->conic_opacity, 16) || !aligned(out->rgb_depth, 16) || !aligned(out->rect, 16) ||
+        !aligned(out->xy, 8))
+        return SPLAT_ERR_INVALID_ARG;
+    if (g4.n > 0 && dt == SPLAT_F32 && (!aligned(g4.mean, 16) || !aligned(g4.log_scale, 16) || !aligned(g4.ql, 16) ||
+                                        !aligned(g4.qr, 16) || !aligned(g4.sh, 16)))
+        return SPLAT_ERR_INVALID_ARG;
+    if (g3.n > 0 && dt == SPLAT_F32 && (!aligned(g3.quat, 16) || !aligned(g3.sh, 16))) return SPLAT_ERR_INVALID_ARG;
+    const LaunchCtx ctx = launch_ctx(stream);
+    cudaError_t e = cudaMemsetAsync(status, 0, 4 * sizeof(int32_t), ctx.stream);
+    if (e != cudaSuccess) return SPLAT_ERR_CUDA;
+    const ViewBatch vb = make_batch(views, V);
+    return cuda_status(launch_slice_project(g3, g4, vb, *out, status, dt, ctx));
+}
+
+splat_status splat_bin_sort(const splat_proj* proj, const splat_view* views, int V, splat_bins* bins,
+                            int32_t* status, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !status) return SPLAT_ERR_INVALID_ARG;
+    if (bins->capacity < 0 || bins->capacity > SPLAT_MAX_INSTANCES || !bins->ranges || !bins->n_instances)
+        return SPLAT_ERR_INVALID_ARG;
+    if (bins->capacity > 0 && (!bins->keys || !bins->vals)) return SPLAT_ERR_INVALID_ARG;
+    if (!aligned(bins->ranges, 8) || !aligned(bins->n_instances, 8)) return SPLAT_ERR_INVALID_ARG;
+    const size_t need = bin_sort_workspace(proj->n * V, bins->capacity);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
+    const LaunchCtx ctx = launch_ctx(stream);
+    const ViewBatch vb = make_batch(views, V);
+    return cuda_status(launch_bin_sort(*proj, vb, *bins, status, workspace, ctx));
+}
+
+splat_status splat_composite_fwd(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
+                                 splat_image* img, int32_t* status, void* stream)
+{
+    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !status) return SPLAT_ERR_INVALID_ARG;
+    if (!img->rgb || !img->final_T || !img->last || !bins->ranges || (bins->capacity > 0 && !bins->vals))
+        return SPLAT_ERR_INVALID_ARG;
+    const LaunchCtx ctx = launch_ctx(stream);
+    const ViewBatch vb = make_batch(views, V);
+    return cuda_status(launch_composite_fwd(*proj, *bins, vb, *img, status, g_ppl_fwd.load(), ctx));
+}
+
+splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
+                                 const splat_image* img, const float* dL_drgb, const splat_g3* g3p, const splat_g4* g4p,
+                                 splat_grads3* dg3, splat_grads4* dg4, float* dproj, uint32_t flags, int32_t* status,
+                                 void* workspace, size_t workspace_bytes, void* stream)
+{
+    const splat_g3 g3 = g3_or_empty(g3p);
+    const splat_g4 g4 = g4_or_empty(g4p);
+    bool same = true;
+    const int dt = common_dtype(g3, g4, &same);
+    if (!same || !valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !dL_drgb || !status)
+        return SPLAT_ERR_INVALID_ARG;
+    if (!img->final_T || !img->last || !bins->ranges) return SPLAT_ERR_INVALID_ARG;
+    const bool stop2d = (flags & SPLAT_BWD_STOP_2D) != 0;
+    if (!stop2d) {
+        if (!valid_g3(g3) || !valid_g4(g4) || proj->n != g3.n + g4.n) return SPLAT_ERR_INVALID_ARG;
+        if (g3.n > 0 && (!dg3 || !dg3->mean || !dg3->log_scale || !dg3->quat || !dg3->opacity || !dg3->sh))
+            return SPLAT_ERR_INVALID_ARG;
+        if (g4.n > 0 && (!dg4 || !dg4->mean || !dg4->log_scale || !dg4->ql || !dg4->qr || !dg4->opacity || !dg4->sh))
+            return SPLAT_ERR_INVALID_ARG;
+        if (g4.n > 0 && (!aligned(dg4->mean, 16) || !aligned(dg4->log_scale, 16) || !aligned(dg4->ql, 16) ||
+                         !aligned(dg4->qr, 16) || !aligned(dg4->sh, 16)))
+            return SPLAT_ERR_INVALID_ARG;
+        if (g3.n > 0 && (!aligned(dg3->quat, 16) || !aligned(dg3->sh, 16))) return SPLAT_ERR_INVALID_ARG;
+        if (g4.n > 0 && dt == SPLAT_F32 && (!aligned(g4.mean, 16) || !aligned(g4.ql, 16) || !aligned(g4.qr, 16) ||
+                                            !aligned(g4.log_scale, 16) || !aligned(g4.sh, 16)))
+            return SPLAT_ERR_INVALID_ARG;
+        if (g3.n > 0 && dt == SPLAT_F32 && (!aligned(g3.quat, 16) || !aligned(g3.sh, 16))) return SPLAT_ERR_INVALID_ARG;
+    }
+    const size_t dproj_bytes = (size_t)proj->n * V * 48;
+    float* dp = dproj;
+    if (!dp) {
+        if (!workspace || workspace_bytes < dproj_bytes || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
+        dp = (float*)workspace;
+    } else if (!aligned(dp, 16)) {
+        return SPLAT_ERR_INVALID_ARG;
+    }
+    const LaunchCtx ctx = launch_ctx(stream);
+    const ViewBatch vb = make_batch(views, V);
+    cudaError_t e = cudaMemsetAsync(dp, 0, dproj_bytes, ctx.stream);
+    if (e != cudaSuccess) return SPLAT_ERR_CUDA;
+    e = launch_composite_bwd(*proj, *bins, vb, *img, dL_drgb, dp, status, g_ppl_bwd.load(), ctx);
+    if (e != cudaSuccess) return SPLAT_ERR_CUDA;
+    if (stop2d) return SPLAT_OK;
+    splat_grads3 d3 = dg3 ? *dg3 : splat_grads3{};
+    splat_grads4 d4 = dg4 ? *dg4 : splat_grads4{};
+    return cuda_status(launch_adjoint(g3, g4, vb, *proj, dp, d3, d4, status, dt, ctx));
+}
+
+splat_status splat_convert_4d_to_3d(splat_g4* g4, splat_g3* g3, float tau, int64_t* n_moved_dev, int32_t* status,
+                                    void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!g4 || !g3 || !n_moved_dev || !status || !std::isfinite(tau)) return SPLAT_ERR_INVALID_ARG;
+    if (!valid_g4(*g4) || g3->n < 0 || g3->capacity < g3->n) return SPLAT_ERR_INVALID_ARG;
+    if (g4->n > 0 && (!g3->mean || !g3->log_scale || !g3->quat || !g3->opacity || !g3->sh)) return SPLAT_ERR_INVALID_ARG;
+    if (g4->n > 0 && g3->dtype != g4->dtype) return SPLAT_ERR_INVALID_ARG;
+    if (g4->n > 0 && g4->dtype == SPLAT_F32 && (!aligned(g4->ql, 16) || !aligned(g4->qr, 16)))
+        return SPLAT_ERR_INVALID_ARG;
+    const int bytes = g4->dtype == SPLAT_F32 ? 4 : 2;
+    const size_t need = convert_workspace(g4->n, bytes);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
+    const LaunchCtx ctx = launch_ctx(stream);
+    return cuda_status(launch_convert(*g4, *g3, tau, n_moved_dev, status, workspace, ctx));
+}
+
+splat_status splat_l1_loss(const float* img, const float* target, int64_t n, float scale, float* dL_dimg,
+                           float* loss, void* stream)
+{
+    if (n < 0 || !loss || (n > 0 && (!img || !target || !dL_dimg)) || !std::isfinite(scale)) return SPLAT_ERR_INVALID_ARG;
+    if (!aligned(img, 16) || !aligned(target, 16) || !aligned(dL_dimg, 16)) return SPLAT_ERR_INVALID_ARG;
+    const LaunchCtx ctx = launch_ctx(stream);
+    return cuda_status(launch_l1_loss(img, target, n, scale, dL_dimg, loss, ctx));
+}
+
+}  // extern "C"

@@ -1,0 +1,366 @@
+// composite.cu -- Alg. 1 BlendInOrder (Eq. 3) and its adjoint.
+//
+// Work decomposition: a "unit" is one tile (or a horizontal band of it, see
+// PPL) handled by ONE warp, independently of every other warp: no block
+// barriers.  Lane l owns pixel column l % 16 and rows (l / 16) + 2k, k < PPL,
+// of the band, so a warp covers 32 * PPL pixels (PPL = 8: the whole 16x16
+// tile).  The warp walks the tile's sorted list in batches of 32 Gaussians:
+// each lane gathers one Gaussian's projected features into the warp's
+// shared-memory slot, then every lane evaluates all its pixels against the
+// 32 staged Gaussians (broadcast reads).  The warp leaves the list as soon as
+// a vote shows every one of its pixels has saturated (T would drop below
+// 1e-4).
+//
+// The adjoint walks the same list back to front from each pixel's stored last
+// contributor, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
+// transmittance.  Per Gaussian the 9 gradient components of all the warp's
+// pixels are summed with a 14-shuffle reduce-scatter and written with one
+// global atomic per component.
+#include "splat_internal.cuh"
+
+namespace splat {
+
+constexpr int kCompWarps = 4;  // warps (units) per CTA
+
+// Decision shared by forward and backward: returns false when the Gaussian
+// does not touch the pixel (power > 0, or alpha below 1/255).
+struct Feat {
+    float px, py, a, b, c, op, r, g, bl, pcut;
+};
+
+__device__ __forceinline__ void load_feat(const float4* s, Feat& f)
+{
+    const float4 f0 = s[0], f1 = s[1], f2 = s[2];
+    f.px = f0.x; f.py = f0.y; f.a = f0.z; f.b = f0.w;
+    f.c = f1.x; f.op = f1.y; f.r = f1.z; f.g = f1.w;
+    f.bl = f2.x; f.pcut = f2.y;
+}
+
+__device__ __forceinline__ void stage_feat(const splat_proj& proj, uint32_t row, float4* s)
+{
+    const float2 xy = ((const float2*)proj.xy)[row];
+    const float4 co = ((const float4*)proj.conic_opacity)[row];
+    const float4 rd = ((const float4*)proj.rgb_depth)[row];
+    // power below log(1/(255 alpha_max)) cannot reach alpha = 1/255
+    const float pcut = __logf(kAlphaMin / co.w);
+    s[0] = make_float4(xy.x, xy.y, co.x, co.y);
+    s[1] = make_float4(co.z, co.w, rd.x, rd.y);
+    s[2] = make_float4(rd.z, pcut, 0.f, 0.f);
+}
+
+__device__ __forceinline__ int find_view(const ViewBatch& vb, int tile)
+{
+    int v = 0;
+    for (int w = 1; w < vb.V; ++w)
+        if (tile >= vb.v[w].tile_base) v = w;
+    return v;
+}
+
+template <int PPL>
+__global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj proj, const uint32_t* __restrict__ vals,
+                                                                   const uint2* __restrict__ ranges, ViewBatch vb,
+                                                                   splat_image img, int32_t* status)
+{
+    constexpr int BANDS = 8 / PPL;
+    __shared__ float4 s_feat[kCompWarps][32][3];
+    if (status_failed(status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
+    if (unit >= (int64_t)vb.total_tiles * BANDS) return;
+    const int tile = (int)(unit / BANDS), band = (int)(unit % BANDS);
+    const int v = find_view(vb, tile);
+    const ViewParams& vp = vb.v[v];
+    const int local = tile - vp.tile_base;
+    const int ty = local / vp.TX, tx = local - ty * vp.TX;
+    const int u = tx * kTile + (lane & 15);
+    const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
+    const float uf = (float)u;
+    float T[PPL], C[PPL][3];
+    int last[PPL];
+    unsigned done = 0;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        T[k] = 1.f;
+        C[k][0] = C[k][1] = C[k][2] = 0.f;
+        last[k] = 0;
+        if (u >= vp.W || y0 + 2 * k >= vp.H) done |= 1u << k;
+    }
+    const uint2 rg = ranges[tile];
+    const unsigned all_done = (1u << PPL) - 1;
+    float4* sf = &s_feat[warp][0][0];
+    for (uint32_t b = rg.x; b < rg.y; b += 32) {
+        if (__all_sync(0xffffffffu, done == all_done)) break;
+        const uint32_t idx = b + lane;
+        if (idx < rg.y) stage_feat(proj, vals[idx], sf + lane * 3);
+        __syncwarp();
+        const int n = (int)min(32u, rg.y - b);
+        if (done != all_done) {
+            for (int j = 0; j < n; ++j) {
+                Feat f;
+                load_feat(sf + j * 3, f);
+                const float dx = f.px - uf;
+                const float A = -0.5f * f.a * dx * dx, Bx = -f.b * dx, Cc = -0.5f * f.c;
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    if (done & (1u << k)) continue;
+                    const float dy = f.py - (float)(y0 + 2 * k);
+                    const float power = A + dy * (Bx + Cc * dy);
+                    if (power > 0.f || power < f.pcut) continue;
+                    const float alpha = fminf(kAlphaClamp, f.op * __expf(power));
+                    if (alpha < kAlphaMin) continue;
+                    const float tT = T[k] * (1.f - alpha);
+                    if (tT < kTMin) {
+                        done |= 1u << k;
+                        continue;
+                    }
+                    const float w = alpha * T[k];
+                    C[k][0] += f.r * w;
+                    C[k][1] += f.g * w;
+                    C[k][2] += f.bl * w;
+                    T[k] = tT;
+                    last[k] = (int)(b - rg.x) + j + 1;
+                }
+                if (done == all_done) break;
+            }
+        }
+        __syncwarp();
+    }
+    const int64_t HW = (int64_t)vp.W * vp.H;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int y = y0 + 2 * k;
+        if (u >= vp.W || y >= vp.H) continue;
+        const int64_t p = (int64_t)y * vp.W + u;
+        float* rgb = img.rgb + 3 * vp.pix_base;
+        rgb[p] = C[k][0] + T[k] * vp.bg[0];
+        rgb[HW + p] = C[k][1] + T[k] * vp.bg[1];
+        rgb[2 * HW + p] = C[k][2] + T[k] * vp.bg[2];
+        img.final_T[vp.pix_base + p] = T[k];
+        img.last[vp.pix_base + p] = last[k];
+    }
+}
+
+// Sum 8 values over the warp; afterwards lanes 4m..4m+3 hold the total of value m.
+__device__ __forceinline__ float reduce_scatter8(const float v[8], int lane)
+{
+    float h[4];
+    const bool b4 = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[i + 4];
+        const float keep = b4 ? v[i + 4] : v[i];
+        h[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float q[2];
+    const bool b3 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? h[i] : h[i + 2];
+        const float keep = b3 ? h[i + 2] : h[i];
+        q[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const bool b2 = lane & 4;
+    float x = (b2 ? q[1] : q[0]) + __shfl_xor_sync(0xffffffffu, b2 ? q[0] : q[1], 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return x;
+}
+
+template <int PPL>
+__global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj proj, const uint32_t* __restrict__ vals,
+                                                                   const uint2* __restrict__ ranges, ViewBatch vb,
+                                                                   splat_image img, const float* __restrict__ dL,
+                                                                   float* dproj, int32_t* status)
+{
+    constexpr int BANDS = 8 / PPL;
+    __shared__ float4 s_feat[kCompWarps][32][3];
+    __shared__ uint32_t s_row[kCompWarps][32];
+    if (status_failed(status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
+    if (unit >= (int64_t)vb.total_tiles * BANDS) return;
+    const int tile = (int)(unit / BANDS), band = (int)(unit % BANDS);
+    const int v = find_view(vb, tile);
+    const ViewParams& vp = vb.v[v];
+    const int local = tile - vp.tile_base;
+    const int ty = local / vp.TX, tx = local - ty * vp.TX;
+    const int u = tx * kTile + (lane & 15);
+    const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
+    const float uf = (float)u;
+    const int64_t HW = (int64_t)vp.W * vp.H;
+    float T[PPL], S[PPL][3], G[PPL][3];
+    int last[PPL];
+    int maxlast = 0;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int y = y0 + 2 * k;
+        last[k] = 0;
+        T[k] = 1.f;
+        S[k][0] = S[k][1] = S[k][2] = 0.f;
+        G[k][0] = G[k][1] = G[k][2] = 0.f;
+        if (u < vp.W && y < vp.H) {
+            const int64_t p = (int64_t)y * vp.W + u;
+            const float* g = dL + 3 * vp.pix_base;
+            G[k][0] = g[p];
+            G[k][1] = g[HW + p];
+            G[k][2] = g[2 * HW + p];
+            T[k] = img.final_T[vp.pix_base + p];
+            last[k] = img.last[vp.pix_base + p];
+            // colour behind the last contributor: T_final * bg
+            S[k][0] = T[k] * vp.bg[0];
+            S[k][1] = T[k] * vp.bg[1];
+            S[k][2] = T[k] * vp.bg[2];
+            maxlast = max(maxlast, last[k]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
+    if (maxlast == 0) return;
+    const uint2 rg = ranges[tile];
+    float4* sf = &s_feat[warp][0][0];
+    const int nb = (maxlast + 31) / 32;
+    for (int bi = nb - 1; bi >= 0; --bi) {
+        const uint32_t b = rg.x + 32u * bi;
+        const uint32_t end = min(rg.x + (uint32_t)maxlast, rg.y);
+        const uint32_t idx = b + lane;
+        if (idx < end) {
+            const uint32_t row = vals[idx];
+            s_row[warp][lane] = row;
+            stage_feat(proj, row, sf + lane * 3);
+        }
+        __syncwarp();
+        const int n = (int)min(32u, end - b);
+        for (int j = n - 1; j >= 0; --j) {
+            Feat f;
+            load_feat(sf + j * 3, f);
+            const int li = 32 * bi + j;  // position in the tile list
+            const float dx = f.px - uf;
+            const float A = -0.5f * f.a * dx * dx, Bx = -f.b * dx, Cc = -0.5f * f.c;
+            float acc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc[q] = 0.f;
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                if (li >= last[k]) continue;
+                const float dy = f.py - (float)(y0 + 2 * k);
+                const float power = A + dy * (Bx + Cc * dy);
+                if (power > 0.f || power < f.pcut) continue;
+                const float Gs = __expf(power);
+                const float raw = f.op * Gs;
+                const float alpha = fminf(kAlphaClamp, raw);
+                if (alpha < kAlphaMin) continue;
+                any = true;
+                const float om = 1.f - alpha;
+                const float Tj = T[k] / om;
+                const float w = alpha * Tj;
+                acc[6] += w * G[k][0];
+                acc[7] += w * G[k][1];
+                acc[8] += w * G[k][2];
+                const float dLda = G[k][0] * (f.r * Tj - S[k][0] / om) + G[k][1] * (f.g * Tj - S[k][1] / om) +
+                                   G[k][2] * (f.bl * Tj - S[k][2] / om);
+                S[k][0] += f.r * w;
+                S[k][1] += f.g * w;
+                S[k][2] += f.bl * w;
+                T[k] = Tj;
+                if (raw < kAlphaClamp) {
+                    const float dpow = dLda * alpha;
+                    acc[5] += dLda * Gs;
+                    acc[0] += -dpow * (f.a * dx + f.b * dy);
+                    acc[1] += -dpow * (f.c * dy + f.b * dx);
+                    acc[2] += -0.5f * dpow * dx * dx;
+                    acc[3] += -dpow * dx * dy;
+                    acc[4] += -0.5f * dpow * dy * dy;
+                }
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                const float r8 = reduce_scatter8(acc, lane);
+                float r9 = acc[8];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r9 += __shfl_xor_sync(0xffffffffu, r9, o);
+                float* dst = dproj + (int64_t)s_row[warp][j] * 12;
+                if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), r8);
+                if (lane == 0) atomicAdd(dst + 8, r9);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// L1 photometric loss of the rendered images against a target (the loss of
+// the paper's training step): loss += sum |img - target|, dL/dimg =
+// sign(img - target) * scale.
+__global__ void __launch_bounds__(256) k_l1_loss(const float* __restrict__ img, const float* __restrict__ target,
+                                                 int64_t n, float scale, float* __restrict__ dL, float* loss)
+{
+    float acc = 0.f;
+    const int64_t n4 = n / 4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = ((const float4*)img)[i], b = ((const float4*)target)[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        auto sg = [](float d) { return d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f); };
+        ((float4*)dL)[i] = make_float4(sg(d0) * scale, sg(d1) * scale, sg(d2) * scale, sg(d3) * scale);
+    }
+    for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = img[i] - target[i];
+        acc += fabsf(d);
+        dL[i] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * scale;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float s_acc[8];
+    if ((threadIdx.x & 31) == 0) s_acc[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += s_acc[w];
+        atomicAdd(loss, t);
+    }
+}
+
+cudaError_t launch_l1_loss(const float* img, const float* target, int64_t n, float scale, float* dL, float* loss,
+                           const LaunchCtx& ctx)
+{
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), ctx.stream);
+    if (e != cudaSuccess || n == 0) return e;
+    const int64_t want = (n / 4 + 255) / 256 + 1;
+    const int blocks = (int)(want < (int64_t)ctx.num_sms * 8 ? want : (int64_t)ctx.num_sms * 8);
+    k_l1_loss<<<blocks, 256, 0, ctx.stream>>>(img, target, n, scale, dL, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_fwd(const splat_proj& proj, const splat_bins& bins, const ViewBatch& vb,
+                                 const splat_image& img, int32_t* status, int ppl, const LaunchCtx& ctx)
+{
+    if (vb.total_tiles == 0) return cudaSuccess;
+    const int bands = 8 / ppl;
+    const int64_t units = (int64_t)vb.total_tiles * bands;
+    const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
+    switch (ppl) {
+    case 8: k_composite_fwd<8><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
+    case 4: k_composite_fwd<4><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
+    case 2: k_composite_fwd<2><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
+    default: k_composite_fwd<1><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_bwd(const splat_proj& proj, const splat_bins& bins, const ViewBatch& vb,
+                                 const splat_image& img, const float* dL, float* dproj, int32_t* status, int ppl,
+                                 const LaunchCtx& ctx)
+{
+    if (vb.total_tiles == 0) return cudaSuccess;
+    const int bands = 8 / ppl;
+    const int64_t units = (int64_t)vb.total_tiles * bands;
+    const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
+    switch (ppl) {
+    case 8: k_composite_bwd<8><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
+    case 4: k_composite_bwd<4><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
+    case 2: k_composite_bwd<2><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
+    default: k_composite_bwd<1><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace splat

@@ -1,0 +1,337 @@
+"""PyTorch front end of libsplat: device buffers, streams, autograd and CUDA graphs.
+
+PyTorch supplies device memory and streams only; every stage of the
+rasterizer (slice/project, bin/sort, composite forward/backward, adjoint,
+4D->3D conversion, L1 loss) is a libsplat kernel reached through the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import abi
+from .abi import SplatError
+
+FIELDS3 = ("mean3", "log_scale3", "quat3", "opacity3", "sh3")
+FIELDS4 = ("mean4", "log_scale4", "ql", "qr", "opacity4", "sh4")
+SHAPES = {"mean3": (3,), "log_scale3": (3,), "quat3": (4,), "opacity3": (), "sh3": (16, 3),
+          "mean4": (4,), "log_scale4": (4,), "ql": (4,), "qr": (4,), "opacity4": (), "sh4": (16, 3)}
+
+_DTYPES = {torch.float32: abi.SPLAT_F32, torch.bfloat16: abi.SPLAT_BF16, torch.float16: abi.SPLAT_F16}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Gaussians:
+    """One hybrid parameter set on the device: static 3D and dynamic 4D Gaussians,
+    raw (pre-activation) values in a storage dtype (float32, bfloat16 or float16).
+    The 3D arrays have `capacity3` rows so that 4D->3D conversion can append."""
+
+    def __init__(self, t: Dict[str, torch.Tensor], n3: int, n4: int):
+        self.t = t
+        self.n3, self.n4 = int(n3), int(n4)
+        dt = t["mean3"].dtype
+        if any(t[k].dtype != dt for k in FIELDS3 + FIELDS4):
+            raise ValueError("all fields must share one dtype")
+        self.dtype = dt
+        self.code = _DTYPES[dt]
+
+    @property
+    def capacity3(self) -> int:
+        return int(self.t["mean3"].shape[0])
+
+    @property
+    def n(self) -> int:
+        return self.n3 + self.n4
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda", dtype=torch.float32, capacity3: Optional[int] = None) -> "Gaussians":
+        cap = scene.n3 if capacity3 is None else max(int(capacity3), scene.n3)
+        t = {}
+        for k in FIELDS3 + FIELDS4:
+            a = torch.from_numpy(np.ascontiguousarray(getattr(scene, k), dtype=np.float32))
+            if k in FIELDS3 and cap > scene.n3:
+                pad = torch.zeros((cap - scene.n3,) + tuple(SHAPES[k]), dtype=torch.float32)
+                a = torch.cat([a, pad], 0)
+            t[k] = a.to(device=device, dtype=dtype).contiguous()
+        return cls(t, scene.n3, scene.n4)
+
+    def dequantised(self) -> Dict[str, np.ndarray]:
+        """The stored values as float64 host arrays (first n rows)."""
+        out = {}
+        for k in FIELDS3:
+            out[k] = self.t[k][: self.n3].float().cpu().double().numpy()
+        for k in FIELDS4:
+            out[k] = self.t[k][: self.n4].float().cpu().double().numpy()
+        return out
+
+    def c_g3(self) -> abi.splat_g3:
+        t = self.t
+        return abi.splat_g3(self.n3, self.capacity3, self.code, 0, t["mean3"].data_ptr(), t["log_scale3"].data_ptr(),
+                            t["quat3"].data_ptr(), t["opacity3"].data_ptr(), t["sh3"].data_ptr())
+
+    def c_g4(self) -> abi.splat_g4:
+        t = self.t
+        return abi.splat_g4(self.n4, self.code, 0, t["mean4"].data_ptr(), t["log_scale4"].data_ptr(),
+                            t["ql"].data_ptr(), t["qr"].data_ptr(), t["opacity4"].data_ptr(), t["sh4"].data_ptr())
+
+
+def c_views(views) -> "C.Array":
+    arr = (abi.splat_view * len(views))()
+    for i, v in enumerate(views):
+        R = np.asarray(v.R, dtype=np.float32).reshape(9)
+        T = np.asarray(v.T, dtype=np.float32).reshape(3)
+        s = arr[i]
+        for k in range(9):
+            s.R[k] = float(R[k])
+        for k in range(3):
+            s.T[k] = float(T[k])
+            s.bg[k] = float(v.bg[k])
+        s.fx, s.fy, s.cx, s.cy = float(v.fx), float(v.fy), float(v.cx), float(v.cy)
+        s.W, s.H = int(v.W), int(v.H)
+        s.t = float(v.t)
+        s.z_near = float(v.z_near)
+    return arr
+
+
+class Rasterizer:
+    """Owns the device buffers of one (Gaussian count, view batch) shape and runs
+    the pipeline on a CUDA stream.  All V views are rendered by one launch per
+    stage.  `capacity` is the tile-instance capacity; `None` picks it from a
+    first render (see `autotune_capacity`)."""
+
+    def __init__(self, n3: int, n4: int, views: Sequence, device="cuda", capacity: Optional[int] = None,
+                 headroom: float = 1.25):
+        self.n3, self.n4 = int(n3), int(n4)
+        self.N = self.n3 + self.n4
+        self.views = list(views)
+        self.V = len(self.views)
+        if not 1 <= self.V <= abi.SPLAT_MAX_VIEWS:
+            raise ValueError("1..%d views per batch" % abi.SPLAT_MAX_VIEWS)
+        self.device = torch.device(device)
+        self.cviews = c_views(self.views)
+        self.W = [int(v.W) for v in self.views]
+        self.H = [int(v.H) for v in self.views]
+        self.total_tiles = abi.splat_total_tiles(self.W, self.H)
+        self.pix = [w * h for w, h in zip(self.W, self.H)]
+        self.pix_base = np.concatenate([[0], np.cumsum(self.pix)]).astype(np.int64)
+        self.headroom = headroom
+        rows = self.V * self.N
+        d, f32, i32 = self.device, torch.float32, torch.int32
+        self.xy = torch.zeros((rows, 2), dtype=f32, device=d)
+        self.conic_opacity = torch.zeros((rows, 4), dtype=f32, device=d)
+        self.rgb_depth = torch.zeros((rows, 4), dtype=f32, device=d)
+        self.rect = torch.zeros((rows, 4), dtype=i32, device=d)
+        self.radius = torch.zeros((rows,), dtype=i32, device=d)
+        self.n_tiles = torch.zeros((rows,), dtype=i32, device=d)
+        self.cproj = abi.splat_proj(self.N, self.V, 0, self.xy.data_ptr(), self.conic_opacity.data_ptr(),
+                                    self.rgb_depth.data_ptr(), self.rect.data_ptr(), self.radius.data_ptr(),
+                                    self.n_tiles.data_ptr())
+        total_pix = int(self.pix_base[-1])
+        self.rgb = torch.zeros((3 * total_pix,), dtype=f32, device=d)
+        self.final_T = torch.zeros((total_pix,), dtype=f32, device=d)
+        self.last = torch.zeros((total_pix,), dtype=i32, device=d)
+        self.cimg = abi.splat_image(self.rgb.data_ptr(), self.final_T.data_ptr(), self.last.data_ptr())
+        self.status = torch.zeros((4,), dtype=i32, device=d)
+        self.n_instances = torch.zeros((1,), dtype=torch.int64, device=d)
+        self.ranges = torch.zeros((max(1, self.total_tiles) * 2,), dtype=i32, device=d)
+        self.dproj = torch.zeros((rows * 12,), dtype=f32, device=d)
+        self.loss = torch.zeros((1,), dtype=f32, device=d)
+        self.dL = torch.zeros_like(self.rgb)
+        self.grads = {k: torch.zeros((self.n3 if k in FIELDS3 else self.n4,) + SHAPES[k], dtype=f32, device=d)
+                      for k in FIELDS3 + FIELDS4}
+        self.cg3 = abi.splat_grads3(*[self.grads[k].data_ptr() for k in FIELDS3])
+        self.cg4 = abi.splat_grads4(*[self.grads[k].data_ptr() for k in FIELDS4])
+        if capacity is None:
+            capacity = max(1 << 16, 16 * rows)
+        self.set_capacity(capacity)
+
+    # -- buffers ------------------------------------------------------------
+    def set_capacity(self, capacity: int):
+        capacity = int(min(max(1, capacity), abi.SPLAT_MAX_INSTANCES))
+        self.capacity = capacity
+        self.keys = torch.empty((capacity,), dtype=torch.int32, device=self.device)
+        self.vals = torch.empty((capacity,), dtype=torch.int32, device=self.device)
+        self.cbins = abi.splat_bins(capacity, self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
+                                    self.n_instances.data_ptr())
+        ws = abi.splat_workspace_size(abi.SPLAT_OP_ALL, self.n3, self.n4, self.W, self.H, capacity)
+        if ws == 0:
+            raise ValueError("invalid sizes for the workspace")
+        self.ws_bytes = int(ws)
+        self.ws = torch.empty((self.ws_bytes,), dtype=torch.uint8, device=self.device)
+
+    # -- stages -------------------------------------------------------------
+    def forward(self, G: Gaussians, stream=None):
+        """Slice/project, bin/sort and composite all views (asynchronous)."""
+        if G.n3 != self.n3 or G.n4 != self.n4:
+            raise ValueError("Gaussian counts differ from the rasterizer's")
+        s = _stream(stream)
+        g3, g4 = G.c_g3(), G.c_g4()
+        st = _ptr(self.status)
+        abi.check(abi.splat_slice_project(C.byref(g3), C.byref(g4), self.cviews, self.V, C.byref(self.cproj), st, s),
+                  "splat_slice_project")
+        abi.check(abi.splat_bin_sort(C.byref(self.cproj), self.cviews, self.V, C.byref(self.cbins), st,
+                                     _ptr(self.ws), self.ws_bytes, s), "splat_bin_sort")
+        abi.check(abi.splat_composite_fwd(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
+                                          C.byref(self.cimg), st, s), "splat_composite_fwd")
+        return self.rgb
+
+    def backward(self, G: Gaussians, dL_drgb: torch.Tensor, stream=None, stop_2d: bool = False):
+        """Gradients of all parameters for pixel gradient dL_drgb (asynchronous);
+        results in self.grads (overwritten) and self.dproj."""
+        s = _stream(stream)
+        g3, g4 = G.c_g3(), G.c_g4()
+        flags = abi.SPLAT_BWD_STOP_2D if stop_2d else 0
+        abi.check(abi.splat_composite_bwd(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
+                                          C.byref(self.cimg), _ptr(dL_drgb), C.byref(g3), C.byref(g4),
+                                          C.byref(self.cg3), C.byref(self.cg4), _ptr(self.dproj), flags,
+                                          _ptr(self.status), _ptr(self.ws), self.ws_bytes, s), "splat_composite_bwd")
+        return self.grads
+
+    def l1_loss(self, target: torch.Tensor, stream=None):
+        """L1 loss (mean over pixels and channels) and its pixel gradient into self.dL."""
+        n = self.rgb.numel()
+        abi.check(abi.splat_l1_loss(_ptr(self.rgb), _ptr(target), n, 1.0 / max(1, n), _ptr(self.dL),
+                                    _ptr(self.loss), _stream(stream)), "splat_l1_loss")
+        return self.loss
+
+    def step(self, G: Gaussians, target: torch.Tensor, stream=None):
+        """One training step of the rasterizer: forward, L1 loss, backward."""
+        self.forward(G, stream)
+        self.l1_loss(target, stream)
+        self.backward(G, self.dL, stream)
+
+    # -- status / capacity -------------------------------------------------
+    def read_status(self):
+        """Synchronising read of the device status word."""
+        s = self.status.cpu().numpy()
+        aux = (int(s[3]) << 32) | (int(s[2]) & 0xFFFFFFFF)
+        return int(s[0]), int(s[1]), aux
+
+    def check(self, where="rasterizer"):
+        code, stage, aux = self.read_status()
+        if code != abi.SPLAT_OK:
+            raise SplatError(code, where, stage, aux)
+
+    def instances(self) -> int:
+        return int(self.n_instances.item())
+
+    def autotune_capacity(self, G: Gaussians, retries: int = 3) -> int:
+        """Render once; when the instance list overflows, grow it to the required
+        count times the headroom and render again.  Returns K."""
+        for _ in range(retries):
+            self.forward(G)
+            code, stage, aux = self.read_status()
+            if code == abi.SPLAT_ERR_CAPACITY:
+                self.set_capacity(int(math.ceil(aux * self.headroom)) + 1024)
+                continue
+            if code != abi.SPLAT_OK:
+                raise SplatError(code, "autotune_capacity", stage, aux)
+            K = self.instances()
+            want = int(math.ceil(K * self.headroom)) + 1024
+            if want < self.capacity // 2 or want > self.capacity:
+                self.set_capacity(want)
+            return K
+        raise SplatError(abi.SPLAT_ERR_CAPACITY, "autotune_capacity")
+
+    # -- views of the flat buffers -----------------------------------------
+    def image(self, v: int, buf: Optional[torch.Tensor] = None) -> torch.Tensor:
+        b = self.rgb if buf is None else buf
+        p0 = int(self.pix_base[v])
+        return b[3 * p0: 3 * p0 + 3 * self.pix[v]].view(3, self.H[v], self.W[v])
+
+    def plane(self, v: int, buf: torch.Tensor) -> torch.Tensor:
+        p0 = int(self.pix_base[v])
+        return buf[p0: p0 + self.pix[v]].view(self.H[v], self.W[v])
+
+
+class GraphedStep:
+    """A CUDA graph of one full rasterizer training step (forward, L1 loss,
+    backward) over the whole view batch: one replay launches every kernel of
+    the step with no host work in between."""
+
+    def __init__(self, R: Rasterizer, G: Gaussians, target: torch.Tensor, warmup: int = 2):
+        self.R, self.G, self.target = R, G, target
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                R.step(G, target, s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        R.check("GraphedStep warm-up")
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            R.step(G, target)
+
+    def replay(self):
+        self.graph.replay()
+
+
+class HybridRasterize(torch.autograd.Function):
+    """autograd entry: HybridRasterize.apply(R, G, *param_tensors) -> flat rgb of
+    all views.  The parameter tensors must be the ones held by G (11 of them,
+    3D fields first); gradients come from the hand-written adjoint kernels."""
+
+    @staticmethod
+    def forward(ctx, R: Rasterizer, G: Gaussians, *params):
+        R.forward(G)
+        ctx.R, ctx.G = R, G
+        return R.rgb.clone()
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        R, G = ctx.R, ctx.G
+        R.backward(G, grad_rgb.contiguous())
+        out = [None, None]
+        for k in FIELDS3:
+            g = torch.zeros_like(G.t[k], dtype=torch.float32)
+            g[: G.n3] = R.grads[k]
+            out.append(g.to(G.t[k].dtype))
+        for k in FIELDS4:
+            out.append(R.grads[k].clone().to(G.t[k].dtype))
+        return tuple(out)
+
+
+def render(G: Gaussians, views, capacity=None) -> List[torch.Tensor]:
+    """Convenience: render the views, return [3, H, W] images (synchronises)."""
+    R = Rasterizer(G.n3, G.n4, views, device=G.t["mean3"].device, capacity=capacity)
+    R.autotune_capacity(G)
+    R.forward(G)
+    R.check("render")
+    return [R.image(v).clone() for v in range(R.V)]
+
+
+def convert_4d_to_3d(G: Gaussians, tau: float, stream=None) -> int:
+    """Sec. 4.1-4.2 in place on G: moves every 4D Gaussian with exp(s_t) > tau to the
+    3D set (appending within capacity3) and compacts the 4D set.  Synchronises
+    once to read the moved count.  Returns the number moved."""
+    dev = G.t["mean3"].device
+    bytes_ = abi.lib().splat_workspace_size(abi.SPLAT_OP_CONVERT, G.n3, G.n4, 0, None, None, 0)
+    if G.code != abi.SPLAT_F32:
+        bytes_ = max(bytes_, 256)
+    ws = torch.empty((int(bytes_),), dtype=torch.uint8, device=dev)
+    status = torch.zeros((4,), dtype=torch.int32, device=dev)
+    n_moved = torch.zeros((1,), dtype=torch.int64, device=dev)
+    g3, g4 = G.c_g3(), G.c_g4()
+    abi.check(abi.splat_convert_4d_to_3d(C.byref(g4), C.byref(g3), float(tau), _ptr(n_moved), _ptr(status),
+                                         _ptr(ws), int(bytes_), _stream(stream)), "splat_convert_4d_to_3d")
+    s = status.cpu().numpy()
+    if s[0] != 0:
+        raise SplatError(int(s[0]), "splat_convert_4d_to_3d", int(s[1]), (int(s[3]) << 32) | (int(s[2]) & 0xFFFFFFFF))
+    m = int(n_moved.item())
+    G.n3 += m
+    G.n4 -= m
+    return m

@@ -1,0 +1,102 @@
+"""C-ABI library checks that need no GPU: it loads, exports every symbol that
+include/splat.h declares (under the same names in the Python binding), and
+its host-side logic (sizes, argument checks, status strings) behaves."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2505_13215_gb300 import abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "splat.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(splat_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_13215_gb300 import build
+    build.build()
+    return abi.lib()
+
+
+def test_header_declares_the_pipeline():
+    names = declared_functions()
+    for n in ("splat_slice_project", "splat_bin_sort", "splat_composite_fwd", "splat_composite_bwd",
+              "splat_convert_4d_to_3d", "splat_workspace_size", "splat_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in abi.EXPORTS, name
+        assert callable(getattr(abi, name, None)), "python binding lacks %s" % name
+
+
+def test_status_strings(lib):
+    for code in range(6):
+        assert abi.status_string(code) != "unknown status"
+    assert abi.status_string(99) == "unknown status"
+
+
+def test_total_tiles_and_workspace(lib):
+    assert abi.splat_total_tiles([1352], [1014]) == 85 * 64
+    assert abi.splat_total_tiles([1352, 676], [1014, 507]) == 85 * 64 + 43 * 32
+    a = abi.splat_workspace_size(abi.SPLAT_OP_BIN_SORT, 200000, 100000, [1352], [1014], 30_000_000)
+    b = abi.splat_workspace_size(abi.SPLAT_OP_BIN_SORT, 200000, 100000, [1352], [1014], 60_000_000)
+    assert 0 < a < b
+    assert abi.splat_workspace_size(abi.SPLAT_OP_ALL, 10, 10, [64], [64], 1000) >= \
+        abi.splat_workspace_size(abi.SPLAT_OP_COMPOSITE_BWD, 10, 10, [64], [64], 1000)
+    # invalid: capacity above the limit, no views, unknown op
+    assert abi.splat_workspace_size(abi.SPLAT_OP_BIN_SORT, 1, 1, [64], [64], abi.SPLAT_MAX_INSTANCES + 1) == 0
+    assert abi.splat_workspace_size(abi.SPLAT_OP_BIN_SORT, 1, 1, [], [], 10) == 0
+    assert abi.splat_workspace_size(17, 1, 1, [64], [64], 10) == 0
+
+
+def test_invalid_arguments_rejected_before_any_device_work(lib):
+    v = (abi.splat_view * 1)()
+    v[0].W, v[0].H, v[0].fx, v[0].fy, v[0].z_near = 64, 64, 50.0, 50.0, 0.2
+    proj = abi.splat_proj(0, 1, 0, None, None, None, None, None, None)
+    g3 = abi.splat_g3()
+    g4 = abi.splat_g4()
+    st = C.c_void_p(0)
+    # no status buffer
+    assert abi.splat_slice_project(C.byref(g3), C.byref(g4), v, 1, C.byref(proj), st, None) == abi.SPLAT_ERR_INVALID_ARG
+    # zero views / too many views
+    assert abi.splat_slice_project(C.byref(g3), C.byref(g4), v, 0, C.byref(proj), C.c_void_p(16), None) == \
+        abi.SPLAT_ERR_INVALID_ARG
+    # image size out of range
+    v[0].W = 0
+    assert abi.splat_slice_project(C.byref(g3), C.byref(g4), v, 1, C.byref(proj), C.c_void_p(16), None) == \
+        abi.SPLAT_ERR_INVALID_ARG
+    v[0].W = 64
+    # mixed storage dtypes
+    g3.n, g3.capacity, g3.dtype = 1, 1, abi.SPLAT_F32
+    g4.n, g4.dtype = 1, abi.SPLAT_BF16
+    for f in ("mean", "log_scale", "quat", "opacity", "sh"):
+        setattr(g3, f, 256)
+    for f in ("mean", "log_scale", "ql", "qr", "opacity", "sh"):
+        setattr(g4, f, 256)
+    proj.n = 2
+    assert abi.splat_slice_project(C.byref(g3), C.byref(g4), v, 1, C.byref(proj), C.c_void_p(16), None) == \
+        abi.SPLAT_ERR_INVALID_ARG
+    # convert: non-finite tau
+    assert abi.splat_convert_4d_to_3d(C.byref(g4), C.byref(g3), float("nan"), C.c_void_p(16), C.c_void_p(16),
+                                      None, 0, None) == abi.SPLAT_ERR_INVALID_ARG
+    # loss: misaligned
+    assert abi.splat_l1_loss(C.c_void_p(4), C.c_void_p(16), 8, 1.0, C.c_void_p(16), C.c_void_p(16), None) == \
+        abi.SPLAT_ERR_INVALID_ARG
+
+
+def test_knobs_are_host_side(lib):
+    abi.splat_set_spin_limit(123)
+    abi.splat_set_spin_limit(1 << 22)
+    abi.splat_set_pixels_per_lane(3, 5)  # ignored
+    abi.splat_set_pixels_per_lane(8, 8)
+    assert abi.splat_version() == 0x000100

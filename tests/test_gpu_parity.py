@@ -1,0 +1,544 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (see parity_util): rendered RGB max-abs 2e-4 on every pixel whose
+result is unique at FP32; parameter gradients 1e-3 relative L2 per tensor;
+sorted per-tile instance lists bit-exact when both sides sort the same keys.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2505_13215_gb300 import abi, raster, scenes
+
+from parity_util import (EPS_GAUSS, EPS_PIXEL, GRAD_RTOL, RGB_TOL, fragile_pixels, grad_fragile_gaussians, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+F3 = raster.FIELDS3
+F4 = raster.FIELDS4
+
+
+def make(scene, views, dtype=torch.float32, capacity3=None):
+    G = raster.Gaussians.from_scene(scene, "cuda", dtype=dtype, capacity3=capacity3)
+    R = raster.Rasterizer(G.n3, G.n4, views)
+    R.autotune_capacity(G)
+    R.forward(G)
+    torch.cuda.synchronize()
+    R.check()
+    return G, R
+
+
+@pytest.fixture(scope="module")
+def small():
+    scene, views = scenes.small_scene(seed=0)
+    G, R = make(scene, views)
+    P = O.project(scene, views[0])
+    ref = O.render(scene, views[0])
+    return scene, views, G, R, P, ref
+
+
+# ---------------------------------------------------------------------------
+# A1-A4: slice + project
+# ---------------------------------------------------------------------------
+
+def check_projection(R, P, v=0):
+    N = R.N
+    sl = slice(v * N, (v + 1) * N)
+    rad = R.radius[sl].cpu().numpy()
+    rect = R.rect[sl].cpu().numpy()
+    nt = R.n_tiles[sl].cpu().numpy()
+    xy = R.xy[sl].cpu().numpy().astype(np.float64)
+    co = R.conic_opacity[sl].cpu().numpy().astype(np.float64)
+    rd = R.rgb_depth[sl].cpu().numpy().astype(np.float64)
+    sure = P["margin_fwd"] >= EPS_GAUSS
+    vis_o = P["visible"] == 1
+    vis_g = rad > 0
+    np.testing.assert_array_equal(vis_g[sure], vis_o[sure])
+    np.testing.assert_array_equal(rad[sure & vis_o], P["radius"][sure & vis_o])
+    np.testing.assert_array_equal(rect[sure & vis_o], P["rect"][sure & vis_o])
+    np.testing.assert_array_equal(nt[sure & vis_o], P["n_tiles"][sure & vis_o])
+    both = vis_g & vis_o
+    assert both.sum() > 0
+    o = P[both]
+    np.testing.assert_allclose(xy[both, 0], o["px"], rtol=1e-5, atol=2e-3)
+    np.testing.assert_allclose(xy[both, 1], o["py"], rtol=1e-5, atol=2e-3)
+    scale = np.maximum(np.abs(o["conic"][:, 0]), np.abs(o["conic"][:, 2]))
+    for k in range(3):
+        assert np.max(np.abs(co[both, k] - o["conic"][:, k]) / scale) < 1e-4
+    np.testing.assert_allclose(co[both, 3], o["alpha"], rtol=2e-5, atol=1e-7)
+    np.testing.assert_allclose(rd[both, :3], o["rgb"], atol=2e-5)
+    np.testing.assert_allclose(rd[both, 3], o["depth"], rtol=1e-6)
+    return int((~sure).sum())
+
+
+def test_slice_project_matches_oracle(small):
+    scene, views, G, R, P, ref = small
+    n_fragile = check_projection(R, P)
+    assert n_fragile < 0.01 * R.N
+
+
+# ---------------------------------------------------------------------------
+# A5-A8: bin + sort (staged: both sides sort the same keys)
+# ---------------------------------------------------------------------------
+
+def staged_sort(views, proj_per_view, N, depth_override=None):
+    """Feed oracle rectangles / float32 depths to splat_bin_sort; return the GPU
+    lists and the oracle's stable sort of the same keys."""
+    V = len(views)
+    R = raster.Rasterizer(N, 0, views)
+    keys_o, ids_o = [], []
+    tile_base = 0
+    for v, (view, P) in enumerate(zip(views, proj_per_view)):
+        dep = P["depth"].astype(np.float32) if depth_override is None else depth_override[v]
+        sl = slice(v * N, (v + 1) * N)
+        vis = P["visible"] == 1
+        R.rect[sl] = torch.from_numpy(np.where(vis[:, None], P["rect"], 0).astype(np.int32)).cuda()
+        R.n_tiles[sl] = torch.from_numpy(np.where(vis, P["n_tiles"], 0).astype(np.int32)).cuda()
+        R.radius[sl] = torch.from_numpy(np.where(vis, P["radius"], 0).astype(np.int32)).cuda()
+        rd = np.zeros((N, 4), np.float32)
+        rd[:, 3] = dep
+        R.rgb_depth[sl] = torch.from_numpy(rd).cuda()
+        k, ids = O.tile_keys(P, view, depth_f32=dep)
+        k = k + (np.uint64(tile_base) << np.uint64(32))
+        keys_o.append(k)
+        ids_o.append(ids + v * N)
+        tile_base += ((view.W + 15) // 16) * ((view.H + 15) // 16)
+    keys_o = np.concatenate(keys_o) if keys_o else np.zeros(0, np.uint64)
+    ids_o = np.concatenate(ids_o) if ids_o else np.zeros(0, np.int64)
+    perm = O.stable_sort_u64(keys_o)
+    K = len(keys_o)
+    R.set_capacity(K + 100)
+    R.status.zero_()
+    st = C.c_void_p(R.status.data_ptr())
+    abi.check(abi.splat_bin_sort(C.byref(R.cproj), R.cviews, V, C.byref(R.cbins), st, C.c_void_p(R.ws.data_ptr()),
+                                 R.ws_bytes, C.c_void_p(torch.cuda.current_stream().cuda_stream)), "bin_sort")
+    torch.cuda.synchronize()
+    R.check()
+    assert R.instances() == K
+    gk = R.keys[:K].cpu().numpy().astype(np.uint32)
+    gv = R.vals[:K].cpu().numpy().astype(np.uint32)
+    ok = (keys_o[perm] >> np.uint64(32)).astype(np.uint32)
+    ov = ids_o[perm].astype(np.uint32)
+    ranges = R.ranges.cpu().numpy().reshape(-1, 2)
+    return gk, gv, ok, ov, ranges, tile_base
+
+
+def expected_ranges(sorted_tiles, total):
+    r = np.zeros((total, 2), np.int64)
+    for t in np.unique(sorted_tiles):
+        w = np.nonzero(sorted_tiles == t)[0]
+        r[t] = (w[0], w[-1] + 1)
+    return r
+
+
+def test_bin_sort_bitexact_given_keys(small):
+    scene, views, G, R, P, ref = small
+    gk, gv, ok, ov, ranges, T = staged_sort(views, [P], R.N)
+    np.testing.assert_array_equal(gk, ok)
+    np.testing.assert_array_equal(gv, ov)
+    np.testing.assert_array_equal(ranges, expected_ranges(ok, T))
+
+
+def test_bin_sort_ties_and_multiview():
+    """Equal depths everywhere (ties broken by emission order) over three views of
+    different sizes in one call."""
+    scene, _ = scenes.small_scene(seed=2, n3=700, n4=300)
+    views = [scenes.identity_view(128, 128, 128.0, 0.5), scenes.identity_view(80, 48, 70.0, 0.2),
+             scenes.identity_view(200, 120, 150.0, 0.9)]
+    Ps = [O.project(scene, v) for v in views]
+    rng = np.random.default_rng(3)
+    deps = [rng.choice(np.array([2.0, 3.0, 3.0000002, 5.0], np.float32), size=scene.n) for _ in views]
+    gk, gv, ok, ov, ranges, T = staged_sort(views, Ps, scene.n, depth_override=deps)
+    np.testing.assert_array_equal(gk, ok)
+    np.testing.assert_array_equal(gv, ov)
+    np.testing.assert_array_equal(ranges, expected_ranges(ok, T))
+
+
+def test_bin_sort_end_to_end_lists(small):
+    """The GPU's own keys: per tile the same Gaussians, in non-decreasing oracle depth."""
+    scene, views, G, R, P, ref = small
+    K = R.instances()
+    gk = R.keys[:K].cpu().numpy()
+    gv = R.vals[:K].cpu().numpy()
+    ranges = R.ranges.cpu().numpy().reshape(-1, 2)
+    fragile = P["margin_fwd"] < EPS_GAUSS
+    for t in range(R.total_tiles):
+        s, e = ranges[t]
+        assert np.all(gk[s:e] == t)
+        ids = gv[s:e].astype(np.int64)
+        ref_ids = O.tile_list(scene, views[0], t % 8, t // 8)
+        a = set(ids[~fragile[ids]].tolist())
+        b = set(ref_ids[~fragile[ref_ids]].tolist())
+        assert a == b, "tile %d" % t
+        d = P["depth"][ids]
+        assert np.all(np.diff(d) >= -1e-6 * d[1:])
+
+
+# ---------------------------------------------------------------------------
+# A9: composite forward
+# ---------------------------------------------------------------------------
+
+def check_image(R, P, ref, view, v=0):
+    img = R.image(v).cpu().numpy().reshape(3, -1).astype(np.float64)
+    T = R.plane(v, R.final_T).cpu().numpy().reshape(-1)
+    last = R.plane(v, R.last).cpu().numpy().reshape(-1)
+    frag = fragile_pixels(P, ref, view)
+    err = np.abs(img - ref["rgb"])[:, ~frag]
+    assert err.max() <= RGB_TOL, "rgb max-abs %.3g" % err.max()
+    np.testing.assert_array_equal(last[~frag], ref["last"][~frag])
+    np.testing.assert_allclose(T[~frag], ref["T"][~frag], rtol=1e-4, atol=1e-6)
+    return frag.mean(), err.max()
+
+
+def test_composite_fwd_matches_oracle(small):
+    scene, views, G, R, P, ref = small
+    frac, err = check_image(R, P, ref, views[0])
+    assert frac < 0.01, "fragile pixels %.4f" % frac
+
+
+@pytest.mark.parametrize("ppl", [1, 2, 4])
+def test_composite_pixels_per_lane_variants(small, ppl):
+    scene, views, G, R, P, ref = small
+    abi.splat_set_pixels_per_lane(ppl, ppl)
+    try:
+        R.forward(G)
+        torch.cuda.synchronize()
+        R.check()
+        check_image(R, P, ref, views[0])
+    finally:
+        abi.splat_set_pixels_per_lane(8, 8)
+        R.forward(G)
+        torch.cuda.synchronize()
+
+
+def test_forward_is_deterministic(small):
+    scene, views, G, R, P, ref = small
+    R.forward(G)
+    a = R.rgb.clone()
+    k = R.vals[: R.instances()].clone()
+    R.forward(G)
+    torch.cuda.synchronize()
+    assert torch.equal(a, R.rgb)
+    assert torch.equal(k, R.vals[: R.instances()])
+
+
+# ---------------------------------------------------------------------------
+# A10 + A11: backward
+# ---------------------------------------------------------------------------
+
+def loss_grad(R, refs, Ps, views, seed=0):
+    """dL/dC of an L1 loss against a seeded target, from the oracle image, zero at
+    pixels whose value or gradient is not unique at FP32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for v, (ref, P, view) in enumerate(zip(refs, Ps, views)):
+        target = rng.uniform(0, 1, ref["rgb"].shape)
+        g = np.sign(ref["rgb"] - target) / ref["rgb"].size
+        frag = fragile_pixels(P, ref, view) | (ref["margin_grad"] < EPS_PIXEL)
+        g[:, frag] = 0.0
+        out.append(g.reshape(3, view.H, view.W))
+    return out
+
+
+def check_grads(R, G, scene, Ps, views, dls, exclude=None):
+    dl = torch.from_numpy(np.concatenate([g.reshape(-1) for g in dls]).astype(np.float32)).cuda()
+    R.backward(G, dl)
+    torch.cuda.synchronize()
+    R.check()
+    tot = None
+    for view, g in zip(views, dls):
+        r = O.render_bwd(scene, view, g.astype(np.float32).astype(np.float64))
+        r.pop("dproj")
+        tot = r if tot is None else {k: tot[k] + r[k] for k in tot}
+    bad = np.zeros(R.N, bool)
+    for P in Ps:
+        bad |= grad_fragile_gaussians(P)
+    if exclude is not None:
+        bad |= exclude
+    bad4, bad3 = bad[: R.n4], bad[R.n4:]
+    worst = {}
+    for k in F3 + F4:
+        a = R.grads[k].cpu().numpy().astype(np.float64)
+        b = tot[k]
+        keep = ~(bad3 if k in F3 else bad4)
+        if keep.sum() == 0:
+            continue
+        e = rel_l2(a[keep], b[keep])
+        worst[k] = e
+    for k, e in worst.items():
+        assert e <= GRAD_RTOL, "%s rel-L2 %.3g (all: %s)" % (k, e, worst)
+    return worst
+
+
+def test_gradients_match_oracle(small):
+    scene, views, G, R, P, ref = small
+    dls = loss_grad(R, [ref], [P], views)
+    check_grads(R, G, scene, [P], views, dls)
+
+
+def test_dproj_matches_oracle(small):
+    scene, views, G, R, P, ref = small
+    dls = loss_grad(R, [ref], [P], views, seed=1)
+    dl = torch.from_numpy(dls[0].reshape(-1).astype(np.float32)).cuda()
+    R.backward(G, dl, stop_2d=True)
+    torch.cuda.synchronize()
+    R.check()
+    got = R.dproj.view(-1, 12)[:, :9].cpu().numpy().astype(np.float64)
+    want = O.render_bwd(scene, views[0], dls[0].astype(np.float32).astype(np.float64))["dproj"]
+    for name, cols in (("xy", [0, 1]), ("conic", [2, 3, 4]), ("alpha", [5]), ("rgb", [6, 7, 8])):
+        assert rel_l2(got[:, cols], want[:, cols]) <= GRAD_RTOL, name
+
+
+# ---------------------------------------------------------------------------
+# Multi-view batch in one launch per stage, uneven resolutions
+# ---------------------------------------------------------------------------
+
+def test_batched_views_match_oracle():
+    scene, views = scenes.arc_scene(seed=5, n=20000, frac4=0.3, n_views=3, full=(256, 192, 280.0),
+                                    half=(120, 96, 130.0))
+    G, R = make(scene, views)
+    Ps = [O.project(scene, v) for v in views]
+    refs = [O.render(scene, v) for v in views]
+    for v in range(3):
+        check_projection(R, Ps[v], v)
+        frac, _ = check_image(R, Ps[v], refs[v], views[v], v)
+        assert frac < 0.02
+    dls = loss_grad(R, refs, Ps, views, seed=4)
+    check_grads(R, G, scene, Ps, views, dls)
+
+
+# ---------------------------------------------------------------------------
+# Full size (1352x1014, 200k 3D + 100k 4D), per-view launch: sampled outputs
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def big():
+    scene, views = scenes.video_scene(seed=1)
+    G, R = make(scene, views)
+    P = O.project(scene, views[0])
+    return scene, views, G, R, P
+
+
+def test_full_size_projection(big):
+    scene, views, G, R, P = big
+    n_fragile = check_projection(R, P)
+    assert n_fragile < 0.002 * R.N
+
+
+def test_full_size_sampled_pixels_and_gradients(big):
+    scene, views, G, R, P = big
+    view = views[0]
+    rng = np.random.default_rng(7)
+    pix = rng.choice(view.W * view.H, size=600, replace=False)
+    ref = O.render(scene, view, pixels=pix)
+    img = R.image(0).cpu().numpy().reshape(3, -1)[:, pix]
+    # fragile: own decisions, or a tile whose membership could flip
+    from parity_util import uncertain_tiles
+    tiles = uncertain_tiles(P, view)
+    TX = (view.W + 15) // 16
+    tb = tiles.reshape(-1)[(pix // view.W) // 16 * TX + (pix % view.W) // 16]
+    frag = (ref["margin_fwd"] < EPS_PIXEL) | tb
+    assert frag.mean() < 0.05
+    err = np.abs(img - ref["rgb"])[:, ~frag]
+    assert err.max() <= RGB_TOL, err.max()
+    # gradient of a loss on the sampled, unique pixels only
+    sel = pix[~frag & (ref["margin_grad"] >= EPS_PIXEL)]
+    g = np.zeros((3, view.W * view.H))
+    g[:, sel] = rng.choice([-1.0, 1.0], size=(3, len(sel))) * 1e-2
+    check_grads(R, G, scene, [P], views, [g.reshape(3, view.H, view.W)])
+
+
+# ---------------------------------------------------------------------------
+# Storage precision: BF16 / FP16 parameters, FP32 arithmetic
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_half_storage_matches_oracle_on_stored_values(dtype):
+    scene, views = scenes.small_scene(seed=6)
+    G, R = make(scene, views, dtype=dtype)
+    deq = G.dequantised()
+    P = O.project(deq, views[0])
+    ref = O.render(deq, views[0])
+    check_projection(R, P)
+    check_image(R, P, ref, views[0])
+    dls = loss_grad(R, [ref], [P], views, seed=2)
+    check_grads(R, G, deq, [P], views, dls)
+
+
+# ---------------------------------------------------------------------------
+# A12: 4D -> 3D conversion
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_convert_matches_oracle(dtype):
+    scene, _ = scenes.small_scene(seed=8, n3=500, n4=1500)
+    G = raster.Gaussians.from_scene(scene, "cuda", dtype=dtype, capacity3=scene.n3 + scene.n4)
+    deq = G.dequantised()
+    tau = 0.15
+    moved, app, keep = O.convert(deq, tau)
+    n3_0 = G.n3
+    m = raster.convert_4d_to_3d(G, tau)
+    assert m == int(moved.sum()) and 0 < m < scene.n4
+    got3 = {k: G.t[k][n3_0: n3_0 + m].float().cpu().double().numpy() for k in F3}
+    for k in ("mean3", "log_scale3", "opacity3", "sh3"):
+        np.testing.assert_array_equal(got3[k], app[k])  # copied bit for bit
+    qtol = 2e-5 if dtype == torch.float32 else 8e-3
+    np.testing.assert_allclose(got3["quat3"], app["quat3"], atol=qtol)
+    for k in F4:
+        got = G.t[k][: G.n4].float().cpu().double().numpy()
+        np.testing.assert_array_equal(got, deq[k][keep])
+    # the old 3D rows are untouched
+    for k in F3:
+        np.testing.assert_array_equal(G.t[k][:n3_0].float().cpu().double().numpy(), deq[k])
+
+
+def test_convert_capacity_overflow_changes_nothing():
+    scene, _ = scenes.small_scene(seed=8, n3=100, n4=400)
+    G = raster.Gaussians.from_scene(scene, "cuda", capacity3=110)
+    before = {k: G.t[k].clone() for k in F3 + F4}
+    with pytest.raises(abi.SplatError) as e:
+        raster.convert_4d_to_3d(G, 0.05)
+    assert e.value.code == abi.SPLAT_ERR_CAPACITY
+    for k in F3 + F4:
+        assert torch.equal(before[k], G.t[k])
+
+
+# ---------------------------------------------------------------------------
+# Edge cases and device-side error reporting
+# ---------------------------------------------------------------------------
+
+def test_capacity_overflow_is_reported_then_autotuned(small):
+    scene, views, G, R0, P, ref = small
+    R = raster.Rasterizer(G.n3, G.n4, views, capacity=100)
+    R.forward(G)
+    code, stage, aux = R.read_status()
+    assert code == abi.SPLAT_ERR_CAPACITY and aux == R0.instances()
+    R.autotune_capacity(G)
+    R.forward(G)
+    torch.cuda.synchronize()
+    R.check()
+    assert torch.equal(R.rgb, R0.rgb)
+
+
+def test_empty_and_fully_culled_scenes():
+    empty = scenes.empty_scene()
+    view = scenes.identity_view(40, 24, 40.0, 0.0)
+    view.bg = (0.25, 0.5, 1.0)
+    G = raster.Gaussians.from_scene(empty, "cuda")
+    R = raster.Rasterizer(0, 0, [view])
+    R.forward(G)
+    torch.cuda.synchronize()
+    R.check()
+    img = R.image(0).cpu().numpy()
+    np.testing.assert_array_equal(img, np.broadcast_to(np.array(view.bg, np.float32)[:, None, None], img.shape))
+    # everything behind the camera
+    scene, _ = scenes.small_scene(seed=1, n3=50, n4=20)
+    back = scenes.View(R=np.diag([-1.0, 1.0, -1.0]).astype(np.float32), T=np.zeros(3, np.float32), fx=40.0, fy=40.0,
+                       cx=20.0, cy=12.0, W=40, H=24, t=0.5, bg=(0.1, 0.2, 0.3))
+    G = raster.Gaussians.from_scene(scene, "cuda")
+    R = raster.Rasterizer(G.n3, G.n4, [back])
+    R.forward(G)
+    torch.cuda.synchronize()
+    R.check()
+    assert R.instances() == 0
+    np.testing.assert_allclose(R.image(0).cpu().numpy()[:, 5, 7], [0.1, 0.2, 0.3])
+    dl = torch.ones_like(R.rgb)
+    R.backward(G, dl)
+    torch.cuda.synchronize()
+    R.check()
+    for k in F3 + F4:
+        assert float(R.grads[k].abs().max()) == 0.0
+
+
+def test_only_3d_and_only_4d():
+    for n3, n4 in ((200, 0), (0, 200)):
+        scene, views = scenes.small_scene(seed=9, n3=n3, n4=n4)
+        G, R = make(scene, views)
+        P = O.project(scene, views[0])
+        ref = O.render(scene, views[0])
+        check_image(R, P, ref, views[0])
+
+
+def test_spin_limit_zero_reports_or_completes(big):
+    scene, views, G, R, P = big
+    good = R.rgb.clone()
+    abi.splat_set_spin_limit(0)
+    try:
+        R.forward(G)
+        torch.cuda.synchronize()
+        code, stage, aux = R.read_status()
+        assert code in (abi.SPLAT_OK, abi.SPLAT_ERR_TIMEOUT)
+        if code == abi.SPLAT_ERR_TIMEOUT:
+            assert abi.STAGES[stage] in ("depth_sort", "scan", "tile_sort")
+    finally:
+        abi.splat_set_spin_limit(1 << 22)
+    R.forward(G)
+    torch.cuda.synchronize()
+    R.check()
+    assert torch.equal(good, R.rgb)
+
+
+def test_invalid_arguments_are_rejected_on_host(small):
+    scene, views, G, R, P, ref = small
+    st = C.c_void_p(R.status.data_ptr())
+    s = C.c_void_p(0)
+    g3, g4 = G.c_g3(), G.c_g4()
+    assert abi.splat_slice_project(C.byref(g3), C.byref(g4), R.cviews, 0, C.byref(R.cproj), st, s) == abi.SPLAT_ERR_INVALID_ARG
+    bad = abi.splat_proj.from_buffer_copy(R.cproj)
+    bad.n = R.N + 1
+    assert abi.splat_slice_project(C.byref(g3), C.byref(g4), R.cviews, 1, C.byref(bad), st, s) == abi.SPLAT_ERR_INVALID_ARG
+    assert abi.splat_bin_sort(C.byref(R.cproj), R.cviews, 1, C.byref(R.cbins), st, C.c_void_p(R.ws.data_ptr()), 16,
+                              s) == abi.SPLAT_ERR_INVALID_ARG
+
+
+def test_l1_loss_kernel(small):
+    scene, views, G, R, P, ref = small
+    target = torch.rand_like(R.rgb)
+    R.l1_loss(target)
+    torch.cuda.synchronize()
+    d = (R.rgb - target).double()
+    assert abs(float(R.loss.item()) - float(d.abs().sum())) < 1e-3 * float(d.abs().sum())
+    np.testing.assert_array_equal(R.dL.cpu().numpy(), (torch.sign(d) / R.rgb.numel()).float().cpu().numpy())
+
+
+def test_graph_replay_matches_eager(small):
+    scene, views, G, R0, P, ref = small
+    R = raster.Rasterizer(G.n3, G.n4, views, capacity=R0.capacity)
+    target = torch.rand_like(R.rgb)
+    R.step(G, target)
+    torch.cuda.synchronize()
+    eager = {k: v.clone() for k, v in R.grads.items()}
+    img = R.rgb.clone()
+    gs = raster.GraphedStep(R, G, target)
+    for k in R.grads:
+        R.grads[k].zero_()
+    R.rgb.zero_()
+    gs.replay()
+    torch.cuda.synchronize()
+    R.check()
+    assert torch.equal(img, R.rgb)
+    for k in R.grads:
+        assert rel_l2(R.grads[k].cpu().numpy(), eager[k].cpu().numpy()) < 1e-5, k
+
+
+def test_autograd_function(small):
+    scene, views, G, R, P, ref = small
+    params = [G.t[k] for k in F3 + F4]
+    for p in params:
+        p.requires_grad_(True)
+    try:
+        out = raster.HybridRasterize.apply(R, G, *params)
+        w = torch.randn_like(out)
+        (out * w).sum().backward()
+        R.backward(G, w)
+        torch.cuda.synchronize()
+        for k, p in zip(F3 + F4, params):
+            n = G.n3 if k in F3 else G.n4
+            assert torch.allclose(p.grad[:n].float(), R.grads[k], rtol=1e-4, atol=1e-7)
+    finally:
+        for p in params:
+            p.requires_grad_(False)
+            p.grad = None
