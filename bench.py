@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the hybrid 3D-4D Gaussian rasterizer.
+
+Metric: forward + backward views/s at 1352x1014 with 300k Gaussians (200k
+static 3D + 100k dynamic 4D, the video workload), batched views with BF16
+parameter storage, beside the plain per-view FP32 path on the same GPU.
+
+A step is one full pass of the rasterizer over one batch of views: slice and
+project, bin and sort, composite, L1 loss, compositing adjoint and projection
+adjoint, replayed as one CUDA graph.  Inputs are resident in HBM when the
+timed region starts (`value`); `e2e` adds the host->device copy of the step's
+parameters and targets from pinned memory and the device->host read of the
+loss.  L2 is flushed (a 512 MB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--views V] [--impl reference]
+
+Under torchrun each rank renders its own batch of views (independent
+replicas, weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd views/s at 1352×1014, 300k Gaussians: batched/BF16 vs plain FP32"
+UNIT = "views/s"
+N3, N4, W, H = 200_000, 100_000, 1352, 1014
+
+
+# ---------------------------------------------------------------------------
+# process group plumbing (barrier and max-over-ranks timing only)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, local, world
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, init_method="env://")
+    return dist
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def reduce_max(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Each replica renders its own cameras / timestamps of the same scene."""
+    return 100 + rank
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = [n for j, n in enumerate(names) if any(r[5 + j].lower().startswith("active") for r in rows)]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# roofline model
+# ---------------------------------------------------------------------------
+
+def param_bytes(n3, n4, elem):
+    return elem * (n3 * (3 + 3 + 4 + 1 + 48) + n4 * (4 + 4 + 4 + 4 + 1 + 48))
+
+
+def algorithmic_bytes(stage, n3, n4, V, pix, K, elem):
+    """Bytes each stage must move to/from HBM once (inputs read once, outputs
+    written once), per launch over the batch."""
+    N = n3 + n4
+    rows = V * N
+    proj_row = 8 + 16 + 16 + 16 + 4 + 4       # xy, conic/opacity, rgb/depth, rect, radius, n_tiles
+    if stage == "slice_project":
+        return param_bytes(n3, n4, elem) + rows * proj_row
+    if stage == "adjoint":
+        return param_bytes(n3, n4, elem) + rows * (48 + 4) + param_bytes(n3, n4, 4)
+    if stage == "composite_fwd":
+        return K * 4 + rows * 36 + pix * (12 + 4 + 4)
+    if stage == "composite_bwd":
+        return K * 4 + rows * 36 + pix * (12 + 4 + 4) + rows * 48
+    if stage == "loss":
+        return pix * 12 * 3
+    if stage == "bin_sort":
+        # depth keys of the rows, instances written once by the duplication and
+        # read once by the (tile-digit) sort, sorted ids and tile keys written once
+        return rows * (4 + 4 + 16) + K * 8 * 2
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, local, world):
+    import numpy as np
+    import torch
+
+    from paper_2505_13215_gb300 import abi, autotune, raster, scenes
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the CUDA path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist(world, "nccl")
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    scene, base = scenes.video_scene(seed=1, n3=N3, n4=N4, W=W, H=H)
+    views = scenes.jittered_views(base[0], args.views, seed=rank_seed(rank))
+    V = len(views)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+
+    # ---- batched BF16 path (the headline) ----
+    G = raster.Gaussians.from_scene(scene, dev, dtype=torch.bfloat16)
+    R = raster.Rasterizer(G.n3, G.n4, views, device=dev)
+    target = torch.rand(R.rgb.shape, generator=gen, device=dev)
+    tune = autotune.tune(R, G, target)
+    K_inst = R.instances()
+    copies = args.steps
+    try:
+        gs = raster.GraphedStep(R, G, target, copies=copies, with_marks=True)
+        marks_ok = True
+    except Exception as e:  # external events inside captures unsupported: stage times from an eager pass
+        sys.stderr.write("graph with stage events failed (%s); capturing without\n" % e)
+        gs = raster.GraphedStep(R, G, target, copies=1, with_marks=False)
+        marks_ok = False
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        flush.zero_()
+        gs.replay(i)
+    torch.cuda.synchronize()
+    R.check("warm-up")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        gs.replay(k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    R.check("timed steps")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    t_max = reduce_max(total_s, dev)
+    views_total = reduce_sum(V * args.steps, dev)
+    value = views_total / t_max
+    if marks_ok:
+        per = [gs.stage_ms(k) for k in range(args.steps)]
+        stages = {s: sum(p[s] for p in per) / len(per) for s in raster.Rasterizer.STAGES}
+    else:
+        stages = eager_stage_ms(R, G, target, 5)
+    launches = gs.launches_per_step * args.steps
+
+    # ---- plain per-view FP32 path, same views ----
+    G32 = raster.Gaussians.from_scene(scene, dev, dtype=torch.float32)
+    plain = []
+    for v in views:
+        Rv = raster.Rasterizer(G32.n3, G32.n4, [v], device=dev)
+        tv = torch.rand(Rv.rgb.shape, generator=gen, device=dev)
+        Rv.autotune_capacity(G32)
+        plain.append((Rv, tv))
+    abi.splat_set_pixels_per_lane(8, 8)
+    plain_steps = max(2, args.steps // 2)
+    for Rv, tv in plain:
+        Rv.step(G32, tv)
+    torch.cuda.synchronize()
+    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(plain_steps)]
+    for k in range(plain_steps):
+        flush.zero_()
+        pe[k][0].record(stream)
+        for Rv, tv in plain:
+            Rv.step(G32, tv)
+        pe[k][1].record(stream)
+    torch.cuda.synchronize()
+    for Rv, _ in plain:
+        Rv.check("plain FP32 path")
+    plain_s = sum(a.elapsed_time(b) for a, b in pe) / 1e3
+    plain_value = reduce_sum(V * plain_steps, dev) / reduce_max(plain_s, dev)
+    abi.splat_set_pixels_per_lane(tune["ppl_fwd"], tune["ppl_bwd"])
+    del plain
+
+    # ---- end to end: pinned host inputs in, loss out, every step ----
+    host_params = {k: G.t[k].cpu().pin_memory() for k in G.t}
+    host_target = target.cpu().pin_memory()
+    loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+    status_host = torch.zeros(4, dtype=torch.int32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_params.values()) + host_target.numel() * 4
+    d2h = 4 + 16
+
+    def e2e_step(i):
+        for k, t in host_params.items():
+            G.t[k].copy_(t, non_blocking=True)
+        target.copy_(host_target, non_blocking=True)
+        gs.replay(i)
+        loss_host.copy_(R.loss, non_blocking=True)
+        status_host.copy_(R.status, non_blocking=True)
+
+    for i in range(2):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if int(status_host[0]) != 0:
+        raise abi.SplatError(int(status_host[0]), "e2e steps", int(status_host[1]))
+    e2e_value = views_total / reduce_max(e2e_s, dev)
+
+    # ---- roofline of the dominant stage ----
+    pix = int(sum(R.pix))
+    dom = max(stages, key=lambda s: stages[s])
+    alg = algorithmic_bytes(dom, G.n3, G.n4, V, pix, K_inst, 2)
+    ach = alg / (stages[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes": alg}
+    if dom in ("composite_fwd", "composite_bwd"):
+        roofline["note"] = "compositing is FP32-pipe/MUFU/atomic bound; HBM fraction shown for reference"
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 storage, f32 compute", "data": "synthetic",
+        "config": {"workload": "video scene 200k 3D + 100k 4D Gaussians, %d views/step at %dx%d, BF16 storage, "
+                               "one CUDA graph per step" % (V, W, H),
+                   "views_per_step": V, "gaussians": N3 + N4, "resolution": [W, H], "l2": "flushed before each step",
+                   "instances_K": K_inst, "autotune": {k: tune[k] for k in ("ppl_fwd", "ppl_bwd", "capacity")},
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "plain_fp32": {"value": round(plain_value, 2), "unit": UNIT, "path": "per-view launches, FP32 storage, eager"},
+        "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scene, views, samples=args.cpu_samples)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def eager_stage_ms(R, G, target, reps):
+    import torch
+    from paper_2505_13215_gb300 import raster
+    acc = {s: 0.0 for s in raster.Rasterizer.STAGES}
+    for _ in range(reps):
+        m = raster.stage_events()
+        R.step(G, target, marks=m)
+        torch.cuda.synchronize()
+        names = ("start",) + raster.Rasterizer.STAGES
+        for a, b in zip(names[:-1], names[1:]):
+            acc[b] += m[a].elapsed_time(m[b]) / reps
+    return acc
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(scene, views, samples=1500, seed=0):
+    """Oracle forward at `samples` random pixels of view 0 plus the backward of a
+    loss on those pixels, scaled to views/s by the fraction of the view sampled."""
+    import numpy as np
+
+    import oracle as O
+    v = views[0]
+    rng = np.random.default_rng(seed)
+    npix = v.W * v.H
+    pix = rng.choice(npix, size=min(samples, npix), replace=False)
+    t0 = time.perf_counter()
+    ref = O.render(scene, v, pixels=pix)
+    g = np.zeros((3, npix))
+    g[:, pix] = np.sign(ref["rgb"] - 0.5)
+    O.render_bwd(scene, v, g.reshape(3, v.H, v.W))
+    dt = time.perf_counter() - t0
+    frac = len(pix) / npix
+    return {"value": round(frac / dt, 6), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "FP64 oracle forward at %d random pixels of one %dx%d view (of %d Gaussians) plus the "
+                      "backward of a loss on them: %.1f s; scaled by the sampled fraction %.2e of a view"
+                      % (len(pix), v.W, v.H, scene.n, dt, frac)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, local, world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="gloo", init_method="env://")
+        dist.barrier()
+        if rank != 0:
+            return
+    from paper_2505_13215_gb300 import scenes
+    scene, base = scenes.video_scene(seed=1, n3=N3, n4=N4, W=W, H=H)
+    views = scenes.jittered_views(base[0], args.views, seed=rank_seed(0))
+    for i in range(args.warmup):
+        cpu_baseline(scene, views, samples=args.ref_samples // 4, seed=1000 + i)
+    vals, total, cores, sample = [], 0.0, None, None
+    for k in range(args.steps):
+        r = cpu_baseline(scene, [views[k % len(views)]], samples=args.ref_samples, seed=k)
+        vals.append(r["value"])
+        cores, sample = r["cores"], r["sample"]
+    value = len(vals) / sum(1.0 / x for x in vals)  # views per total second
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / value, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "video scene 200k 3D + 100k 4D Gaussians at %dx%d, oracle on a pixel sample" % (W, H),
+                      "views_per_step": 1, "gaussians": N3 + N4, "resolution": [W, H]},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--views", type=int, default=4, help="views per batched step (<= 16)")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-samples", type=int, default=1500)
+    ap.add_argument("--ref-samples", type=int, default=600)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank, local, world = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, local, world)
+    else:
+        run_ours(args, rank, local, world)
+
+
+if __name__ == "__main__":
+    main()

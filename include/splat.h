@@ -182,7 +182,9 @@ enum {
 };
 
 /* splat_composite_bwd flags */
-#define SPLAT_BWD_STOP_2D 1u /* stop after the 2D gradients (dproj), skip the adjoint */
+#define SPLAT_BWD_STOP_2D 1u      /* stop after the 2D gradients (dproj), skip the adjoint */
+#define SPLAT_BWD_ADJOINT_ONLY 2u /* skip the compositing adjoint: chain the caller's dproj
+                                     (not cleared) through the projection into dg3 / dg4 */
 
 /*
  * Bytes of workspace an entry point needs.  N3, N4: Gaussian counts (for
@@ -248,8 +250,10 @@ splat_status splat_composite_fwd(const splat_proj *proj, const splat_bins *bins,
  * (dpx, dpy, da, db, dc, dalpha_max, dr, dg, db, 0, 0, 0), then chains them
  * through the colour, EWA, slicing and covariance of every Gaussian and
  * OVERWRITES dg3 / dg4 with the gradient summed over the V views.  With
- * SPLAT_BWD_STOP_2D only dproj is written.  g3, g4 must be the parameters the
- * forward used.
+ * SPLAT_BWD_STOP_2D only dproj is written; with SPLAT_BWD_ADJOINT_ONLY the
+ * given dproj (caller memory, required) is only chained through the
+ * projection (img and dL_drgb are then unused).  g3, g4 must be the
+ * parameters the forward used.
  */
 splat_status splat_composite_bwd(const splat_proj *proj, const splat_bins *bins, const splat_view *views, int V,
                                  const splat_image *img, const float *dL_drgb, const splat_g3 *g3,
@@ -298,6 +302,10 @@ void splat_set_spin_limit(int64_t iterations);
  * on it beyond floating-point summation order of the gradients.
  */
 void splat_set_pixels_per_lane(int fwd, int bwd);
+
+/* Number of kernels this library has launched (or enqueued into a stream
+ * capture) in this process; a diagnostic counter. */
+int64_t splat_launch_count(void);
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int32_t splat_version(void);

@@ -64,7 +64,7 @@ def lib():
         L.oracle_sh_basis.argtypes = [_dp, _dp, _dp]
         L.oracle_project.argtypes = [C.POINTER(_G3), C.POINTER(_G4), C.POINTER(_View), C.c_void_p]
         L.oracle_render.argtypes = [C.POINTER(_G3), C.POINTER(_G4), C.POINTER(_View), _i64p, C.c_int64,
-                                    _dp, _dp, _i32p, _dp, _dp]
+                                    _dp, _dp, _i32p, _dp]
         L.oracle_render_bwd.argtypes = [C.POINTER(_G3), C.POINTER(_G4), C.POINTER(_View), _dp] + [_dp] * 12
         L.oracle_tile_list.argtypes = [C.POINTER(_G3), C.POINTER(_G4), C.POINTER(_View), C.c_int, C.c_int, _i64p]
         L.oracle_tile_list.restype = C.c_int64
@@ -74,6 +74,7 @@ def lib():
         L.oracle_stable_sort_u64.argtypes = [C.POINTER(C.c_uint64), C.c_int64, _i64p]
         L.oracle_num_threads.restype = C.c_int
         L.oracle_set_num_threads.argtypes = [C.c_int]
+        L.oracle_set_margin_impact.argtypes = [C.c_double]
         _lib = L
     return _lib
 
@@ -203,7 +204,9 @@ def project(scene, view):
 
 def render(scene, view, pixels=None):
     """Eq. 3 as the plain definition.  pixels: flat indices y*W+x (None = all).
-    Returns dict rgb [3, npix], T [npix], last [npix], margin_fwd, margin_grad."""
+    Returns dict rgb [3, npix], T [npix], last [npix], the per-decision margins
+    (dict 'margins': power, alpha, stop, tie, clamp), margin_fwd (min of the
+    first four) and margin_grad (the clamp)."""
     pk = _Packed(scene)
     v = _view(view)
     if pixels is None:
@@ -216,11 +219,12 @@ def render(scene, view, pixels=None):
     rgb = np.zeros((3, npix))
     T = np.zeros(npix)
     last = np.zeros(npix, dtype=np.int32)
-    mf = np.zeros(npix)
-    mg = np.zeros(npix)
+    mg = np.zeros((5, npix))
     lib().oracle_render(C.byref(pk.g3), C.byref(pk.g4), C.byref(v), pix_p, npix, _p(rgb), _p(T),
-                        last.ctypes.data_as(_i32p), _p(mf), _p(mg))
-    return {"rgb": rgb, "T": T, "last": last, "margin_fwd": mf, "margin_grad": mg}
+                        last.ctypes.data_as(_i32p), _p(mg))
+    names = ("power", "alpha", "stop", "tie", "clamp")
+    return {"rgb": rgb, "T": T, "last": last, "margins": dict(zip(names, mg)),
+            "margin_fwd": mg[:4].min(0), "margin_grad": mg[4]}
 
 
 def tile_list(scene, view, tx, ty):
@@ -271,6 +275,12 @@ def stable_sort_u64(keys):
     perm = np.zeros(k.shape[0], dtype=np.int64)
     lib().oracle_stable_sort_u64(k.ctypes.data_as(C.POINTER(C.c_uint64)), k.shape[0], perm.ctypes.data_as(_i64p))
     return perm
+
+
+def set_margin_impact(impact: float) -> None:
+    """Record a forward decision's margin only when flipping it could change the
+    pixel by at least `impact` (0 = every decision)."""
+    lib().oracle_set_margin_impact(float(impact))
 
 
 def num_threads() -> int:

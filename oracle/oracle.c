@@ -494,36 +494,62 @@ typedef struct {
 
 /* Walks the list front to back for pixel (u,v); returns the number of tape
  * entries (contributing Gaussians).  Reading D5 for the skip / stop rules. */
+/* margins of one pixel, each the min over its walk of |quantity - threshold| / scale */
+enum { MG_POWER = 0, MG_ALPHA = 1, MG_STOP = 2, MG_TIE = 3, MG_CLAMP = 4, MG_COUNT = 5 };
+
+/* A forward decision's margin is recorded only when flipping it could change
+ * the pixel by at least this much (0: record every decision).  Bounds used:
+ * alpha skip 2 T c_max / 255; power sign 2 T alpha_max c_max; order of two
+ * touching Gaussians T alpha_1 alpha_2 |c_1 - c_2|; the stop is always kept. */
+static double g_margin_impact = 0.0;
+static double g_cmax = 1.0;  /* largest colour channel of the current render */
+
+void oracle_set_margin_impact(double impact) { g_margin_impact = impact > 0.0 ? impact : 0.0; }
+
 static int64_t blend_pixel(const oproj *P, const dkey *list, int64_t m, int u, int vpix,
                            const double bg[3], double rgb[3], double *T_out, int32_t *last_out,
-                           double *margin_fwd, double *margin_grad, tape_ent *tape)
+                           double mg_out[MG_COUNT], tape_ent *tape)
 {
     double T = 1.0, C[3] = { 0, 0, 0 };
-    double mf = INFINITY, mg = INFINITY;
+    double mgn[MG_COUNT] = { INFINITY, INFINITY, INFINITY, INFINITY, INFINITY };
     int32_t last = 0;
     int64_t nt = 0;
-    double prev_depth = -1.0;  /* depth of the previous Gaussian that touched the pixel */
+    double prev_depth = -1.0;  /* depth, T, alpha, colour of the previous Gaussian that touched the pixel */
+    double prev_T = 0.0, prev_alpha = 0.0;
+    const double *prev_rgb = NULL;
+    const double imp = g_margin_impact;
     for (int64_t j = 0; j < m; ++j) {
         const oproj *o = &P[list[j].idx];
         double dx = o->px - u, dy = o->py - vpix;
         double a = o->conic[0], b = o->conic[1], c = o->conic[2];
         double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
         double pmag = 0.5 * fabs(a) * dx * dx + 0.5 * fabs(c) * dy * dy + fabs(b * dx * dy);
-        if (pmag > 0.0) mf = dmin(mf, fabs(power) / pmag);
+        if (pmag > 0.0 && 2.0 * T * o->alpha * g_cmax >= imp)
+            mgn[MG_POWER] = dmin(mgn[MG_POWER], fabs(power) / pmag);
         if (power > 0.0) continue;
         double G = exp(power);
         double raw = o->alpha * G;
-        mf = dmin(mf, fabs(raw - ALPHA_MIN) / ALPHA_MIN);
-        mg = dmin(mg, fabs(raw - ALPHA_MAX_CLAMP) / ALPHA_MAX_CLAMP);
+        if (2.0 * T * g_cmax * ALPHA_MIN >= imp)
+            mgn[MG_ALPHA] = dmin(mgn[MG_ALPHA], fabs(raw - ALPHA_MIN) / ALPHA_MIN);
+        mgn[MG_CLAMP] = dmin(mgn[MG_CLAMP], fabs(raw - ALPHA_MAX_CLAMP) / ALPHA_MAX_CLAMP);
         if (raw >= ALPHA_MIN) {
             /* two touching Gaussians at (nearly) equal depth: their order is a decision too */
-            if (prev_depth > 0.0) mf = dmin(mf, fabs(o->depth - prev_depth) / o->depth);
+            double a_cur = raw < ALPHA_MAX_CLAMP ? raw : ALPHA_MAX_CLAMP;
+            if (prev_depth > 0.0) {
+                double dc = 0.0;
+                for (int ch = 0; ch < 3; ++ch) dc = fmax(dc, fabs(o->rgb[ch] - prev_rgb[ch]));
+                if (prev_T * prev_alpha * a_cur * dc >= imp)
+                    mgn[MG_TIE] = dmin(mgn[MG_TIE], fabs(o->depth - prev_depth) / o->depth);
+            }
             prev_depth = o->depth;
+            prev_T = T;
+            prev_alpha = a_cur;
+            prev_rgb = o->rgb;
         }
         double alpha = raw < ALPHA_MAX_CLAMP ? raw : ALPHA_MAX_CLAMP;
         if (alpha < ALPHA_MIN) continue;
         double test_T = T * (1.0 - alpha);
-        mf = dmin(mf, fabs(test_T - T_MIN) / T_MIN);
+        mgn[MG_STOP] = dmin(mgn[MG_STOP], fabs(test_T - T_MIN) / T_MIN);
         if (test_T < T_MIN) break;  /* this Gaussian does not contribute */
         if (tape) {
             tape[nt].idx = list[j].idx;
@@ -542,20 +568,26 @@ static int64_t blend_pixel(const oproj *P, const dkey *list, int64_t m, int u, i
     for (int ch = 0; ch < 3; ++ch) rgb[ch] = C[ch] + T * bg[ch];
     *T_out = T;
     *last_out = last;
-    if (margin_fwd) *margin_fwd = mf;
-    if (margin_grad) *margin_grad = mg;
+    if (mg_out)
+        for (int k = 0; k < MG_COUNT; ++k) mg_out[k] = mgn[k];
     return nt;
 }
 
 /* Render the given pixels (flat indices v*W+u; NULL = the whole image).
- * rgb is [3][npix] planar, T and last are [npix]. */
+ * rgb is [3][npix] planar, T and last are [npix]; margins (may be NULL) is
+ * [5][npix]: power sign, alpha skip, transmittance stop, depth order of two
+ * touching Gaussians, alpha clamp (the last only matters to gradients). */
 void oracle_render(const og3 *g3, const og4 *g4, const oview *v, const int64_t *pix, int64_t npix,
-                   double *rgb, double *T, int32_t *last, double *margin_fwd, double *margin_grad)
+                   double *rgb, double *T, int32_t *last, double *margins)
 {
     int64_t n = (g4 ? g4->n : 0) + (g3 ? g3->n : 0);
     oproj *P = malloc(sizeof(oproj) * (size_t)(n > 0 ? n : 1));
     oracle_project(g3, g4, v, P);
     if (!pix) npix = (int64_t)v->W * v->H;
+    g_cmax = fmax(fmax(v->bg[0], v->bg[1]), v->bg[2]);
+    for (int64_t i = 0; i < n; ++i)
+        if (P[i].visible)
+            for (int ch = 0; ch < 3; ++ch) g_cmax = fmax(g_cmax, P[i].rgb[ch]);
 #pragma omp parallel
     {
         dkey *buf = malloc(sizeof(dkey) * (size_t)(n > 0 ? n : 1));
@@ -564,11 +596,11 @@ void oracle_render(const og3 *g3, const og4 *g4, const oview *v, const int64_t *
             int64_t p = pix ? pix[q] : q;
             int u = (int)(p % v->W), vv = (int)(p / v->W);
             int64_t m = pixel_list(P, n, u / TILE, vv / TILE, buf);
-            double c3[3], mf, mg;
-            blend_pixel(P, buf, m, u, vv, v->bg, c3, &T[q], &last[q], &mf, &mg, NULL);
+            double c3[3], mg[MG_COUNT];
+            blend_pixel(P, buf, m, u, vv, v->bg, c3, &T[q], &last[q], mg, NULL);
             for (int ch = 0; ch < 3; ++ch) rgb[ch * npix + q] = c3[ch];
-            if (margin_fwd) margin_fwd[q] = mf;
-            if (margin_grad) margin_grad[q] = mg;
+            if (margins)
+                for (int k = 0; k < MG_COUNT; ++k) margins[k * npix + q] = mg[k];
         }
         free(buf);
     }
@@ -879,7 +911,7 @@ void oracle_render_bwd(const og3 *g3, const og4 *g4, const oview *v, const doubl
             int64_t m = pixel_list(P, n, u / TILE, vv / TILE, buf);
             double c3[3], T;
             int32_t last;
-            int64_t nt = blend_pixel(P, buf, m, u, vv, v->bg, c3, &T, &last, NULL, NULL, tape);
+            int64_t nt = blend_pixel(P, buf, m, u, vv, v->bg, c3, &T, &last, NULL, tape);
             blend_pixel_bwd(P, tape, nt, T, v->bg, g, dproj);
         }
         free(tape);

@@ -21,6 +21,7 @@ SPLAT_ERR_CUDA = 5
 SPLAT_F32, SPLAT_BF16, SPLAT_F16 = 0, 1, 2
 SPLAT_OP_BIN_SORT, SPLAT_OP_COMPOSITE_BWD, SPLAT_OP_CONVERT, SPLAT_OP_ALL = 1, 2, 3, 4
 SPLAT_BWD_STOP_2D = 1
+SPLAT_BWD_ADJOINT_ONLY = 2
 SPLAT_MAX_VIEWS = 16
 SPLAT_MAX_INSTANCES = 1 << 30
 
@@ -74,6 +75,7 @@ class splat_grads4(C.Structure):
 _P = C.POINTER
 EXPORTS = {
     "splat_version": (C.c_int32, []),
+    "splat_launch_count": (C.c_int64, []),
     "splat_set_spin_limit": (None, [C.c_int64]),
     "splat_set_pixels_per_lane": (None, [C.c_int, C.c_int]),
     "splat_status_string": (C.c_char_p, [C.c_int32]),
@@ -139,6 +141,10 @@ def check(code, where):
 
 def splat_version():
     return lib().splat_version()
+
+
+def splat_launch_count():
+    return lib().splat_launch_count()
 
 
 def splat_set_spin_limit(n):

@@ -24,6 +24,7 @@ size_t convert_workspace(int64_t n4, int dtype_bytes);
 cudaError_t launch_l1_loss(const float*, const float*, int64_t, float, float*, float*, const LaunchCtx&);
 
 static std::atomic<int64_t> g_spin_limit{1ll << 22};
+std::atomic<int64_t> g_launches{0};
 static std::atomic<int> g_ppl_fwd{8}, g_ppl_bwd{8};
 static int g_num_sms[64];
 
@@ -142,6 +143,8 @@ extern "C" {
 
 int32_t splat_version(void) { return 0x000100; }
 
+int64_t splat_launch_count(void) { return g_launches.load(); }
+
 void splat_set_spin_limit(int64_t iterations) { g_spin_limit.store(iterations < 0 ? 0 : iterations); }
 
 void splat_set_pixels_per_lane(int fwd, int bwd)
@@ -253,10 +256,13 @@ splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins,
     const splat_g4 g4 = g4_or_empty(g4p);
     bool same = true;
     const int dt = common_dtype(g3, g4, &same);
-    if (!same || !valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !dL_drgb || !status)
-        return SPLAT_ERR_INVALID_ARG;
-    if (!img->final_T || !img->last || !bins->ranges) return SPLAT_ERR_INVALID_ARG;
     const bool stop2d = (flags & SPLAT_BWD_STOP_2D) != 0;
+    const bool adj_only = (flags & SPLAT_BWD_ADJOINT_ONLY) != 0;
+    if (!same || !valid_views(views, V) || !valid_proj(proj, V) || !status || (stop2d && adj_only))
+        return SPLAT_ERR_INVALID_ARG;
+    if (!adj_only && (!bins || !img || !dL_drgb || !img->final_T || !img->last || !bins->ranges))
+        return SPLAT_ERR_INVALID_ARG;
+    if (adj_only && !dproj) return SPLAT_ERR_INVALID_ARG;
     if (!stop2d) {
         if (!valid_g3(g3) || !valid_g4(g4) || proj->n != g3.n + g4.n) return SPLAT_ERR_INVALID_ARG;
         if (g3.n > 0 && (!dg3 || !dg3->mean || !dg3->log_scale || !dg3->quat || !dg3->opacity || !dg3->sh))
@@ -282,10 +288,12 @@ splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins,
     }
     const LaunchCtx ctx = launch_ctx(stream);
     const ViewBatch vb = make_batch(views, V);
-    cudaError_t e = cudaMemsetAsync(dp, 0, dproj_bytes, ctx.stream);
-    if (e != cudaSuccess) return SPLAT_ERR_CUDA;
-    e = launch_composite_bwd(*proj, *bins, vb, *img, dL_drgb, dp, status, g_ppl_bwd.load(), ctx);
-    if (e != cudaSuccess) return SPLAT_ERR_CUDA;
+    if (!adj_only) {
+        cudaError_t e = cudaMemsetAsync(dp, 0, dproj_bytes, ctx.stream);
+        if (e != cudaSuccess) return SPLAT_ERR_CUDA;
+        e = launch_composite_bwd(*proj, *bins, vb, *img, dL_drgb, dp, status, g_ppl_bwd.load(), ctx);
+        if (e != cudaSuccess) return SPLAT_ERR_CUDA;
+    }
     if (stop2d) return SPLAT_OK;
     splat_grads3 d3 = dg3 ? *dg3 : splat_grads3{};
     splat_grads4 d4 = dg4 ? *dg4 : splat_grads4{};

@@ -326,6 +326,7 @@ cudaError_t launch_l1_loss(const float* img, const float* target, int64_t n, flo
     if (e != cudaSuccess || n == 0) return e;
     const int64_t want = (n / 4 + 255) / 256 + 1;
     const int blocks = (int)(want < (int64_t)ctx.num_sms * 8 ? want : (int64_t)ctx.num_sms * 8);
+    count_launch();
     k_l1_loss<<<blocks, 256, 0, ctx.stream>>>(img, target, n, scale, dL, loss);
     return cudaGetLastError();
 }
@@ -337,6 +338,7 @@ cudaError_t launch_composite_fwd(const splat_proj& proj, const splat_bins& bins,
     const int bands = 8 / ppl;
     const int64_t units = (int64_t)vb.total_tiles * bands;
     const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
+    count_launch();
     switch (ppl) {
     case 8: k_composite_fwd<8><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
     case 4: k_composite_fwd<4><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
@@ -354,6 +356,7 @@ cudaError_t launch_composite_bwd(const splat_proj& proj, const splat_bins& bins,
     const int bands = 8 / ppl;
     const int64_t units = (int64_t)vb.total_tiles * bands;
     const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
+    count_launch();
     switch (ppl) {
     case 8: k_composite_bwd<8><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
     case 4: k_composite_bwd<4><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;

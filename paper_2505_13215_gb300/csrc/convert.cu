@@ -238,6 +238,7 @@ static cudaError_t convert_impl(const splat_g4& g4, const splat_g3& g3, float ta
     tmp.sh = w + o;
     cudaStream_t s = ctx.stream;
     if (n4 == 0) return cudaMemsetAsync(n_moved, 0, sizeof(int64_t), s);
+    count_launch(4);
     k_conv_count<DT><<<(int)nb, kConvThreads, 0, s>>>(g4, tau, counts);
     k_conv_scan<<<1, 1024, 0, s>>>(counts, nb, g3.n, g3.capacity, n_moved, status);
     k_conv_scatter<DT><<<(int)nb, kConvThreads, 0, s>>>(g4, g3, tau, counts, tmp, status);

@@ -231,8 +231,11 @@ __global__ void __launch_bounds__(128) k_slice_project(splat_g3 g3, splat_g4 g4,
             if (!culled) {
                 const float idet = 1.f / e.det;
                 co = make_float4(e.s11 * idet, -e.s01 * idet, e.s00 * idet, alpha);
+                // lambda_max = mid + sqrt(max(0.1, mid^2 - det)); mid^2 - det is evaluated as
+                // ((s00 - s11)/2)^2 + s01^2, the same number without the FP32 cancellation
                 const float mid = 0.5f * (e.s00 + e.s11);
-                const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - e.det));
+                const float hd = 0.5f * (e.s00 - e.s11);
+                const float lam = mid + sqrtf(fmaxf(0.1f, hd * hd + e.s01 * e.s01));
                 const float rf = ceilf(3.f * sqrtf(lam));
                 const float px = vp.fx * e.ux + vp.cx, py = vp.fy * e.uy + vp.cy;
                 xy = make_float2(px, py);
@@ -609,6 +612,7 @@ cudaError_t launch_slice_project(const splat_g3& g3, const splat_g4& g4, const V
     const int threads = 128;
     const int64_t want = (N + threads - 1) / threads;
     const int blocks = (int)(want < (int64_t)ctx.num_sms * 64 ? want : (int64_t)ctx.num_sms * 64);
+    count_launch();
     switch (dtype) {
     case SPLAT_F32: k_slice_project<SPLAT_F32><<<blocks, threads, 0, ctx.stream>>>(g3, g4, vb, out, status); break;
     case SPLAT_BF16: k_slice_project<SPLAT_BF16><<<blocks, threads, 0, ctx.stream>>>(g3, g4, vb, out, status); break;
@@ -626,6 +630,7 @@ cudaError_t launch_adjoint(const splat_g3& g3, const splat_g4& g4, const ViewBat
     const int threads = 128;
     const int64_t want = (N + threads - 1) / threads;
     const int blocks = (int)(want < (int64_t)ctx.num_sms * 64 ? want : (int64_t)ctx.num_sms * 64);
+    count_launch();
     switch (dtype) {
     case SPLAT_F32: k_adjoint<SPLAT_F32><<<blocks, threads, 0, ctx.stream>>>(g3, g4, vb, proj, dproj, dg3, dg4, status); break;
     case SPLAT_BF16: k_adjoint<SPLAT_BF16><<<blocks, threads, 0, ctx.stream>>>(g3, g4, vb, proj, dproj, dg3, dg4, status); break;

@@ -498,6 +498,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     // 1. depth keys + digit histograms; zero the first depth look-back buffer and the scan look-back
     {
         const int blocks = (int)std::min<int64_t>((n_rows + 255) / 256, (int64_t)ctx.num_sms * 8);
+        count_launch();
         k_depth_keys<<<blocks, 256, 0, s>>>(proj, n_rows, U(L.off_dkeys[0]), U(L.off_dvals[0]), hist,
                                             U(L.off_dlb[0]), L.parts_d * kRadix,
                                             (unsigned long long*)(w + L.off_scan_lb), L.parts_scan);
@@ -522,6 +523,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.shift = 8 * p;
         a.spin_limit = ctx.spin_limit;
         const int blocks = (int)std::min<int64_t>(L.parts_d, resident);
+        count_launch();
         k_onesweep<<<blocks, kSortThreads, 0, s>>>(a);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
@@ -542,6 +544,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.status = status;
         a.spin_limit = ctx.spin_limit;
         const int blocks = (int)std::min<int64_t>(L.parts_scan, (int64_t)ctx.num_sms * 4);
+        count_launch();
         k_scan_tiles<<<blocks, kScanThreads, 0, s>>>(a);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
@@ -573,6 +576,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
             a.TX[v] = vb.v[v].TX;
         }
         const int blocks = ctx.num_sms * 4;
+        count_launch();
         k_duplicate<<<blocks, kDupThreads, 0, s>>>(a);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
@@ -595,6 +599,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.shift = 8 * p;
         a.spin_limit = ctx.spin_limit;
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(L.parts_t, resident));
+        count_launch();
         k_onesweep<<<blocks, kSortThreads, 0, s>>>(a);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         cur ^= 1;
@@ -602,6 +607,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     // 6. ranges
     {
         const int blocks = ctx.num_sms * 8;
+        count_launch();
         k_ranges<<<blocks, 256, 0, s>>>(bins.keys, bins.n_instances, bins.capacity, (uint2*)bins.ranges, status);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }

@@ -245,7 +245,10 @@ __device__ __forceinline__ float inv_norm4(const float q[4])
 }  // namespace splat
 
 // Host-side launch helpers shared by the .cu files (defined in api.cu).
+#include <atomic>
 namespace splat {
+extern std::atomic<int64_t> g_launches;  // kernels launched or captured (diagnostic)
+inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 struct LaunchCtx {
     cudaStream_t stream;
     int num_sms;

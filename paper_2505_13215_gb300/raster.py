@@ -173,31 +173,46 @@ class Rasterizer:
         self.ws = torch.empty((self.ws_bytes,), dtype=torch.uint8, device=self.device)
 
     # -- stages -------------------------------------------------------------
-    def forward(self, G: Gaussians, stream=None):
-        """Slice/project, bin/sort and composite all views (asynchronous)."""
+    def slice_project(self, G: Gaussians, stream=None):
         if G.n3 != self.n3 or G.n4 != self.n4:
             raise ValueError("Gaussian counts differ from the rasterizer's")
-        s = _stream(stream)
         g3, g4 = G.c_g3(), G.c_g4()
-        st = _ptr(self.status)
-        abi.check(abi.splat_slice_project(C.byref(g3), C.byref(g4), self.cviews, self.V, C.byref(self.cproj), st, s),
-                  "splat_slice_project")
-        abi.check(abi.splat_bin_sort(C.byref(self.cproj), self.cviews, self.V, C.byref(self.cbins), st,
-                                     _ptr(self.ws), self.ws_bytes, s), "splat_bin_sort")
+        abi.check(abi.splat_slice_project(C.byref(g3), C.byref(g4), self.cviews, self.V, C.byref(self.cproj),
+                                          _ptr(self.status), _stream(stream)), "splat_slice_project")
+
+    def bin_sort(self, stream=None):
+        abi.check(abi.splat_bin_sort(C.byref(self.cproj), self.cviews, self.V, C.byref(self.cbins), _ptr(self.status),
+                                     _ptr(self.ws), self.ws_bytes, _stream(stream)), "splat_bin_sort")
+
+    def composite(self, stream=None):
         abi.check(abi.splat_composite_fwd(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
-                                          C.byref(self.cimg), st, s), "splat_composite_fwd")
+                                          C.byref(self.cimg), _ptr(self.status), _stream(stream)),
+                  "splat_composite_fwd")
+
+    def forward(self, G: Gaussians, stream=None):
+        """Slice/project, bin/sort and composite all views (asynchronous)."""
+        self.slice_project(G, stream)
+        self.bin_sort(stream)
+        self.composite(stream)
         return self.rgb
+
+    def _bwd(self, G: Gaussians, dL_drgb: Optional[torch.Tensor], flags: int, stream=None):
+        g3, g4 = G.c_g3(), G.c_g4()
+        abi.check(abi.splat_composite_bwd(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
+                                          C.byref(self.cimg), _ptr(dL_drgb), C.byref(g3), C.byref(g4),
+                                          C.byref(self.cg3), C.byref(self.cg4), _ptr(self.dproj), flags,
+                                          _ptr(self.status), _ptr(self.ws), self.ws_bytes, _stream(stream)),
+                  "splat_composite_bwd")
 
     def backward(self, G: Gaussians, dL_drgb: torch.Tensor, stream=None, stop_2d: bool = False):
         """Gradients of all parameters for pixel gradient dL_drgb (asynchronous);
         results in self.grads (overwritten) and self.dproj."""
-        s = _stream(stream)
-        g3, g4 = G.c_g3(), G.c_g4()
-        flags = abi.SPLAT_BWD_STOP_2D if stop_2d else 0
-        abi.check(abi.splat_composite_bwd(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
-                                          C.byref(self.cimg), _ptr(dL_drgb), C.byref(g3), C.byref(g4),
-                                          C.byref(self.cg3), C.byref(self.cg4), _ptr(self.dproj), flags,
-                                          _ptr(self.status), _ptr(self.ws), self.ws_bytes, s), "splat_composite_bwd")
+        self._bwd(G, dL_drgb, abi.SPLAT_BWD_STOP_2D if stop_2d else 0, stream)
+        return self.grads
+
+    def adjoint(self, G: Gaussians, stream=None):
+        """Chain self.dproj through the projection into self.grads (asynchronous)."""
+        self._bwd(G, None, abi.SPLAT_BWD_ADJOINT_ONLY, stream)
         return self.grads
 
     def l1_loss(self, target: torch.Tensor, stream=None):
@@ -207,11 +222,31 @@ class Rasterizer:
                                     _ptr(self.loss), _stream(stream)), "splat_l1_loss")
         return self.loss
 
-    def step(self, G: Gaussians, target: torch.Tensor, stream=None):
-        """One training step of the rasterizer: forward, L1 loss, backward."""
-        self.forward(G, stream)
+    STAGES = ("slice_project", "bin_sort", "composite_fwd", "loss", "composite_bwd", "adjoint")
+
+    def step(self, G: Gaussians, target: torch.Tensor, stream=None, marks: Optional[dict] = None):
+        """One training step of the rasterizer over the whole view batch: forward,
+        L1 loss, backward.  `marks` (optional) maps "start" and each name of
+        STAGES to a CUDA event recorded after that stage."""
+        st = torch.cuda.current_stream() if stream is None else stream
+
+        def mark(name):
+            if marks is not None:
+                marks[name].record(st)
+
+        mark("start")
+        self.slice_project(G, stream)
+        mark("slice_project")
+        self.bin_sort(stream)
+        mark("bin_sort")
+        self.composite(stream)
+        mark("composite_fwd")
         self.l1_loss(target, stream)
-        self.backward(G, self.dL, stream)
+        mark("loss")
+        self._bwd(G, self.dL, abi.SPLAT_BWD_STOP_2D, stream)
+        mark("composite_bwd")
+        self._bwd(G, None, abi.SPLAT_BWD_ADJOINT_ONLY, stream)
+        mark("adjoint")
 
     # -- status / capacity -------------------------------------------------
     def read_status(self):
@@ -257,12 +292,22 @@ class Rasterizer:
         return buf[p0: p0 + self.pix[v]].view(self.H[v], self.W[v])
 
 
-class GraphedStep:
-    """A CUDA graph of one full rasterizer training step (forward, L1 loss,
-    backward) over the whole view batch: one replay launches every kernel of
-    the step with no host work in between."""
+def stage_events(external: bool = False) -> dict:
+    kw = {"enable_timing": True}
+    if external:
+        kw["external"] = True
+    return {k: torch.cuda.Event(**kw) for k in ("start",) + Rasterizer.STAGES}
 
-    def __init__(self, R: Rasterizer, G: Gaussians, target: torch.Tensor, warmup: int = 2):
+
+class GraphedStep:
+    """CUDA graphs of one full rasterizer training step (forward, L1 loss,
+    backward) over the whole view batch: one replay launches every kernel of
+    the step with no host work in between.  With copies > 1 several identical
+    graphs are captured, each recording its own per-stage events, so that a
+    run of consecutive replays can be broken down by stage afterwards."""
+
+    def __init__(self, R: Rasterizer, G: Gaussians, target: torch.Tensor, warmup: int = 2, copies: int = 1,
+                 with_marks: bool = False):
         self.R, self.G, self.target = R, G, target
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -272,12 +317,25 @@ class GraphedStep:
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
         R.check("GraphedStep warm-up")
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            R.step(G, target)
+        self.graphs, self.marks = [], []
+        n0 = abi.lib().splat_launch_count()
+        for _ in range(max(1, copies)):
+            g = torch.cuda.CUDAGraph()
+            marks = stage_events(external=True) if with_marks else None
+            with torch.cuda.graph(g):
+                R.step(G, target, marks=marks)
+            self.graphs.append(g)
+            self.marks.append(marks)
+        self.launches_per_step = (abi.lib().splat_launch_count() - n0) // max(1, copies)
+        self.graph = self.graphs[0]
 
-    def replay(self):
-        self.graph.replay()
+    def replay(self, i: int = 0):
+        self.graphs[i % len(self.graphs)].replay()
+
+    def stage_ms(self, i: int) -> dict:
+        m = self.marks[i]
+        names = ("start",) + Rasterizer.STAGES
+        return {b: m[a].elapsed_time(m[b]) for a, b in zip(names[:-1], names[1:])}
 
 
 class HybridRasterize(torch.autograd.Function):

@@ -14,12 +14,46 @@ import numpy as np
 
 import oracle as O
 
-# relative window of FP32 rounding on the decided quantities (conic, power and
-# alpha accumulate a few 1e-6 relative error through the projection chain)
-EPS_PIXEL = 1e-4
-EPS_GAUSS = 2e-5
+# a flipped decision counts only if it can move a pixel by half the tolerance
+O.set_margin_impact(1e-4)
+
+# Relative windows of FP32 rounding per decision type.  Each is a few times
+# the error an FP32 evaluation of that quantity carries:
+#  - rectangle edges (px +- r)/16: px carries ~1e-7 relative error
+#  - radius 3 sqrt(lambda): lambda carries a few 1e-7 relative error
+#  - cull: alpha_max = sigmoid(o) p(t), p(t) = exp(-dt^2/2S) carries ~5e-6
+#  - per pixel: power (conic ~1e-6 relative, |power| <= 5.5) -> alpha ~1e-5;
+#    transmittance accumulates ~1e-7 per blended Gaussian; depth ~2e-7
+EPS_RECT = 1e-6
+EPS_RADIUS = 1e-6
+EPS_CULL = 3e-5
+EPS_PIXEL = {"power": 1e-5, "alpha": 5e-5, "stop": 5e-5, "tie": 1e-6}
+EPS_CLAMP = 5e-5      # alpha clamp at 0.99: a kink of the gradient only
+EPS_GRAD_GAUSS = 3e-5  # Jacobian clamp, rgb clamp: kinks of one Gaussian's gradient
 RGB_TOL = 2e-4        # max-abs on colours in [0, 1]
 GRAD_RTOL = 1e-3      # relative L2 per gradient tensor
+
+
+def _int_margin(q):
+    q = np.asarray(q, np.float64)
+    return np.abs(q - np.rint(q)) / np.maximum(1.0, np.abs(q))
+
+
+def gaussian_flags(P):
+    """Per Gaussian: (any decision fragile, cull fragile, radius fragile)."""
+    finite = np.isfinite(P["r3"]) & (P["depth"] > 0)
+    cull = P["margin_cull"] < EPS_CULL
+    rad = finite & (_int_margin(np.where(finite, P["r3"], 0.5)) < EPS_RADIUS)
+    r = np.ceil(np.where(finite, P["r3"], 0.0))
+    edges = np.zeros(len(P), bool)
+    for q in ((P["px"] - r) / 16, (P["px"] + r) / 16, (P["py"] - r) / 16, (P["py"] + r) / 16):
+        edges |= finite & (_int_margin(np.where(finite, q, 0.5)) < EPS_RECT)
+    relevant = (P["visible"] == 1) | cull
+    return relevant & (cull | rad | edges), cull, rad
+
+
+def fragile_gaussians(P):
+    return gaussian_flags(P)[0]
 
 
 def _alt_floor(q, eps):
@@ -32,49 +66,92 @@ def _alt_ceil(q, eps):
     return {math.ceil(q - w), math.ceil(q + w)}
 
 
-def uncertain_tiles(P, view, eps=EPS_GAUSS):
+def _alternative_rects(p, cull, TX, TY):
+    """Union and intersection of the tile rectangles over the alternative
+    radius / edge decisions of one Gaussian."""
+    r3 = p["r3"]
+    radii = {math.ceil(r3 * (1 - EPS_RADIUS)), math.ceil(r3 * (1 + EPS_RADIUS))}
+    xs0, xs1, ys0, ys1 = set(), set(), set(), set()
+    for rr in radii:
+        xs0 |= _alt_floor((p["px"] - rr) / 16, EPS_RECT)
+        xs1 |= _alt_ceil((p["px"] + rr) / 16, EPS_RECT)
+        ys0 |= _alt_floor((p["py"] - rr) / 16, EPS_RECT)
+        ys1 |= _alt_ceil((p["py"] + rr) / 16, EPS_RECT)
+    cl = lambda v, hi: min(max(v, 0), hi)
+    union = (cl(min(xs0), TX), cl(min(ys0), TY), cl(max(xs1), TX), cl(max(ys1), TY))
+    inter = (cl(max(xs0), TX), cl(max(ys0), TY), cl(min(xs1), TX), cl(min(ys1), TY))
+    if cull or inter[2] <= inter[0] or inter[3] <= inter[1]:
+        inter = (0, 0, 0, 0)
+    return union, inter
+
+
+def uncertain_tiles(P, view):
     """Boolean [TY, TX]: tiles whose membership in some Gaussian's rectangle
-    could flip within eps (union minus intersection over the alternatives)."""
+    could flip (union minus intersection over the alternative decisions)."""
     TX, TY = (view.W + 15) // 16, (view.H + 15) // 16
     bad = np.zeros((TY, TX), bool)
-    idx = np.nonzero((P["margin_fwd"] < eps) & (P["depth"] > 0))[0]
-    for i in idx:
-        p = P[i]
-        r3 = p["r3"]
-        if not np.isfinite(r3) or r3 <= 0:
-            continue
-        radii = {math.ceil(r3 * (1 - eps)), math.ceil(r3 * (1 + eps))}
-        xs0, xs1, ys0, ys1 = set(), set(), set(), set()
-        for rr in radii:
-            xs0 |= _alt_floor((p["px"] - rr) / 16, eps)
-            xs1 |= _alt_ceil((p["px"] + rr) / 16, eps)
-            ys0 |= _alt_floor((p["py"] - rr) / 16, eps)
-            ys1 |= _alt_ceil((p["py"] + rr) / 16, eps)
-        cl = lambda v, hi: min(max(v, 0), hi)
-        ux0, ux1 = cl(min(xs0), TX), cl(max(xs1), TX)
-        uy0, uy1 = cl(min(ys0), TY), cl(max(ys1), TY)
-        ix0, ix1 = cl(max(xs0), TX), cl(min(xs1), TX)
-        iy0, iy1 = cl(max(ys0), TY), cl(min(ys1), TY)
+    frag, cull, rad = gaussian_flags(P)
+    for i in np.nonzero(frag)[0]:
+        (ux0, uy0, ux1, uy1), (ix0, iy0, ix1, iy1) = _alternative_rects(P[i], cull[i], TX, TY)
         union = np.zeros((TY, TX), bool)
         union[uy0:uy1, ux0:ux1] = True
-        inter = np.zeros((TY, TX), bool)
-        if p["margin_cull"] >= eps and ix1 > ix0 and iy1 > iy0:
-            inter[iy0:iy1, ix0:ix1] = True
-        bad |= union & ~inter
+        union[iy0:iy1, ix0:ix1] = False
+        bad |= union
     return bad
 
 
-def fragile_pixels(P, ref, view, eps_pixel=EPS_PIXEL, eps_gauss=EPS_GAUSS):
-    """[H*W] mask of pixels whose forward result is not unique at FP32."""
-    m = ref["margin_fwd"] < eps_pixel
-    tiles = uncertain_tiles(P, view, eps_gauss)
-    tile_of_pix = np.kron(tiles, np.ones((16, 16), bool))[: view.H, : view.W].reshape(-1)
-    return m | tile_of_pix
+def uncertain_pixels(P, view, pix):
+    """Of the flat pixel indices `pix`, those inside a tile whose membership in a
+    Gaussian's rectangle could flip AND where that Gaussian reaches alpha >= 1/255
+    (only there can the flip change the pixel)."""
+    TX, TY = (view.W + 15) // 16, (view.H + 15) // 16
+    pix = np.asarray(pix, np.int64)
+    u = (pix % view.W).astype(np.float64)
+    v = (pix // view.W).astype(np.float64)
+    tx, ty = (pix % view.W) // 16, (pix // view.W) // 16
+    out = np.zeros(len(pix), bool)
+    frag, cull, rad = gaussian_flags(P)
+    for i in np.nonzero(frag)[0]:
+        p = P[i]
+        (ux0, uy0, ux1, uy1), (ix0, iy0, ix1, iy1) = _alternative_rects(p, cull[i], TX, TY)
+        inside_u = (tx >= ux0) & (tx < ux1) & (ty >= uy0) & (ty < uy1)
+        inside_i = (tx >= ix0) & (tx < ix1) & (ty >= iy0) & (ty < iy1)
+        cand = inside_u & ~inside_i
+        if not cand.any():
+            continue
+        dx, dy = p["px"] - u[cand], p["py"] - v[cand]
+        a, b, c = p["conic"]
+        power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+        alpha = p["alpha"] * np.exp(np.minimum(power, 0.0))
+        hit = alpha >= (1.0 / 255.0) * (1 - 1e-3)
+        idx = np.nonzero(cand)[0]
+        out[idx[hit]] = True
+    return out
 
 
-def grad_fragile_gaussians(P, eps=EPS_GAUSS):
-    """Gaussians whose own gradient has a kink within eps (Jacobian clamp, rgb clamp)."""
-    return P["margin_grad"] < eps
+def pixel_fragile_from_margins(ref):
+    m = ref["margins"]
+    out = np.zeros_like(m["power"], dtype=bool)
+    for k, eps in EPS_PIXEL.items():
+        out |= m[k] < eps
+    return out
+
+
+def fragile_pixels(P, ref, view, pix=None):
+    """Mask of pixels whose forward result is not unique at FP32 (pix: the flat
+    pixel indices ref was rendered at; None = the whole image)."""
+    if pix is None:
+        pix = np.arange(view.W * view.H)
+    return pixel_fragile_from_margins(ref) | uncertain_pixels(P, view, pix)
+
+
+def grad_fragile_pixels(ref):
+    return ref["margins"]["clamp"] < EPS_CLAMP
+
+
+def grad_fragile_gaussians(P):
+    """Gaussians whose own gradient has a kink within its window (Jacobian clamp, rgb clamp)."""
+    return P["margin_grad"] < EPS_GRAD_GAUSS
 
 
 def rel_l2(a, b):

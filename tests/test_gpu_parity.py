@@ -13,7 +13,8 @@ import torch
 import oracle as O
 from paper_2505_13215_gb300 import abi, raster, scenes
 
-from parity_util import (EPS_GAUSS, EPS_PIXEL, GRAD_RTOL, RGB_TOL, fragile_pixels, grad_fragile_gaussians, rel_l2)
+from parity_util import (GRAD_RTOL, RGB_TOL, fragile_gaussians, fragile_pixels, grad_fragile_gaussians,
+                         grad_fragile_pixels, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +54,7 @@ def check_projection(R, P, v=0):
     xy = R.xy[sl].cpu().numpy().astype(np.float64)
     co = R.conic_opacity[sl].cpu().numpy().astype(np.float64)
     rd = R.rgb_depth[sl].cpu().numpy().astype(np.float64)
-    sure = P["margin_fwd"] >= EPS_GAUSS
+    sure = ~fragile_gaussians(P)
     vis_o = P["visible"] == 1
     vis_g = rad > 0
     np.testing.assert_array_equal(vis_g[sure], vis_o[sure])
@@ -164,7 +165,7 @@ def test_bin_sort_end_to_end_lists(small):
     gk = R.keys[:K].cpu().numpy()
     gv = R.vals[:K].cpu().numpy()
     ranges = R.ranges.cpu().numpy().reshape(-1, 2)
-    fragile = P["margin_fwd"] < EPS_GAUSS
+    fragile = fragile_gaussians(P)
     for t in range(R.total_tiles):
         s, e = ranges[t]
         assert np.all(gk[s:e] == t)
@@ -237,7 +238,7 @@ def loss_grad(R, refs, Ps, views, seed=0):
     for v, (ref, P, view) in enumerate(zip(refs, Ps, views)):
         target = rng.uniform(0, 1, ref["rgb"].shape)
         g = np.sign(ref["rgb"] - target) / ref["rgb"].size
-        frag = fragile_pixels(P, ref, view) | (ref["margin_grad"] < EPS_PIXEL)
+        frag = fragile_pixels(P, ref, view) | grad_fragile_pixels(ref)
         g[:, frag] = 0.0
         out.append(g.reshape(3, view.H, view.W))
     return out
@@ -335,17 +336,12 @@ def test_full_size_sampled_pixels_and_gradients(big):
     pix = rng.choice(view.W * view.H, size=600, replace=False)
     ref = O.render(scene, view, pixels=pix)
     img = R.image(0).cpu().numpy().reshape(3, -1)[:, pix]
-    # fragile: own decisions, or a tile whose membership could flip
-    from parity_util import uncertain_tiles
-    tiles = uncertain_tiles(P, view)
-    TX = (view.W + 15) // 16
-    tb = tiles.reshape(-1)[(pix // view.W) // 16 * TX + (pix % view.W) // 16]
-    frag = (ref["margin_fwd"] < EPS_PIXEL) | tb
+    frag = fragile_pixels(P, ref, view, pix)
     assert frag.mean() < 0.05
     err = np.abs(img - ref["rgb"])[:, ~frag]
     assert err.max() <= RGB_TOL, err.max()
     # gradient of a loss on the sampled, unique pixels only
-    sel = pix[~frag & (ref["margin_grad"] >= EPS_PIXEL)]
+    sel = pix[~frag & ~grad_fragile_pixels(ref)]
     g = np.zeros((3, view.W * view.H))
     g[:, sel] = rng.choice([-1.0, 1.0], size=(3, len(sel))) * 1e-2
     check_grads(R, G, scene, [P], views, [g.reshape(3, view.H, view.W)])
