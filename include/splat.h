@@ -227,6 +227,8 @@ splat_status splat_slice_project(const splat_g3 *g3, const splat_g4 *g4, const s
  * same.  Writes bins->keys/vals (first K entries), bins->ranges (every tile,
  * [0,0) when empty) and *bins->n_instances = K.  K > capacity sets
  * SPLAT_ERR_CAPACITY with the required K in status[2..3] and n_instances.
+ * bins->keys may be NULL when the binned partition is in use (see
+ * splat_set_tile_sort); the tile of entry s is then implied by ranges.
  */
 splat_status splat_bin_sort(const splat_proj *proj, const splat_view *views, int V, splat_bins *bins,
                             int32_t *status, void *workspace, size_t workspace_bytes, void *stream);
@@ -306,6 +308,15 @@ void splat_set_pixels_per_lane(int fwd, int bwd);
 /* Number of kernels this library has launched (or enqueued into a stream
  * capture) in this process; a diagnostic counter. */
 int64_t splat_launch_count(void);
+
+/*
+ * Selects how splat_bin_sort orders the instances by tile (the result is the
+ * same):  0 = automatic (default), 1 = tile-digit radix passes over the
+ * instance list, 2 = binned partition with per-tile shared-memory counters
+ * (used automatically when every view has at most 40960 tiles).  Host-side
+ * global; splat_workspace_size depends on it.
+ */
+void splat_set_tile_sort(int mode);
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int32_t splat_version(void);

@@ -78,6 +78,7 @@ EXPORTS = {
     "splat_launch_count": (C.c_int64, []),
     "splat_set_spin_limit": (None, [C.c_int64]),
     "splat_set_pixels_per_lane": (None, [C.c_int, C.c_int]),
+    "splat_set_tile_sort": (None, [C.c_int]),
     "splat_status_string": (C.c_char_p, [C.c_int32]),
     "splat_total_tiles": (C.c_int64, [C.c_int, _P(C.c_int32), _P(C.c_int32)]),
     "splat_workspace_size": (C.c_size_t, [C.c_int, C.c_int64, C.c_int64, C.c_int, _P(C.c_int32), _P(C.c_int32),
@@ -149,6 +150,10 @@ def splat_launch_count():
 
 def splat_set_spin_limit(n):
     lib().splat_set_spin_limit(int(n))
+
+
+def splat_set_tile_sort(mode):
+    lib().splat_set_tile_sort(int(mode))
 
 
 def splat_set_pixels_per_lane(fwd, bwd):

@@ -14,7 +14,8 @@ cudaError_t launch_slice_project(const splat_g3&, const splat_g4&, const ViewBat
 cudaError_t launch_adjoint(const splat_g3&, const splat_g4&, const ViewBatch&, const splat_proj&, const float*,
                            const splat_grads3&, const splat_grads4&, int32_t*, int, const LaunchCtx&);
 cudaError_t launch_bin_sort(const splat_proj&, const ViewBatch&, const splat_bins&, int32_t*, void*, const LaunchCtx&);
-size_t bin_sort_workspace(int64_t n_rows, int64_t capacity);
+size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY);
+void set_tile_sort_mode(int mode);
 cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&, int32_t*,
                                  int, const LaunchCtx&);
 cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
@@ -147,6 +148,8 @@ int64_t splat_launch_count(void) { return g_launches.load(); }
 
 void splat_set_spin_limit(int64_t iterations) { g_spin_limit.store(iterations < 0 ? 0 : iterations); }
 
+void splat_set_tile_sort(int mode) { set_tile_sort_mode(mode); }
+
 void splat_set_pixels_per_lane(int fwd, int bwd)
 {
     auto ok = [](int p) { return p == 1 || p == 2 || p == 4 || p == 8; };
@@ -187,7 +190,14 @@ size_t splat_workspace_size(int op, int64_t N3, int64_t N4, int V, const int32_t
     if (op == SPLAT_OP_BIN_SORT || op == SPLAT_OP_ALL || op == SPLAT_OP_COMPOSITE_BWD) {
         if (V < 1 || V > SPLAT_MAX_VIEWS || splat_total_tiles(V, W, H) < 0) return 0;
     }
-    if (op == SPLAT_OP_BIN_SORT || op == SPLAT_OP_ALL) sort_b = bin_sort_workspace(N * V, capacity);
+    if (op == SPLAT_OP_BIN_SORT || op == SPLAT_OP_ALL) {
+        int TX[SPLAT_MAX_VIEWS], TY[SPLAT_MAX_VIEWS];
+        for (int v = 0; v < V; ++v) {
+            TX[v] = (W[v] + kTile - 1) / kTile;
+            TY[v] = (H[v] + kTile - 1) / kTile;
+        }
+        sort_b = bin_sort_workspace(N * V, capacity, V, TX, TY);
+    }
     if (op == SPLAT_OP_COMPOSITE_BWD || op == SPLAT_OP_ALL) bwd_b = ((size_t)N * V * 48 + 255) & ~(size_t)255;
     if (op == SPLAT_OP_CONVERT || op == SPLAT_OP_ALL) conv_b = convert_workspace(N4, 4);
     if (op < SPLAT_OP_BIN_SORT || op > SPLAT_OP_ALL) return 0;
@@ -227,9 +237,14 @@ splat_status splat_bin_sort(const splat_proj* proj, const splat_view* views, int
     if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !status) return SPLAT_ERR_INVALID_ARG;
     if (bins->capacity < 0 || bins->capacity > SPLAT_MAX_INSTANCES || !bins->ranges || !bins->n_instances)
         return SPLAT_ERR_INVALID_ARG;
-    if (bins->capacity > 0 && (!bins->keys || !bins->vals)) return SPLAT_ERR_INVALID_ARG;
+    if (bins->capacity > 0 && !bins->vals) return SPLAT_ERR_INVALID_ARG;
     if (!aligned(bins->ranges, 8) || !aligned(bins->n_instances, 8)) return SPLAT_ERR_INVALID_ARG;
-    const size_t need = bin_sort_workspace(proj->n * V, bins->capacity);
+    int TX[SPLAT_MAX_VIEWS], TY[SPLAT_MAX_VIEWS];
+    for (int v = 0; v < V; ++v) {
+        TX[v] = (views[v].W + kTile - 1) / kTile;
+        TY[v] = (views[v].H + kTile - 1) / kTile;
+    }
+    const size_t need = bin_sort_workspace(proj->n * V, bins->capacity, V, TX, TY);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
     const LaunchCtx ctx = launch_ctx(stream);
     const ViewBatch vb = make_batch(views, V);

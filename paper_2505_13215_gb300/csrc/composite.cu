@@ -188,7 +188,11 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
     const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
     const float uf = (float)u;
     const int64_t HW = (int64_t)vp.W * vp.H;
-    float T[PPL], S[PPL][3], G[PPL][3];
+    // Per pixel: T (replayed transmittance), G = dL/dC, and GS = <G, S> where S is
+    // the colour accumulated behind the current Gaussian, S = sum_{i>j} c_i alpha_i T_i
+    // + T_final bg.  dL/dalpha_j = T_j <G, c_j> - GS / (1 - alpha_j), and GS grows by
+    // alpha_j T_j <G, c_j>, so S itself is never needed per channel.
+    float T[PPL], GS[PPL], G[PPL][3];
     int last[PPL];
     int maxlast = 0;
 #pragma unroll
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
         const int y = y0 + 2 * k;
         last[k] = 0;
         T[k] = 1.f;
-        S[k][0] = S[k][1] = S[k][2] = 0.f;
+        GS[k] = 0.f;
         G[k][0] = G[k][1] = G[k][2] = 0.f;
         if (u < vp.W && y < vp.H) {
             const int64_t p = (int64_t)y * vp.W + u;
@@ -206,10 +210,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
             G[k][2] = g[2 * HW + p];
             T[k] = img.final_T[vp.pix_base + p];
             last[k] = img.last[vp.pix_base + p];
-            // colour behind the last contributor: T_final * bg
-            S[k][0] = T[k] * vp.bg[0];
-            S[k][1] = T[k] * vp.bg[1];
-            S[k][2] = T[k] * vp.bg[2];
+            GS[k] = T[k] * (G[k][0] * vp.bg[0] + G[k][1] * vp.bg[1] + G[k][2] * vp.bg[2]);
             maxlast = max(maxlast, last[k]);
         }
     }
@@ -251,17 +252,15 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
                 const float alpha = fminf(kAlphaClamp, raw);
                 if (alpha < kAlphaMin) continue;
                 any = true;
-                const float om = 1.f - alpha;
-                const float Tj = T[k] / om;
+                const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
+                const float Tj = T[k] * iom;
                 const float w = alpha * Tj;
                 acc[6] += w * G[k][0];
                 acc[7] += w * G[k][1];
                 acc[8] += w * G[k][2];
-                const float dLda = G[k][0] * (f.r * Tj - S[k][0] / om) + G[k][1] * (f.g * Tj - S[k][1] / om) +
-                                   G[k][2] * (f.bl * Tj - S[k][2] / om);
-                S[k][0] += f.r * w;
-                S[k][1] += f.g * w;
-                S[k][2] += f.bl * w;
+                const float gc = G[k][0] * f.r + G[k][1] * f.g + G[k][2] * f.bl;
+                const float dLda = Tj * gc - GS[k] * iom;
+                GS[k] += w * gc;
                 T[k] = Tj;
                 if (raw < kAlphaClamp) {
                     const float dpow = dLda * alpha;

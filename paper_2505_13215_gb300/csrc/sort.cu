@@ -63,11 +63,13 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_t
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int64_t n_rows, uint32_t* keys, uint32_t* vals,
-                                                    uint32_t* hist /*[4][256]*/, uint32_t* zero_a, int64_t n_zero_a,
+                                                    uint32_t* hist /*[9][256]*/, uint32_t* zero_a, int64_t n_zero_a,
                                                     unsigned long long* zero_b, int64_t n_zero_b)
 {
     __shared__ uint32_t s_hist[4][kRadix];
+    __shared__ uint32_t s_view[SPLAT_MAX_VIEWS];
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+    if (threadIdx.x < SPLAT_MAX_VIEWS) s_view[threadIdx.x] = 0;
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows; r += stride) {
@@ -78,6 +80,7 @@ __global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int64_t n_r
         vals[r] = (uint32_t)r;
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xff], 1u);
+        atomicAdd(&s_view[r / proj.n], 1u);
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_a; i += stride) zero_a[i] = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_b; i += stride) zero_b[i] = 0;
@@ -86,6 +89,7 @@ __global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int64_t n_r
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&hist[i], c);
     }
+    if (threadIdx.x < SPLAT_MAX_VIEWS && s_view[threadIdx.x]) atomicAdd(&hist[8 * kRadix + threadIdx.x], s_view[threadIdx.x]);
 }
 
 // ---------------------------------------------------------------------------
@@ -108,6 +112,7 @@ struct PassArgs {
     int stage;
     int shift;
     int64_t spin_limit;
+    int64_t view_div;      // > 0: write keys_out = value / view_div (the row's view) instead of the key
 };
 
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
@@ -223,8 +228,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
             const uint32_t key = s_keys[i];
             const uint32_t out = s_base[(key >> a.shift) & 0xff] + i;
             if (out >= (uint64_t)n) continue;  // only after a timed-out look-back
-            if (a.keys_out) a.keys_out[out] = key;
-            a.vals_out[out] = s_vals[i];
+            const uint32_t val = s_vals[i];
+            if (a.keys_out) a.keys_out[out] = a.view_div ? (uint32_t)(val / a.view_div) : key;
+            a.vals_out[out] = val;
         }
         __syncthreads();
     }
@@ -238,6 +244,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
 struct ScanArgs {
     const uint32_t* rows;      // [n_rows] depth-sorted rows
     const uint32_t* n_tiles;   // [n_rows] per row
+    const int4* rect;          // [n_rows] tile rectangles (used when shift > 0)
+    int shift;                 // > 0: count the rectangle's (2^shift)^2 super-tiles instead
     int64_t n_rows;
     uint32_t* offsets;         // [n_rows] exclusive prefix (saturated at 2^32-1)
     uint32_t* chunk_row;       // [n_chunks_max] first sorted position of each duplicate chunk
@@ -249,6 +257,21 @@ struct ScanArgs {
     int32_t* status;
     int64_t spin_limit;
 };
+
+__device__ __forceinline__ int4 shifted_rect(int4 rc, int shift)
+{
+    if (shift == 0) return rc;
+    const int m = (1 << shift) - 1;
+    return make_int4(rc.x >> shift, rc.y >> shift, (rc.z + m) >> shift, (rc.w + m) >> shift);
+}
+
+__device__ __forceinline__ uint32_t row_count(const ScanArgs& a, uint32_t row)
+{
+    const uint32_t n = a.n_tiles[row];
+    if (a.shift == 0 || n == 0) return n;
+    const int4 rc = shifted_rect(a.rect[row], a.shift);
+    return (uint32_t)((rc.z - rc.x) * (rc.w - rc.y));
+}
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
 {
@@ -270,7 +293,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
 #pragma unroll
         for (int j = 0; j < kScanItems; ++j) {
             const int64_t idx = base + (int64_t)j * kScanThreads + tid;
-            const uint32_t c = idx < a.n_rows ? a.n_tiles[a.rows[idx]] : 0u;
+            const uint32_t c = idx < a.n_rows ? row_count(a, a.rows[idx]) : 0u;
             uint32_t tot;
             const uint32_t ex = block_excl_scan256(c, s_tmp, &tot);
             local[j] = running + ex;
@@ -314,7 +337,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
             if (idx >= a.n_rows) continue;
             const unsigned long long off = excl + local[j];
             a.offsets[idx] = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
-            const uint32_t c = a.n_tiles[a.rows[idx]];
+            const uint32_t c = row_count(a, a.rows[idx]);
             if (c == 0) continue;
             // chunks whose first slot falls inside [off, off + c)
             const unsigned long long lo = (off + kDupChunk - 1) / kDupChunk;
@@ -426,30 +449,574 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* keys, const int6
 }
 
 // ---------------------------------------------------------------------------
+// Binned tile partition (replaces the tile-digit radix passes when one view's
+// tile counters fit in shared memory).  Rows are sorted by (view, depth); the
+// instance stream of each view is cut into chunks of consecutive slots.
+//   count:   per chunk, instances per tile (shared-memory counters)
+//   prefix:  per tile, exclusive sum over the view's chunks + tile total
+//   ranges:  exclusive sum of the tile totals -> [start, end) of every tile
+//   scatter: per chunk, rows in order, each tile's slot = its cursor++ ; the
+//            result is the stable sort of the instances by tile.
+// ---------------------------------------------------------------------------
+
+constexpr int kBinThreads = 256;
+constexpr int64_t kBinMaxTiles = 40960;  // per view, shared-memory counters
+
+struct BinPlan {
+    uint32_t S[SPLAT_MAX_VIEWS + 1];      // first slot of each view
+    uint32_t R[SPLAT_MAX_VIEWS + 1];      // first (view, depth)-sorted row of each view
+    uint32_t cbase[SPLAT_MAX_VIEWS + 1];  // first chunk of each view; cbase[V] = chunk count
+};
+
+struct BinArgs {
+    splat_proj proj;
+    int shift;                  // level: 0 tiles, 3 super-tiles of 8x8 tiles
+    const uint32_t* rows;
+    const uint32_t* offsets;
+    const uint32_t* view_hist;  // [V] rows per view
+    BinPlan* plan;
+    int V;
+    int64_t n_rows;
+    uint32_t chunk;
+    int tmax;                   // row stride of counts
+    int total_tiles;
+    int tile_base[SPLAT_MAX_VIEWS + 1];
+    int TX[SPLAT_MAX_VIEWS];
+    uint32_t* counts;           // [chunks][tmax]
+    uint32_t* first_row;        // [chunks]
+    uint32_t* tile_total;       // [total_tiles]
+    uint2* ranges;
+    uint32_t* vals_out;
+    uint32_t* keys_out;         // may be null
+    const int64_t* n_instances;
+    int64_t capacity;
+    int32_t* status;
+};
+
+// the row's rectangle at this level and its cell count
+__device__ __forceinline__ int4 level_rect(const BinArgs& a, uint32_t row, uint32_t& n)
+{
+    const int4 rc = shifted_rect(((const int4*)a.proj.rect)[row], a.shift);
+    n = a.proj.n_tiles[row] ? (uint32_t)((rc.z - rc.x) * (rc.w - rc.y)) : 0u;
+    return rc;
+}
+
+__global__ void k_bin_plan(BinArgs a)
+{
+    if (threadIdx.x != 0 || status_failed(a.status)) return;
+    const int64_t K = min(*a.n_instances, a.capacity);
+    BinPlan P;
+    P.R[0] = 0;
+    for (int v = 0; v < a.V; ++v) P.R[v + 1] = P.R[v] + (a.V > 1 ? a.view_hist[v] : (uint32_t)a.n_rows);
+    for (int v = 0; v < a.V; ++v) P.S[v] = P.R[v] < (uint32_t)a.n_rows ? a.offsets[P.R[v]] : (uint32_t)K;
+    P.S[a.V] = (uint32_t)K;
+    P.cbase[0] = 0;
+    for (int v = 0; v < a.V; ++v) P.cbase[v + 1] = P.cbase[v] + (P.S[v + 1] - P.S[v] + a.chunk - 1) / a.chunk;
+    *a.plan = P;
+}
+
+struct ChunkGeo {
+    int v;
+    uint32_t cs, ce;   // slot range
+};
+
+__device__ __forceinline__ ChunkGeo chunk_geo(const BinPlan& P, int V, uint32_t chunk, uint32_t g)
+{
+    ChunkGeo c;
+    c.v = 0;
+    for (int w = 1; w < V; ++w)
+        if (g >= P.cbase[w]) c.v = w;
+    c.cs = P.S[c.v] + (g - P.cbase[c.v]) * chunk;
+    c.ce = min(c.cs + chunk, P.S[c.v + 1]);
+    return c;
+}
+
+// Last row r in [lo, hi) with offsets[r] <= s (offsets[lo] <= s), by one warp.
+__device__ __forceinline__ uint32_t warp_search(const uint32_t* offsets, uint32_t lo, uint32_t hi, uint32_t s)
+{
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t p = lo + lane * step;
+        const bool ok = p < hi && offsets[p] <= s;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        const int L = 31 - __clz(m);
+        const uint32_t nlo = lo + L * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
+    }
+    return lo;
+}
+
+// Adds +1 on the tiles of the rectangle [x0,x1) x [y0,y1) to a 2D difference
+// array of (TX+1) x (TY+1) entries.
+__device__ __forceinline__ void diff_rect(int* d, int TXp, int x0, int y0, int x1, int y1)
+{
+    if (x1 <= x0 || y1 <= y0) return;
+    atomicAdd(&d[y0 * TXp + x0], 1);
+    atomicAdd(&d[y0 * TXp + x1], -1);
+    atomicAdd(&d[y1 * TXp + x0], -1);
+    atomicAdd(&d[y1 * TXp + x1], 1);
+}
+
+// Per chunk: instances per tile.  Each row's slots inside the chunk are a run of
+// its row-major tile sequence, i.e. at most three rectangles, recorded in a 2D
+// difference array whose 2D prefix sum gives the per-tile counts.
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(BinArgs a)
+{
+    extern __shared__ int dsm[];  // [(TY+1) * (TX+1)] of the largest view
+    __shared__ uint32_t s_first;
+    __shared__ BinPlan P;
+    if (status_failed(a.status)) return;
+    if (threadIdx.x == 0) P = *a.plan;
+    __syncthreads();
+    const uint32_t nchunks = P.cbase[a.V];
+    for (uint32_t g = blockIdx.x; g < nchunks; g += gridDim.x) {
+        const ChunkGeo c = chunk_geo(P, a.V, a.chunk, g);
+        const int TX = a.TX[c.v];
+        const int T = a.tile_base[c.v + 1] - a.tile_base[c.v];
+        const int TY = T / TX;
+        const int TXp = TX + 1;
+        const int nd = TXp * (TY + 1);
+        for (int i = threadIdx.x; i < nd; i += kBinThreads) dsm[i] = 0;
+        if (threadIdx.x < 32) {
+            const uint32_t r0 = warp_search(a.offsets, P.R[c.v], P.R[c.v + 1], c.cs);
+            if (threadIdx.x == 0) {
+                s_first = r0;
+                a.first_row[g] = r0;
+            }
+        }
+        __syncthreads();
+        const uint32_t r0 = s_first, rend = P.R[c.v + 1];
+        // rows r0 .. while offsets < ce, row-parallel
+        for (uint32_t j = r0 + threadIdx.x;; j += kBinThreads) {
+            const bool in = j < rend && a.offsets[j] < c.ce;
+            if (__syncthreads_or(in) == 0) break;
+            if (!in) continue;
+            const uint32_t off = a.offsets[j];
+            const uint32_t row = a.rows[j];
+            uint32_t n;
+            const int4 rc = level_rect(a, row, n);
+            const int w = rc.z - rc.x;
+            const uint32_t lo = max(off, c.cs) - off, hi = min(off + n, c.ce) - off;  // [lo, hi) of the row's tiles
+            const int ylo = (int)(lo / w), xlo = (int)(lo - ylo * w);
+            const int yhi = (int)((hi - 1) / w), xhi = (int)(hi - 1 - yhi * w);       // last tile, inclusive
+            if (ylo == yhi) {
+                diff_rect(dsm, TXp, rc.x + xlo, rc.y + ylo, rc.x + xhi + 1, rc.y + ylo + 1);
+            } else {
+                diff_rect(dsm, TXp, rc.x + xlo, rc.y + ylo, rc.z, rc.y + ylo + 1);
+                diff_rect(dsm, TXp, rc.x, rc.y + ylo + 1, rc.z, rc.y + yhi);
+                diff_rect(dsm, TXp, rc.x, rc.y + yhi, rc.x + xhi + 1, rc.y + yhi + 1);
+            }
+        }
+        __syncthreads();
+        // 2D inclusive prefix sum: along x per row, then along y per column
+        for (int y = threadIdx.x; y < TY; y += kBinThreads) {
+            int run = 0;
+            for (int x = 0; x < TX; ++x) {
+                run += dsm[y * TXp + x];
+                dsm[y * TXp + x] = run;
+            }
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < TX; x += kBinThreads) {
+            int run = 0;
+            for (int y = 0; y < TY; ++y) {
+                run += dsm[y * TXp + x];
+                dsm[y * TXp + x] = run;
+            }
+        }
+        __syncthreads();
+        uint32_t* dst = a.counts + (size_t)g * a.tmax;
+        for (int t = threadIdx.x; t < T; t += kBinThreads) {
+            const int y = t / TX, x = t - y * TX;
+            dst[t] = (uint32_t)dsm[y * TXp + x];
+        }
+        __syncthreads();
+    }
+}
+
+// Per-tile sums over the view's chunks.  A block covers 32 tiles (lanes,
+// coalesced) x 8 segments of chunks (warps).  Pass 0 writes the tile totals;
+// pass 1 (after k_bin_ranges turned the totals into tile starts) rewrites every
+// count as the absolute first slot of that (chunk, tile).
+template <int PASS>
+__global__ void __launch_bounds__(256) k_bin_prefix(BinArgs a)
+{
+    __shared__ uint32_t s_seg[8][33];
+    if (status_failed(a.status)) return;
+    const BinPlan& P = *a.plan;
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int gt = blockIdx.x * 32 + lane;
+    const bool ok = gt < a.total_tiles;
+    int v = 0;
+    for (int w = 1; w < a.V; ++w)
+        if (gt >= a.tile_base[w]) v = w;
+    const int tl = gt - a.tile_base[v];
+    const uint32_t cb = P.cbase[v], ce = P.cbase[v + 1];
+    const uint32_t per = (ce - cb + 7) / 8;
+    const uint32_t g0 = min(cb + seg * per, ce), g1 = min(g0 + per, ce);
+    uint32_t sum = 0;
+    if (ok) {
+        uint32_t g = g0;
+        for (; g + 4 <= g1; g += 4) {
+            const uint32_t c0 = a.counts[(size_t)g * a.tmax + tl], c1 = a.counts[(size_t)(g + 1) * a.tmax + tl];
+            const uint32_t c2 = a.counts[(size_t)(g + 2) * a.tmax + tl], c3 = a.counts[(size_t)(g + 3) * a.tmax + tl];
+            sum += c0 + c1 + c2 + c3;
+        }
+        for (; g < g1; ++g) sum += a.counts[(size_t)g * a.tmax + tl];
+    }
+    s_seg[seg][lane] = sum;
+    __syncthreads();
+    uint32_t base = 0, tot = 0;
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t x = s_seg[k][lane];
+        if (k < seg) base += x;
+        tot += x;
+    }
+    if (!ok) return;
+    if (PASS == 0) {
+        if (seg == 0) a.tile_total[gt] = tot;
+        return;
+    }
+    uint32_t run = a.tile_total[gt] + base;  // tile start (after k_bin_ranges) + earlier segments
+    for (uint32_t g = g0; g < g1; ++g) {
+        uint32_t* p = a.counts + (size_t)g * a.tmax + tl;
+        const uint32_t c = *p;
+        *p = run;
+        run += c;
+    }
+}
+
+// one block: ranges[t] = [start, start + total); tile_total becomes the start.
+// With K_out, also the instance count K and the capacity check.
+__global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, int64_t capacity)
+{
+    __shared__ uint32_t s_tmp[8];
+    if (status_failed(a.status)) return;
+    unsigned long long carry = 0;
+    for (int base = 0; base < a.total_tiles; base += 256) {
+        const int t = base + threadIdx.x;
+        const uint32_t c = t < a.total_tiles ? a.tile_total[t] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan256(c, s_tmp, &tot);
+        const uint32_t st = (uint32_t)(carry + ex);
+        if (t < a.total_tiles) {
+            a.ranges[t] = c ? make_uint2(st, st + c) : make_uint2(0u, 0u);
+            a.tile_total[t] = st;
+        }
+        carry += tot;
+    }
+    if (K_out && threadIdx.x == 0) {
+        *K_out = (int64_t)carry;
+        if ((int64_t)carry > capacity) set_status(a.status, SPLAT_ERR_CAPACITY, SPLAT_STAGE_DUPLICATE, (int64_t)carry);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile level.  Tile totals: every visible row adds its tile rectangle to its
+// view's 2D difference array; the 2D prefix sum of the array is the number of
+// instances of every tile.
+// ---------------------------------------------------------------------------
+
+struct TileArgs {
+    splat_proj proj;
+    int V;
+    int64_t n_rows;
+    int total_tiles;
+    int tile_base[SPLAT_MAX_VIEWS + 1];
+    int TX[SPLAT_MAX_VIEWS], TY[SPLAT_MAX_VIEWS];
+    int diff_base[SPLAT_MAX_VIEWS];   // offset of view v's (TY+1) x (TX+1) difference array
+    int* diff;
+    uint32_t* tile_total;
+    // per-super-tile filter
+    const uint32_t* list;             // rows grouped by super-tile, depth order inside
+    const uint2* sranges;             // [total_super]
+    int total_super;
+    int super_base[SPLAT_MAX_VIEWS + 1];
+    int STX[SPLAT_MAX_VIEWS];
+    const uint2* ranges;              // tile ranges (cursor starts)
+    uint32_t* vals_out;
+    uint32_t* keys_out;               // may be null
+    int32_t* status;
+};
+
+__global__ void __launch_bounds__(256) k_tile_diff(TileArgs a)
+{
+    if (status_failed(a.status)) return;
+    const int64_t N = a.proj.n;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n_rows; r += (int64_t)gridDim.x * blockDim.x) {
+        if (a.proj.n_tiles[r] == 0) continue;
+        const int v = (int)(r / N);
+        const int4 rc = ((const int4*)a.proj.rect)[r];
+        int* d = a.diff + a.diff_base[v];
+        const int TXp = a.TX[v] + 1;
+        atomicAdd(&d[rc.y * TXp + rc.x], 1);
+        atomicAdd(&d[rc.y * TXp + rc.z], -1);
+        atomicAdd(&d[rc.w * TXp + rc.x], -1);
+        atomicAdd(&d[rc.w * TXp + rc.z], 1);
+    }
+}
+
+// one block per view: 2D inclusive prefix of the difference array -> tile totals
+__global__ void __launch_bounds__(1024) k_tile_totals(TileArgs a)
+{
+    if (status_failed(a.status)) return;
+    const int v = blockIdx.x;
+    const int TX = a.TX[v], TY = a.TY[v], TXp = TX + 1;
+    int* d = a.diff + a.diff_base[v];
+    for (int y = threadIdx.x; y < TY; y += blockDim.x) {
+        int run = 0;
+        for (int x = 0; x < TX; ++x) {
+            run += d[y * TXp + x];
+            d[y * TXp + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < TX; x += blockDim.x) {
+        int run = 0;
+        for (int y = 0; y < TY; ++y) {
+            run += d[y * TXp + x];
+            a.tile_total[a.tile_base[v] + y * TX + x] = (uint32_t)run;
+        }
+    }
+}
+
+// One CTA per super-tile (8x8 tiles).  It streams the super-tile's rows in depth
+// order through shared memory; warp w keeps the cursors of tile row w (8 tiles)
+// and appends every row covering one of its tiles, in order: each tile's list is
+// written contiguously.
+__global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
+{
+    __shared__ int4 s_rect[256];
+    __shared__ uint32_t s_row[256];
+    if (status_failed(a.status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    for (int gs = blockIdx.x; gs < a.total_super; gs += gridDim.x) {
+        int v = 0;
+        for (int w = 1; w < a.V; ++w)
+            if (gs >= a.super_base[w]) v = w;
+        const int ls = gs - a.super_base[v];
+        const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
+        const int TX = a.TX[v], TY = a.TY[v];
+        const int ty = sy * 8 + warp;
+        const int tx0 = sx * 8;
+        uint32_t cur[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool ok = ty < TY && tx0 + k < TX;
+            cur[k] = ok ? a.ranges[a.tile_base[v] + ty * TX + tx0 + k].x : 0u;
+        }
+        const uint2 rg = a.sranges[gs];
+        for (uint32_t b = rg.x; b < rg.y; b += 256) {
+            __syncthreads();
+            const uint32_t j = b + threadIdx.x;
+            if (j < rg.y) {
+                const uint32_t row = a.list[j];
+                s_row[threadIdx.x] = row;
+                s_rect[threadIdx.x] = ((const int4*)a.proj.rect)[row];
+            }
+            __syncthreads();
+            if (ty >= TY) continue;
+            const int n = (int)min(256u, rg.y - b);
+            for (int sb = 0; sb < n; sb += 32) {
+                const int e = sb + lane;
+                bool cy = false;
+                int4 rc = make_int4(0, 0, 0, 0);
+                uint32_t row = 0;
+                if (e < n) {
+                    rc = s_rect[e];
+                    row = s_row[e];
+                    cy = rc.y <= ty && ty < rc.w;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int tx = tx0 + k;
+                    const bool cov = cy && rc.x <= tx && tx < rc.z;
+                    const unsigned m = __ballot_sync(0xffffffffu, cov);
+                    if (cov) {
+                        const uint32_t pos = cur[k] + __popc(m & lt);
+                        a.vals_out[pos] = row;
+                        if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx);
+                    }
+                    cur[k] += __popc(m);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int kScatterStage = 512;  // rows staged by the scatter warp
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// One warp per chunk.  Slots are taken 32 at a time in order, across row
+// boundaries; lanes holding the same tile are ordered by lane (= slot order) with
+// match_any, and the group's lowest lane advances the tile's cursor.
+__global__ void __launch_bounds__(32) k_bin_scatter(BinArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ BinPlan P;
+    __shared__ uint32_t s_off[kScatterStage + 1], s_base[kScatterStage], s_w[kScatterStage], s_row[kScatterStage];
+    if (status_failed(a.status)) return;
+    const int lane = threadIdx.x;
+    if (lane == 0) P = *a.plan;
+    __syncwarp();
+    uint32_t* s_cur = smem;
+    const unsigned lt = lanemask_lt();
+    const uint32_t nchunks = P.cbase[a.V];
+    for (uint32_t g = blockIdx.x; g < nchunks; g += gridDim.x) {
+        const ChunkGeo c = chunk_geo(P, a.V, a.chunk, g);
+        const int tb = a.tile_base[c.v];
+        const int T = a.tile_base[c.v + 1] - tb;
+        const int TX = a.TX[c.v];
+        // absolute cursors of this chunk: one burst of 16-byte async copies (tmax % 4 == 0)
+        const uint32_t* cnt = a.counts + (size_t)g * a.tmax;
+        for (int t = lane * 4; t < T; t += 128) cp_async16(s_cur + t, cnt + t);
+        cp_async_wait_all();
+        __syncwarp();
+        const uint32_t rend = P.R[c.v + 1];
+        uint32_t rbase = a.first_row[g];  // first staged row
+        int qcur = 0;                      // staged row holding slot s0 - 1 (s0 at the start)
+        int nst = 0;
+        bool more = true;                  // rows of the chunk beyond the staged ones may exist
+        for (uint32_t s0 = c.cs; s0 < c.ce; s0 += 32) {
+            if (more && qcur + 33 > nst) {  // (re)stage rows from the current one
+                rbase += qcur;
+                qcur = 0;
+                __syncwarp();
+                nst = 0;
+                constexpr int PER = kScatterStage / 32;
+                uint32_t offv[PER], rowv[PER];
+                bool inv[PER];
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const uint32_t j = rbase + lane + 32 * i;
+                    offv[i] = j < rend ? a.offsets[j] : c.ce;
+                }
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    inv[i] = offv[i] < c.ce;
+                    rowv[i] = inv[i] ? a.rows[rbase + lane + 32 * i] : 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const int q = lane + 32 * i;
+                    if (inv[i]) {
+                        uint32_t n_;
+                        const int4 rc = level_rect(a, rowv[i], n_);
+                        s_off[q] = offv[i];
+                        s_base[q] = (uint32_t)(rc.y * TX + rc.x);
+                        s_w[q] = (uint32_t)max(rc.z - rc.x, 1);
+                        s_row[q] = rowv[i];
+                    }
+                    nst += __popc(__ballot_sync(0xffffffffu, inv[i]));
+                }
+                more = nst == kScatterStage;
+                if (lane == 0) s_off[nst] = c.ce;  // sentinel, read only when every row is staged
+                __syncwarp();
+            }
+            // rows starting inside [s0, s0 + 31] (a row starting at s0 follows qcur)
+            const int k = qcur + 1 + lane;
+            const uint32_t ok_ = k <= nst ? s_off[k] : c.ce;
+            const uint32_t p = ok_ - s0;  // >= 0 for rows after qcur
+            const unsigned M = __reduce_or_sync(0xffffffffu, p < 32u ? (1u << p) : 0u);
+            const int q = qcur + __popc(M & ((2u << lane) - 1u));
+            const uint32_t s = s0 + lane;
+            const bool act = s < c.ce;
+            uint32_t tl = 0xffffffffu;
+            if (act) {
+                const uint32_t l = s - s_off[q], w = s_w[q];
+                const uint32_t ty = l / w;
+                tl = s_base[q] + ty * TX + (l - ty * w);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, tl);
+            const int leader = __ffs(peers) - 1;
+            uint32_t pos = 0;
+            if (lane == leader && act) {
+                pos = s_cur[tl];
+                s_cur[tl] = pos + __popc(peers);
+            }
+            pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lt);
+            if (act) {
+                a.vals_out[pos] = s_row[q];
+                if (a.keys_out) a.keys_out[pos] = (uint32_t)tb + tl;
+            }
+            qcur += __popc(M);
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
+static int g_tile_sort_mode = 0;  // 0 auto, 1 radix passes, 2 binned
+
 struct SortLayout {
     int64_t n_rows, capacity;
+    int V, tmax, smax;
+    bool binned;
+    uint32_t chunk;
+    int64_t max_chunks;
     int64_t parts_d, parts_t, parts_scan, n_chunks;
+    int64_t total_tiles, total_super, diff_len;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
-        off_tvals, off_hist, off_tickets;
+        off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
+    size_t off_diff, off_vals1, off_sranges, off_stotal, off_ninst1;
     size_t bytes;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-SortLayout sort_layout(int64_t n_rows, int64_t capacity)
+constexpr int kSuperShift = 3;  // super-tiles of 8 x 8 tiles
+
+// level-1 (row, super-tile) slots per chunk: about 64k chunks at full capacity
+static uint32_t bin_chunk(int64_t capacity)
+{
+    int64_t c = (capacity / 65536 + 255) / 256 * 256;
+    return (uint32_t)std::min<int64_t>(std::max<int64_t>(c, 1024), 1 << 20);
+}
+
+SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY)
 {
     SortLayout L{};
     L.n_rows = n_rows;
     L.capacity = capacity;
+    L.V = V;
+    int tmax = 1, smax = 1;
+    for (int v = 0; v < V; ++v) {
+        tmax = std::max(tmax, TX[v] * TY[v]);
+        const int sx = (TX[v] + 7) >> kSuperShift, sy = (TY[v] + 7) >> kSuperShift;
+        smax = std::max(smax, sx * sy);
+        L.total_tiles += (int64_t)TX[v] * TY[v];
+        L.total_super += (int64_t)sx * sy;
+        L.diff_len += (int64_t)(TX[v] + 1) * (TY[v] + 1);
+    }
+    L.tmax = (tmax + 3) & ~3;
+    L.smax = (smax + 3) & ~3;
+    L.binned = g_tile_sort_mode == 2 || (g_tile_sort_mode == 0 && tmax <= kBinMaxTiles);
+    L.chunk = bin_chunk(capacity);
+    L.max_chunks = (capacity + L.chunk - 1) / L.chunk + V;
     L.parts_d = (n_rows + kSortPart - 1) / kSortPart;
-    L.parts_t = (capacity + kSortPart - 1) / kSortPart;
+    L.parts_t = L.binned ? 0 : (capacity + kSortPart - 1) / kSortPart;
     L.parts_scan = (n_rows + kScanPart - 1) / kScanPart;
-    L.n_chunks = (capacity + kDupChunk - 1) / kDupChunk + 1;
+    L.n_chunks = L.binned ? 1 : (capacity + kDupChunk - 1) / kDupChunk + 1;
     size_t o = 0;
-    auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+    auto take = [&](size_t bytes) { size_t r = o; o = align256(o + std::max<size_t>(bytes, 4)); return r; };
     for (int b = 0; b < 2; ++b) L.off_dkeys[b] = take(4 * (size_t)n_rows);
     for (int b = 0; b < 2; ++b) L.off_dvals[b] = take(4 * (size_t)n_rows);
     L.off_offsets = take(4 * (size_t)n_rows);
@@ -457,10 +1024,19 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity)
     L.off_scan_lb = take(8 * (size_t)std::max<int64_t>(L.parts_scan, 1));
     for (int b = 0; b < 2; ++b) L.off_dlb[b] = take(4 * (size_t)kRadix * std::max<int64_t>(L.parts_d, 1));
     for (int b = 0; b < 2; ++b) L.off_tlb[b] = take(4 * (size_t)kRadix * std::max<int64_t>(L.parts_t, 1));
-    L.off_tkeys = take(4 * (size_t)capacity);
-    L.off_tvals = take(4 * (size_t)capacity);
-    L.off_hist = take(4 * (size_t)kRadix * 8);
+    L.off_tkeys = take(L.binned ? 4 : 4 * (size_t)capacity);
+    L.off_tvals = take(L.binned ? 4 : 4 * (size_t)capacity);
+    L.off_hist = take(4 * (size_t)kRadix * 9);
     L.off_tickets = take(4 * 16);
+    L.off_plan = take(sizeof(BinPlan));
+    L.off_counts = take(L.binned ? 4 * (size_t)L.max_chunks * L.smax : 4);
+    L.off_first = take(L.binned ? 4 * (size_t)L.max_chunks : 4);
+    L.off_total = take(L.binned ? 4 * (size_t)L.total_tiles : 4);
+    L.off_diff = take(L.binned ? 4 * (size_t)L.diff_len : 4);
+    L.off_vals1 = take(L.binned ? 4 * (size_t)capacity : 4);
+    L.off_sranges = take(L.binned ? 8 * (size_t)L.total_super : 4);
+    L.off_stotal = take(L.binned ? 4 * (size_t)L.total_super : 4);
+    L.off_ninst1 = take(8);
     L.bytes = o;
     return L;
 }
@@ -476,16 +1052,30 @@ static int sort_ctas_per_sm()
     return cached;
 }
 
+
+static cudaError_t run_pass(const PassArgs& a, int64_t parts, int resident, cudaStream_t s)
+{
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(parts, resident));
+    count_launch();
+    k_onesweep<<<blocks, kSortThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const splat_bins& bins, int32_t* status,
                             void* ws, const LaunchCtx& ctx)
 {
     const int64_t n_rows = proj.n * vb.V;
-    const SortLayout L = sort_layout(n_rows, bins.capacity);
+    int TXs[SPLAT_MAX_VIEWS], TYs[SPLAT_MAX_VIEWS];
+    for (int v = 0; v < vb.V; ++v) {
+        TXs[v] = vb.v[v].TX;
+        TYs[v] = vb.v[v].TY;
+    }
+    const SortLayout L = sort_layout(n_rows, bins.capacity, vb.V, TXs, TYs);
+    if (!L.binned && bins.capacity > 0 && !bins.keys) return cudaErrorInvalidValue;
     char* w = (char*)ws;
     auto U = [&](size_t off) { return (uint32_t*)(w + off); };
     cudaStream_t s = ctx.stream;
     cudaError_t err;
-    // tickets + histograms, then all tile ranges
     if ((err = cudaMemsetAsync(w + L.off_hist, 0, (L.off_tickets - L.off_hist) + 64, s)) != cudaSuccess) return err;
     if ((err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)vb.total_tiles, s)) != cudaSuccess)
         return err;
@@ -494,8 +1084,9 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     uint32_t* hist = U(L.off_hist);
     uint32_t* tickets = U(L.off_tickets);
     const int resident = ctx.num_sms * sort_ctas_per_sm();
+    const bool by_view = L.binned && vb.V > 1;
 
-    // 1. depth keys + digit histograms; zero the first depth look-back buffer and the scan look-back
+    // 1. depth keys + digit histograms (+ rows per view); zero the first depth look-back buffer and the scan's
     {
         const int blocks = (int)std::min<int64_t>((n_rows + 255) / 256, (int64_t)ctx.num_sms * 8);
         count_launch();
@@ -504,43 +1095,45 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
                                             (unsigned long long*)(w + L.off_scan_lb), L.parts_scan);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    // 2. four depth passes: buffers 0 -> 1 -> 0 -> 1 -> 0
-    for (int p = 0; p < 4; ++p) {
+    // 2. depth passes (buffers 0 -> 1 -> 0 -> 1 -> 0), then (binned, V > 1) a stable pass on the view
+    const int passes = by_view ? 5 : 4;
+    for (int p = 0; p < passes; ++p) {
         PassArgs a{};
         a.keys_in = U(L.off_dkeys[p & 1]);
         a.vals_in = U(L.off_dvals[p & 1]);
-        a.keys_out = p < 3 ? U(L.off_dkeys[(p + 1) & 1]) : nullptr;
+        a.keys_out = p + 1 < passes ? U(L.off_dkeys[(p + 1) & 1]) : nullptr;
         a.vals_out = U(L.off_dvals[(p + 1) & 1]);
         a.n_dev = nullptr;
         a.n_host = n_rows;
         a.cap = n_rows;
-        a.hist = hist + p * kRadix;
+        a.hist = hist + (p < 4 ? p : 8) * kRadix;
         a.lb = U(L.off_dlb[p & 1]);
-        a.lb_next = p < 3 ? U(L.off_dlb[(p + 1) & 1]) : nullptr;
-        a.ticket = tickets + p;
+        a.lb_next = p + 1 < passes ? U(L.off_dlb[(p + 1) & 1]) : nullptr;
+        a.ticket = tickets + (p < 4 ? p : 9);
         a.status = status;
         a.stage = SPLAT_STAGE_DEPTH_SORT;
-        a.shift = 8 * p;
+        a.shift = p < 4 ? 8 * p : 0;
         a.spin_limit = ctx.spin_limit;
-        const int blocks = (int)std::min<int64_t>(L.parts_d, resident);
-        count_launch();
-        k_onesweep<<<blocks, kSortThreads, 0, s>>>(a);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        a.view_div = (by_view && p == 3) ? proj.n : 0;
+        if ((err = run_pass(a, L.parts_d, resident, s)) != cudaSuccess) return err;
     }
-    const uint32_t* rows = U(L.off_dvals[0]);
-    // 3. scan of tile counts in depth order
+    const uint32_t* rows = U(L.off_dvals[passes & 1]);
+    // 3. scan of the per-row counts in that order: tiles (radix path) or super-tiles (binned path)
     {
         ScanArgs a{};
         a.rows = rows;
         a.n_tiles = proj.n_tiles;
+        a.rect = (const int4*)proj.rect;
+        a.shift = L.binned ? kSuperShift : 0;
         a.n_rows = n_rows;
         a.offsets = U(L.off_offsets);
         a.chunk_row = U(L.off_chunk);
-        a.n_chunks_max = L.n_chunks;
+        a.n_chunks_max = L.binned ? 0 : L.n_chunks;
         a.lb = (unsigned long long*)(w + L.off_scan_lb);
         a.ticket = tickets + 4;
-        a.n_instances = bins.n_instances;
-        a.capacity = bins.capacity;
+        a.n_instances = L.binned ? (int64_t*)(w + L.off_ninst1) : bins.n_instances;
+        // binned: the super-tile count K1 <= K; K itself is checked by the tile ranges
+        a.capacity = L.binned ? INT64_MAX : bins.capacity;
         a.status = status;
         a.spin_limit = ctx.spin_limit;
         const int blocks = (int)std::min<int64_t>(L.parts_scan, (int64_t)ctx.num_sms * 4);
@@ -548,7 +1141,107 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_scan_tiles<<<blocks, kScanThreads, 0, s>>>(a);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    // 4. duplicate
+    if (L.binned) {
+        // tile level: totals from difference arrays, ranges, K and the capacity check
+        TileArgs t{};
+        t.proj = proj;
+        t.V = vb.V;
+        t.n_rows = n_rows;
+        t.total_tiles = vb.total_tiles;
+        int db = 0, sb = 0;
+        for (int v = 0; v < vb.V; ++v) {
+            t.tile_base[v] = vb.v[v].tile_base;
+            t.TX[v] = vb.v[v].TX;
+            t.TY[v] = vb.v[v].TY;
+            t.diff_base[v] = db;
+            db += (vb.v[v].TX + 1) * (vb.v[v].TY + 1);
+            t.super_base[v] = sb;
+            t.STX[v] = (vb.v[v].TX + 7) >> kSuperShift;
+            sb += t.STX[v] * ((vb.v[v].TY + 7) >> kSuperShift);
+        }
+        t.tile_base[vb.V] = vb.total_tiles;
+        t.super_base[vb.V] = sb;
+        t.total_super = sb;
+        t.diff = (int*)(w + L.off_diff);
+        t.tile_total = U(L.off_total);
+        t.list = U(L.off_vals1);
+        t.sranges = (const uint2*)(w + L.off_sranges);
+        t.ranges = (const uint2*)bins.ranges;
+        t.vals_out = bins.vals;
+        t.keys_out = bins.keys;
+        t.status = status;
+        if ((err = cudaMemsetAsync(t.diff, 0, 4 * (size_t)L.diff_len, s)) != cudaSuccess) return err;
+        BinArgs tr{};
+        tr.total_tiles = vb.total_tiles;
+        tr.tile_total = U(L.off_total);
+        tr.ranges = (uint2*)bins.ranges;
+        tr.status = status;
+        count_launch(3);
+        k_tile_diff<<<(int)std::min<int64_t>((n_rows + 255) / 256, (int64_t)ctx.num_sms * 8), 256, 0, s>>>(t);
+        k_tile_totals<<<vb.V, 1024, 0, s>>>(t);
+        k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity);
+        // super-tile level: stable partition of the (view, depth)-ordered rows by super-tile
+        BinArgs a{};
+        a.proj = proj;
+        a.shift = kSuperShift;
+        a.rows = rows;
+        a.offsets = U(L.off_offsets);
+        a.view_hist = hist + 8 * kRadix;
+        a.plan = (BinPlan*)(w + L.off_plan);
+        a.V = vb.V;
+        a.n_rows = n_rows;
+        a.chunk = L.chunk;
+        a.tmax = L.smax;
+        a.total_tiles = sb;
+        for (int v = 0; v < vb.V; ++v) {
+            a.tile_base[v] = t.super_base[v];
+            a.TX[v] = t.STX[v];
+        }
+        a.tile_base[vb.V] = sb;
+        a.counts = U(L.off_counts);
+        a.first_row = U(L.off_first);
+        a.tile_total = U(L.off_stotal);
+        a.ranges = (uint2*)(w + L.off_sranges);
+        a.vals_out = U(L.off_vals1);
+        a.keys_out = nullptr;
+        a.n_instances = (const int64_t*)(w + L.off_ninst1);
+        a.capacity = bins.capacity;
+        a.status = status;
+        int dmax = 1;
+        for (int v = 0; v < vb.V; ++v)
+            dmax = std::max(dmax, (t.STX[v] + 1) * (((vb.v[v].TY + 7) >> kSuperShift) + 1));
+        const size_t smem_count = 4 * (size_t)dmax;
+        const size_t smem_scatter = 4 * (size_t)L.smax;
+        static size_t set_count = 0, set_scatter = 0;
+        if (smem_count > set_count) {
+            if ((err = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_count)) != cudaSuccess)
+                return err;
+            set_count = smem_count;
+        }
+        if (smem_scatter > set_scatter) {
+            if ((err = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_scatter)) != cudaSuccess)
+                return err;
+            set_scatter = smem_scatter;
+        }
+        int per_sm_c = 0, per_sm_s = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, k_bin_count, kBinThreads, smem_count);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_bin_scatter, 32, smem_scatter);
+        const int blocks_c = (int)std::min<int64_t>(L.max_chunks, (int64_t)ctx.num_sms * std::max(1, per_sm_c));
+        const int blocks_s = (int)std::min<int64_t>(L.max_chunks, (int64_t)ctx.num_sms * std::max(1, per_sm_s));
+        count_launch(7);
+        k_bin_plan<<<1, 32, 0, s>>>(a);
+        k_bin_count<<<blocks_c, kBinThreads, smem_count, s>>>(a);
+        k_bin_prefix<0><<<(sb + 31) / 32, 256, 0, s>>>(a);
+        k_bin_ranges<<<1, 256, 0, s>>>(a, nullptr, 0);
+        k_bin_prefix<1><<<(sb + 31) / 32, 256, 0, s>>>(a);
+        k_bin_scatter<<<blocks_s, 32, smem_scatter, s>>>(a);
+        // tile level: each super-tile's rows filtered into its tiles' lists
+        k_tile_filter<<<(int)std::min<int64_t>(sb, (int64_t)ctx.num_sms * 8), 256, 0, s>>>(t);
+        return cudaGetLastError();
+    }
+    // 4. radix path: duplicate, tile-digit passes, ranges
     int bits = 1;
     while ((1ll << bits) < (int64_t)vb.total_tiles) ++bits;
     const int tile_passes = (bits + 7) / 8;
@@ -580,7 +1273,6 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_duplicate<<<blocks, kDupThreads, 0, s>>>(a);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    // 5. tile passes
     for (int p = 0; p < tile_passes; ++p) {
         PassArgs a{};
         a.keys_in = tk[cur];
@@ -598,13 +1290,9 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.stage = SPLAT_STAGE_TILE_SORT;
         a.shift = 8 * p;
         a.spin_limit = ctx.spin_limit;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(L.parts_t, resident));
-        count_launch();
-        k_onesweep<<<blocks, kSortThreads, 0, s>>>(a);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        if ((err = run_pass(a, L.parts_t, resident, s)) != cudaSuccess) return err;
         cur ^= 1;
     }
-    // 6. ranges
     {
         const int blocks = ctx.num_sms * 8;
         count_launch();
@@ -614,6 +1302,11 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     return cudaSuccess;
 }
 
-size_t bin_sort_workspace(int64_t n_rows, int64_t capacity) { return sort_layout(n_rows, capacity).bytes; }
+size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY)
+{
+    return sort_layout(n_rows, capacity, V, TX, TY).bytes;
+}
+
+void set_tile_sort_mode(int mode) { g_tile_sort_mode = (mode >= 0 && mode <= 2) ? mode : 0; }
 
 }  // namespace splat

@@ -113,7 +113,8 @@ class Rasterizer:
     first render (see `autotune_capacity`)."""
 
     def __init__(self, n3: int, n4: int, views: Sequence, device="cuda", capacity: Optional[int] = None,
-                 headroom: float = 1.25):
+                 headroom: float = 1.25, keep_keys: bool = True):
+        self.keep_keys = keep_keys
         self.n3, self.n4 = int(n3), int(n4)
         self.N = self.n3 + self.n4
         self.views = list(views)
@@ -162,10 +163,10 @@ class Rasterizer:
     def set_capacity(self, capacity: int):
         capacity = int(min(max(1, capacity), abi.SPLAT_MAX_INSTANCES))
         self.capacity = capacity
-        self.keys = torch.empty((capacity,), dtype=torch.int32, device=self.device)
+        self.keys = torch.empty((capacity if self.keep_keys else 0,), dtype=torch.int32, device=self.device)
         self.vals = torch.empty((capacity,), dtype=torch.int32, device=self.device)
-        self.cbins = abi.splat_bins(capacity, self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
-                                    self.n_instances.data_ptr())
+        self.cbins = abi.splat_bins(capacity, self.keys.data_ptr() if self.keep_keys else None, self.vals.data_ptr(),
+                                    self.ranges.data_ptr(), self.n_instances.data_ptr())
         ws = abi.splat_workspace_size(abi.SPLAT_OP_ALL, self.n3, self.n4, self.W, self.H, capacity)
         if ws == 0:
             raise ValueError("invalid sizes for the workspace")

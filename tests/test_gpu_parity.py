@@ -135,7 +135,14 @@ def expected_ranges(sorted_tiles, total):
     return r
 
 
-def test_bin_sort_bitexact_given_keys(small):
+@pytest.fixture(params=[2, 1], ids=["binned", "radix"])
+def tile_sort_mode(request):
+    abi.splat_set_tile_sort(request.param)
+    yield request.param
+    abi.splat_set_tile_sort(0)
+
+
+def test_bin_sort_bitexact_given_keys(small, tile_sort_mode):
     scene, views, G, R, P, ref = small
     gk, gv, ok, ov, ranges, T = staged_sort(views, [P], R.N)
     np.testing.assert_array_equal(gk, ok)
@@ -143,7 +150,7 @@ def test_bin_sort_bitexact_given_keys(small):
     np.testing.assert_array_equal(ranges, expected_ranges(ok, T))
 
 
-def test_bin_sort_ties_and_multiview():
+def test_bin_sort_ties_and_multiview(tile_sort_mode):
     """Equal depths everywhere (ties broken by emission order) over three views of
     different sizes in one call."""
     scene, _ = scenes.small_scene(seed=2, n3=700, n4=300)
@@ -213,6 +220,27 @@ def test_composite_pixels_per_lane_variants(small, ppl):
         abi.splat_set_pixels_per_lane(8, 8)
         R.forward(G)
         torch.cuda.synchronize()
+
+
+def test_tile_sort_modes_render_identically(small):
+    scene, views, G, R0, P, ref = small
+    out = []
+    for mode in (1, 2):
+        abi.splat_set_tile_sort(mode)
+        try:
+            R = raster.Rasterizer(G.n3, G.n4, views, capacity=R0.capacity)
+            target = torch.rand(R.rgb.shape, generator=torch.Generator(device="cuda").manual_seed(5), device="cuda")
+            R.step(G, target)
+            torch.cuda.synchronize()
+            R.check()
+            K = R.instances()
+            out.append((R.rgb.clone(), R.vals[:K].clone(), R.ranges.clone(), R.grads["mean3"].clone()))
+        finally:
+            abi.splat_set_tile_sort(0)
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    assert torch.equal(out[0][2], out[1][2])
+    assert rel_l2(out[0][3].cpu().numpy(), out[1][3].cpu().numpy()) < 1e-5
 
 
 def test_forward_is_deterministic(small):
