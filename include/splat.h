@@ -287,6 +287,29 @@ splat_status splat_convert_4d_to_3d(splat_g4 *g4, splat_g3 *g3, float tau, int64
 splat_status splat_l1_loss(const float *img, const float *target, int64_t n, float scale, float *dL_dimg,
                            float *loss, void *stream);
 
+/*
+ * splat_bin_sort for callers that cannot allocate device memory when they
+ * sort -- e.g. a plugin whose host application has reserved the whole GPU
+ * memory budget, or a frame loop that must not reach cudaMalloc / cudaFree
+ * because those calls can synchronise the device.  The paper has no
+ * counterpart to this entry point.  Same arguments and results as
+ * splat_bin_sort minus the workspace: the scratch is a fixed array of
+ * SPLAT_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads this part of the library keeps until the process exits.
+ *  - Problems whose splat_bin_sort workspace would exceed that size are
+ *    rejected on the host with SPLAT_ERR_CAPACITY, before any device work.
+ *  - The first call on each device looks up the array's device address with
+ *    the device current (cudaGetSymbolAddress); make that first call before
+ *    any stream capture.
+ *  - All calls share the array and its contents persist between calls (the
+ *    sort clears what must start at zero); calls that overlap on the GPU --
+ *    other streams, or other host threads without ordering -- race on it.
+ * No allocation routine is called.
+ */
+#define SPLAT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+splat_status splat_bin_sort_noalloc(const splat_proj *proj, const splat_view *views, int V, splat_bins *bins,
+                                    int32_t *status, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *splat_status_string(int32_t code);
 

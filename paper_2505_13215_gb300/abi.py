@@ -24,6 +24,7 @@ SPLAT_BWD_STOP_2D = 1
 SPLAT_BWD_ADJOINT_ONLY = 2
 SPLAT_MAX_VIEWS = 16
 SPLAT_MAX_INSTANCES = 1 << 30
+SPLAT_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STAGES = {1: "slice_project", 2: "depth_sort", 3: "scan", 4: "duplicate", 5: "tile_sort",
           6: "composite_fwd", 7: "composite_bwd", 8: "adjoint", 9: "convert"}
@@ -96,6 +97,8 @@ EXPORTS = {
                                          C.c_void_p, C.c_size_t, C.c_void_p]),
     "splat_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_void_p,
                                 C.c_void_p]),
+    "splat_bin_sort_noalloc": (C.c_int, [_P(splat_proj), _P(splat_view), C.c_int, _P(splat_bins), C.c_void_p,
+                                         C.c_void_p]),
 }
 
 _lib = None
@@ -196,3 +199,10 @@ def splat_convert_4d_to_3d(g4, g3, tau, n_moved, status, ws, ws_bytes, stream):
 
 def splat_l1_loss(img, target, n, scale, dL, loss, stream):
     return lib().splat_l1_loss(img, target, n, scale, dL, loss, stream)
+
+
+def splat_bin_sort_noalloc(proj, views, V, bins, status, stream):
+    """splat_bin_sort without a workspace argument, for callers that cannot
+    allocate device memory when they sort (scratch: a fixed array inside the
+    library, shared by all calls)."""
+    return lib().splat_bin_sort_noalloc(proj, views, V, bins, status, stream)

@@ -1,0 +1,66 @@
+"""splat_bin_sort_noalloc against splat_bin_sort, through the C ABI.
+
+The allocation-free variant is for callers that cannot allocate device memory
+when they sort -- a plugin whose host application owns the whole GPU memory
+budget, or a frame loop that must not call cudaMalloc / cudaFree because those
+can synchronise the device.  It takes its scratch from a fixed array inside the
+library instead of a workspace argument.  Its output must equal the regular
+entry point's output exactly (integer lists), call after call, since every call
+reuses the same array.
+"""
+import ctypes as C
+
+import pytest
+import torch
+
+from paper_2505_13215_gb300 import abi, raster, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _bins(capacity, total_tiles):
+    keys = torch.zeros(capacity, dtype=torch.int32, device="cuda")
+    vals = torch.zeros(capacity, dtype=torch.int32, device="cuda")
+    ranges = torch.zeros(2 * total_tiles, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    c = abi.splat_bins(capacity, keys.data_ptr(), vals.data_ptr(), ranges.data_ptr(), n.data_ptr())
+    return c, keys, vals, ranges, n
+
+
+def test_noalloc_bin_sort_matches_workspace_version_twice():
+    scene, views = scenes.small_scene(seed=0)
+    G = raster.Gaussians.from_scene(scene, "cuda")
+    R = raster.Rasterizer(G.n3, G.n4, views)
+    R.autotune_capacity(G)
+    R.slice_project(G)
+    R.bin_sort()
+    torch.cuda.synchronize()
+    R.check()
+    K = R.instances()
+    ref_keys, ref_vals, ref_ranges = R.keys[:K].clone(), R.vals[:K].clone(), R.ranges.clone()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    c, keys, vals, ranges, n = _bins(R.capacity, R.total_tiles)
+    status = torch.zeros(4, dtype=torch.int32, device="cuda")
+    for call in range(2):
+        keys.fill_(-1)
+        vals.fill_(-1)
+        ranges.fill_(-1)
+        rc = abi.splat_bin_sort_noalloc(C.byref(R.cproj), R.cviews, R.V, C.byref(c), C.c_void_p(status.data_ptr()),
+                                        stream)
+        assert rc == abi.SPLAT_OK, abi.status_string(rc)
+        torch.cuda.synchronize()
+        assert int(status[0]) == abi.SPLAT_OK, "call %d: %s" % (call, abi.status_string(int(status[0])))
+        assert int(n.item()) == K
+        assert torch.equal(keys[:K], ref_keys), "call %d keys" % call
+        assert torch.equal(vals[:K], ref_vals), "call %d vals" % call
+        assert torch.equal(ranges, ref_ranges), "call %d ranges" % call
+
+
+def test_noalloc_rejects_problems_larger_than_its_scratch():
+    scene, views = scenes.small_scene(seed=0, n3=300, n4=100)
+    R = raster.Rasterizer(scene.n3, scene.n4, views, capacity=1024)
+    big = abi.splat_bins(1 << 28, R.keys.data_ptr(), R.vals.data_ptr(), R.ranges.data_ptr(),
+                         R.n_instances.data_ptr())
+    rc = abi.splat_bin_sort_noalloc(C.byref(R.cproj), R.cviews, R.V, C.byref(big), C.c_void_p(R.status.data_ptr()),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == abi.SPLAT_ERR_CAPACITY
