@@ -226,7 +226,10 @@ splat_status splat_slice_project(const splat_g3 *g3, const splat_g4 *g4, const s
  * duplication, then the tile digits after it; the resulting order is the
  * same.  Writes bins->keys/vals (first K entries), bins->ranges (every tile,
  * [0,0) when empty) and *bins->n_instances = K.  K > capacity sets
- * SPLAT_ERR_CAPACITY with the required K in status[2..3] and n_instances.
+ * SPLAT_ERR_CAPACITY with the required count in status[2..3] and n_instances;
+ * on the binned path (see splat_set_tile_sort) the intermediate super-tile
+ * list may overflow first, and the count reported is then a lower bound of K
+ * (retrying with at least that capacity converges in a few calls).
  * bins->keys may be NULL when the binned partition is in use (see
  * splat_set_tile_sort); the tile of entry s is then implied by ranges.
  */
@@ -340,6 +343,17 @@ int64_t splat_launch_count(void);
  * global; splat_workspace_size depends on it.
  */
 void splat_set_tile_sort(int mode);
+
+/*
+ * Binned tile sort only: when on (default), a Gaussian is listed for a tile of
+ * its rectangle only if its opacity footprint -- the ellipse where alpha_max
+ * exp(power) can reach 1/255, enlarged by a margin covering FP32 rounding --
+ * meets the tile.  Every pixel skips the dropped pairs anyway, so images and
+ * gradients do not change; the lists (and so `last`) are shorter.  Off: every
+ * tile of the rectangle, as in splat_bin_sort's key definition.  Host-side
+ * global.
+ */
+void splat_set_tile_cull(int on);
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int32_t splat_version(void);

@@ -16,6 +16,7 @@ cudaError_t launch_adjoint(const splat_g3&, const splat_g4&, const ViewBatch&, c
 cudaError_t launch_bin_sort(const splat_proj&, const ViewBatch&, const splat_bins&, int32_t*, void*, const LaunchCtx&);
 size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY);
 void set_tile_sort_mode(int mode);
+void set_tile_cull(int on);
 cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&, int32_t*,
                                  int, const LaunchCtx&);
 cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
@@ -149,6 +150,8 @@ int64_t splat_launch_count(void) { return g_launches.load(); }
 void splat_set_spin_limit(int64_t iterations) { g_spin_limit.store(iterations < 0 ? 0 : iterations); }
 
 void splat_set_tile_sort(int mode) { set_tile_sort_mode(mode); }
+
+void splat_set_tile_cull(int on) { set_tile_cull(on); }
 
 void splat_set_pixels_per_lane(int fwd, int bwd)
 {

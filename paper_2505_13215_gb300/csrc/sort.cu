@@ -714,9 +714,9 @@ __global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, i
 }
 
 // ---------------------------------------------------------------------------
-// Tile level.  Tile totals: every visible row adds its tile rectangle to its
-// view's 2D difference array; the 2D prefix sum of the array is the number of
-// instances of every tile.
+// Tile level.  A counting pass of the per-super-tile filter gives every tile's
+// total, k_bin_ranges scans them into ranges (and K), and the writing pass of
+// the same filter emits the lists.
 // ---------------------------------------------------------------------------
 
 struct TileArgs {
@@ -726,8 +726,6 @@ struct TileArgs {
     int total_tiles;
     int tile_base[SPLAT_MAX_VIEWS + 1];
     int TX[SPLAT_MAX_VIEWS], TY[SPLAT_MAX_VIEWS];
-    int diff_base[SPLAT_MAX_VIEWS];   // offset of view v's (TY+1) x (TX+1) difference array
-    int* diff;
     uint32_t* tile_total;
     // per-super-tile filter
     const uint32_t* list;             // rows grouped by super-tile, depth order inside
@@ -738,62 +736,128 @@ struct TileArgs {
     const uint2* ranges;              // tile ranges (cursor starts)
     uint32_t* vals_out;
     uint32_t* keys_out;               // may be null
+    int cull;                         // drop tiles the opacity footprint cannot reach
+    uint32_t* seg_base;               // [total_super + 1] first segment of each super-tile's list
+    uint32_t* seg_cnt;                // [segments][64] per-segment tile counts, then offsets
     int32_t* status;
 };
 
-__global__ void __launch_bounds__(256) k_tile_diff(TileArgs a)
+constexpr int kFilterSeg = 1024;  // list entries per filter segment (one CTA)
+
+// one block: segments per super-tile list, exclusive scan -> seg_base
+__global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
 {
+    __shared__ uint32_t s_tmp[8];
     if (status_failed(a.status)) return;
-    const int64_t N = a.proj.n;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n_rows; r += (int64_t)gridDim.x * blockDim.x) {
-        if (a.proj.n_tiles[r] == 0) continue;
-        const int v = (int)(r / N);
-        const int4 rc = ((const int4*)a.proj.rect)[r];
-        int* d = a.diff + a.diff_base[v];
-        const int TXp = a.TX[v] + 1;
-        atomicAdd(&d[rc.y * TXp + rc.x], 1);
-        atomicAdd(&d[rc.y * TXp + rc.z], -1);
-        atomicAdd(&d[rc.w * TXp + rc.x], -1);
-        atomicAdd(&d[rc.w * TXp + rc.z], 1);
+    uint32_t carry = 0;
+    for (int base = 0; base < a.total_super; base += 256) {
+        const int gs = base + threadIdx.x;
+        uint32_t c = 0;
+        if (gs < a.total_super) {
+            const uint2 rg = a.sranges[gs];
+            c = (rg.y - rg.x + kFilterSeg - 1) / kFilterSeg;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan256(c, s_tmp, &tot);
+        if (gs < a.total_super) a.seg_base[gs] = carry + ex;
+        carry += tot;
     }
+    if (threadIdx.x == 0) a.seg_base[a.total_super] = carry;
 }
 
-// one block per view: 2D inclusive prefix of the difference array -> tile totals
-__global__ void __launch_bounds__(1024) k_tile_totals(TileArgs a)
+// thread per (super-tile, tile of its 8x8 block): exclusive sum of the tile's
+// counts over the super-tile's segments; the tile's total
+__global__ void __launch_bounds__(256) k_seg_prefix(TileArgs a)
 {
     if (status_failed(a.status)) return;
-    const int v = blockIdx.x;
-    const int TX = a.TX[v], TY = a.TY[v], TXp = TX + 1;
-    int* d = a.diff + a.diff_base[v];
-    for (int y = threadIdx.x; y < TY; y += blockDim.x) {
-        int run = 0;
-        for (int x = 0; x < TX; ++x) {
-            run += d[y * TXp + x];
-            d[y * TXp + x] = run;
-        }
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)a.total_super * 64) return;
+    const int gs = (int)(idx >> 6), lt = (int)(idx & 63);
+    int v = 0;
+    for (int w = 1; w < a.V; ++w)
+        if (gs >= a.super_base[w]) v = w;
+    const int ls = gs - a.super_base[v];
+    const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
+    const int ty = sy * 8 + (lt >> 3), tx = sx * 8 + (lt & 7);
+    uint32_t run = 0;
+    for (uint32_t g = a.seg_base[gs]; g < a.seg_base[gs + 1]; ++g) {
+        uint32_t* p = a.seg_cnt + (size_t)g * 64 + lt;
+        const uint32_t c = *p;
+        *p = run;
+        run += c;
     }
-    __syncthreads();
-    for (int x = threadIdx.x; x < TX; x += blockDim.x) {
-        int run = 0;
-        for (int y = 0; y < TY; ++y) {
-            run += d[y * TXp + x];
-            a.tile_total[a.tile_base[v] + y * TX + x] = (uint32_t)run;
-        }
-    }
+    if (ty < a.TY[v] && tx < a.TX[v]) a.tile_total[a.tile_base[v] + ty * a.TX[v] + tx] = run;
 }
 
-// One CTA per super-tile (8x8 tiles).  It streams the super-tile's rows in depth
-// order through shared memory; warp w keeps the cursors of tile row w (8 tiles)
-// and appends every row covering one of its tiles, in order: each tile's list is
-// written contiguously.
+// Horizontal pixel extent [ul, ur] of the ellipse {power >= pcut} of one
+// projected Gaussian inside the pixel band v in [vlo, vhi] (power =
+// -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = px - u, dy = py - v; R2 = -2 pcut,
+// enlarged).  Returns false when the ellipse misses the band.
+__device__ __forceinline__ bool ellipse_band_extent(float px, float py, float a, float b, float c, float R2,
+                                                    float vlo, float vhi, float& ul, float& ur)
+{
+    const float det = a * c - b * b;
+    if (!(det > 0.f) || !(a > 0.f) || !(c > 0.f)) {  // degenerate: keep the whole band
+        ul = -3.0e38f;
+        ur = 3.0e38f;
+        return true;
+    }
+    const float d0 = py - vhi, d1 = py - vlo;           // dy range of the band
+    const float Y = sqrtf(R2 * a / det);                // |dy| reach of the ellipse
+    const float e0 = fmaxf(d0, -Y), e1 = fminf(d1, Y);
+    if (e0 > e1) return false;
+    const float X = sqrtf(R2 * c / det);                // |dx| reach of the ellipse
+    const float ba = b / a, ha = det / a;
+    // rightmost point of the ellipse at dy = -(b/c) X, leftmost at +(b/c) X
+    const float yr = -b / c * X, yl = -yr;
+    float dxmax, dxmin;
+    if (yr >= e0 && yr <= e1) {
+        dxmax = X;
+    } else {
+        const float dy = fminf(fmaxf(yr, e0), e1);
+        dxmax = -ba * dy + sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) / a));
+    }
+    if (yl >= e0 && yl <= e1) {
+        dxmin = -X;
+    } else {
+        const float dy = fminf(fmaxf(yl, e0), e1);
+        dxmin = -ba * dy - sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) / a));
+    }
+    ul = px - dxmax;
+    ur = px - dxmin;
+    return true;
+}
+
+// One CTA per segment (kFilterSeg entries) of a super-tile's row list (8x8
+// tiles): it streams the rows in depth order through shared memory; warp w
+// serves tile row w (8 tiles) and keeps a
+// row only for the tiles of its rectangle that its opacity footprint reaches
+// (the footprint enlarged by a margin that covers FP32 rounding, so no pixel
+// result changes).  COUNT: per-(segment, tile) counts.  Otherwise: each tile's
+// list is written contiguously, in order, from the segment's offsets.
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
 {
     __shared__ int4 s_rect[256];
+    __shared__ float4 s_geo[256];   // px, py, R2, -
+    __shared__ float4 s_con[256];   // a, b, c, -
     __shared__ uint32_t s_row[256];
+    __shared__ int s_gs;
     if (status_failed(a.status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    for (int gs = blockIdx.x; gs < a.total_super; gs += gridDim.x) {
+    const uint32_t nseg = a.seg_base[a.total_super];
+    for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+        if (threadIdx.x == 0) {  // super-tile of segment g: last gs with seg_base[gs] <= g
+            int lo = 0, hi = a.total_super - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.seg_base[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            s_gs = lo;
+        }
+        __syncthreads();
+        const int gs = s_gs;
         int v = 0;
         for (int w = 1; w < a.V; ++w)
             if (gs >= a.super_base[w]) v = w;
@@ -802,13 +866,17 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
         const int TX = a.TX[v], TY = a.TY[v];
         const int ty = sy * 8 + warp;
         const int tx0 = sx * 8;
+        const float vlo = (float)(ty * kTile), vhi = vlo + (float)(kTile - 1);
         uint32_t cur[8];
+        const uint32_t* off = a.seg_cnt + (size_t)g * 64 + warp * 8;  // (after k_seg_prefix) segment offsets
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const bool ok = ty < TY && tx0 + k < TX;
-            cur[k] = ok ? a.ranges[a.tile_base[v] + ty * TX + tx0 + k].x : 0u;
+            cur[k] = (!COUNT && ok) ? a.tile_total[a.tile_base[v] + ty * TX + tx0 + k] + off[k] : 0u;
         }
-        const uint2 rg = a.sranges[gs];
+        const uint2 rgs = a.sranges[gs];
+        const uint32_t sb0 = rgs.x + (g - a.seg_base[gs]) * kFilterSeg;
+        const uint2 rg = make_uint2(sb0, min(sb0 + kFilterSeg, rgs.y));
         for (uint32_t b = rg.x; b < rg.y; b += 256) {
             __syncthreads();
             const uint32_t j = b + threadIdx.x;
@@ -816,6 +884,12 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                 const uint32_t row = a.list[j];
                 s_row[threadIdx.x] = row;
                 s_rect[threadIdx.x] = ((const int4*)a.proj.rect)[row];
+                const float2 xy = ((const float2*)a.proj.xy)[row];
+                const float4 co = ((const float4*)a.proj.conic_opacity)[row];
+                // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
+                const float R2 = -2.f * __logf(kAlphaMin / co.w) * 1.0001f + 2e-3f;
+                s_geo[threadIdx.x] = make_float4(xy.x, xy.y, R2, 0.f);
+                s_con[threadIdx.x] = make_float4(co.x, co.y, co.z, 0.f);
             }
             __syncthreads();
             if (ty >= TY) continue;
@@ -823,19 +897,34 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
             for (int sb = 0; sb < n; sb += 32) {
                 const int e = sb + lane;
                 bool cy = false;
-                int4 rc = make_int4(0, 0, 0, 0);
                 uint32_t row = 0;
+                int cx0 = 0, cx1 = 0;  // tile columns kept in this tile row
                 if (e < n) {
-                    rc = s_rect[e];
+                    const int4 rc = s_rect[e];
                     row = s_row[e];
                     cy = rc.y <= ty && ty < rc.w;
+                    cx0 = rc.x;
+                    cx1 = rc.z;
+                    if (cy && a.cull) {
+                        const float4 g = s_geo[e], q = s_con[e];
+                        float ul, ur;
+                        if (!ellipse_band_extent(g.x, g.y, q.x, q.y, q.z, g.z, vlo, vhi, ul, ur)) {
+                            cy = false;
+                        } else {
+                            // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
+                            const float lo = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
+                            const float hi = floorf(ur * (1.f / kTile));
+                            cx0 = max(cx0, (int)fminf(fmaxf(lo, -1.f), 1.0e6f));
+                            cx1 = min(cx1, (int)fminf(fmaxf(hi, -2.f), 1.0e6f) + 1);
+                        }
+                    }
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int tx = tx0 + k;
-                    const bool cov = cy && rc.x <= tx && tx < rc.z;
+                    const bool cov = cy && cx0 <= tx && tx < cx1;
                     const unsigned m = __ballot_sync(0xffffffffu, cov);
-                    if (cov) {
+                    if (!COUNT && cov) {
                         const uint32_t pos = cur[k] + __popc(m & lt);
                         a.vals_out[pos] = row;
                         if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx);
@@ -843,6 +932,11 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                     cur[k] += __popc(m);
                 }
             }
+        }
+        if (COUNT) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (lane == k) a.seg_cnt[(size_t)g * 64 + warp * 8 + k] = cur[k];
         }
         __syncthreads();
     }
@@ -965,6 +1059,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(BinArgs a)
 // ---------------------------------------------------------------------------
 
 static int g_tile_sort_mode = 0;  // 0 auto, 1 radix passes, 2 binned
+static int g_tile_cull = 1;       // binned path: drop tiles the opacity footprint cannot reach
 
 struct SortLayout {
     int64_t n_rows, capacity;
@@ -973,10 +1068,11 @@ struct SortLayout {
     uint32_t chunk;
     int64_t max_chunks;
     int64_t parts_d, parts_t, parts_scan, n_chunks;
-    int64_t total_tiles, total_super, diff_len;
+    int64_t total_tiles, total_super;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
         off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
-    size_t off_diff, off_vals1, off_sranges, off_stotal, off_ninst1;
+    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt;
+    int64_t max_segs;
     size_t bytes;
 };
 
@@ -1004,7 +1100,6 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
         smax = std::max(smax, sx * sy);
         L.total_tiles += (int64_t)TX[v] * TY[v];
         L.total_super += (int64_t)sx * sy;
-        L.diff_len += (int64_t)(TX[v] + 1) * (TY[v] + 1);
     }
     L.tmax = (tmax + 3) & ~3;
     L.smax = (smax + 3) & ~3;
@@ -1032,11 +1127,13 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.off_counts = take(L.binned ? 4 * (size_t)L.max_chunks * L.smax : 4);
     L.off_first = take(L.binned ? 4 * (size_t)L.max_chunks : 4);
     L.off_total = take(L.binned ? 4 * (size_t)L.total_tiles : 4);
-    L.off_diff = take(L.binned ? 4 * (size_t)L.diff_len : 4);
     L.off_vals1 = take(L.binned ? 4 * (size_t)capacity : 4);
     L.off_sranges = take(L.binned ? 8 * (size_t)L.total_super : 4);
     L.off_stotal = take(L.binned ? 4 * (size_t)L.total_super : 4);
     L.off_ninst1 = take(8);
+    L.max_segs = L.binned ? (capacity + kFilterSeg - 1) / kFilterSeg + L.total_super : 1;
+    L.off_segbase = take(4 * (size_t)(L.total_super + 1));
+    L.off_segcnt = take(L.binned ? 4 * 64 * (size_t)L.max_segs : 4);
     L.bytes = o;
     return L;
 }
@@ -1132,8 +1229,10 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.lb = (unsigned long long*)(w + L.off_scan_lb);
         a.ticket = tickets + 4;
         a.n_instances = L.binned ? (int64_t*)(w + L.off_ninst1) : bins.n_instances;
-        // binned: the super-tile count K1 <= K; K itself is checked by the tile ranges
-        a.capacity = L.binned ? INT64_MAX : bins.capacity;
+        // binned: the super-tile list (K1 <= K entries) lives in a capacity-sized
+        // buffer, so K1 is checked here, before anything is written; K itself is
+        // checked by the tile ranges once the lists are counted
+        a.capacity = bins.capacity;
         a.status = status;
         a.spin_limit = ctx.spin_limit;
         const int blocks = (int)std::min<int64_t>(L.parts_scan, (int64_t)ctx.num_sms * 4);
@@ -1148,13 +1247,11 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.V = vb.V;
         t.n_rows = n_rows;
         t.total_tiles = vb.total_tiles;
-        int db = 0, sb = 0;
+        int sb = 0;
         for (int v = 0; v < vb.V; ++v) {
             t.tile_base[v] = vb.v[v].tile_base;
             t.TX[v] = vb.v[v].TX;
             t.TY[v] = vb.v[v].TY;
-            t.diff_base[v] = db;
-            db += (vb.v[v].TX + 1) * (vb.v[v].TY + 1);
             t.super_base[v] = sb;
             t.STX[v] = (vb.v[v].TX + 7) >> kSuperShift;
             sb += t.STX[v] * ((vb.v[v].TY + 7) >> kSuperShift);
@@ -1162,7 +1259,6 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.tile_base[vb.V] = vb.total_tiles;
         t.super_base[vb.V] = sb;
         t.total_super = sb;
-        t.diff = (int*)(w + L.off_diff);
         t.tile_total = U(L.off_total);
         t.list = U(L.off_vals1);
         t.sranges = (const uint2*)(w + L.off_sranges);
@@ -1170,16 +1266,14 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.vals_out = bins.vals;
         t.keys_out = bins.keys;
         t.status = status;
-        if ((err = cudaMemsetAsync(t.diff, 0, 4 * (size_t)L.diff_len, s)) != cudaSuccess) return err;
+        t.cull = g_tile_cull;
+        t.seg_base = U(L.off_segbase);
+        t.seg_cnt = U(L.off_segcnt);
         BinArgs tr{};
         tr.total_tiles = vb.total_tiles;
         tr.tile_total = U(L.off_total);
         tr.ranges = (uint2*)bins.ranges;
         tr.status = status;
-        count_launch(3);
-        k_tile_diff<<<(int)std::min<int64_t>((n_rows + 255) / 256, (int64_t)ctx.num_sms * 8), 256, 0, s>>>(t);
-        k_tile_totals<<<vb.V, 1024, 0, s>>>(t);
-        k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity);
         // super-tile level: stable partition of the (view, depth)-ordered rows by super-tile
         BinArgs a{};
         a.proj = proj;
@@ -1237,8 +1331,15 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_bin_ranges<<<1, 256, 0, s>>>(a, nullptr, 0);
         k_bin_prefix<1><<<(sb + 31) / 32, 256, 0, s>>>(a);
         k_bin_scatter<<<blocks_s, 32, smem_scatter, s>>>(a);
-        // tile level: each super-tile's rows filtered into its tiles' lists
-        k_tile_filter<<<(int)std::min<int64_t>(sb, (int64_t)ctx.num_sms * 8), 256, 0, s>>>(t);
+        // tile level: segment the super-tile lists, count each (segment, tile),
+        // prefix over segments, ranges + K + capacity check, then write the lists
+        const int blocks_f = (int)std::min<int64_t>(L.max_segs, (int64_t)ctx.num_sms * 8);
+        count_launch(5);
+        k_seg_plan<<<1, 256, 0, s>>>(t);
+        k_tile_filter<true><<<blocks_f, 256, 0, s>>>(t);
+        k_seg_prefix<<<(int)(((int64_t)sb * 64 + 255) / 256), 256, 0, s>>>(t);
+        k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity);
+        k_tile_filter<false><<<blocks_f, 256, 0, s>>>(t);
         return cudaGetLastError();
     }
     // 4. radix path: duplicate, tile-digit passes, ranges
@@ -1308,5 +1409,7 @@ size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX
 }
 
 void set_tile_sort_mode(int mode) { g_tile_sort_mode = (mode >= 0 && mode <= 2) ? mode : 0; }
+
+void set_tile_cull(int on) { g_tile_cull = on ? 1 : 0; }
 
 }  // namespace splat

@@ -264,7 +264,7 @@ class Rasterizer:
     def instances(self) -> int:
         return int(self.n_instances.item())
 
-    def autotune_capacity(self, G: Gaussians, retries: int = 3) -> int:
+    def autotune_capacity(self, G: Gaussians, retries: int = 5) -> int:
         """Render once; when the instance list overflows, grow it to the required
         count times the headroom and render again.  Returns K."""
         for _ in range(retries):
