@@ -79,6 +79,14 @@ def reduce_sum(x: float, device=None) -> float:
     return float(t.item())
 
 
+def aggregate(views_done: float, seconds: float, device=None):
+    """Whole-job throughput of independent replicas: views of all ranks over the
+    slowest rank's time.  Returns (views/s, total views, max seconds)."""
+    total = reduce_sum(views_done, device)
+    t_max = reduce_max(seconds, device)
+    return total / t_max, total, t_max
+
+
 def rank_seed(rank: int) -> int:
     """Each replica renders its own cameras / timestamps of the same scene."""
     return 100 + rank
@@ -99,10 +107,17 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.fh,
+                                          "-i", str(gpu_index), "-lms", "100"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: the timed region begins after its first sample
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -160,6 +175,40 @@ def algorithmic_bytes(stage, n3, n4, V, pix, K, elem):
         # read once by the (tile-digit) sort, sorted ids and tile keys written once
         return rows * (4 + 4 + 16) + K * 8 * 2
     return 0
+
+
+# FP32 operations per pixel-Gaussian pair on each path of the compositing
+# kernels, counted from their source (FMA = 2): evaluating the power (dy and two
+# FMA) costs 5; a blended pair costs 18 in the forward (exp, alpha, transmittance,
+# colour) and 37 in the backward (replayed T, colour and alpha gradients, moments).
+FLOPS_EVAL = 5
+FLOPS_BLEND = {"composite_fwd": 18, "composite_bwd": 37}
+KERNEL_SOURCES = {"composite_fwd": ["composite.cu", "splat_internal.cuh"],
+                  "composite_bwd": ["composite.cu", "splat_internal.cuh"],
+                  "slice_project": ["project.cu", "splat_internal.cuh"],
+                  "adjoint": ["project.cu", "splat_internal.cuh"]}
+
+
+def source_digest(stage):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(stage, []):
+        with open(os.path.join(ROOT, "paper_2505_13215_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(stage, views):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, scaled to
+    `views` views; None when the kernel's source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)[stage]
+    except (OSError, ValueError, KeyError):
+        return None
+    if t.get("source_digest") != source_digest(stage):
+        return None
+    return int(t["dram_bytes_per_view"] * views)
 
 
 # ---------------------------------------------------------------------------
@@ -228,9 +277,7 @@ def run_ours(args, rank, local, world):
     R.check("timed steps")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
-    t_max = reduce_max(total_s, dev)
-    views_total = reduce_sum(V * args.steps, dev)
-    value = views_total / t_max
+    value, views_total, t_max = aggregate(V * args.steps, total_s, dev)
     if marks_ok:
         per = [gs.stage_ms(k) for k in range(copies)]
         stages = {s: sum(p[s] for p in per) / len(per) for s in raster.Rasterizer.STAGES}
@@ -262,7 +309,7 @@ def run_ours(args, rank, local, world):
     for Rv, _ in plain:
         Rv.check("plain FP32 path")
     plain_s = sum(a.elapsed_time(b) for a, b in pe) / 1e3
-    plain_value = reduce_sum(V * plain_steps, dev) / reduce_max(plain_s, dev)
+    plain_value = aggregate(V * plain_steps, plain_s, dev)[0]
     abi.splat_set_pixels_per_lane(tune["ppl_fwd"], tune["ppl_bwd"])
     del plain
 
@@ -294,18 +341,40 @@ def run_ours(args, rank, local, world):
     barrier()
     if int(status_host[0]) != 0:
         raise abi.SplatError(int(status_host[0]), "e2e steps", int(status_host[1]))
-    e2e_value = views_total / reduce_max(e2e_s, dev)
+    e2e_value = aggregate(V * args.steps, e2e_s, dev)[0]
+
+    # ---- pair counts of the compositing kernels (one instrumented step, untimed) ----
+    counters = torch.zeros(4, dtype=torch.int64, device=dev)
+    abi.splat_set_stats(counters.data_ptr())
+    try:
+        R.step(G, target)
+        torch.cuda.synchronize()
+    finally:
+        abi.splat_set_stats(None)
+    fe, fb, be, bb = [int(x) for x in counters.cpu().tolist()]
+    pairs = {"fwd_evaluated": fe, "fwd_blended": fb, "bwd_evaluated": be, "bwd_blended": bb}
+    flops = {"composite_fwd": FLOPS_EVAL * fe + (FLOPS_BLEND["composite_fwd"] - FLOPS_EVAL) * fb,
+             "composite_bwd": FLOPS_EVAL * be + (FLOPS_BLEND["composite_bwd"] - FLOPS_EVAL) * bb}
 
     # ---- roofline of the dominant stage ----
     pix = int(sum(R.pix))
     dom = max(stages, key=lambda s: stages[s])
-    alg = algorithmic_bytes(dom, G.n3, G.n4, V, pix, K_inst, 2)
-    ach = alg / (stages[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
-                "algorithmic_bytes": alg}
-    if dom in ("composite_fwd", "composite_bwd"):
-        roofline["note"] = "compositing is FP32-pipe/MUFU/atomic bound; HBM fraction shown for reference"
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", clk.get("sm_max_mhz") or 2070.0))
+    if dom in flops:
+        # FP32 peak from unit counts and the maximum SM clock: SMs x 128 lanes x 2 (FMA)
+        fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        ach = flops[dom] / (stages[dom] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(fp32_peak, 1),
+                    "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                    "traffic": measured_traffic(dom, V), "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz"
+                    % (props.multi_processor_count, sm_max), "algorithmic_flops": flops[dom]}
+    else:
+        alg = algorithmic_bytes(dom, G.n3, G.n4, V, pix, K_inst, 2)
+        ach = alg / (stages[dom] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(ach / hbm_peak, 4), "traffic": measured_traffic(dom, V),
+                    "peak_source": peak_src + " (copy bandwidth)", "algorithmic_bytes": alg}
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -321,6 +390,7 @@ def run_ours(args, rank, local, world):
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "composite_pairs": pairs,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -404,17 +474,44 @@ def run_reference(args, rank, local, world):
     print(json.dumps(out), flush=True)
 
 
+def run_profile(args):
+    """Untimed eager steps of the workload, for profilers (ncu); prints K."""
+    import torch
+
+    from paper_2505_13215_gb300 import abi, raster, scenes
+    torch.cuda.set_device(0)
+    scene, base = scenes.video_scene(seed=1, n3=N3, n4=N4, W=W, H=H)
+    views = scenes.jittered_views(base[0], args.views, seed=rank_seed(0))
+    dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    G = raster.Gaussians.from_scene(scene, "cuda", dtype=dt)
+    R = raster.Rasterizer(G.n3, G.n4, views, keep_keys=False)
+    ppl_f, ppl_b = (int(x) for x in args.ppl.split(","))
+    abi.splat_set_pixels_per_lane(ppl_f, ppl_b)
+    R.autotune_capacity(G)
+    target = torch.rand(R.rgb.shape, device="cuda")
+    for _ in range(args.profile):
+        R.step(G, target)
+    torch.cuda.synchronize()
+    R.check("profile steps")
+    print("K", R.instances())
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--views", type=int, default=4, help="views per batched step (<= 16)")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-samples", type=int, default=1500)
     ap.add_argument("--ref-samples", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=0, help="run this many untimed eager steps (for ncu) and exit")
+    ap.add_argument("--dtype", choices=("bf16", "f32"), default="bf16", help="storage dtype of --profile")
+    ap.add_argument("--ppl", default="2,4", help="pixels per lane (forward,backward) of --profile")
     args = ap.parse_args(argv)
+    if args.profile:
+        return run_profile(args)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank, local, world = dist_env()

@@ -355,6 +355,15 @@ void splat_set_tile_sort(int mode);
  */
 void splat_set_tile_cull(int on);
 
+/*
+ * Diagnostic: when dev_counters (device uint64[4]) is not NULL, later
+ * compositing launches use an instrumented variant that adds the numbers of
+ * pixel-Gaussian pairs evaluated (power computed) and blended by the forward
+ * (counters 0, 1) and by the backward (2, 3).  NULL (default) turns it off.
+ * Host-side global; the caller zeroes the counters.
+ */
+void splat_set_stats(unsigned long long *dev_counters);
+
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int32_t splat_version(void);
 

@@ -81,6 +81,7 @@ EXPORTS = {
     "splat_set_pixels_per_lane": (None, [C.c_int, C.c_int]),
     "splat_set_tile_sort": (None, [C.c_int]),
     "splat_set_tile_cull": (None, [C.c_int]),
+    "splat_set_stats": (None, [C.c_void_p]),
     "splat_status_string": (C.c_char_p, [C.c_int32]),
     "splat_total_tiles": (C.c_int64, [C.c_int, _P(C.c_int32), _P(C.c_int32)]),
     "splat_workspace_size": (C.c_size_t, [C.c_int, C.c_int64, C.c_int64, C.c_int, _P(C.c_int32), _P(C.c_int32),
@@ -158,6 +159,10 @@ def splat_set_spin_limit(n):
 
 def splat_set_tile_sort(mode):
     lib().splat_set_tile_sort(int(mode))
+
+
+def splat_set_stats(dev_counters_ptr):
+    lib().splat_set_stats(dev_counters_ptr)
 
 
 def splat_set_tile_cull(on):

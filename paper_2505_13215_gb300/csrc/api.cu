@@ -18,9 +18,9 @@ size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX
 void set_tile_sort_mode(int mode);
 void set_tile_cull(int on);
 cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&, int32_t*,
-                                 int, const LaunchCtx&);
+                                 int, unsigned long long*, const LaunchCtx&);
 cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
-                                 const float*, float*, int32_t*, int, const LaunchCtx&);
+                                 const float*, float*, int32_t*, int, unsigned long long*, const LaunchCtx&);
 cudaError_t launch_convert(const splat_g4&, const splat_g3&, float, int64_t*, int32_t*, void*, const LaunchCtx&);
 size_t convert_workspace(int64_t n4, int dtype_bytes);
 cudaError_t launch_l1_loss(const float*, const float*, int64_t, float, float*, float*, const LaunchCtx&);
@@ -28,6 +28,7 @@ cudaError_t launch_l1_loss(const float*, const float*, int64_t, float, float*, f
 static std::atomic<int64_t> g_spin_limit{1ll << 22};
 std::atomic<int64_t> g_launches{0};
 static std::atomic<int> g_ppl_fwd{8}, g_ppl_bwd{8};
+static std::atomic<unsigned long long*> g_stats{nullptr};
 static int g_num_sms[64];
 
 LaunchCtx launch_ctx(void* stream)
@@ -151,6 +152,8 @@ void splat_set_spin_limit(int64_t iterations) { g_spin_limit.store(iterations < 
 
 void splat_set_tile_sort(int mode) { set_tile_sort_mode(mode); }
 
+void splat_set_stats(unsigned long long* dev_counters) { g_stats.store(dev_counters); }
+
 void splat_set_tile_cull(int on) { set_tile_cull(on); }
 
 void splat_set_pixels_per_lane(int fwd, int bwd)
@@ -262,7 +265,7 @@ splat_status splat_composite_fwd(const splat_proj* proj, const splat_bins* bins,
         return SPLAT_ERR_INVALID_ARG;
     const LaunchCtx ctx = launch_ctx(stream);
     const ViewBatch vb = make_batch(views, V);
-    return cuda_status(launch_composite_fwd(*proj, *bins, vb, *img, status, g_ppl_fwd.load(), ctx));
+    return cuda_status(launch_composite_fwd(*proj, *bins, vb, *img, status, g_ppl_fwd.load(), g_stats.load(), ctx));
 }
 
 splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
@@ -309,7 +312,7 @@ splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins,
     if (!adj_only) {
         cudaError_t e = cudaMemsetAsync(dp, 0, dproj_bytes, ctx.stream);
         if (e != cudaSuccess) return SPLAT_ERR_CUDA;
-        e = launch_composite_bwd(*proj, *bins, vb, *img, dL_drgb, dp, status, g_ppl_bwd.load(), ctx);
+        e = launch_composite_bwd(*proj, *bins, vb, *img, dL_drgb, dp, status, g_ppl_bwd.load(), g_stats.load(), ctx);
         if (e != cudaSuccess) return SPLAT_ERR_CUDA;
     }
     if (stop2d) return SPLAT_OK;

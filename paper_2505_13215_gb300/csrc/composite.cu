@@ -22,8 +22,9 @@ namespace splat {
 
 constexpr int kCompWarps = 4;  // warps (units) per CTA
 
-// Decision shared by forward and backward: returns false when the Gaussian
-// does not touch the pixel (power > 0, or alpha below 1/255).
+// Projected features of one Gaussian as staged in shared memory; pcut =
+// log(1/(255 alpha_max)) turns the alpha < 1/255 skip into a test on the power
+// that forward and backward evaluate identically.
 struct Feat {
     float px, py, a, b, c, op, r, g, bl, pcut;
 };
@@ -56,10 +57,13 @@ __device__ __forceinline__ int find_view(const ViewBatch& vb, int tile)
     return v;
 }
 
-template <int PPL>
+// STATS: also count, per warp, the pixel-Gaussian pairs evaluated (power
+// computed) and blended, into stats[0..1] (diagnostic instantiation only).
+template <int PPL, bool STATS>
 __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj proj, const uint32_t* __restrict__ vals,
                                                                    const uint2* __restrict__ ranges, ViewBatch vb,
-                                                                   splat_image img, int32_t* status)
+                                                                   splat_image img, int32_t* status,
+                                                                   unsigned long long* stats)
 {
     constexpr int BANDS = 8 / PPL;
     __shared__ float4 s_feat[kCompWarps][32][3];
@@ -88,6 +92,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     const uint2 rg = ranges[tile];
     const unsigned all_done = (1u << PPL) - 1;
     float4* sf = &s_feat[warp][0][0];
+    unsigned n_eval = 0, n_blend = 0;
     for (uint32_t b = rg.x; b < rg.y; b += 32) {
         if (__all_sync(0xffffffffu, done == all_done)) break;
         const uint32_t idx = b + lane;
@@ -105,14 +110,16 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
                     if (done & (1u << k)) continue;
                     const float dy = f.py - (float)(y0 + 2 * k);
                     const float power = A + dy * (Bx + Cc * dy);
+                    if (STATS) ++n_eval;
+                    // skip power > 0 and alpha < 1/255, the latter as power < log(1/(255 alpha_max))
                     if (power > 0.f || power < f.pcut) continue;
                     const float alpha = fminf(kAlphaClamp, f.op * __expf(power));
-                    if (alpha < kAlphaMin) continue;
                     const float tT = T[k] * (1.f - alpha);
                     if (tT < kTMin) {
                         done |= 1u << k;
                         continue;
                     }
+                    if (STATS) ++n_blend;
                     const float w = alpha * T[k];
                     C[k][0] += f.r * w;
                     C[k][1] += f.g * w;
@@ -124,6 +131,13 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
             }
         }
         __syncwarp();
+    }
+    if (STATS) {
+        const unsigned e = __reduce_add_sync(0xffffffffu, n_eval), bl = __reduce_add_sync(0xffffffffu, n_blend);
+        if (lane == 0) {
+            atomicAdd(stats + 0, (unsigned long long)e);
+            atomicAdd(stats + 1, (unsigned long long)bl);
+        }
     }
     const int64_t HW = (int64_t)vp.W * vp.H;
 #pragma unroll
@@ -166,11 +180,13 @@ __device__ __forceinline__ float reduce_scatter8(const float v[8], int lane)
     return x;
 }
 
-template <int PPL>
+// STATS: also count the pairs evaluated and blended into stats[2..3].
+template <int PPL, bool STATS>
 __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj proj, const uint32_t* __restrict__ vals,
                                                                    const uint2* __restrict__ ranges, ViewBatch vb,
                                                                    splat_image img, const float* __restrict__ dL,
-                                                                   float* dproj, int32_t* status)
+                                                                   float* dproj, int32_t* status,
+                                                                   unsigned long long* stats)
 {
     constexpr int BANDS = 8 / PPL;
     __shared__ float4 s_feat[kCompWarps][32][3];
@@ -220,6 +236,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
     const uint2 rg = ranges[tile];
     float4* sf = &s_feat[warp][0][0];
     const int nb = (maxlast + 31) / 32;
+    unsigned n_eval = 0, n_blend = 0;
     for (int bi = nb - 1; bi >= 0; --bi) {
         const uint32_t b = rg.x + 32u * bi;
         const uint32_t end = min(rg.x + (uint32_t)maxlast, rg.y);
@@ -237,20 +254,25 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
             const int li = 32 * bi + j;  // position in the tile list
             const float dx = f.px - uf;
             const float A = -0.5f * f.a * dx * dx, Bx = -f.b * dx, Cc = -0.5f * f.c;
+            // per lane: dL/dalpha_max and dL/drgb summed over its pixels, and the moments
+            // W0 = sum dL/dpower, W1 = sum dL/dpower dy, W2 = sum dL/dpower dy^2 from which
+            // the gradients of the mean and the conic follow (dx is the lane's own)
             float acc[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) acc[q] = 0.f;
+            float W0 = 0.f, W1 = 0.f, W2 = 0.f;
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
                 if (li >= last[k]) continue;
                 const float dy = f.py - (float)(y0 + 2 * k);
                 const float power = A + dy * (Bx + Cc * dy);
-                if (power > 0.f || power < f.pcut) continue;
+                if (STATS) ++n_eval;
+                if (power > 0.f || power < f.pcut) continue;  // the forward's skip, bit for bit
                 const float Gs = __expf(power);
                 const float raw = f.op * Gs;
                 const float alpha = fminf(kAlphaClamp, raw);
-                if (alpha < kAlphaMin) continue;
+                if (STATS) ++n_blend;
                 any = true;
                 const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
                 const float Tj = T[k] * iom;
@@ -265,13 +287,18 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
                 if (raw < kAlphaClamp) {
                     const float dpow = dLda * alpha;
                     acc[5] += dLda * Gs;
-                    acc[0] += -dpow * (f.a * dx + f.b * dy);
-                    acc[1] += -dpow * (f.c * dy + f.b * dx);
-                    acc[2] += -0.5f * dpow * dx * dx;
-                    acc[3] += -dpow * dx * dy;
-                    acc[4] += -0.5f * dpow * dy * dy;
+                    const float t = dpow * dy;
+                    W0 += dpow;
+                    W1 += t;
+                    W2 += t * dy;
                 }
             }
+            // power = -(a dx^2 + c dy^2)/2 - b dx dy with (dx, dy) = mean - pixel
+            acc[0] = -(f.a * dx * W0 + f.b * W1);
+            acc[1] = -(f.c * W1 + f.b * dx * W0);
+            acc[2] = -0.5f * dx * dx * W0;
+            acc[3] = -dx * W1;
+            acc[4] = -0.5f * W2;
             if (__any_sync(0xffffffffu, any)) {
                 const float r8 = reduce_scatter8(acc, lane);
                 float r9 = acc[8];
@@ -283,6 +310,13 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
             }
         }
         __syncwarp();
+    }
+    if (STATS) {
+        const unsigned e = __reduce_add_sync(0xffffffffu, n_eval), bl = __reduce_add_sync(0xffffffffu, n_blend);
+        if (lane == 0) {
+            atomicAdd(stats + 2, (unsigned long long)e);
+            atomicAdd(stats + 3, (unsigned long long)bl);
+        }
     }
 }
 
@@ -330,25 +364,35 @@ cudaError_t launch_l1_loss(const float* img, const float* target, int64_t n, flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_fwd(const splat_proj& proj, const splat_bins& bins, const ViewBatch& vb,
-                                 const splat_image& img, int32_t* status, int ppl, const LaunchCtx& ctx)
+template <bool ST>
+static void fwd_launch(int ppl, int blocks, cudaStream_t st, const splat_proj& proj, const splat_bins& bins,
+                       const ViewBatch& vb, const splat_image& img, int32_t* status, unsigned long long* stats)
 {
-    if (vb.total_tiles == 0) return cudaSuccess;
-    const int bands = 8 / ppl;
-    const int64_t units = (int64_t)vb.total_tiles * bands;
-    const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
-    count_launch();
+    const uint2* rg = (const uint2*)bins.ranges;
     switch (ppl) {
-    case 8: k_composite_fwd<8><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
-    case 4: k_composite_fwd<4><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
-    case 2: k_composite_fwd<2><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
-    default: k_composite_fwd<1><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, status); break;
+    case 8: k_composite_fwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, status, stats); break;
+    case 4: k_composite_fwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, status, stats); break;
+    case 2: k_composite_fwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, status, stats); break;
+    default: k_composite_fwd<1, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, status, stats); break;
     }
-    return cudaGetLastError();
 }
 
-cudaError_t launch_composite_bwd(const splat_proj& proj, const splat_bins& bins, const ViewBatch& vb,
-                                 const splat_image& img, const float* dL, float* dproj, int32_t* status, int ppl,
+template <bool ST>
+static void bwd_launch(int ppl, int blocks, cudaStream_t st, const splat_proj& proj, const splat_bins& bins,
+                       const ViewBatch& vb, const splat_image& img, const float* dL, float* dproj, int32_t* status,
+                       unsigned long long* stats)
+{
+    const uint2* rg = (const uint2*)bins.ranges;
+    switch (ppl) {
+    case 8: k_composite_bwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, dL, dproj, status, stats); break;
+    case 4: k_composite_bwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, dL, dproj, status, stats); break;
+    case 2: k_composite_bwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, dL, dproj, status, stats); break;
+    default: k_composite_bwd<1, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, dL, dproj, status, stats); break;
+    }
+}
+
+cudaError_t launch_composite_fwd(const splat_proj& proj, const splat_bins& bins, const ViewBatch& vb,
+                                 const splat_image& img, int32_t* status, int ppl, unsigned long long* stats,
                                  const LaunchCtx& ctx)
 {
     if (vb.total_tiles == 0) return cudaSuccess;
@@ -356,12 +400,22 @@ cudaError_t launch_composite_bwd(const splat_proj& proj, const splat_bins& bins,
     const int64_t units = (int64_t)vb.total_tiles * bands;
     const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
     count_launch();
-    switch (ppl) {
-    case 8: k_composite_bwd<8><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
-    case 4: k_composite_bwd<4><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
-    case 2: k_composite_bwd<2><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
-    default: k_composite_bwd<1><<<blocks, kCompWarps * 32, 0, ctx.stream>>>(proj, bins.vals, (const uint2*)bins.ranges, vb, img, dL, dproj, status); break;
-    }
+    if (stats) fwd_launch<true>(ppl, blocks, ctx.stream, proj, bins, vb, img, status, stats);
+    else fwd_launch<false>(ppl, blocks, ctx.stream, proj, bins, vb, img, status, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_bwd(const splat_proj& proj, const splat_bins& bins, const ViewBatch& vb,
+                                 const splat_image& img, const float* dL, float* dproj, int32_t* status, int ppl,
+                                 unsigned long long* stats, const LaunchCtx& ctx)
+{
+    if (vb.total_tiles == 0) return cudaSuccess;
+    const int bands = 8 / ppl;
+    const int64_t units = (int64_t)vb.total_tiles * bands;
+    const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
+    count_launch();
+    if (stats) bwd_launch<true>(ppl, blocks, ctx.stream, proj, bins, vb, img, dL, dproj, status, stats);
+    else bwd_launch<false>(ppl, blocks, ctx.stream, proj, bins, vb, img, dL, dproj, status, nullptr);
     return cudaGetLastError();
 }
 

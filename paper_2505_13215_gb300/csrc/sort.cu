@@ -789,39 +789,56 @@ __global__ void __launch_bounds__(256) k_seg_prefix(TileArgs a)
     if (ty < a.TY[v] && tx < a.TX[v]) a.tile_total[a.tile_base[v] + ty * a.TX[v] + tx] = run;
 }
 
-// Horizontal pixel extent [ul, ur] of the ellipse {power >= pcut} of one
-// projected Gaussian inside the pixel band v in [vlo, vhi] (power =
-// -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = px - u, dy = py - v; R2 = -2 pcut,
-// enlarged).  Returns false when the ellipse misses the band.
-__device__ __forceinline__ bool ellipse_band_extent(float px, float py, float a, float b, float c, float R2,
-                                                    float vlo, float vhi, float& ul, float& ur)
+// Opacity footprint of one projected Gaussian: the ellipse {power >= pcut},
+// power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = px - u, dy = py - v,
+// i.e. q(dx, dy) <= R2 = -2 pcut (R2 enlarged by the caller).  Constants per
+// Gaussian, computed once: g0 = (px, py, R2, Y) with Y the |dy| reach,
+// g1 = (X, yr, b/a, det/a) with X the |dx| reach and yr the dy of the rightmost
+// point, g2.x = 1/a.  Degenerate conics keep the whole band (Y = inf).
+__device__ __forceinline__ void ellipse_consts(float px, float py, float a, float b, float c, float R2, float4& g0,
+                                               float4& g1, float4& g2)
 {
     const float det = a * c - b * b;
-    if (!(det > 0.f) || !(a > 0.f) || !(c > 0.f)) {  // degenerate: keep the whole band
+    if (!(det > 0.f) || !(a > 0.f) || !(c > 0.f)) {
+        g0 = make_float4(px, py, R2, __int_as_float(0x7f800000));
+        g1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        g2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float ia = 1.f / a, idet = 1.f / det;
+    const float X = sqrtf(R2 * c * idet);
+    g0 = make_float4(px, py, R2, sqrtf(R2 * a * idet));
+    g1 = make_float4(X, -b / c * X, b * ia, det * ia);
+    g2 = make_float4(ia, 0.f, 0.f, 0.f);
+}
+
+// Horizontal pixel extent [ul, ur] of the footprint inside the pixel band
+// v in [vlo, vhi]; false when the footprint misses the band.
+__device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const float4& g1, const float4& g2, float vlo,
+                                                    float vhi, float& ul, float& ur)
+{
+    const float px = g0.x, py = g0.y, R2 = g0.z, Y = g0.w;
+    if (isinf(Y)) {
         ul = -3.0e38f;
         ur = 3.0e38f;
         return true;
     }
-    const float d0 = py - vhi, d1 = py - vlo;           // dy range of the band
-    const float Y = sqrtf(R2 * a / det);                // |dy| reach of the ellipse
-    const float e0 = fmaxf(d0, -Y), e1 = fminf(d1, Y);
+    const float e0 = fmaxf(py - vhi, -Y), e1 = fminf(py - vlo, Y);  // dy range of the band inside the reach
     if (e0 > e1) return false;
-    const float X = sqrtf(R2 * c / det);                // |dx| reach of the ellipse
-    const float ba = b / a, ha = det / a;
-    // rightmost point of the ellipse at dy = -(b/c) X, leftmost at +(b/c) X
-    const float yr = -b / c * X, yl = -yr;
+    const float X = g1.x, yr = g1.y, ba = g1.z, ha = g1.w, ia = g2.x;
     float dxmax, dxmin;
     if (yr >= e0 && yr <= e1) {
         dxmax = X;
     } else {
         const float dy = fminf(fmaxf(yr, e0), e1);
-        dxmax = -ba * dy + sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) / a));
+        dxmax = -ba * dy + sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
     }
+    const float yl = -yr;  // leftmost point
     if (yl >= e0 && yl <= e1) {
         dxmin = -X;
     } else {
         const float dy = fminf(fmaxf(yl, e0), e1);
-        dxmin = -ba * dy - sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) / a));
+        dxmin = -ba * dy - sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
     }
     ul = px - dxmax;
     ur = px - dxmin;
@@ -839,8 +856,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
 {
     __shared__ int4 s_rect[256];
-    __shared__ float4 s_geo[256];   // px, py, R2, -
-    __shared__ float4 s_con[256];   // a, b, c, -
+    __shared__ float4 s_g0[256], s_g1[256], s_g2[256];  // footprint constants
     __shared__ uint32_t s_row[256];
     __shared__ int s_gs;
     if (status_failed(a.status)) return;
@@ -884,12 +900,17 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                 const uint32_t row = a.list[j];
                 s_row[threadIdx.x] = row;
                 s_rect[threadIdx.x] = ((const int4*)a.proj.rect)[row];
-                const float2 xy = ((const float2*)a.proj.xy)[row];
-                const float4 co = ((const float4*)a.proj.conic_opacity)[row];
-                // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
-                const float R2 = -2.f * __logf(kAlphaMin / co.w) * 1.0001f + 2e-3f;
-                s_geo[threadIdx.x] = make_float4(xy.x, xy.y, R2, 0.f);
-                s_con[threadIdx.x] = make_float4(co.x, co.y, co.z, 0.f);
+                if (a.cull) {
+                    const float2 xy = ((const float2*)a.proj.xy)[row];
+                    const float4 co = ((const float4*)a.proj.conic_opacity)[row];
+                    // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
+                    const float R2 = -2.f * __logf(kAlphaMin / co.w) * 1.0001f + 2e-3f;
+                    float4 g0, g1, g2;
+                    ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1, g2);
+                    s_g0[threadIdx.x] = g0;
+                    s_g1[threadIdx.x] = g1;
+                    s_g2[threadIdx.x] = g2;
+                }
             }
             __syncthreads();
             if (ty >= TY) continue;
@@ -906,9 +927,8 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                     cx0 = rc.x;
                     cx1 = rc.z;
                     if (cy && a.cull) {
-                        const float4 g = s_geo[e], q = s_con[e];
                         float ul, ur;
-                        if (!ellipse_band_extent(g.x, g.y, q.x, q.y, q.z, g.z, vlo, vhi, ul, ur)) {
+                        if (!ellipse_band_extent(s_g0[e], s_g1[e], s_g2[e], vlo, vhi, ul, ur)) {
                             cy = false;
                         } else {
                             // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
