@@ -205,8 +205,11 @@ def project(scene, view):
 def render(scene, view, pixels=None):
     """Eq. 3 as the plain definition.  pixels: flat indices y*W+x (None = all).
     Returns dict rgb [3, npix], T [npix], last [npix], the per-decision margins
-    (dict 'margins': power, alpha, stop, tie, clamp), margin_fwd (min of the
-    first four) and margin_grad (the clamp)."""
+    (dict 'margins': power, alpha, stop, tie, clamp, tie3), margin_fwd (min of
+    the first four) and margin_grad (the clamp).  'tie' is the relative depth gap
+    of two touching Gaussians of which one is 4D; 'tie3' the distance of a 3D
+    pair's depth to an FP32 rounding boundary when their FP32 keys are at most
+    one step apart."""
     pk = _Packed(scene)
     v = _view(view)
     if pixels is None:
@@ -219,10 +222,10 @@ def render(scene, view, pixels=None):
     rgb = np.zeros((3, npix))
     T = np.zeros(npix)
     last = np.zeros(npix, dtype=np.int32)
-    mg = np.zeros((5, npix))
+    mg = np.zeros((6, npix))
     lib().oracle_render(C.byref(pk.g3), C.byref(pk.g4), C.byref(v), pix_p, npix, _p(rgb), _p(T),
                         last.ctypes.data_as(_i32p), _p(mg))
-    names = ("power", "alpha", "stop", "tie", "clamp")
+    names = ("power", "alpha", "stop", "tie", "clamp", "tie3")
     return {"rgb": rgb, "T": T, "last": last, "margins": dict(zip(names, mg)),
             "margin_fwd": mg[:4].min(0), "margin_grad": mg[4]}
 

@@ -17,7 +17,7 @@
  *     "ProjGaussian4D", "ProjGaussian3D"; 3DGS conventions, readings D5, D8)
  *   - the rendered pixel as the PLAIN DEFINITION of alpha compositing (Eq. 3):
  *     every visible Gaussian whose tile rectangle holds the pixel's tile,
- *     ordered by (depth, merged index), blended front to back
+ *     ordered by (depth rounded to FP32, merged index), blended front to back
  *     (Alg. 1 "CreateTiles" .. "BlendInOrder", readings D4, D6, D7)
  *   - the reverse-mode gradient of all of the above, hand written
  *   - the 4D -> 3D conversion of Sec. 4.1-4.2 with the quaternion of Eq. 9
@@ -459,14 +459,27 @@ void oracle_project(const og3 *g3, const og4 *g4, const oview *v, oproj *out)
 /* Per-pixel compositing: the plain definition of Eq. 3                      */
 /* ------------------------------------------------------------------------ */
 
-typedef struct { double depth; int64_t idx; } dkey;
+/* Sort key of one Gaussian in a tile list (reading D6): the depth as an FP32
+ * number, the precision of the key that Alg. 1's SortByKeys orders (tile id in
+ * the high bits, the depth's float bits in the low 32), then the merged index. */
+typedef struct { float key; int64_t idx; } dkey;
 
 static int cmp_dkey(const void *pa, const void *pb)
 {
     const dkey *a = pa, *b = pb;
-    if (a->depth < b->depth) return -1;
-    if (a->depth > b->depth) return 1;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
     return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/* relative distance of d > 0 to the nearest rounding boundary (midpoint between
+ * two neighbouring FP32 numbers): how far d is from rounding differently */
+static double fp32_midpoint_margin(double d)
+{
+    float f = (float)d;
+    double lo = 0.5 * ((double)f + (double)nextafterf(f, 0.0f));
+    double hi = 0.5 * ((double)f + (double)nextafterf(f, INFINITY));
+    return fmin(fabs(d - lo), fabs(hi - d)) / d;
 }
 
 /* the pixel's ordered list: visible Gaussians whose rectangle holds tile (tx,ty) */
@@ -477,7 +490,7 @@ static int64_t pixel_list(const oproj *P, int64_t n, int tx, int ty, dkey *buf)
         const oproj *o = &P[i];
         if (!o->visible) continue;
         if (tx < o->rect[0] || tx >= o->rect[2] || ty < o->rect[1] || ty >= o->rect[3]) continue;
-        buf[m].depth = o->depth;
+        buf[m].key = (float)o->depth;
         buf[m].idx = i;
         ++m;
     }
@@ -495,7 +508,7 @@ typedef struct {
 /* Walks the list front to back for pixel (u,v); returns the number of tape
  * entries (contributing Gaussians).  Reading D5 for the skip / stop rules. */
 /* margins of one pixel, each the min over its walk of |quantity - threshold| / scale */
-enum { MG_POWER = 0, MG_ALPHA = 1, MG_STOP = 2, MG_TIE = 3, MG_CLAMP = 4, MG_COUNT = 5 };
+enum { MG_POWER = 0, MG_ALPHA = 1, MG_STOP = 2, MG_TIE = 3, MG_CLAMP = 4, MG_TIE3 = 5, MG_COUNT = 6 };
 
 /* A forward decision's margin is recorded only when flipping it could change
  * the pixel by at least this much (0: record every decision).  Bounds used:
@@ -506,15 +519,16 @@ static double g_cmax = 1.0;  /* largest colour channel of the current render */
 
 void oracle_set_margin_impact(double impact) { g_margin_impact = impact > 0.0 ? impact : 0.0; }
 
-static int64_t blend_pixel(const oproj *P, const dkey *list, int64_t m, int u, int vpix,
+static int64_t blend_pixel(const oproj *P, int64_t n4, const dkey *list, int64_t m, int u, int vpix,
                            const double bg[3], double rgb[3], double *T_out, int32_t *last_out,
                            double mg_out[MG_COUNT], tape_ent *tape)
 {
     double T = 1.0, C[3] = { 0, 0, 0 };
-    double mgn[MG_COUNT] = { INFINITY, INFINITY, INFINITY, INFINITY, INFINITY };
+    double mgn[MG_COUNT] = { INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY };
     int32_t last = 0;
     int64_t nt = 0;
     double prev_depth = -1.0;  /* depth, T, alpha, colour of the previous Gaussian that touched the pixel */
+    int prev_3d = 0;
     double prev_T = 0.0, prev_alpha = 0.0;
     const double *prev_rgb = NULL;
     const double imp = g_margin_impact;
@@ -533,14 +547,31 @@ static int64_t blend_pixel(const oproj *P, const dkey *list, int64_t m, int u, i
             mgn[MG_ALPHA] = dmin(mgn[MG_ALPHA], fabs(raw - ALPHA_MIN) / ALPHA_MIN);
         mgn[MG_CLAMP] = dmin(mgn[MG_CLAMP], fabs(raw - ALPHA_MAX_CLAMP) / ALPHA_MAX_CLAMP);
         if (raw >= ALPHA_MIN) {
-            /* two touching Gaussians at (nearly) equal depth: their order is a decision too */
+            /* two touching Gaussians at nearly equal depth: their order is a decision too.
+             * Keys are FP32 depths.  A 3D Gaussian's depth is a dot product of FP32
+             * inputs, which a compensated evaluation rounds exactly; two of them swap
+             * only if one depth sits at an FP32 rounding boundary while their keys are
+             * at most one step apart (MG_TIE3).  A sliced 4D Gaussian's depth carries
+             * the FP32 rounding of the slice: any FP64 gap below a few FP32 steps is a
+             * decision (MG_TIE); an exact FP64 tie comes only from equal inputs and is
+             * resolved by the merged index on both sides. */
             double a_cur = raw < ALPHA_MAX_CLAMP ? raw : ALPHA_MAX_CLAMP;
+            const int cur_3d = list[j].idx >= n4;
             if (prev_depth > 0.0) {
                 double dc = 0.0;
                 for (int ch = 0; ch < 3; ++ch) dc = fmax(dc, fabs(o->rgb[ch] - prev_rgb[ch]));
-                if (prev_T * prev_alpha * a_cur * dc >= imp)
-                    mgn[MG_TIE] = dmin(mgn[MG_TIE], fabs(o->depth - prev_depth) / o->depth);
+                if (prev_T * prev_alpha * a_cur * dc >= imp) {
+                    if (cur_3d && prev_3d) {
+                        float kp = (float)prev_depth, kc = (float)o->depth;
+                        if (kc <= nextafterf(kp, INFINITY))
+                            mgn[MG_TIE3] = dmin(mgn[MG_TIE3], fmin(fp32_midpoint_margin(prev_depth),
+                                                                   fp32_midpoint_margin(o->depth)));
+                    } else if (o->depth != prev_depth) {
+                        mgn[MG_TIE] = dmin(mgn[MG_TIE], fabs(o->depth - prev_depth) / o->depth);
+                    }
+                }
             }
+            prev_3d = cur_3d;
             prev_depth = o->depth;
             prev_T = T;
             prev_alpha = a_cur;
@@ -575,8 +606,9 @@ static int64_t blend_pixel(const oproj *P, const dkey *list, int64_t m, int u, i
 
 /* Render the given pixels (flat indices v*W+u; NULL = the whole image).
  * rgb is [3][npix] planar, T and last are [npix]; margins (may be NULL) is
- * [5][npix]: power sign, alpha skip, transmittance stop, depth order of two
- * touching Gaussians, alpha clamp (the last only matters to gradients). */
+ * [6][npix]: power sign, alpha skip, transmittance stop, depth order of two
+ * touching Gaussians (one of them 4D), alpha clamp (only matters to gradients),
+ * depth order of two touching 3D Gaussians (FP32 rounding boundary). */
 void oracle_render(const og3 *g3, const og4 *g4, const oview *v, const int64_t *pix, int64_t npix,
                    double *rgb, double *T, int32_t *last, double *margins)
 {
@@ -597,7 +629,7 @@ void oracle_render(const og3 *g3, const og4 *g4, const oview *v, const int64_t *
             int u = (int)(p % v->W), vv = (int)(p / v->W);
             int64_t m = pixel_list(P, n, u / TILE, vv / TILE, buf);
             double c3[3], mg[MG_COUNT];
-            blend_pixel(P, buf, m, u, vv, v->bg, c3, &T[q], &last[q], mg, NULL);
+            blend_pixel(P, g4 ? g4->n : 0, buf, m, u, vv, v->bg, c3, &T[q], &last[q], mg, NULL);
             for (int ch = 0; ch < 3; ++ch) rgb[ch * npix + q] = c3[ch];
             if (margins)
                 for (int k = 0; k < MG_COUNT; ++k) margins[k * npix + q] = mg[k];
@@ -911,7 +943,7 @@ void oracle_render_bwd(const og3 *g3, const og4 *g4, const oview *v, const doubl
             int64_t m = pixel_list(P, n, u / TILE, vv / TILE, buf);
             double c3[3], T;
             int32_t last;
-            int64_t nt = blend_pixel(P, buf, m, u, vv, v->bg, c3, &T, &last, NULL, tape);
+            int64_t nt = blend_pixel(P, g4 ? g4->n : 0, buf, m, u, vv, v->bg, c3, &T, &last, NULL, tape);
             blend_pixel_bwd(P, tape, nt, T, v->bg, g, dproj);
         }
         free(tape);

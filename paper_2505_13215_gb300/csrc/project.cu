@@ -41,11 +41,35 @@ struct Ewa {
     float det;
 };
 
+// r . m + t in FP32 with compensated products and sums (the Dot2 scheme of
+// Ogita, Rump and Oishi, 2005): the result is the FP32 rounding of the exact
+// value unless that value lies within ~1e-13 x (|r0 m0| + |r1 m1| + |r2 m2| + |t|)
+// of a rounding boundary.  Used for the
+// camera depth, whose float bits are the sort key: Gaussians whose exact depths
+// round to the same FP32 number then tie exactly and keep their merged-index
+// order, whatever the evaluation order.
+__device__ __forceinline__ float dot3_exact_rounded(const float r[3], const float m[3], float t)
+{
+    float s = t, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float p = __fmul_rn(r[k], m[k]);
+        const float pe = __fmaf_rn(r[k], m[k], -p);  // product error, exact
+        const float s2 = __fadd_rn(s, p);
+        const float bv = __fsub_rn(s2, s);
+        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(p, bv));  // sum error, exact
+        s = s2;
+        c = __fadd_rn(c, __fadd_rn(pe, se));
+    }
+    return __fadd_rn(s, c);
+}
+
 __device__ __forceinline__ void ewa_setup(const ViewParams& vp, const float mu[3], const Sym3& S, Ewa& e)
 {
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < 2; ++r)
         e.xc[r] = vp.R[r * 3 + 0] * mu[0] + vp.R[r * 3 + 1] * mu[1] + vp.R[r * 3 + 2] * mu[2] + vp.T[r];
+    e.xc[2] = dot3_exact_rounded(&vp.R[6], mu, vp.T[2]);
     e.z = e.xc[2];
     const float iz = 1.f / e.z;
     e.ux = e.xc[0] * iz;

@@ -27,7 +27,9 @@ O.set_margin_impact(1e-4)
 EPS_RECT = 1e-6
 EPS_RADIUS = 1e-6
 EPS_CULL = 3e-5
-EPS_PIXEL = {"power": 1e-5, "alpha": 5e-5, "stop": 5e-5, "tie": 1e-6}
+# tie3: a 3D Gaussian's depth is rounded to FP32 exactly by the kernel's
+# compensated dot product, up to ~1e-12 of the depth for the scenes here
+EPS_PIXEL = {"power": 1e-5, "alpha": 5e-5, "stop": 5e-5, "tie": 1e-6, "tie3": 1e-10}
 EPS_CLAMP = 5e-5      # alpha clamp at 0.99: a kink of the gradient only
 EPS_GRAD_GAUSS = 3e-5  # Jacobian clamp, rgb clamp: kinks of one Gaussian's gradient
 RGB_TOL = 2e-4        # max-abs on colours in [0, 1]

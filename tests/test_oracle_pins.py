@@ -5,6 +5,7 @@ footprints, sphere quadrature and central finite differences.
 Each check is chosen so that a plausible slip in the oracle (a dropped term, a
 wrong sign or index, a transposed operand) fails at least one of them.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -426,6 +427,32 @@ def test_two_splats_order_by_depth():
     np.testing.assert_allclose(r1["rgb"].reshape(3, 64, 64)[:, v, u], c1, atol=1e-14)
 
 
+def test_depth_key_is_fp32_then_merged_index():
+    """Reading D6: the sort key holds the depth as an FP32 number (Alg. 1 sorts
+    tile|depth keys), so two splats whose depths round to the same FP32 value are
+    composited in merged-index order even when FP64 puts them the other way."""
+    th = 1e-3
+    view = scenes.identity_view(64, 64, 64.0, 0.0)
+    R = np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+    view = dataclasses.replace(view, R=R)
+    a = one_splat([0.0, 0.0, 3.0], [-1.5] * 3, 1.0, dc=(1.0, 0.0, 0.0))
+    b = one_splat([-1e-5, 0.0, 3.0], [-1.5] * 3, 1.0, dc=(0.0, 1.0, 0.0))  # 1e-8 farther
+    Pa, Pb = O.project(a, view)[0], O.project(b, view)[0]
+    assert Pb["depth"] > Pa["depth"] and np.float32(Pb["depth"]) == np.float32(Pa["depth"])
+    u, v = int(Pa["px"]), int(Pa["py"])
+    pix = [v * 64 + u]
+    alpha = {}
+    for name, P in (("a", Pa), ("b", Pb)):
+        dx, dy = P["px"] - u, P["py"] - v
+        ca, cb, cc = P["conic"]
+        alpha[name] = min(0.99, P["alpha"] * math.exp(-0.5 * (ca * dx * dx + cc * dy * dy) - cb * dx * dy))
+    for first, second, scene in (("b", "a", cat(b, a)), ("a", "b", cat(a, b))):
+        P = {"a": Pa, "b": Pb}
+        want = P[first]["rgb"] * alpha[first] + P[second]["rgb"] * alpha[second] * (1 - alpha[first])
+        got = O.render(scene, view, pixels=pix)["rgb"][:, 0]
+        np.testing.assert_allclose(got, want, atol=1e-14)
+
+
 def test_transmittance_stop_and_bounds():
     """Final T stays in [1e-4, 1], composite colour <= (1 - T) max c for a black
     background, and 'last' counts the walk."""
@@ -444,7 +471,7 @@ def test_transmittance_monotone_along_list():
     P = O.project(scene, v)
     for (tx, ty) in [(3, 3), (4, 2), (0, 7)]:
         ids = O.tile_list(scene, v, tx, ty)
-        assert np.all(np.diff(P["depth"][ids]) >= 0)
+        assert np.all(np.diff(P["depth"][ids].astype(np.float32)) >= 0)
         u, vv = tx * 16 + 5, ty * 16 + 9
         T = 1.0
         for i in ids:
