@@ -179,10 +179,10 @@ def algorithmic_bytes(stage, n3, n4, V, pix, K, elem):
 
 # FP32 operations per pixel-Gaussian pair on each path of the compositing
 # kernels, counted from their source (FMA = 2): evaluating the power (dy and two
-# FMA) costs 5; a blended pair costs 18 in the forward (exp, alpha, transmittance,
-# colour) and 37 in the backward (replayed T, colour and alpha gradients, moments).
+# FMA) costs 5; a blended pair costs 17 in the forward (exp2, alpha, transmittance,
+# colour) and 35 in the backward (replayed T, colour and alpha gradients, moments).
 FLOPS_EVAL = 5
-FLOPS_BLEND = {"composite_fwd": 18, "composite_bwd": 37}
+FLOPS_BLEND = {"composite_fwd": 17, "composite_bwd": 35}
 KERNEL_SOURCES = {"composite_fwd": ["composite.cu", "splat_internal.cuh"],
                   "composite_bwd": ["composite.cu", "splat_internal.cuh"],
                   "slice_project": ["project.cu", "splat_internal.cuh"],

@@ -251,7 +251,7 @@ splat_status splat_composite_fwd(const splat_proj *proj, const splat_bins *bins,
  * dL_drgb (same layout as img->rgb).  Replays each pixel back to front from
  * its stored final_T and last (T_i = T_{i+1} / (1 - alpha_i)); no per-splat
  * state is stored by the forward.  Writes the 2D gradients to dproj (caller
- * memory [V*N][12] f32, or workspace when dproj is NULL): per row
+ * memory [V*N][12] f32, 16-byte aligned, or workspace when dproj is NULL): per row
  * (dpx, dpy, da, db, dc, dalpha_max, dr, dg, db, 0, 0, 0), then chains them
  * through the colour, EWA, slicing and covariance of every Gaussian and
  * OVERWRITES dg3 / dg4 with the gradient summed over the V views.  With

@@ -284,6 +284,7 @@ splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins,
     if (!adj_only && (!bins || !img || !dL_drgb || !img->final_T || !img->last || !bins->ranges))
         return SPLAT_ERR_INVALID_ARG;
     if (adj_only && !dproj) return SPLAT_ERR_INVALID_ARG;
+    if (dproj && !aligned(dproj, 16)) return SPLAT_ERR_INVALID_ARG;
     if (!stop2d) {
         if (!valid_g3(g3) || !valid_g4(g4) || proj->n != g3.n + g4.n) return SPLAT_ERR_INVALID_ARG;
         if (g3.n > 0 && (!dg3 || !dg3->mean || !dg3->log_scale || !dg3->quat || !dg3->opacity || !dg3->sh))

@@ -13,28 +13,41 @@
 //
 // The adjoint walks the same list back to front from each pixel's stored last
 // contributor, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
-// transmittance.  Per Gaussian the 9 gradient components of all the warp's
-// pixels are summed with a 14-shuffle reduce-scatter and written with one
-// global atomic per component.
+// transmittance.  Per Gaussian each lane keeps 9 sums over its pixels; batches
+// of kRedBatch Gaussians are summed over the warp through shared memory and
+// added to the 2D gradients with one vector atomic per 4 components.
 #include "splat_internal.cuh"
 
 namespace splat {
 
 constexpr int kCompWarps = 4;  // warps (units) per CTA
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2x2 = 1.3862943611198906f;  // 2 ln 2: converts the staged log2-scaled conic back
 
-// Projected features of one Gaussian as staged in shared memory; pcut =
-// log(1/(255 alpha_max)) turns the alpha < 1/255 skip into a test on the power
-// that forward and backward evaluate identically.
+// 2^x by the PTX approximate base-2 exponential (relative error about 2^-22)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Projected features of one Gaussian as staged in shared memory.  The conic is
+// staged scaled by -log2(e)/2 (a2, c2) and -log2(e) (b2), so that
+// p2 = a2 dx^2 + b2 dx dy + c2 dy^2 is the power in base 2 and
+// alpha = alpha_max 2^p2 needs no extra multiply; pcut2 = log2(1/(255 alpha_max))
+// turns the alpha < 1/255 skip into a test on p2.  Forward and backward take
+// every decision (p2 > 0, p2 < pcut2, the clamp, the stop) on the same values.
 struct Feat {
-    float px, py, a, b, c, op, r, g, bl, pcut;
+    float px, py, a2, b2, c2, op, r, g, bl, pcut2;
 };
 
 __device__ __forceinline__ void load_feat(const float4* s, Feat& f)
 {
     const float4 f0 = s[0], f1 = s[1], f2 = s[2];
-    f.px = f0.x; f.py = f0.y; f.a = f0.z; f.b = f0.w;
-    f.c = f1.x; f.op = f1.y; f.r = f1.z; f.g = f1.w;
-    f.bl = f2.x; f.pcut = f2.y;
+    f.px = f0.x; f.py = f0.y; f.a2 = f0.z; f.b2 = f0.w;
+    f.c2 = f1.x; f.op = f1.y; f.r = f1.z; f.g = f1.w;
+    f.bl = f2.x; f.pcut2 = f2.y;
 }
 
 __device__ __forceinline__ void stage_feat(const splat_proj& proj, uint32_t row, float4* s)
@@ -42,11 +55,10 @@ __device__ __forceinline__ void stage_feat(const splat_proj& proj, uint32_t row,
     const float2 xy = ((const float2*)proj.xy)[row];
     const float4 co = ((const float4*)proj.conic_opacity)[row];
     const float4 rd = ((const float4*)proj.rgb_depth)[row];
-    // power below log(1/(255 alpha_max)) cannot reach alpha = 1/255
-    const float pcut = __logf(kAlphaMin / co.w);
-    s[0] = make_float4(xy.x, xy.y, co.x, co.y);
-    s[1] = make_float4(co.z, co.w, rd.x, rd.y);
-    s[2] = make_float4(rd.z, pcut, 0.f, 0.f);
+    const float pcut2 = __log2f(kAlphaMin / co.w);
+    s[0] = make_float4(xy.x, xy.y, -0.5f * kLog2e * co.x, -kLog2e * co.y);
+    s[1] = make_float4(-0.5f * kLog2e * co.z, co.w, rd.x, rd.y);
+    s[2] = make_float4(rd.z, pcut2, 0.f, 0.f);
 }
 
 __device__ __forceinline__ int find_view(const ViewBatch& vb, int tile)
@@ -79,7 +91,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     const int u = tx * kTile + (lane & 15);
     const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
     const float uf = (float)u;
-    float T[PPL], C[PPL][3];
+    // yk[k]: row of pixel k, +inf once the pixel is done (outside the image or
+    // saturated): dy = -inf then makes p2 = -inf, which the skip test rejects
+    float T[PPL], C[PPL][3], yk[PPL];
     int last[PPL];
     unsigned done = 0;
 #pragma unroll
@@ -87,7 +101,11 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
         T[k] = 1.f;
         C[k][0] = C[k][1] = C[k][2] = 0.f;
         last[k] = 0;
-        if (u >= vp.W || y0 + 2 * k >= vp.H) done |= 1u << k;
+        yk[k] = (float)(y0 + 2 * k);
+        if (u >= vp.W || y0 + 2 * k >= vp.H) {
+            done |= 1u << k;
+            yk[k] = __int_as_float(0x7f800000);
+        }
     }
     const uint2 rg = ranges[tile];
     const unsigned all_done = (1u << PPL) - 1;
@@ -100,23 +118,24 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
         __syncwarp();
         const int n = (int)min(32u, rg.y - b);
         if (done != all_done) {
+            const int pos0 = (int)(b - rg.x) + 1;
             for (int j = 0; j < n; ++j) {
                 Feat f;
                 load_feat(sf + j * 3, f);
                 const float dx = f.px - uf;
-                const float A = -0.5f * f.a * dx * dx, Bx = -f.b * dx, Cc = -0.5f * f.c;
+                const float A2 = f.a2 * dx * dx, Bx2 = f.b2 * dx;
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
-                    if (done & (1u << k)) continue;
-                    const float dy = f.py - (float)(y0 + 2 * k);
-                    const float power = A + dy * (Bx + Cc * dy);
-                    if (STATS) ++n_eval;
-                    // skip power > 0 and alpha < 1/255, the latter as power < log(1/(255 alpha_max))
-                    if (power > 0.f || power < f.pcut) continue;
-                    const float alpha = fminf(kAlphaClamp, f.op * __expf(power));
+                    const float dy = f.py - yk[k];
+                    const float p2 = A2 + dy * (Bx2 + f.c2 * dy);
+                    if (STATS) n_eval += (done >> k & 1u) ^ 1u;
+                    // skip power > 0 and alpha < 1/255 (as p2 < pcut2); NaN and -inf skip too
+                    if (!(p2 <= 0.f && p2 >= f.pcut2)) continue;
+                    const float alpha = fminf(kAlphaClamp, f.op * ex2_approx(p2));
                     const float tT = T[k] * (1.f - alpha);
                     if (tT < kTMin) {
                         done |= 1u << k;
+                        yk[k] = __int_as_float(0x7f800000);
                         continue;
                     }
                     if (STATS) ++n_blend;
@@ -125,7 +144,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
                     C[k][1] += f.g * w;
                     C[k][2] += f.bl * w;
                     T[k] = tT;
-                    last[k] = (int)(b - rg.x) + j + 1;
+                    last[k] = pos0 + j;
                 }
                 if (done == all_done) break;
             }
@@ -154,30 +173,59 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     }
 }
 
-// Sum 8 values over the warp; afterwards lanes 4m..4m+3 hold the total of value m.
-__device__ __forceinline__ float reduce_scatter8(const float v[8], int lane)
+// Gradient sums of a batch of kRedBatch Gaussians over the warp's 32 lanes.
+// Each lane leaves 12 floats per Gaussian in shared memory, as three float4
+// groups:
+//   g0 = (S dx W0, W1, S dx^2 W0, S dx W1)   g1 = (W2, W0, dr, dg)   g2 = (db, 0, 0, 0)
+// (W0, W1, W2: the lane's moments of dL/dpower, 1, dy, dy^2, over its pixels;
+// dx is the lane's own).  Lane 6 jj + 2 g + h sums group g of Gaussian jj over
+// source lanes 16 h .. 16 h + 15, the lane pair adds up, and the h = 0 lane
+// turns the sums into the Gaussian's dproj components (4 g .. 4 g + 3) and adds
+// them with one vector atomic.
+constexpr int kRedBatch = 4;
+
+__device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint32_t pend_row, int pend_j,
+                                                const float4* sf, float* dproj, int lane)
 {
-    float h[4];
-    const bool b4 = lane & 16;
+    __syncwarp();
+    const int jj = lane / 6, rem = lane - 6 * jj, g = rem >> 1, h = rem & 1;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (jj < nq) {
+        // source lane 16 h + (i ^ x): the quarter-warp's loads fall in distinct banks
+        const float4* col = red + (jj * 3 + g) * 32 + 16 * h;
+        const int x = lane & 7;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = b4 ? v[i] : v[i + 4];
-        const float keep = b4 ? v[i + 4] : v[i];
-        h[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        for (int i = 0; i < 16; ++i) {
+            const float4 t = col[i ^ x];
+            acc.x += t.x;
+            acc.y += t.y;
+            acc.z += t.z;
+            acc.w += t.w;
+        }
     }
-    float q[2];
-    const bool b3 = lane & 8;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = b3 ? h[i] : h[i + 2];
-        const float keep = b3 ? h[i + 2] : h[i];
-        q[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, 1);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, 1);
+    const int src = jj < kRedBatch ? jj : 0;
+    const uint32_t row = __shfl_sync(0xffffffffu, pend_row, src);
+    const int jv = __shfl_sync(0xffffffffu, pend_j, src);
+    if (jj < nq && h == 0) {
+        float4 out;
+        if (g == 2) {
+            out = make_float4(acc.x, 0.f, 0.f, 0.f);  // db (colour); the row's padding stays zero
+        } else {
+            const float4 f0 = sf[jv * 3], f1 = sf[jv * 3 + 1];
+            if (g == 0) {  // dpx, dpy, da, db with the natural-unit conic (a, b, c)
+                const float ca = -kLn2x2 * f0.z, cb = -0.5f * kLn2x2 * f0.w, cc = -kLn2x2 * f1.x;
+                out = make_float4(-(ca * acc.x + cb * acc.y), -(cc * acc.y + cb * acc.x), -0.5f * acc.z, -acc.w);
+            } else {  // dc, dalpha_max = W0 / alpha_max (unclamped pairs only), dr, dg
+                out = make_float4(-0.5f * acc.x, acc.y / f1.y, acc.z, acc.w);
+            }
+        }
+        atomicAdd((float4*)(dproj + (int64_t)row * 12) + g, out);
     }
-    const bool b2 = lane & 4;
-    float x = (b2 ? q[1] : q[0]) + __shfl_xor_sync(0xffffffffu, b2 ? q[0] : q[1], 4);
-    x += __shfl_xor_sync(0xffffffffu, x, 2);
-    x += __shfl_xor_sync(0xffffffffu, x, 1);
-    return x;
+    __syncwarp();
 }
 
 // STATS: also count the pairs evaluated and blended into stats[2..3].
@@ -191,6 +239,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
     constexpr int BANDS = 8 / PPL;
     __shared__ float4 s_feat[kCompWarps][32][3];
     __shared__ uint32_t s_row[kCompWarps][32];
+    __shared__ float4 s_red[kCompWarps][kRedBatch * 3][32];
     if (status_failed(status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
@@ -208,12 +257,13 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
     // the colour accumulated behind the current Gaussian, S = sum_{i>j} c_i alpha_i T_i
     // + T_final bg.  dL/dalpha_j = T_j <G, c_j> - GS / (1 - alpha_j), and GS grows by
     // alpha_j T_j <G, c_j>, so S itself is never needed per channel.
-    float T[PPL], GS[PPL], G[PPL][3];
+    float T[PPL], GS[PPL], G[PPL][3], yk[PPL];
     int last[PPL];
     int maxlast = 0;
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
         const int y = y0 + 2 * k;
+        yk[k] = (float)y;
         last[k] = 0;
         T[k] = 1.f;
         GS[k] = 0.f;
@@ -235,6 +285,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
     if (maxlast == 0) return;
     const uint2 rg = ranges[tile];
     float4* sf = &s_feat[warp][0][0];
+    float4* red = &s_red[warp][0][0];
     const int nb = (maxlast + 31) / 32;
     unsigned n_eval = 0, n_blend = 0;
     for (int bi = nb - 1; bi >= 0; --bi) {
@@ -248,67 +299,63 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj pr
         }
         __syncwarp();
         const int n = (int)min(32u, end - b);
+        int nq = 0;            // Gaussians waiting in the reduction buffer
+        uint32_t pend_row = 0; // lane q: row of waiting Gaussian q
+        int pend_j = 0;        // lane q: its slot in the staged batch
         for (int j = n - 1; j >= 0; --j) {
             Feat f;
             load_feat(sf + j * 3, f);
             const int li = 32 * bi + j;  // position in the tile list
             const float dx = f.px - uf;
-            const float A = -0.5f * f.a * dx * dx, Bx = -f.b * dx, Cc = -0.5f * f.c;
-            // per lane: dL/dalpha_max and dL/drgb summed over its pixels, and the moments
-            // W0 = sum dL/dpower, W1 = sum dL/dpower dy, W2 = sum dL/dpower dy^2 from which
-            // the gradients of the mean and the conic follow (dx is the lane's own)
-            float acc[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) acc[q] = 0.f;
-            float W0 = 0.f, W1 = 0.f, W2 = 0.f;
+            const float A2 = f.a2 * dx * dx, Bx2 = f.b2 * dx;
+            // per lane, over its pixels: dL/drgb and the moments W0 = sum dL/dpower,
+            // W1 = sum dL/dpower dy, W2 = sum dL/dpower dy^2
+            float W0 = 0.f, W1 = 0.f, W2 = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                if (li >= last[k]) continue;
-                const float dy = f.py - (float)(y0 + 2 * k);
-                const float power = A + dy * (Bx + Cc * dy);
-                if (STATS) ++n_eval;
-                if (power > 0.f || power < f.pcut) continue;  // the forward's skip, bit for bit
-                const float Gs = __expf(power);
-                const float raw = f.op * Gs;
+                const float dy = f.py - yk[k];
+                const float p2 = A2 + dy * (Bx2 + f.c2 * dy);
+                if (STATS) n_eval += li < last[k];
+                // the forward's skip, bit for bit, on the pixels that reached this Gaussian
+                if (!(li < last[k] && p2 <= 0.f && p2 >= f.pcut2)) continue;
+                const float raw = f.op * ex2_approx(p2);
                 const float alpha = fminf(kAlphaClamp, raw);
                 if (STATS) ++n_blend;
                 any = true;
                 const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
                 const float Tj = T[k] * iom;
                 const float w = alpha * Tj;
-                acc[6] += w * G[k][0];
-                acc[7] += w * G[k][1];
-                acc[8] += w * G[k][2];
+                cr += w * G[k][0];
+                cg += w * G[k][1];
+                cb += w * G[k][2];
                 const float gc = G[k][0] * f.r + G[k][1] * f.g + G[k][2] * f.bl;
                 const float dLda = Tj * gc - GS[k] * iom;
                 GS[k] += w * gc;
                 T[k] = Tj;
-                if (raw < kAlphaClamp) {
-                    const float dpow = dLda * alpha;
-                    acc[5] += dLda * Gs;
-                    const float t = dpow * dy;
-                    W0 += dpow;
-                    W1 += t;
-                    W2 += t * dy;
-                }
+                // dL/dpower = dL/dalpha * alpha where alpha is not clamped
+                const float dpow = raw < kAlphaClamp ? dLda * alpha : 0.f;
+                const float t = dpow * dy;
+                W0 += dpow;
+                W1 += t;
+                W2 += t * dy;
             }
-            // power = -(a dx^2 + c dy^2)/2 - b dx dy with (dx, dy) = mean - pixel
-            acc[0] = -(f.a * dx * W0 + f.b * W1);
-            acc[1] = -(f.c * W1 + f.b * dx * W0);
-            acc[2] = -0.5f * dx * dx * W0;
-            acc[3] = -dx * W1;
-            acc[4] = -0.5f * W2;
-            if (__any_sync(0xffffffffu, any)) {
-                const float r8 = reduce_scatter8(acc, lane);
-                float r9 = acc[8];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) r9 += __shfl_xor_sync(0xffffffffu, r9, o);
-                float* dst = dproj + (int64_t)s_row[warp][j] * 12;
-                if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), r8);
-                if (lane == 0) atomicAdd(dst + 8, r9);
+            if (!__any_sync(0xffffffffu, any)) continue;
+            float4* slot = red + nq * 3 * 32 + lane;
+            const float dxW0 = dx * W0;
+            slot[0] = make_float4(dxW0, W1, dx * dxW0, dx * W1);
+            slot[32] = make_float4(W2, W0, cr, cg);
+            slot[64] = make_float4(cb, 0.f, 0.f, 0.f);
+            if (lane == nq) {
+                pend_row = s_row[warp][j];
+                pend_j = j;
+            }
+            if (++nq == kRedBatch) {
+                flush_reduction(red, nq, pend_row, pend_j, sf, dproj, lane);
+                nq = 0;
             }
         }
+        if (nq) flush_reduction(red, nq, pend_row, pend_j, sf, dproj, lane);
         __syncwarp();
     }
     if (STATS) {

@@ -35,6 +35,30 @@ constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
 // Exclusive scan of one value per thread across a 256-thread block.
+__device__ __forceinline__ unsigned long long block_excl_scan256_u64(unsigned long long v, unsigned long long* s_tmp,
+                                                                     unsigned long long* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_tmp[warp] = x;
+    __syncthreads();
+    unsigned long long wsum = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const unsigned long long t = s_tmp[w];
+        if (w < warp) wsum += t;
+        all += t;
+    }
+    __syncthreads();
+    *total = all;
+    return wsum + x - v;
+}
+
 __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_tmp, uint32_t* total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -275,7 +299,7 @@ __device__ __forceinline__ uint32_t row_count(const ScanArgs& a, uint32_t row)
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
 {
-    __shared__ uint32_t s_tmp[8];
+    __shared__ unsigned long long s_tmp64[8];
     __shared__ int64_t s_ticket;
     __shared__ unsigned long long s_excl;
     constexpr unsigned long long kA = 1ull << 62, kP = 2ull << 62, kM = (1ull << 62) - 1;
@@ -288,17 +312,29 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
         const int64_t ticket = s_ticket;
         if (ticket >= parts) break;
         const int64_t base = ticket * kScanPart;
-        unsigned long long local[kScanItems];
-        unsigned long long running = 0;  // total of the earlier rounds of this partition
+        // blocked layout: thread tid owns the kScanItems consecutive rows from base + tid * kScanItems,
+        // so one block scan of the per-thread sums serves the whole partition
+        const int64_t i0 = base + (int64_t)tid * kScanItems;
+        uint32_t c[kScanItems];
+        if (i0 + kScanItems <= a.n_rows) {
+            const uint4* r4 = (const uint4*)(a.rows + i0);
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            const int64_t idx = base + (int64_t)j * kScanThreads + tid;
-            const uint32_t c = idx < a.n_rows ? row_count(a, a.rows[idx]) : 0u;
-            uint32_t tot;
-            const uint32_t ex = block_excl_scan256(c, s_tmp, &tot);
-            local[j] = running + ex;
-            running += tot;
+            for (int q = 0; q < kScanItems / 4; ++q) {
+                const uint4 r = r4[q];
+                c[4 * q + 0] = row_count(a, r.x);
+                c[4 * q + 1] = row_count(a, r.y);
+                c[4 * q + 2] = row_count(a, r.z);
+                c[4 * q + 3] = row_count(a, r.w);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) c[j] = i0 + j < a.n_rows ? row_count(a, a.rows[i0 + j]) : 0u;
         }
+        unsigned long long tsum = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) tsum += c[j];
+        unsigned long long running;
+        const unsigned long long texcl = block_excl_scan256_u64(tsum, s_tmp64, &running);
         const unsigned long long agg = running;
         if (tid == 0) {
             unsigned long long excl = 0;
@@ -331,19 +367,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
         }
         __syncthreads();
         const unsigned long long excl = s_excl;
+        unsigned long long off = excl + texcl;
 #pragma unroll
         for (int j = 0; j < kScanItems; ++j) {
-            const int64_t idx = base + (int64_t)j * kScanThreads + tid;
-            if (idx >= a.n_rows) continue;
-            const unsigned long long off = excl + local[j];
-            a.offsets[idx] = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
-            const uint32_t c = row_count(a, a.rows[idx]);
-            if (c == 0) continue;
-            // chunks whose first slot falls inside [off, off + c)
-            const unsigned long long lo = (off + kDupChunk - 1) / kDupChunk;
-            const unsigned long long hi = (off + c - 1) / kDupChunk;
-            for (unsigned long long q = lo; q <= hi && q < (unsigned long long)a.n_chunks_max; ++q)
-                a.chunk_row[q] = (uint32_t)idx;
+            const int64_t idx = i0 + j;
+            if (idx < a.n_rows) {
+                a.offsets[idx] = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
+                if (c[j] != 0 && a.n_chunks_max > 0) {
+                    // chunks whose first slot falls inside [off, off + c)
+                    const unsigned long long lo = (off + kDupChunk - 1) / kDupChunk;
+                    const unsigned long long hi = (off + c[j] - 1) / kDupChunk;
+                    for (unsigned long long q = lo; q <= hi && q < (unsigned long long)a.n_chunks_max; ++q)
+                        a.chunk_row[q] = (uint32_t)idx;
+                }
+            }
+            off += c[j];
         }
         __syncthreads();
     }
@@ -637,13 +675,15 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(BinArgs a)
 }
 
 // Per-tile sums over the view's chunks.  A block covers 32 tiles (lanes,
-// coalesced) x 8 segments of chunks (warps).  Pass 0 writes the tile totals;
-// pass 1 (after k_bin_ranges turned the totals into tile starts) rewrites every
-// count as the absolute first slot of that (chunk, tile).
+// coalesced) x kPrefixSegs segments of chunks (warps).  Pass 0 writes the tile
+// totals; pass 1 (after k_bin_ranges turned the totals into tile starts)
+// rewrites every count as the absolute first slot of that (chunk, tile).
+constexpr int kPrefixSegs = 32;
+
 template <int PASS>
-__global__ void __launch_bounds__(256) k_bin_prefix(BinArgs a)
+__global__ void __launch_bounds__(32 * kPrefixSegs) k_bin_prefix(BinArgs a)
 {
-    __shared__ uint32_t s_seg[8][33];
+    __shared__ uint32_t s_seg[kPrefixSegs][33];
     if (status_failed(a.status)) return;
     const BinPlan& P = *a.plan;
     const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
@@ -654,22 +694,24 @@ __global__ void __launch_bounds__(256) k_bin_prefix(BinArgs a)
         if (gt >= a.tile_base[w]) v = w;
     const int tl = gt - a.tile_base[v];
     const uint32_t cb = P.cbase[v], ce = P.cbase[v + 1];
-    const uint32_t per = (ce - cb + 7) / 8;
+    const uint32_t per = (ce - cb + kPrefixSegs - 1) / kPrefixSegs;
     const uint32_t g0 = min(cb + seg * per, ce), g1 = min(g0 + per, ce);
+    uint32_t* col = a.counts + tl;
     uint32_t sum = 0;
     if (ok) {
         uint32_t g = g0;
         for (; g + 4 <= g1; g += 4) {
-            const uint32_t c0 = a.counts[(size_t)g * a.tmax + tl], c1 = a.counts[(size_t)(g + 1) * a.tmax + tl];
-            const uint32_t c2 = a.counts[(size_t)(g + 2) * a.tmax + tl], c3 = a.counts[(size_t)(g + 3) * a.tmax + tl];
+            const uint32_t c0 = col[(size_t)g * a.tmax], c1 = col[(size_t)(g + 1) * a.tmax];
+            const uint32_t c2 = col[(size_t)(g + 2) * a.tmax], c3 = col[(size_t)(g + 3) * a.tmax];
             sum += c0 + c1 + c2 + c3;
         }
-        for (; g < g1; ++g) sum += a.counts[(size_t)g * a.tmax + tl];
+        for (; g < g1; ++g) sum += col[(size_t)g * a.tmax];
     }
     s_seg[seg][lane] = sum;
     __syncthreads();
     uint32_t base = 0, tot = 0;
-    for (int k = 0; k < 8; ++k) {
+#pragma unroll 8
+    for (int k = 0; k < kPrefixSegs; ++k) {
         const uint32_t x = s_seg[k][lane];
         if (k < seg) base += x;
         tot += x;
@@ -680,32 +722,69 @@ __global__ void __launch_bounds__(256) k_bin_prefix(BinArgs a)
         return;
     }
     uint32_t run = a.tile_total[gt] + base;  // tile start (after k_bin_ranges) + earlier segments
-    for (uint32_t g = g0; g < g1; ++g) {
-        uint32_t* p = a.counts + (size_t)g * a.tmax + tl;
-        const uint32_t c = *p;
-        *p = run;
-        run += c;
+    for (uint32_t g = g0; g < g1; g += 8) {
+        uint32_t c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = g + k < g1 ? col[(size_t)(g + k) * a.tmax] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (g + k < g1) col[(size_t)(g + k) * a.tmax] = run;
+            run += c[k];
+        }
     }
 }
 
 // one block: ranges[t] = [start, start + total); tile_total becomes the start.
-// With K_out, also the instance count K and the capacity check.
+// With K_out, also the instance count K and the capacity check.  Each round
+// stages 256 x kRangeItems tile totals in shared memory with coalesced loads;
+// thread i then scans its kRangeItems consecutive tiles (one block scan per
+// round) and the starts and ranges go back out coalesced.
+constexpr int kRangeItems = 16;
+constexpr int kRangeRound = 256 * kRangeItems;
+
+__device__ __forceinline__ int range_pad(int i) { return i + (i >> 5); }  // conflict-free strided reads
+
 __global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, int64_t capacity)
 {
-    __shared__ uint32_t s_tmp[8];
+    __shared__ uint32_t s_c[kRangeRound + kRangeRound / 32], s_st[kRangeRound + kRangeRound / 32];
+    __shared__ unsigned long long s_tmp64[8];
     if (status_failed(a.status)) return;
     unsigned long long carry = 0;
-    for (int base = 0; base < a.total_tiles; base += 256) {
-        const int t = base + threadIdx.x;
-        const uint32_t c = t < a.total_tiles ? a.tile_total[t] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan256(c, s_tmp, &tot);
-        const uint32_t st = (uint32_t)(carry + ex);
-        if (t < a.total_tiles) {
-            a.ranges[t] = c ? make_uint2(st, st + c) : make_uint2(0u, 0u);
-            a.tile_total[t] = st;
+    const int n = a.total_tiles;
+    for (int base = 0; base < n; base += kRangeRound) {
+#pragma unroll
+        for (int q = 0; q < kRangeItems; ++q) {
+            const int i = q * 256 + threadIdx.x;
+            s_c[range_pad(i)] = base + i < n ? a.tile_total[base + i] : 0u;
+        }
+        __syncthreads();
+        uint32_t c[kRangeItems];
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int k = 0; k < kRangeItems; ++k) {
+            c[k] = s_c[range_pad(threadIdx.x * kRangeItems + k)];
+            sum += c[k];
+        }
+        unsigned long long tot;
+        // slots past 2^32 only arise with K beyond any capacity: the check below reports them
+        uint32_t st = (uint32_t)(carry + block_excl_scan256_u64(sum, s_tmp64, &tot));
+#pragma unroll
+        for (int k = 0; k < kRangeItems; ++k) {
+            s_st[range_pad(threadIdx.x * kRangeItems + k)] = st;
+            st += c[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kRangeItems; ++q) {
+            const int i = q * 256 + threadIdx.x;
+            if (base + i < n) {
+                const uint32_t ci = s_c[range_pad(i)], si = s_st[range_pad(i)];
+                a.ranges[base + i] = ci ? make_uint2(si, si + ci) : make_uint2(0u, 0u);
+                a.tile_total[base + i] = si;
+            }
         }
         carry += tot;
+        __syncthreads();
     }
     if (K_out && threadIdx.x == 0) {
         *K_out = (int64_t)carry;
@@ -739,6 +818,7 @@ struct TileArgs {
     int cull;                         // drop tiles the opacity footprint cannot reach
     uint32_t* seg_base;               // [total_super + 1] first segment of each super-tile's list
     uint32_t* seg_cnt;                // [segments][64] per-segment tile counts, then offsets
+    uint2* mask;                      // per super-tile list entry: byte w = its tile columns in tile row w
     int32_t* status;
 };
 
@@ -847,17 +927,20 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
 
 // One CTA per segment (kFilterSeg entries) of a super-tile's row list (8x8
 // tiles): it streams the rows in depth order through shared memory; warp w
-// serves tile row w (8 tiles) and keeps a
-// row only for the tiles of its rectangle that its opacity footprint reaches
-// (the footprint enlarged by a margin that covers FP32 rounding, so no pixel
-// result changes).  COUNT: per-(segment, tile) counts.  Otherwise: each tile's
-// list is written contiguously, in order, from the segment's offsets.
+// serves tile row w (8 tiles).
+// COUNT: warp w keeps a row for the tiles of its rectangle in tile row w that
+// its opacity footprint reaches (the footprint enlarged by a margin that covers
+// FP32 rounding, so no pixel result changes), records them as byte w of the
+// entry's coverage word (bit k: tile column k of the super-tile) and counts
+// per (segment, tile).  Write pass: each tile's list is written contiguously,
+// in order, from the segment's offsets, driven by the coverage words alone.
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
 {
-    __shared__ int4 s_rect[256];
-    __shared__ float4 s_g0[256], s_g1[256], s_g2[256];  // footprint constants
-    __shared__ uint32_t s_row[256];
+    __shared__ int4 s_rect[COUNT ? 256 : 1];
+    __shared__ float4 s_g0[COUNT ? 256 : 1], s_g1[COUNT ? 256 : 1], s_g2[COUNT ? 256 : 1];  // footprint constants
+    __shared__ uint32_t s_row[COUNT ? 1 : 256];
+    __shared__ uint2 s_mask[256];
     __shared__ int s_gs;
     if (status_failed(a.status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -898,59 +981,74 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
             const uint32_t j = b + threadIdx.x;
             if (j < rg.y) {
                 const uint32_t row = a.list[j];
-                s_row[threadIdx.x] = row;
-                s_rect[threadIdx.x] = ((const int4*)a.proj.rect)[row];
-                if (a.cull) {
-                    const float2 xy = ((const float2*)a.proj.xy)[row];
-                    const float4 co = ((const float4*)a.proj.conic_opacity)[row];
-                    // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
-                    const float R2 = -2.f * __logf(kAlphaMin / co.w) * 1.0001f + 2e-3f;
-                    float4 g0, g1, g2;
-                    ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1, g2);
-                    s_g0[threadIdx.x] = g0;
-                    s_g1[threadIdx.x] = g1;
-                    s_g2[threadIdx.x] = g2;
+                if (COUNT) {
+                    s_rect[threadIdx.x] = ((const int4*)a.proj.rect)[row];
+                    s_mask[threadIdx.x] = make_uint2(0u, 0u);
+                    if (a.cull) {
+                        const float2 xy = ((const float2*)a.proj.xy)[row];
+                        const float4 co = ((const float4*)a.proj.conic_opacity)[row];
+                        // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
+                        const float R2 = -2.f * __logf(kAlphaMin / co.w) * 1.0001f + 2e-3f;
+                        float4 g0, g1, g2;
+                        ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1, g2);
+                        s_g0[threadIdx.x] = g0;
+                        s_g1[threadIdx.x] = g1;
+                        s_g2[threadIdx.x] = g2;
+                    }
+                } else {
+                    s_row[threadIdx.x] = row;
+                    s_mask[threadIdx.x] = a.mask[j];
                 }
             }
             __syncthreads();
-            if (ty >= TY) continue;
-            const int n = (int)min(256u, rg.y - b);
-            for (int sb = 0; sb < n; sb += 32) {
-                const int e = sb + lane;
-                bool cy = false;
-                uint32_t row = 0;
-                int cx0 = 0, cx1 = 0;  // tile columns kept in this tile row
-                if (e < n) {
-                    const int4 rc = s_rect[e];
-                    row = s_row[e];
-                    cy = rc.y <= ty && ty < rc.w;
-                    cx0 = rc.x;
-                    cx1 = rc.z;
-                    if (cy && a.cull) {
-                        float ul, ur;
-                        if (!ellipse_band_extent(s_g0[e], s_g1[e], s_g2[e], vlo, vhi, ul, ur)) {
-                            cy = false;
+            if (ty < TY) {
+                const int n = (int)min(256u, rg.y - b);
+                for (int sb = 0; sb < n; sb += 32) {
+                    const int e = sb + lane;
+                    unsigned m = 0;  // tile columns of this tile row the entry is listed in
+                    if (e < n) {
+                        if (COUNT) {
+                            const int4 rc = s_rect[e];
+                            if (rc.y <= ty && ty < rc.w) {
+                                int cx0 = rc.x, cx1 = rc.z;
+                                bool cy = true;
+                                if (a.cull) {
+                                    float ul, ur;
+                                    if (!ellipse_band_extent(s_g0[e], s_g1[e], s_g2[e], vlo, vhi, ul, ur)) {
+                                        cy = false;
+                                    } else {
+                                        // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
+                                        const float lo = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
+                                        const float hi = floorf(ur * (1.f / kTile));
+                                        cx0 = max(cx0, (int)fminf(fmaxf(lo, -1.f), 1.0e6f));
+                                        cx1 = min(cx1, (int)fminf(fmaxf(hi, -2.f), 1.0e6f) + 1);
+                                    }
+                                }
+                                const int lo = max(cx0 - tx0, 0), hi = min(cx1 - tx0, 8);
+                                if (cy && hi > lo) m = (1u << hi) - (1u << lo);
+                            }
+                            reinterpret_cast<unsigned char*>(&s_mask[e])[warp] = (unsigned char)m;
                         } else {
-                            // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
-                            const float lo = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
-                            const float hi = floorf(ur * (1.f / kTile));
-                            cx0 = max(cx0, (int)fminf(fmaxf(lo, -1.f), 1.0e6f));
-                            cx1 = min(cx1, (int)fminf(fmaxf(hi, -2.f), 1.0e6f) + 1);
+                            m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu;
                         }
                     }
-                }
+                    const uint32_t row = COUNT ? 0u : s_row[e < n ? e : 0];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int tx = tx0 + k;
-                    const bool cov = cy && cx0 <= tx && tx < cx1;
-                    const unsigned m = __ballot_sync(0xffffffffu, cov);
-                    if (!COUNT && cov) {
-                        const uint32_t pos = cur[k] + __popc(m & lt);
-                        a.vals_out[pos] = row;
-                        if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx);
+                    for (int k = 0; k < 8; ++k) {
+                        const bool cov = (m >> k) & 1u;
+                        const unsigned bal = __ballot_sync(0xffffffffu, cov);
+                        if (!COUNT && cov) {
+                            const uint32_t pos = cur[k] + __popc(bal & lt);
+                            a.vals_out[pos] = row;
+                            if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
+                        }
+                        cur[k] += __popc(bal);
                     }
-                    cur[k] += __popc(m);
                 }
+            }
+            if (COUNT) {
+                __syncthreads();
+                if (j < rg.y) a.mask[j] = s_mask[threadIdx.x];
             }
         }
         if (COUNT) {
@@ -1091,7 +1189,7 @@ struct SortLayout {
     int64_t total_tiles, total_super;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
         off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
-    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt;
+    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_mask;
     int64_t max_segs;
     size_t bytes;
 };
@@ -1154,6 +1252,7 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.max_segs = L.binned ? (capacity + kFilterSeg - 1) / kFilterSeg + L.total_super : 1;
     L.off_segbase = take(4 * (size_t)(L.total_super + 1));
     L.off_segcnt = take(L.binned ? 4 * 64 * (size_t)L.max_segs : 4);
+    L.off_mask = take(L.binned ? 8 * (size_t)capacity : 4);
     L.bytes = o;
     return L;
 }
@@ -1261,7 +1360,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (L.binned) {
-        // tile level: totals from difference arrays, ranges, K and the capacity check
+        // tile level: per-super-tile lists filtered into per-tile lists (see below)
         TileArgs t{};
         t.proj = proj;
         t.V = vb.V;
@@ -1289,6 +1388,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.cull = g_tile_cull;
         t.seg_base = U(L.off_segbase);
         t.seg_cnt = U(L.off_segcnt);
+        t.mask = (uint2*)(w + L.off_mask);
         BinArgs tr{};
         tr.total_tiles = vb.total_tiles;
         tr.tile_total = U(L.off_total);
@@ -1347,9 +1447,9 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         count_launch(7);
         k_bin_plan<<<1, 32, 0, s>>>(a);
         k_bin_count<<<blocks_c, kBinThreads, smem_count, s>>>(a);
-        k_bin_prefix<0><<<(sb + 31) / 32, 256, 0, s>>>(a);
+        k_bin_prefix<0><<<(sb + 31) / 32, 32 * kPrefixSegs, 0, s>>>(a);
         k_bin_ranges<<<1, 256, 0, s>>>(a, nullptr, 0);
-        k_bin_prefix<1><<<(sb + 31) / 32, 256, 0, s>>>(a);
+        k_bin_prefix<1><<<(sb + 31) / 32, 32 * kPrefixSegs, 0, s>>>(a);
         k_bin_scatter<<<blocks_s, 32, smem_scatter, s>>>(a);
         // tile level: segment the super-tile lists, count each (segment, tile),
         // prefix over segments, ranges + K + capacity check, then write the lists
