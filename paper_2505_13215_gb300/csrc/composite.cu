@@ -182,7 +182,17 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
 // source lanes 16 h .. 16 h + 15, the lane pair adds up, and the h = 0 lane
 // turns the sums into the Gaussian's dproj components (4 g .. 4 g + 3) and adds
 // them with one vector atomic.
-constexpr int kRedBatch = 4;
+#ifndef SPLAT_RED_BATCH
+#define SPLAT_RED_BATCH 4
+#endif
+// resident CTAs per SM the backward is compiled for: 7 caps PPL <= 4 at 72
+// registers, without spills; PPL = 8 needs about 125
+template <int PPL>
+struct BwdOccupancy {
+    static constexpr int kMinBlocks = PPL >= 8 ? 4 : 7;
+};
+constexpr int kRedBatch = SPLAT_RED_BATCH;
+static_assert(kRedBatch >= 1 && kRedBatch <= 5, "the flush maps 6 lanes to each batched Gaussian");
 
 __device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint32_t pend_row, int pend_j,
                                                 const float4* sf, float* dproj, int lane)
@@ -230,7 +240,7 @@ __device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint3
 
 // STATS: also count the pairs evaluated and blended into stats[2..3].
 template <int PPL, bool STATS>
-__global__ void __launch_bounds__(kCompWarps * 32) k_composite_bwd(splat_proj proj, const uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks) k_composite_bwd(splat_proj proj, const uint32_t* __restrict__ vals,
                                                                    const uint2* __restrict__ ranges, ViewBatch vb,
                                                                    splat_image img, const float* __restrict__ dL,
                                                                    float* dproj, int32_t* status,
