@@ -178,8 +178,32 @@ enum {
     SPLAT_OP_BIN_SORT = 1,
     SPLAT_OP_COMPOSITE_BWD = 2,
     SPLAT_OP_CONVERT = 3,
-    SPLAT_OP_ALL = 4       /* one workspace good for every entry point           */
+    SPLAT_OP_ALL = 4,      /* one workspace good for every entry point           */
+    SPLAT_OP_CONVERT_STATE = 5
 };
+
+/*
+ * Optimizer state of one parameter set for a training step: FP32 master
+ * values and Adam's first and second moments, one array per field, each
+ * shaped like the field ([rows][width] floats, dense, 16-byte aligned).  Field
+ * order is that of splat_g3 (mean, log_scale, quat, opacity, sh; entries 0-4,
+ * entry 5 unused) or of splat_g4 (mean, log_scale, ql, qr, opacity, sh).  The
+ * arrays of a 3D set have splat_g3.capacity rows.
+ */
+typedef struct {
+    float *param[6];
+    float *m[6];
+    float *v[6];
+} splat_adam_set;
+
+/* Step sizes and Adam constants of one update (host memory). */
+typedef struct {
+    float lr3[5];       /* per 3D field; for sh, the degree-0 coefficients   */
+    float lr4[6];       /* per 4D field; for sh, the degree-0 coefficients   */
+    float lr_sh_rest;   /* SH coefficients of degree 1-3, both sets           */
+    float beta1, beta2, eps;
+    int32_t step;       /* t >= 1, for the bias corrections 1 - beta^t        */
+} splat_adam_hyper;
 
 /* splat_composite_bwd flags */
 #define SPLAT_BWD_STOP_2D 1u      /* stop after the 2D gradients (dproj), skip the adjoint */
@@ -280,6 +304,47 @@ splat_status splat_composite_bwd(const splat_proj *proj, const splat_bins *bins,
  */
 splat_status splat_convert_4d_to_3d(splat_g4 *g4, splat_g3 *g3, float tau, int64_t *n_moved_dev, int32_t *status,
                                     void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Parameter update of a training step (Sec. 4.3 optimises the 3D and the 4D
+ * set in every iteration): one Adam step (Kingma and Ba, 2015) over every
+ * float of the first g3->n rows of each 3D field and g4->n rows of each 4D
+ * field, in one launch:
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ *   p -= lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps),
+ * with g from dg3 / dg4 (as splat_composite_bwd wrote them) and p, m, v in
+ * s3 / s4; then the storage copies g3 / g4 (the arrays the rasterizer reads,
+ * any dtype, round to nearest) receive the new p.  For FP32 storage a field
+ * of g3 / g4 may be the master array itself.  g3->dtype == g4->dtype.  Skips
+ * its work when status already holds an error.
+ */
+splat_status splat_adam_step(const splat_adam_hyper *h, splat_adam_set *s3, const splat_grads3 *dg3, splat_g3 *g3,
+                             splat_adam_set *s4, const splat_grads4 *dg4, splat_g4 *g4, int32_t *status, void *stream);
+
+/*
+ * Storage copies of FP32 master values: the first src3->n rows of every field
+ * of src3 (dtype F32) are rounded to nearest into dst3 (any dtype), likewise
+ * src4 into dst4; dst->n is not read.  After splat_convert_4d_to_3d on the
+ * master sets this refreshes the arrays the rasterizer reads.
+ */
+splat_status splat_cast_params(const splat_g3 *src3, splat_g3 *dst3, const splat_g4 *src4, splat_g4 *dst4,
+                               void *stream);
+
+/*
+ * The optimizer-state side of splat_convert_4d_to_3d (Sec. 4.1-4.2 during
+ * training).  Call it first, with the same g4 / g3 and tau: the decision
+ * exp(s_t) > tau reads g4's log_scale, which the conversion then rewrites.
+ * The moments s4->m / s4->v of the kept 4D Gaussians are compacted in place
+ * like their parameters (order kept); the 3D moments s3->m / s3->v of rows
+ * g3->n .. g3->n + moved - 1, where the converted Gaussians will land, are set
+ * to zero (a converted Gaussian starts with fresh moments, as a Gaussian added
+ * by densification does).  The param arrays are not touched.  Workspace:
+ * splat_workspace_size(SPLAT_OP_CONVERT_STATE, 0, N4, ...).  Capacity overflow
+ * changes nothing and sets SPLAT_ERR_CAPACITY, as the conversion does.
+ */
+splat_status splat_convert_adam_state(const splat_g4 *g4, const splat_g3 *g3, float tau, splat_adam_set *s4,
+                                      splat_adam_set *s3, int32_t *status, void *workspace, size_t workspace_bytes,
+                                      void *stream);
 
 /*
  * L1 photometric loss of a training step (Sec. 4.3 trains the rendered

@@ -8,7 +8,8 @@ Functions follow the paper's equations (see oracle.c for the citations):
   rot4 (Eq. 4), cov3 (Eq. 2), cov4, slice (Eq. 5/6 + temporal factor),
   sh_basis (real SH, degree 3), project (cull + EWA + SH, Alg. 1),
   render (Eq. 3 as the plain per-pixel definition), render_bwd (reverse mode),
-  matrix_to_quat (Eq. 9), convert (Sec. 4.1-4.2), stable_sort_u64.
+  matrix_to_quat (Eq. 9), convert (Sec. 4.1-4.2), stable_sort_u64; adam_step (the
+  optimizer of the training step, Kingma and Ba 2015) in numpy.
 """
 from __future__ import annotations
 
@@ -257,6 +258,20 @@ def render_bwd(scene, view, dLdC):
                             _p(out["sh3"]), _p(out["mean4"]), _p(out["log_scale4"]), _p(out["ql"]),
                             _p(out["qr"]), _p(out["opacity4"]), _p(out["sh4"]), _p(out["dproj"]))
     return out
+
+
+def adam_step(p, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-15):
+    """One step of Adam (Kingma and Ba, 2015, Algorithm 1) in FP64 -- the
+    optimizer of the 3DGS / 4DGS training that the paper's training builds on
+    (Sec. 4.3): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, bias-corrected
+    m / (1 - b1^t) and v / (1 - b2^t), p -= lr m_hat / (sqrt(v_hat) + eps).
+    lr may be an array broadcast against p.  Returns (p, m, v)."""
+    p, m, v, g = (np.asarray(x, dtype=np.float64) for x in (p, m, v, g))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return p - np.asarray(lr, dtype=np.float64) * mh / (np.sqrt(vh) + eps), m, v
 
 
 def convert(scene, tau):

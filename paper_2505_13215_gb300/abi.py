@@ -19,7 +19,7 @@ SPLAT_ERR_NONFINITE = 4
 SPLAT_ERR_CUDA = 5
 
 SPLAT_F32, SPLAT_BF16, SPLAT_F16 = 0, 1, 2
-SPLAT_OP_BIN_SORT, SPLAT_OP_COMPOSITE_BWD, SPLAT_OP_CONVERT, SPLAT_OP_ALL = 1, 2, 3, 4
+SPLAT_OP_BIN_SORT, SPLAT_OP_COMPOSITE_BWD, SPLAT_OP_CONVERT, SPLAT_OP_ALL, SPLAT_OP_CONVERT_STATE = 1, 2, 3, 4, 5
 SPLAT_BWD_STOP_2D = 1
 SPLAT_BWD_ADJOINT_ONLY = 2
 SPLAT_MAX_VIEWS = 16
@@ -73,6 +73,15 @@ class splat_grads4(C.Structure):
                 ("opacity", C.c_void_p), ("sh", C.c_void_p)]
 
 
+class splat_adam_set(C.Structure):
+    _fields_ = [("param", C.c_void_p * 6), ("m", C.c_void_p * 6), ("v", C.c_void_p * 6)]
+
+
+class splat_adam_hyper(C.Structure):
+    _fields_ = [("lr3", C.c_float * 5), ("lr4", C.c_float * 6), ("lr_sh_rest", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("step", C.c_int32)]
+
+
 _P = C.POINTER
 EXPORTS = {
     "splat_version": (C.c_int32, []),
@@ -101,6 +110,11 @@ EXPORTS = {
                                 C.c_void_p]),
     "splat_bin_sort_noalloc": (C.c_int, [_P(splat_proj), _P(splat_view), C.c_int, _P(splat_bins), C.c_void_p,
                                          C.c_void_p]),
+    "splat_adam_step": (C.c_int, [_P(splat_adam_hyper), _P(splat_adam_set), _P(splat_grads3), _P(splat_g3),
+                                  _P(splat_adam_set), _P(splat_grads4), _P(splat_g4), C.c_void_p, C.c_void_p]),
+    "splat_cast_params": (C.c_int, [_P(splat_g3), _P(splat_g3), _P(splat_g4), _P(splat_g4), C.c_void_p]),
+    "splat_convert_adam_state": (C.c_int, [_P(splat_g4), _P(splat_g3), C.c_float, _P(splat_adam_set),
+                                           _P(splat_adam_set), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
 }
 
 _lib = None
@@ -216,3 +230,15 @@ def splat_bin_sort_noalloc(proj, views, V, bins, status, stream):
     allocate device memory when they sort (scratch: a fixed array inside the
     library, shared by all calls)."""
     return lib().splat_bin_sort_noalloc(proj, views, V, bins, status, stream)
+
+
+def splat_adam_step(hyper, s3, dg3, g3, s4, dg4, g4, status, stream):
+    return lib().splat_adam_step(hyper, s3, dg3, g3, s4, dg4, g4, status, stream)
+
+
+def splat_cast_params(src3, dst3, src4, dst4, stream):
+    return lib().splat_cast_params(src3, dst3, src4, dst4, stream)
+
+
+def splat_convert_adam_state(g4, g3, tau, s4, s3, status, ws, ws_bytes, stream):
+    return lib().splat_convert_adam_state(g4, g3, tau, s4, s3, status, ws, ws_bytes, stream)

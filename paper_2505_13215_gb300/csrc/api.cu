@@ -24,6 +24,32 @@ cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const Vie
 cudaError_t launch_convert(const splat_g4&, const splat_g3&, float, int64_t*, int32_t*, void*, const LaunchCtx&);
 size_t convert_workspace(int64_t n4, int dtype_bytes);
 cudaError_t launch_l1_loss(const float*, const float*, int64_t, float, float*, float*, const LaunchCtx&);
+cudaError_t launch_convert_state(const splat_g4&, const splat_g3&, float, const splat_adam_set&,
+                                 const splat_adam_set&, int32_t*, void*, const LaunchCtx&);
+size_t convert_state_workspace(int64_t n4);
+
+constexpr int kMaxSegs = 11;
+struct OptSeg {
+    float* p;
+    float* m;
+    float* v;
+    const float* g;
+    void* st;
+    int64_t n;
+    float lr;
+    float lr_rest;
+    int sh;
+};
+struct OptArgs {
+    OptSeg seg[kMaxSegs];
+    int nseg;
+    int dtype;
+    float b1, b2, eps;
+    float c1, c2;
+    int32_t* status;
+};
+cudaError_t launch_adam(const OptArgs&, const LaunchCtx&);
+cudaError_t launch_cast(const OptArgs&, const LaunchCtx&);
 
 static std::atomic<int64_t> g_spin_limit{1ll << 22};
 std::atomic<int64_t> g_launches{0};
@@ -206,10 +232,13 @@ size_t splat_workspace_size(int op, int64_t N3, int64_t N4, int V, const int32_t
     }
     if (op == SPLAT_OP_COMPOSITE_BWD || op == SPLAT_OP_ALL) bwd_b = ((size_t)N * V * 48 + 255) & ~(size_t)255;
     if (op == SPLAT_OP_CONVERT || op == SPLAT_OP_ALL) conv_b = convert_workspace(N4, 4);
-    if (op < SPLAT_OP_BIN_SORT || op > SPLAT_OP_ALL) return 0;
+    size_t state_b = 0;
+    if (op == SPLAT_OP_CONVERT_STATE || op == SPLAT_OP_ALL) state_b = convert_state_workspace(N4);
+    if (op < SPLAT_OP_BIN_SORT || op > SPLAT_OP_CONVERT_STATE) return 0;
     size_t m = sort_b;
     if (bwd_b > m) m = bwd_b;
     if (conv_b > m) m = conv_b;
+    if (state_b > m) m = state_b;
     return m < 256 ? 256 : m;
 }
 
@@ -336,6 +365,112 @@ splat_status splat_convert_4d_to_3d(splat_g4* g4, splat_g3* g3, float tau, int64
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
     const LaunchCtx ctx = launch_ctx(stream);
     return cuda_status(launch_convert(*g4, *g3, tau, n_moved_dev, status, workspace, ctx));
+}
+
+static const int kWidth3[5] = {3, 3, 4, 1, 48};
+static const int kWidth4[6] = {4, 4, 4, 4, 1, 48};
+
+static bool valid_set(const splat_adam_set* s, int fields, int64_t rows, bool need_param, bool need_moments)
+{
+    if (rows == 0) return true;
+    if (!s) return false;
+    for (int f = 0; f < fields; ++f) {
+        if (need_param && (!s->param[f] || !aligned(s->param[f], 16))) return false;
+        if (need_moments && (!s->m[f] || !s->v[f] || !aligned(s->m[f], 16) || !aligned(s->v[f], 16))) return false;
+    }
+    return true;
+}
+
+static void* field3(const splat_g3& g, int f)
+{
+    void* p[5] = {g.mean, g.log_scale, g.quat, g.opacity, g.sh};
+    return p[f];
+}
+
+static void* field4(const splat_g4& g, int f)
+{
+    void* p[6] = {g.mean, g.log_scale, g.ql, g.qr, g.opacity, g.sh};
+    return p[f];
+}
+
+splat_status splat_adam_step(const splat_adam_hyper* h, splat_adam_set* s3, const splat_grads3* dg3, splat_g3* g3,
+                             splat_adam_set* s4, const splat_grads4* dg4, splat_g4* g4, int32_t* status, void* stream)
+{
+    if (!h || !g3 || !g4 || !status || h->step < 1) return SPLAT_ERR_INVALID_ARG;
+    if (g3->n < 0 || g4->n < 0 || g3->capacity < g3->n || g3->dtype != g4->dtype) return SPLAT_ERR_INVALID_ARG;
+    if (g3->dtype < SPLAT_F32 || g3->dtype > SPLAT_F16) return SPLAT_ERR_INVALID_ARG;
+    if (!(h->beta1 >= 0.f && h->beta1 < 1.f) || !(h->beta2 >= 0.f && h->beta2 < 1.f) || !(h->eps > 0.f))
+        return SPLAT_ERR_INVALID_ARG;
+    if (!valid_set(s3, 5, g3->n, true, true) || !valid_set(s4, 6, g4->n, true, true)) return SPLAT_ERR_INVALID_ARG;
+    if ((g3->n > 0 && !dg3) || (g4->n > 0 && !dg4)) return SPLAT_ERR_INVALID_ARG;
+    OptArgs a{};
+    const float* gr3[5] = {};
+    const float* gr4[6] = {};
+    if (dg3) {
+        gr3[0] = dg3->mean; gr3[1] = dg3->log_scale; gr3[2] = dg3->quat; gr3[3] = dg3->opacity; gr3[4] = dg3->sh;
+    }
+    if (dg4) {
+        gr4[0] = dg4->mean; gr4[1] = dg4->log_scale; gr4[2] = dg4->ql; gr4[3] = dg4->qr; gr4[4] = dg4->opacity;
+        gr4[5] = dg4->sh;
+    }
+    for (int f = 0; f < 5 && g3->n > 0; ++f) {
+        if (!gr3[f] || !field3(*g3, f) || !std::isfinite(h->lr3[f])) return SPLAT_ERR_INVALID_ARG;
+        a.seg[a.nseg++] = OptSeg{s3->param[f], s3->m[f], s3->v[f], gr3[f], field3(*g3, f), g3->n * kWidth3[f],
+                                 h->lr3[f], h->lr_sh_rest, f == 4};
+    }
+    for (int f = 0; f < 6 && g4->n > 0; ++f) {
+        if (!gr4[f] || !field4(*g4, f) || !std::isfinite(h->lr4[f])) return SPLAT_ERR_INVALID_ARG;
+        a.seg[a.nseg++] = OptSeg{s4->param[f], s4->m[f], s4->v[f], gr4[f], field4(*g4, f), g4->n * kWidth4[f],
+                                 h->lr4[f], h->lr_sh_rest, f == 5};
+    }
+    if (!std::isfinite(h->lr_sh_rest)) return SPLAT_ERR_INVALID_ARG;
+    a.dtype = g3->dtype;
+    a.b1 = h->beta1;
+    a.b2 = h->beta2;
+    a.eps = h->eps;
+    a.c1 = (float)(1.0 / (1.0 - std::pow((double)h->beta1, (double)h->step)));
+    a.c2 = (float)(1.0 / (1.0 - std::pow((double)h->beta2, (double)h->step)));
+    a.status = status;
+    const LaunchCtx ctx = launch_ctx(stream);
+    return cuda_status(launch_adam(a, ctx));
+}
+
+splat_status splat_cast_params(const splat_g3* src3, splat_g3* dst3, const splat_g4* src4, splat_g4* dst4,
+                               void* stream)
+{
+    if (!src3 || !dst3 || !src4 || !dst4) return SPLAT_ERR_INVALID_ARG;
+    if (src3->dtype != SPLAT_F32 || src4->dtype != SPLAT_F32 || dst3->dtype != dst4->dtype) return SPLAT_ERR_INVALID_ARG;
+    if (dst3->dtype < SPLAT_F32 || dst3->dtype > SPLAT_F16 || src3->n < 0 || src4->n < 0) return SPLAT_ERR_INVALID_ARG;
+    if (src3->n > dst3->capacity) return SPLAT_ERR_INVALID_ARG;
+    OptArgs a{};
+    for (int f = 0; f < 5 && src3->n > 0; ++f) {
+        if (!field3(*src3, f) || !field3(*dst3, f)) return SPLAT_ERR_INVALID_ARG;
+        a.seg[a.nseg++] = OptSeg{(float*)field3(*src3, f), nullptr, nullptr, nullptr, field3(*dst3, f),
+                                 src3->n * kWidth3[f], 0.f, 0.f, 0};
+    }
+    for (int f = 0; f < 6 && src4->n > 0; ++f) {
+        if (!field4(*src4, f) || !field4(*dst4, f)) return SPLAT_ERR_INVALID_ARG;
+        a.seg[a.nseg++] = OptSeg{(float*)field4(*src4, f), nullptr, nullptr, nullptr, field4(*dst4, f),
+                                 src4->n * kWidth4[f], 0.f, 0.f, 0};
+    }
+    a.dtype = dst3->dtype;
+    const LaunchCtx ctx = launch_ctx(stream);
+    return cuda_status(launch_cast(a, ctx));
+}
+
+splat_status splat_convert_adam_state(const splat_g4* g4, const splat_g3* g3, float tau, splat_adam_set* s4,
+                                      splat_adam_set* s3, int32_t* status, void* workspace, size_t workspace_bytes,
+                                      void* stream)
+{
+    if (!g4 || !g3 || !status || !std::isfinite(tau)) return SPLAT_ERR_INVALID_ARG;
+    if (!valid_g4(*g4) || g3->n < 0 || g3->capacity < g3->n) return SPLAT_ERR_INVALID_ARG;
+    if (!valid_set(s4, 6, g4->n, false, true)) return SPLAT_ERR_INVALID_ARG;
+    if (g4->n > 0 && !valid_set(s3, 5, g3->capacity, false, true)) return SPLAT_ERR_INVALID_ARG;
+    const size_t need = convert_state_workspace(g4->n);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
+    const LaunchCtx ctx = launch_ctx(stream);
+    const splat_adam_set empty{};
+    return cuda_status(launch_convert_state(*g4, *g3, tau, s4 ? *s4 : empty, s3 ? *s3 : empty, status, workspace, ctx));
 }
 
 splat_status splat_l1_loss(const float* img, const float* target, int64_t n, float scale, float* dL_dimg,

@@ -210,7 +210,127 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_copyback(splat_g4 g4, Con
     }
 }
 
+// Optimizer state of the conversion: the moments of the kept 4D rows follow
+// their parameters (same stable compaction), the 3D rows the moved Gaussians
+// land in get zero moments.  The decision reads the parameter set g4, which
+// must still hold the values before the conversion.
+__host__ __device__ constexpr int width3(int f) { return f < 2 ? 3 : (f == 2 ? 4 : (f == 3 ? 1 : 48)); }
+__host__ __device__ constexpr int width4(int f) { return f < 4 ? 4 : (f == 4 ? 1 : 48); }
+
+struct StateTmp {  // workspace copy of the kept 4D rows' moments
+    float* m[6];
+    float* v[6];
+};
+
+template <int DT>
+__global__ void __launch_bounds__(kConvThreads) k_state_scatter(splat_g4 g4, float tau, int64_t n3,
+                                                                const uint32_t* block_offsets, splat_adam_set s4,
+                                                                splat_adam_set s3, StateTmp tmp, int32_t* status)
+{
+    __shared__ uint32_t s_tmp[8];
+    if (status_failed(status)) return;
+    const int64_t base = (int64_t)blockIdx.x * kConvBlock;
+    uint32_t carry = block_offsets[blockIdx.x];
+    for (int k = 0; k < kConvItems; ++k) {
+        const int64_t i = base + k * kConvThreads + threadIdx.x;
+        const bool st = i < g4.n && is_static<DT>(g4, i, tau);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const unsigned bal = __ballot_sync(0xffffffffu, st);
+        if (lane == 0) s_tmp[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t wbase = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) wbase += s_tmp[w];
+            tot += s_tmp[w];
+        }
+        __syncthreads();
+        const uint32_t before = carry + wbase + __popc(bal & lanemask_lt());
+        carry += tot;
+        if (i >= g4.n) continue;
+        if (st) {
+            const int64_t d = n3 + before;
+#pragma unroll
+            for (int f = 0; f < 5; ++f)
+                for (int c = 0; c < width3(f); ++c) {
+                    s3.m[f][d * width3(f) + c] = 0.f;
+                    s3.v[f][d * width3(f) + c] = 0.f;
+                }
+        } else {
+            const int64_t d = i - before;
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+                for (int c = 0; c < width4(f); ++c) {
+                    tmp.m[f][d * width4(f) + c] = s4.m[f][i * width4(f) + c];
+                    tmp.v[f][d * width4(f) + c] = s4.v[f][i * width4(f) + c];
+                }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_state_copyback(int64_t n4, splat_adam_set s4, StateTmp tmp,
+                                                        const int64_t* n_moved, int32_t* status)
+{
+    if (status_failed(status)) return;
+    const int64_t kept = n4 - *n_moved;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < kept; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+            for (int c = 0; c < width4(f); ++c) {
+                s4.m[f][i * width4(f) + c] = tmp.m[f][i * width4(f) + c];
+                s4.v[f][i * width4(f) + c] = tmp.v[f][i * width4(f) + c];
+            }
+    }
+}
+
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t convert_state_workspace(int64_t n4)
+{
+    const int64_t nb = (n4 + kConvBlock - 1) / kConvBlock;
+    size_t o = a256(4 * (size_t)(nb + 1)) + a256(8);
+    for (int f = 0; f < 6; ++f) o += 2 * a256(4 * (size_t)n4 * width4(f));
+    return o;
+}
+
+template <int DT>
+static cudaError_t convert_state_impl(const splat_g4& g4, const splat_g3& g3, float tau, const splat_adam_set& s4,
+                                      const splat_adam_set& s3, int32_t* status, void* ws, const LaunchCtx& ctx)
+{
+    const int64_t n4 = g4.n;
+    if (n4 == 0) return cudaSuccess;
+    const int64_t nb = (n4 + kConvBlock - 1) / kConvBlock;
+    char* w = (char*)ws;
+    uint32_t* counts = (uint32_t*)w;
+    size_t o = a256(4 * (size_t)(nb + 1));
+    int64_t* n_moved = (int64_t*)(w + o);
+    o += a256(8);
+    StateTmp tmp;
+    for (int f = 0; f < 6; ++f) {
+        tmp.m[f] = (float*)(w + o);
+        o += a256(4 * (size_t)n4 * width4(f));
+        tmp.v[f] = (float*)(w + o);
+        o += a256(4 * (size_t)n4 * width4(f));
+    }
+    cudaStream_t s = ctx.stream;
+    count_launch(4);
+    k_conv_count<DT><<<(int)nb, kConvThreads, 0, s>>>(g4, tau, counts);
+    k_conv_scan<<<1, 1024, 0, s>>>(counts, nb, g3.n, g3.capacity, n_moved, status);
+    k_state_scatter<DT><<<(int)nb, kConvThreads, 0, s>>>(g4, tau, g3.n, counts, s4, s3, tmp, status);
+    const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, (int64_t)ctx.num_sms * 8);
+    k_state_copyback<<<blocks, 256, 0, s>>>(n4, s4, tmp, n_moved, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_state(const splat_g4& g4, const splat_g3& g3, float tau, const splat_adam_set& s4,
+                                 const splat_adam_set& s3, int32_t* status, void* ws, const LaunchCtx& ctx)
+{
+    switch (g4.dtype) {
+    case SPLAT_F32: return convert_state_impl<SPLAT_F32>(g4, g3, tau, s4, s3, status, ws, ctx);
+    case SPLAT_BF16: return convert_state_impl<SPLAT_BF16>(g4, g3, tau, s4, s3, status, ws, ctx);
+    default: return convert_state_impl<SPLAT_F16>(g4, g3, tau, s4, s3, status, ws, ctx);
+    }
+}
 
 size_t convert_workspace(int64_t n4, int dtype_bytes)
 {

@@ -151,15 +151,35 @@ class Rasterizer:
         self.dproj = torch.zeros((rows * 12,), dtype=f32, device=d)
         self.loss = torch.zeros((1,), dtype=f32, device=d)
         self.dL = torch.zeros_like(self.rgb)
-        self.grads = {k: torch.zeros((self.n3 if k in FIELDS3 else self.n4,) + SHAPES[k], dtype=f32, device=d)
-                      for k in FIELDS3 + FIELDS4}
-        self.cg3 = abi.splat_grads3(*[self.grads[k].data_ptr() for k in FIELDS3])
-        self.cg4 = abi.splat_grads4(*[self.grads[k].data_ptr() for k in FIELDS4])
+        # gradient rows for N Gaussians in either set, so that the 3D / 4D split can
+        # change (4D -> 3D conversion) without reallocating; self.grads views the first n
+        self._grad_buf = {k: torch.zeros((self.N,) + SHAPES[k], dtype=f32, device=d) for k in FIELDS3 + FIELDS4}
+        self.cg3 = abi.splat_grads3(*[self._grad_buf[k].data_ptr() for k in FIELDS3])
+        self.cg4 = abi.splat_grads4(*[self._grad_buf[k].data_ptr() for k in FIELDS4])
+        self._view_grads()
         if capacity is None:
             capacity = max(1 << 16, 16 * rows)
         self.set_capacity(capacity)
 
     # -- buffers ------------------------------------------------------------
+    def _view_grads(self):
+        self.grads = {k: self._grad_buf[k][: (self.n3 if k in FIELDS3 else self.n4)] for k in FIELDS3 + FIELDS4}
+
+    def set_counts(self, n3: int, n4: int):
+        """New 3D / 4D split of the same N Gaussians (after a 4D -> 3D conversion)."""
+        if int(n3) + int(n4) != self.N:
+            raise ValueError("the split must keep N = %d" % self.N)
+        self.n3, self.n4 = int(n3), int(n4)
+        self._view_grads()
+
+    def set_views(self, views: Sequence):
+        """New cameras / timestamps for the next calls; resolutions must stay the same."""
+        views = list(views)
+        if len(views) != self.V or any((int(v.W), int(v.H)) != (w, h) for v, w, h in zip(views, self.W, self.H)):
+            raise ValueError("set_views keeps the batch's count and resolutions")
+        self.views = views
+        self.cviews = c_views(views)
+
     def set_capacity(self, capacity: int):
         capacity = int(min(max(1, capacity), abi.SPLAT_MAX_INSTANCES))
         self.capacity = capacity

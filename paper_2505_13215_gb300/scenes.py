@@ -218,6 +218,36 @@ def arc_scene(seed: int = 2, n: int = 500_000, frac4: float = 0.3, n_views: int 
     return scene, views
 
 
+def training_scene(seed: int = 4, n: int = 300_000, frac_static: float = 0.7) -> Scene:
+    """Every Gaussian 4D (the paper starts from a full 4D model, Sec. 4.3), world
+    means U[-5, 5]^3.  A fraction frac_static has the wide time scale of a
+    static Gaussian, log s_t ~ N(0.5, 0.3) (exp(s_t) > 1 for 95% of them), the
+    rest the narrow one of the common distribution, log s_t ~ N(-2, 0.5): a
+    conversion pass with tau = 1 leaves about 1 - frac_static of them 4D, the
+    mix the paper's trained models reach."""
+    rng = np.random.default_rng(seed)
+    scene = random_scene(rng, 0, n, np.zeros((0, 3)), rng.uniform(-5, 5, size=(n, 3)))
+    wide = rng.uniform(0.0, 1.0, size=n) < frac_static
+    st = scene.log_scale4[:, 3].astype(np.float64)
+    st[wide] = rng.normal(0.5, 0.3, size=int(wide.sum()))
+    scene.log_scale4[:, 3] = st.astype(np.float32)
+    return scene
+
+
+def random_arc_views(rng: np.random.Generator, n_views: int, W: int = 1352, H: int = 1014, f: float = 1460.0,
+                     radius: float = 11.0, n_frames: int = 300) -> List[View]:
+    """Training batch: cameras at random angles of a 120-degree arc of the given
+    radius about the origin, looking at it, each at a random frame of the
+    sequence."""
+    grid = frames(n_frames)
+    out = []
+    for _ in range(n_views):
+        ang = math.radians(rng.uniform(-60.0, 60.0))
+        eye = np.array([radius * math.sin(ang), rng.uniform(-1.0, 1.0), -radius * math.cos(ang)])
+        out.append(look_at_view(eye, np.zeros(3), W, H, f, float(grid[rng.integers(0, n_frames)])))
+    return out
+
+
 def subset(scene: Scene, idx3: Optional[Sequence[int]] = None, idx4: Optional[Sequence[int]] = None) -> Scene:
     a = scene.arrays()
     out = {}

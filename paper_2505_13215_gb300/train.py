@@ -1,0 +1,136 @@
+"""Training step of the hybrid 3D-4D representation on the GPU (Sec. 4.3).
+
+One step renders a batch of views (cameras and timestamps) in one launch per
+stage, takes the L1 loss against the targets, back-propagates through the
+compositing and the projection, and updates both parameter sets with one fused
+Adam launch.  Every `convert_every` steps the 4D Gaussians whose time scale
+exceeds tau become 3D (Sec. 4.1-4.2; the paper classifies at every
+densification stage, every 100 iterations), moving their optimizer state along.
+
+Parameters live twice: FP32 master values (and Adam's moments) that the
+optimizer updates, and the storage copy the rasterizer reads (BF16, FP16 or the
+FP32 master itself), written by the same Adam launch.  The 3D arrays are
+allocated for all N Gaussians so the conversion appends in place.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Dict, Optional, Sequence
+
+import torch
+
+from . import abi
+from .raster import FIELDS3, FIELDS4, SHAPES, Gaussians, Rasterizer, _ptr, _stream
+
+# step sizes of the 3DGS / 4DGS recipe the paper trains with (positions scaled
+# by a scene extent of 5; SH of degree >= 1 at 1/20 of the DC step)
+DEFAULT_LR3 = {"mean3": 8e-4, "log_scale3": 5e-3, "quat3": 1e-3, "opacity3": 5e-2, "sh3": 2.5e-3}
+DEFAULT_LR4 = {"mean4": 8e-4, "log_scale4": 5e-3, "ql": 1e-3, "qr": 1e-3, "opacity4": 5e-2, "sh4": 2.5e-3}
+DEFAULT_LR_SH_REST = 2.5e-3 / 20
+
+
+class AdamState:
+    """Adam's moments for one parameter set (FP32, shaped like the master arrays)."""
+
+    def __init__(self, master: Gaussians, fields: Sequence[str]):
+        self.fields = tuple(fields)
+        self.m = {k: torch.zeros_like(master.t[k]) for k in self.fields}
+        self.v = {k: torch.zeros_like(master.t[k]) for k in self.fields}
+        self.c = abi.splat_adam_set()
+        for i, k in enumerate(self.fields):
+            self.c.param[i] = master.t[k].data_ptr()
+            self.c.m[i] = self.m[k].data_ptr()
+            self.c.v[i] = self.v[k].data_ptr()
+
+
+class Trainer:
+    """Batched training of one hybrid scene.  `views` fixes the batch size and
+    resolutions; each step may bring other cameras and timestamps."""
+
+    def __init__(self, scene, views: Sequence, dtype=torch.bfloat16, device="cuda", tau: float = 1.0,
+                 convert_every: int = 100, lr3: Optional[Dict[str, float]] = None,
+                 lr4: Optional[Dict[str, float]] = None, lr_sh_rest: float = DEFAULT_LR_SH_REST,
+                 betas=(0.9, 0.999), eps: float = 1e-15, headroom: float = 1.25):
+        n = scene.n3 + scene.n4
+        self.master = Gaussians.from_scene(scene, device, dtype=torch.float32, capacity3=n)
+        self.store = self.master if dtype == torch.float32 else Gaussians.from_scene(scene, device, dtype=dtype,
+                                                                                  capacity3=n)
+        self.s3 = AdamState(self.master, FIELDS3)
+        self.s4 = AdamState(self.master, FIELDS4)
+        self.R = Rasterizer(self.master.n3, self.master.n4, views, device=device, keep_keys=False, headroom=headroom)
+        self.R.autotune_capacity(self.store)
+        self.tau = float(tau)
+        self.convert_every = int(convert_every)
+        self.t = 0
+        lr3 = dict(DEFAULT_LR3, **(lr3 or {}))
+        lr4 = dict(DEFAULT_LR4, **(lr4 or {}))
+        self.hyper = abi.splat_adam_hyper()
+        for i, k in enumerate(FIELDS3):
+            self.hyper.lr3[i] = lr3[k]
+        for i, k in enumerate(FIELDS4):
+            self.hyper.lr4[i] = lr4[k]
+        self.hyper.lr_sh_rest = lr_sh_rest
+        self.hyper.beta1, self.hyper.beta2 = betas
+        self.hyper.eps = eps
+        dev = self.master.t["mean3"].device
+        wb = abi.splat_workspace_size(abi.SPLAT_OP_CONVERT_STATE, 0, self.master.n4, self.R.W, self.R.H, 0)
+        wb = max(wb, abi.splat_workspace_size(abi.SPLAT_OP_CONVERT, 0, self.master.n4, self.R.W, self.R.H, 0))
+        self.conv_ws = torch.empty((int(wb),), dtype=torch.uint8, device=dev)
+        self.n_moved = torch.zeros((1,), dtype=torch.int64, device=dev)
+        self.moved_total = 0
+
+    @property
+    def n3(self) -> int:
+        return self.master.n3
+
+    @property
+    def n4(self) -> int:
+        return self.master.n4
+
+    def adam(self, stream=None):
+        """The fused Adam launch over both sets (asynchronous)."""
+        self.t += 1
+        self.hyper.step = self.t
+        g3, g4 = self.store.c_g3(), self.store.c_g4()
+        abi.check(abi.splat_adam_step(C.byref(self.hyper), C.byref(self.s3.c), C.byref(self.R.cg3), C.byref(g3),
+                                      C.byref(self.s4.c), C.byref(self.R.cg4), C.byref(g4), _ptr(self.R.status),
+                                      _stream(stream)), "splat_adam_step")
+
+    def step(self, views: Sequence, target: torch.Tensor, stream=None, marks: Optional[dict] = None):
+        """Render, loss, backward and update for one batch (asynchronous except at a
+        conversion step, which reads the moved count)."""
+        self.R.set_views(views)
+        self.R.step(self.store, target, stream, marks)
+        self.adam(stream)
+        if self.convert_every > 0 and self.t % self.convert_every == 0:
+            self.convert(stream)
+
+    def convert(self, stream=None) -> int:
+        """Sec. 4.1-4.2 with the optimizer state: moments first (the decision reads the
+        4D time scales before the conversion rewrites them), then the master
+        parameters, then the storage copy.  Synchronises once; returns the count."""
+        m3, m4 = self.master.c_g3(), self.master.c_g4()
+        st = _stream(stream)
+        ws, wb = _ptr(self.conv_ws), self.conv_ws.numel()
+        abi.check(abi.splat_convert_adam_state(C.byref(m4), C.byref(m3), self.tau, C.byref(self.s4.c),
+                                               C.byref(self.s3.c), _ptr(self.R.status), ws, wb, st),
+                  "splat_convert_adam_state")
+        abi.check(abi.splat_convert_4d_to_3d(C.byref(m4), C.byref(m3), self.tau, _ptr(self.n_moved),
+                                             _ptr(self.R.status), ws, wb, st), "splat_convert_4d_to_3d")
+        self.R.check("conversion")
+        moved = int(self.n_moved.item())
+        for G in {id(self.master): self.master, id(self.store): self.store}.values():
+            G.n3 += moved
+            G.n4 -= moved
+        if self.store is not self.master:
+            s3, s4 = self.master.c_g3(), self.master.c_g4()
+            d3, d4 = self.store.c_g3(), self.store.c_g4()
+            abi.check(abi.splat_cast_params(C.byref(s3), C.byref(d3), C.byref(s4), C.byref(d4), st),
+                      "splat_cast_params")
+        self.R.set_counts(self.master.n3, self.master.n4)
+        self.moved_total += moved
+        return moved
+
+    @property
+    def loss(self) -> torch.Tensor:
+        return self.R.loss
