@@ -132,14 +132,14 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
                     // skip power > 0 and alpha < 1/255 (as p2 < pcut2); NaN and -inf skip too
                     if (!(p2 <= 0.f && p2 >= f.pcut2)) continue;
                     const float alpha = fminf(kAlphaClamp, f.op * ex2_approx(p2));
-                    const float tT = T[k] * (1.f - alpha);
+                    const float w = alpha * T[k];
+                    const float tT = T[k] - w;  // T (1 - alpha)
                     if (tT < kTMin) {
                         done |= 1u << k;
                         yk[k] = __int_as_float(0x7f800000);
                         continue;
                     }
                     if (STATS) ++n_blend;
-                    const float w = alpha * T[k];
                     C[k][0] += f.r * w;
                     C[k][1] += f.g * w;
                     C[k][2] += f.bl * w;
@@ -263,20 +263,20 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
     const float uf = (float)u;
     const int64_t HW = (int64_t)vp.W * vp.H;
-    // Per pixel: T (replayed transmittance), G = dL/dC, and GS = <G, S> where S is
-    // the colour accumulated behind the current Gaussian, S = sum_{i>j} c_i alpha_i T_i
-    // + T_final bg.  dL/dalpha_j = T_j <G, c_j> - GS / (1 - alpha_j), and GS grows by
-    // alpha_j T_j <G, c_j>, so S itself is never needed per channel.
-    float T[PPL], GS[PPL], G[PPL][3], yk[PPL];
+    // Per pixel: T = T_{j+1} (replayed transmittance behind the current Gaussian j),
+    // G = dL/dC, and Q = <G, S_j> / T_{j+1} with S_j = sum_{i>j} c_i alpha_i T_i + T_final bg
+    // the colour accumulated behind j.  Then dL/dalpha_j = T_j (<G, c_j> - Q) and
+    // Q_{j-1} = Q + alpha_j (<G, c_j> - Q): S itself is never needed per channel, and
+    // Q starts at <G, bg>.
+    float T[PPL], Q[PPL], G[PPL][3];
     int last[PPL];
     int maxlast = 0;
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
         const int y = y0 + 2 * k;
-        yk[k] = (float)y;
         last[k] = 0;
         T[k] = 1.f;
-        GS[k] = 0.f;
+        Q[k] = 0.f;
         G[k][0] = G[k][1] = G[k][2] = 0.f;
         if (u < vp.W && y < vp.H) {
             const int64_t p = (int64_t)y * vp.W + u;
@@ -286,10 +286,11 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
             G[k][2] = g[2 * HW + p];
             T[k] = img.final_T[vp.pix_base + p];
             last[k] = img.last[vp.pix_base + p];
-            GS[k] = T[k] * (G[k][0] * vp.bg[0] + G[k][1] * vp.bg[1] + G[k][2] * vp.bg[2]);
+            Q[k] = G[k][0] * vp.bg[0] + G[k][1] * vp.bg[1] + G[k][2] * vp.bg[2];
             maxlast = max(maxlast, last[k]);
         }
     }
+    const float y0f = (float)y0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
     if (maxlast == 0) return;
@@ -318,13 +319,15 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
             const int li = 32 * bi + j;  // position in the tile list
             const float dx = f.px - uf;
             const float A2 = f.a2 * dx * dx, Bx2 = f.b2 * dx;
-            // per lane, over its pixels: dL/drgb and the moments W0 = sum dL/dpower,
-            // W1 = sum dL/dpower dy, W2 = sum dL/dpower dy^2
-            float W0 = 0.f, W1 = 0.f, W2 = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
+            const float pyr = f.py - y0f;  // dy of pixel k is pyr - 2 k (up to rounding)
+            // per lane, over its pixels: dL/drgb and the moments of dL/dpower
+            // W0 = sum dpow, V1 = sum k dpow, V2 = sum k^2 dpow
+            float W0 = 0.f, V1 = 0.f, V2 = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                const float dy = f.py - yk[k];
+                // the forward's dy: py minus the row, an exact integer in FP32
+                const float dy = f.py - (y0f + (float)(2 * k));
                 const float p2 = A2 + dy * (Bx2 + f.c2 * dy);
                 if (STATS) n_eval += li < last[k];
                 // the forward's skip, bit for bit, on the pixels that reached this Gaussian
@@ -333,23 +336,24 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
                 const float alpha = fminf(kAlphaClamp, raw);
                 if (STATS) ++n_blend;
                 any = true;
-                const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
-                const float Tj = T[k] * iom;
+                const float Tj = T[k] * __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
                 const float w = alpha * Tj;
                 cr += w * G[k][0];
                 cg += w * G[k][1];
                 cb += w * G[k][2];
-                const float gc = G[k][0] * f.r + G[k][1] * f.g + G[k][2] * f.bl;
-                const float dLda = Tj * gc - GS[k] * iom;
-                GS[k] += w * gc;
+                const float d = G[k][0] * f.r + G[k][1] * f.g + G[k][2] * f.bl - Q[k];
+                Q[k] += alpha * d;
                 T[k] = Tj;
-                // dL/dpower = dL/dalpha * alpha where alpha is not clamped
-                const float dpow = raw < kAlphaClamp ? dLda * alpha : 0.f;
-                const float t = dpow * dy;
+                // dL/dpower = dL/dalpha * alpha = w d where alpha is not clamped
+                const float dpow = raw < kAlphaClamp ? w * d : 0.f;
                 W0 += dpow;
-                W1 += t;
-                W2 += t * dy;
+                if (k > 0) {
+                    V1 += (float)k * dpow;
+                    V2 += (float)(k * k) * dpow;
+                }
             }
+            const float W1 = pyr * W0 - 2.f * V1;                             // sum dpow dy
+            const float W2 = pyr * (pyr * W0 - 4.f * V1) + 4.f * V2;          // sum dpow dy^2
             if (!__any_sync(0xffffffffu, any)) continue;
             float4* slot = red + nq * 3 * 32 + lane;
             const float dxW0 = dx * W0;
