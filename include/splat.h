@@ -85,7 +85,8 @@ enum {
     SPLAT_STAGE_COMPOSITE_FWD = 6,
     SPLAT_STAGE_COMPOSITE_BWD = 7,
     SPLAT_STAGE_ADJOINT = 8,
-    SPLAT_STAGE_CONVERT = 9
+    SPLAT_STAGE_CONVERT = 9,
+    SPLAT_STAGE_DENSIFY = 10
 };
 
 #define SPLAT_MAX_VIEWS 16
@@ -345,6 +346,59 @@ splat_status splat_cast_params(const splat_g3 *src3, splat_g3 *dst3, const splat
 splat_status splat_convert_adam_state(const splat_g4 *g4, const splat_g3 *g3, float tau, splat_adam_set *s4,
                                       splat_adam_set *s3, int32_t *status, void *workspace, size_t workspace_bytes,
                                       void *stream);
+
+/*
+ * Densification statistics (Sec. 4.3 densifies with the 3DGS rule, which
+ * reads the positional gradient of the projected means): for every merged
+ * Gaussian i (4D first) and every view v that sees it (proj->n_tiles[v N + i]
+ * > 0), accum[i] += |(dpx W_v / 2, dpy H_v / 2)| -- the norm of dL/d(mean in
+ * normalised device coordinates), from the dproj splat_composite_bwd wrote
+ * (16-byte aligned) -- and count[i] += 1.  accum, count: [N] f32, device,
+ * accumulated across calls (the caller zeroes them).
+ */
+splat_status splat_densify_stats(const splat_proj *proj, const splat_view *views, int V, const float *dproj,
+                                 float *accum, float *count, void *stream);
+
+/* Rules of splat_densify (host memory). */
+typedef struct {
+    float grad_threshold;  /* mean accum / count at which a Gaussian densifies (3DGS: 2e-4) */
+    float dense_scale;     /* largest spatial scale exp(s) of a clone; larger ones split  */
+    float min_opacity;     /* sigmoid(o) below this prunes the Gaussian (3DGS: 5e-3)      */
+    float split_shrink;    /* log-scale decrease of the two children of a split (log 1.6) */
+} splat_densify_rule;
+
+/* One parameter set as splat_densify sees it. */
+typedef struct {
+    int64_t n;             /* rows in use                                               */
+    int64_t capacity;      /* rows allocated in every array of state                    */
+    splat_adam_set *state; /* FP32 master values and Adam moments (splat_adam_set)      */
+    const float *accum;    /* [n] statistics of splat_densify_stats (this set's rows)   */
+    const float *count;    /* [n]                                                       */
+    const float *noise;    /* [n][2][3] (3D set) or [n][2][4] (4D set) N(0, 1) draws    */
+} splat_densify_set;
+
+/*
+ * Adaptive densification and pruning of each set on its own (Sec. 4.3, the
+ * clone / split / prune rules of 3DGS densification the paper adopts, without
+ * opacity resets).  Per row: sigmoid(o) < min_opacity -> removed; else, when
+ * accum / count >= grad_threshold (count 0 reads as 0), a Gaussian whose
+ * largest spatial scale max(exp(s_x), exp(s_y), exp(s_z)) <= dense_scale is
+ * cloned (an identical copy is added) and a larger one is split: it is
+ * replaced by two Gaussians at mean + M z_h, h = 0, 1 (z from noise, M =
+ * R diag(exp(s)) with R the 3x3 rotation of the quaternion for a 3D Gaussian
+ * and the 4x4 R of Eq. 4 for a 4D one, which moves (x, y, z, t)), every
+ * log-scale lowered by split_shrink, the other fields copied.  New layout of
+ * each set: the kept rows in order, then the clones in order, then the
+ * children two by two in order; new rows get zero moments.  n_out[0] /
+ * n_out[1] (device int64) receive the new 3D / 4D row counts; set->n is not
+ * updated.  A set whose new count exceeds its capacity sets SPLAT_ERR_CAPACITY
+ * and neither set changes.  Workspace: splat_densify_workspace_size().
+ */
+splat_status splat_densify(const splat_densify_rule *rule, splat_densify_set *set3, splat_densify_set *set4,
+                           int64_t *n_out, int32_t *status, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace splat_densify needs for sets of n rows and the given capacities. */
+size_t splat_densify_workspace_size(int64_t n3, int64_t capacity3, int64_t n4, int64_t capacity4);
 
 /*
  * L1 photometric loss of a training step (Sec. 4.3 trains the rendered

@@ -8,8 +8,9 @@ Functions follow the paper's equations (see oracle.c for the citations):
   rot4 (Eq. 4), cov3 (Eq. 2), cov4, slice (Eq. 5/6 + temporal factor),
   sh_basis (real SH, degree 3), project (cull + EWA + SH, Alg. 1),
   render (Eq. 3 as the plain per-pixel definition), render_bwd (reverse mode),
-  matrix_to_quat (Eq. 9), convert (Sec. 4.1-4.2), stable_sort_u64; adam_step (the
-  optimizer of the training step, Kingma and Ba 2015) in numpy.
+  matrix_to_quat (Eq. 9), convert (Sec. 4.1-4.2), stable_sort_u64; in numpy:
+  adam_step (the optimizer of the training step, Kingma and Ba 2015),
+  densify_stats and densify_set (the 3DGS densification rules, Sec. 4.3).
 """
 from __future__ import annotations
 
@@ -272,6 +273,66 @@ def adam_step(p, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-15):
     mh = m / (1.0 - beta1 ** t)
     vh = v / (1.0 - beta2 ** t)
     return p - np.asarray(lr, dtype=np.float64) * mh / (np.sqrt(vh) + eps), m, v
+
+
+FIELDS3 = ("mean3", "log_scale3", "quat3", "opacity3", "sh3")
+FIELDS4 = ("mean4", "log_scale4", "ql", "qr", "opacity4", "sh4")
+
+
+def densify_stats(dproj_xy, visible, W, H):
+    """Densification statistics of one view: per Gaussian |dL/d(NDC mean)| =
+    |(dL/dpx W/2, dL/dpy H/2)| where the view sees it, and the count (0/1)."""
+    g = np.asarray(dproj_xy, dtype=np.float64) * np.array([0.5 * W, 0.5 * H])
+    vis = np.asarray(visible, dtype=bool)
+    return np.where(vis, np.sqrt((g * g).sum(1)), 0.0), vis.astype(np.float64)
+
+
+def densify_set(params, m, v, accum, count, noise, grad_threshold, dense_scale, min_opacity, split_shrink,
+                four_d):
+    """The 3DGS densification rules the paper adopts (Sec. 4.3), on one set, FP64.
+    params / m / v: dicts of the set's fields (FIELDS3 or FIELDS4), n rows.
+    sigmoid(o) < min_opacity: removed.  Otherwise mean statistic accum / count
+    >= grad_threshold: cloned when max(exp(s_x, s_y, s_z)) <= dense_scale, else
+    split into two Gaussians at mean + M z_h (M = R diag(exp(s)), R the
+    rotation of the quaternion (3D) or of Eq. 4 (4D), z_h = noise[i, h]) with
+    every log-scale lowered by split_shrink.  Returns (params, m, v) of the new
+    set: kept rows, clones, children; new rows with zero moments."""
+    fields = FIELDS4 if four_d else FIELDS3
+    P = {k: np.asarray(params[k], dtype=np.float64) for k in fields}
+    n = P[fields[0]].shape[0]
+    o = P["opacity4" if four_d else "opacity3"]
+    ls = P["log_scale4" if four_d else "log_scale3"]
+    mu = P["mean4" if four_d else "mean3"]
+    op = 1.0 / (1.0 + np.exp(-o))
+    c = np.asarray(count, dtype=np.float64)
+    avg = np.where(c > 0, np.asarray(accum, dtype=np.float64) / np.where(c > 0, c, 1.0), 0.0)
+    alive = op >= min_opacity
+    dens = alive & (avg >= grad_threshold)
+    small = np.exp(ls[:, :3].max(1)) <= dense_scale
+    clone, split = dens & small, dens & ~small
+    keep = alive & ~split
+    kids = {k: [] for k in fields}
+    for i in np.nonzero(split)[0]:
+        if four_d:
+            R = rot4(P["ql"][i], P["qr"][i])
+        else:
+            q = P["quat3"][i]
+            R = quat_to_R3(q / np.linalg.norm(q))
+        M = R * np.exp(ls[i])[None, :]
+        for h in range(2):
+            for k in fields:
+                kids[k].append(P[k][i].copy())
+            kids["mean4" if four_d else "mean3"][-1] = mu[i] + M @ np.asarray(noise[i, h], dtype=np.float64)
+            kids["log_scale4" if four_d else "log_scale3"][-1] = ls[i] - split_shrink
+    out_p, out_m, out_v = {}, {}, {}
+    for k in fields:
+        shape = P[k].shape[1:]
+        kid = np.array(kids[k]).reshape((-1,) + shape)
+        out_p[k] = np.concatenate([P[k][keep], P[k][clone], kid], 0)
+        zeros = np.zeros((int(clone.sum()) + kid.shape[0],) + shape)
+        out_m[k] = np.concatenate([np.asarray(m[k], dtype=np.float64)[keep], zeros], 0)
+        out_v[k] = np.concatenate([np.asarray(v[k], dtype=np.float64)[keep], zeros], 0)
+    return out_p, out_m, out_v
 
 
 def convert(scene, tau):

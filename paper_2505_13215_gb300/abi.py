@@ -27,7 +27,7 @@ SPLAT_MAX_INSTANCES = 1 << 30
 SPLAT_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STAGES = {1: "slice_project", 2: "depth_sort", 3: "scan", 4: "duplicate", 5: "tile_sort",
-          6: "composite_fwd", 7: "composite_bwd", 8: "adjoint", 9: "convert"}
+          6: "composite_fwd", 7: "composite_bwd", 8: "adjoint", 9: "convert", 10: "densify"}
 
 
 class splat_g3(C.Structure):
@@ -82,6 +82,16 @@ class splat_adam_hyper(C.Structure):
                 ("beta2", C.c_float), ("eps", C.c_float), ("step", C.c_int32)]
 
 
+class splat_densify_rule(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("dense_scale", C.c_float), ("min_opacity", C.c_float),
+                ("split_shrink", C.c_float)]
+
+
+class splat_densify_set(C.Structure):
+    _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("state", C.POINTER(splat_adam_set)),
+                ("accum", C.c_void_p), ("count", C.c_void_p), ("noise", C.c_void_p)]
+
+
 _P = C.POINTER
 EXPORTS = {
     "splat_version": (C.c_int32, []),
@@ -115,6 +125,11 @@ EXPORTS = {
     "splat_cast_params": (C.c_int, [_P(splat_g3), _P(splat_g3), _P(splat_g4), _P(splat_g4), C.c_void_p]),
     "splat_convert_adam_state": (C.c_int, [_P(splat_g4), _P(splat_g3), C.c_float, _P(splat_adam_set),
                                            _P(splat_adam_set), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "splat_densify_stats": (C.c_int, [_P(splat_proj), _P(splat_view), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    "splat_densify": (C.c_int, [_P(splat_densify_rule), _P(splat_densify_set), _P(splat_densify_set), C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "splat_densify_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64, C.c_int64, C.c_int64]),
 }
 
 _lib = None
@@ -242,3 +257,15 @@ def splat_cast_params(src3, dst3, src4, dst4, stream):
 
 def splat_convert_adam_state(g4, g3, tau, s4, s3, status, ws, ws_bytes, stream):
     return lib().splat_convert_adam_state(g4, g3, tau, s4, s3, status, ws, ws_bytes, stream)
+
+
+def splat_densify_stats(proj, views, V, dproj, accum, count, stream):
+    return lib().splat_densify_stats(proj, views, V, dproj, accum, count, stream)
+
+
+def splat_densify(rule, set3, set4, n_out, status, ws, ws_bytes, stream):
+    return lib().splat_densify(rule, set3, set4, n_out, status, ws, ws_bytes, stream)
+
+
+def splat_densify_workspace_size(n3, cap3, n4, cap4):
+    return int(lib().splat_densify_workspace_size(int(n3), int(cap3), int(n4), int(cap4)))

@@ -51,6 +51,36 @@ struct OptArgs {
 cudaError_t launch_adam(const OptArgs&, const LaunchCtx&);
 cudaError_t launch_cast(const OptArgs&, const LaunchCtx&);
 
+struct StatArgs {
+    const float* dproj;
+    const uint32_t* n_tiles;
+    int64_t N;
+    int V;
+    float half_w[SPLAT_MAX_VIEWS], half_h[SPLAT_MAX_VIEWS];
+    float* accum;
+    float* count;
+};
+struct DensSet {
+    int64_t n, capacity;
+    float* p[6];
+    float* m[6];
+    float* v[6];
+    const float* accum;
+    const float* count;
+    const float* noise;
+    float* tp[6];
+    float* tm[6];
+    float* tv[6];
+    uint32_t* blocks;
+    int64_t* n_out;
+};
+struct DensRule {
+    float grad_threshold, dense_scale, min_opacity, split_shrink;
+};
+cudaError_t launch_dens_stats(const StatArgs&, const LaunchCtx&);
+cudaError_t launch_densify(const DensSet&, const DensSet&, const DensRule&, void*, int32_t*, const LaunchCtx&);
+size_t densify_workspace(int64_t n3, int64_t cap3, int64_t n4, int64_t cap4);
+
 static std::atomic<int64_t> g_spin_limit{1ll << 22};
 std::atomic<int64_t> g_launches{0};
 static std::atomic<int> g_ppl_fwd{8}, g_ppl_bwd{8};
@@ -471,6 +501,73 @@ splat_status splat_convert_adam_state(const splat_g4* g4, const splat_g3* g3, fl
     const LaunchCtx ctx = launch_ctx(stream);
     const splat_adam_set empty{};
     return cuda_status(launch_convert_state(*g4, *g3, tau, s4 ? *s4 : empty, s3 ? *s3 : empty, status, workspace, ctx));
+}
+
+splat_status splat_densify_stats(const splat_proj* proj, const splat_view* views, int V, const float* dproj,
+                                 float* accum, float* count, void* stream)
+{
+    if (!valid_views(views, V) || !valid_proj(proj, V) || proj->n < 0) return SPLAT_ERR_INVALID_ARG;
+    if (proj->n > 0 && (!proj->n_tiles || !dproj || !accum || !count || !aligned(dproj, 16)))
+        return SPLAT_ERR_INVALID_ARG;
+    StatArgs a{};
+    a.dproj = dproj;
+    a.n_tiles = (const uint32_t*)proj->n_tiles;
+    a.N = proj->n;
+    a.V = V;
+    for (int v = 0; v < V; ++v) {
+        a.half_w[v] = 0.5f * (float)views[v].W;
+        a.half_h[v] = 0.5f * (float)views[v].H;
+    }
+    a.accum = accum;
+    a.count = count;
+    const LaunchCtx ctx = launch_ctx(stream);
+    return cuda_status(launch_dens_stats(a, ctx));
+}
+
+size_t splat_densify_workspace_size(int64_t n3, int64_t capacity3, int64_t n4, int64_t capacity4)
+{
+    if (n3 < 0 || n4 < 0 || capacity3 < n3 || capacity4 < n4) return 0;
+    return densify_workspace(n3, capacity3, n4, capacity4);
+}
+
+static bool dens_set_ok(const splat_densify_set* s, int fields)
+{
+    if (!s || s->n < 0 || s->capacity < s->n) return false;
+    if (s->n == 0) return true;
+    if (!s->accum || !s->count || !s->noise || !valid_set(s->state, fields, s->n, true, true)) return false;
+    return true;
+}
+
+static DensSet dens_set_of(const splat_densify_set& s, int fields, int64_t* n_out)
+{
+    DensSet d{};
+    d.n = s.n;
+    d.capacity = s.capacity;
+    for (int f = 0; f < fields && s.n > 0; ++f) {
+        d.p[f] = s.state->param[f];
+        d.m[f] = s.state->m[f];
+        d.v[f] = s.state->v[f];
+    }
+    d.accum = s.accum;
+    d.count = s.count;
+    d.noise = s.noise;
+    d.n_out = n_out;
+    return d;
+}
+
+splat_status splat_densify(const splat_densify_rule* rule, splat_densify_set* set3, splat_densify_set* set4,
+                           int64_t* n_out, int32_t* status, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!rule || !n_out || !status || !dens_set_ok(set3, 5) || !dens_set_ok(set4, 6)) return SPLAT_ERR_INVALID_ARG;
+    if (!std::isfinite(rule->grad_threshold) || !std::isfinite(rule->dense_scale) ||
+        !std::isfinite(rule->min_opacity) || !std::isfinite(rule->split_shrink))
+        return SPLAT_ERR_INVALID_ARG;
+    const size_t need = densify_workspace(set3->n, set3->capacity, set4->n, set4->capacity);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
+    const DensRule r{rule->grad_threshold, rule->dense_scale, rule->min_opacity, rule->split_shrink};
+    const LaunchCtx ctx = launch_ctx(stream);
+    return cuda_status(launch_densify(dens_set_of(*set3, 5, n_out), dens_set_of(*set4, 6, n_out + 1), r, workspace,
+                                      status, ctx));
 }
 
 splat_status splat_l1_loss(const float* img, const float* target, int64_t n, float scale, float* dL_dimg,

@@ -53,17 +53,24 @@ class Gaussians:
         return int(self.t["mean3"].shape[0])
 
     @property
+    def capacity4(self) -> int:
+        return int(self.t["mean4"].shape[0])
+
+    @property
     def n(self) -> int:
         return self.n3 + self.n4
 
     @classmethod
-    def from_scene(cls, scene, device="cuda", dtype=torch.float32, capacity3: Optional[int] = None) -> "Gaussians":
+    def from_scene(cls, scene, device="cuda", dtype=torch.float32, capacity3: Optional[int] = None,
+                   capacity4: Optional[int] = None) -> "Gaussians":
         cap = scene.n3 if capacity3 is None else max(int(capacity3), scene.n3)
+        cap4 = scene.n4 if capacity4 is None else max(int(capacity4), scene.n4)
         t = {}
         for k in FIELDS3 + FIELDS4:
             a = torch.from_numpy(np.ascontiguousarray(getattr(scene, k), dtype=np.float32))
-            if k in FIELDS3 and cap > scene.n3:
-                pad = torch.zeros((cap - scene.n3,) + tuple(SHAPES[k]), dtype=torch.float32)
+            rows, n = (cap, scene.n3) if k in FIELDS3 else (cap4, scene.n4)
+            if rows > n:
+                pad = torch.zeros((rows - n,) + tuple(SHAPES[k]), dtype=torch.float32)
                 a = torch.cat([a, pad], 0)
             t[k] = a.to(device=device, dtype=dtype).contiguous()
         return cls(t, scene.n3, scene.n4)

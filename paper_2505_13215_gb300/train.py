@@ -15,6 +15,7 @@ allocated for all N Gaussians so the conversion appends in place.
 from __future__ import annotations
 
 import ctypes as C
+import math
 from typing import Dict, Optional, Sequence
 
 import torch
@@ -43,18 +44,34 @@ class AdamState:
             self.c.v[i] = self.v[k].data_ptr()
 
 
+# densification rules of 3DGS that the paper adopts (Sec. 4.3): gradient
+# threshold 2e-4 in normalised device coordinates, clones up to 1% of a scene
+# extent of 5, split children at 1/1.6 of the scale, pruning below opacity 0.005
+DEFAULT_DENSIFY = {"grad_threshold": 2e-4, "dense_scale": 0.05, "min_opacity": 5e-3, "split_shrink": math.log(1.6)}
+
+
 class Trainer:
     """Batched training of one hybrid scene.  `views` fixes the batch size and
-    resolutions; each step may bring other cameras and timestamps."""
+    resolutions; each step may bring other cameras and timestamps.  With
+    densify_every > 0 the sets are densified and pruned every densify_every
+    steps up to densify_until (before that step's conversion); capacity3 /
+    capacity4 bound the sets' rows (default: room for every Gaussian in either
+    set, and twice that with densification)."""
 
     def __init__(self, scene, views: Sequence, dtype=torch.bfloat16, device="cuda", tau: float = 1.0,
                  convert_every: int = 100, lr3: Optional[Dict[str, float]] = None,
                  lr4: Optional[Dict[str, float]] = None, lr_sh_rest: float = DEFAULT_LR_SH_REST,
-                 betas=(0.9, 0.999), eps: float = 1e-15, headroom: float = 1.25):
+                 betas=(0.9, 0.999), eps: float = 1e-15, headroom: float = 1.25, densify_every: int = 0,
+                 densify_until: int = 15000, densify: Optional[Dict[str, float]] = None,
+                 capacity3: Optional[int] = None, capacity4: Optional[int] = None):
         n = scene.n3 + scene.n4
-        self.master = Gaussians.from_scene(scene, device, dtype=torch.float32, capacity3=n)
+        grow = 2 if densify_every > 0 else 1
+        cap3 = capacity3 or grow * n
+        cap4 = capacity4 or (grow * n if densify_every > 0 else scene.n4)
+        self.master = Gaussians.from_scene(scene, device, dtype=torch.float32, capacity3=cap3, capacity4=cap4)
         self.store = self.master if dtype == torch.float32 else Gaussians.from_scene(scene, device, dtype=dtype,
-                                                                                  capacity3=n)
+                                                                                  capacity3=cap3,
+                                                                                  capacity4=cap4)
         self.s3 = AdamState(self.master, FIELDS3)
         self.s4 = AdamState(self.master, FIELDS4)
         self.R = Rasterizer(self.master.n3, self.master.n4, views, device=device, keep_keys=False, headroom=headroom)
@@ -78,6 +95,17 @@ class Trainer:
         self.conv_ws = torch.empty((int(wb),), dtype=torch.uint8, device=dev)
         self.n_moved = torch.zeros((1,), dtype=torch.int64, device=dev)
         self.moved_total = 0
+        self.views = list(views)
+        self.headroom = headroom
+        self.densify_every, self.densify_until = int(densify_every), int(densify_until)
+        self.rule = abi.splat_densify_rule()
+        for k, v in dict(DEFAULT_DENSIFY, **(densify or {})).items():
+            setattr(self.rule, k, v)
+        if self.densify_every > 0:
+            rows = self.master.capacity3 + self.master.capacity4
+            self.accum = torch.zeros((rows,), dtype=torch.float32, device=dev)
+            self.count = torch.zeros((rows,), dtype=torch.float32, device=dev)
+            self.n_out = torch.zeros((2,), dtype=torch.int64, device=dev)
 
     @property
     def n3(self) -> int:
@@ -101,7 +129,14 @@ class Trainer:
         conversion step, which reads the moved count)."""
         self.R.set_views(views)
         self.R.step(self.store, target, stream, marks)
+        densifying = self.densify_every > 0 and self.t < self.densify_until
+        if densifying:
+            abi.check(abi.splat_densify_stats(C.byref(self.R.cproj), self.R.cviews, self.R.V, _ptr(self.R.dproj),
+                                              _ptr(self.accum), _ptr(self.count), _stream(stream)),
+                      "splat_densify_stats")
         self.adam(stream)
+        if densifying and self.t % self.densify_every == 0:
+            self.densify(stream)
         if self.convert_every > 0 and self.t % self.convert_every == 0:
             self.convert(stream)
 
@@ -111,6 +146,10 @@ class Trainer:
         parameters, then the storage copy.  Synchronises once; returns the count."""
         m3, m4 = self.master.c_g3(), self.master.c_g4()
         st = _stream(stream)
+        need = max(abi.splat_workspace_size(op, 0, self.master.n4, self.R.W, self.R.H, 0)
+                   for op in (abi.SPLAT_OP_CONVERT_STATE, abi.SPLAT_OP_CONVERT))
+        if need > self.conv_ws.numel():  # the 4D set grew by densification
+            self.conv_ws = torch.empty((int(need),), dtype=torch.uint8, device=self.conv_ws.device)
         ws, wb = _ptr(self.conv_ws), self.conv_ws.numel()
         abi.check(abi.splat_convert_adam_state(C.byref(m4), C.byref(m3), self.tau, C.byref(self.s4.c),
                                                C.byref(self.s3.c), _ptr(self.R.status), ws, wb, st),
@@ -130,6 +169,40 @@ class Trainer:
         self.R.set_counts(self.master.n3, self.master.n4)
         self.moved_total += moved
         return moved
+
+    def densify(self, stream=None) -> tuple:
+        """Clone / split / prune both sets (Sec. 4.3) from the statistics gathered since
+        the last call, then the storage copy and a rasterizer for the new counts.
+        Synchronises once; returns the new (n3, n4)."""
+        n3, n4 = self.master.n3, self.master.n4
+        dev = self.accum.device
+        noise3 = torch.randn((max(1, n3), 2, 3), device=dev)
+        noise4 = torch.randn((max(1, n4), 2, 4), device=dev)
+        a, c = self.accum.data_ptr(), self.count.data_ptr()
+        d3 = abi.splat_densify_set(n3, self.master.capacity3, C.pointer(self.s3.c), a + 4 * n4, c + 4 * n4,
+                                   noise3.data_ptr())
+        d4 = abi.splat_densify_set(n4, self.master.capacity4, C.pointer(self.s4.c), a, c, noise4.data_ptr())
+        wb = abi.splat_densify_workspace_size(n3, self.master.capacity3, n4, self.master.capacity4)
+        ws = torch.empty((wb,), dtype=torch.uint8, device=dev)
+        st = _stream(stream)
+        abi.check(abi.splat_densify(C.byref(self.rule), C.byref(d3), C.byref(d4), _ptr(self.n_out),
+                                    _ptr(self.R.status), _ptr(ws), wb, st), "splat_densify")
+        self.R.check("densification")
+        n3, n4 = (int(x) for x in self.n_out.tolist())
+        for G in {id(self.master): self.master, id(self.store): self.store}.values():
+            G.n3, G.n4 = n3, n4
+        if self.store is not self.master:
+            s3, s4 = self.master.c_g3(), self.master.c_g4()
+            t3, t4 = self.store.c_g3(), self.store.c_g4()
+            abi.check(abi.splat_cast_params(C.byref(s3), C.byref(t3), C.byref(s4), C.byref(t4), st),
+                      "splat_cast_params")
+        self.accum.zero_()
+        self.count.zero_()
+        cap = self.R.capacity
+        self.R = Rasterizer(n3, n4, self.views, device=dev, keep_keys=False, headroom=self.headroom,
+                            capacity=cap)
+        self.R.autotune_capacity(self.store)
+        return n3, n4
 
     @property
     def loss(self) -> torch.Tensor:

@@ -193,3 +193,49 @@ def _trainer_lr(tr, k, n):
     if k in ("sh3", "sh4"):
         lr[:, 1:, :] = tr.hyper.lr_sh_rest
     return lr
+
+
+def test_trainer_densification_matches_oracle():
+    """Statistics gathered over the steps, then Trainer.densify: both master sets and
+    their moments equal the oracle's densification of the snapshot, with the same
+    N(0, 1) draws (the CUDA generator reseeded)."""
+    scene, views = _scene_with_time_scales(26, 900, 900, 1.0)
+    rule = {"grad_threshold": 1e-5, "dense_scale": 0.04}  # low threshold: the few steps densify something
+    tr = train.Trainer(scene, views, dtype=torch.bfloat16, convert_every=0, densify_every=1000, densify=rule)
+    target = torch.rand(tr.R.rgb.shape, device="cuda")
+    for _ in range(4):
+        tr.step(views, target)
+    torch.cuda.synchronize()
+    n3, n4 = tr.n3, tr.n4
+    snap = {k: tr.master.t[k][: (n3 if k in F3 else n4)].double().cpu().numpy() for k in F3 + F4}
+    mom = {k: ((tr.s3 if k in F3 else tr.s4).m[k][: (n3 if k in F3 else n4)].double().cpu().numpy(),
+               (tr.s3 if k in F3 else tr.s4).v[k][: (n3 if k in F3 else n4)].double().cpu().numpy())
+           for k in F3 + F4}
+    acc = tr.accum.double().cpu().numpy()
+    cnt = tr.count.double().cpu().numpy()
+    torch.manual_seed(123)
+    noise3 = torch.randn((max(1, n3), 2, 3), device="cuda").double().cpu().numpy()
+    noise4 = torch.randn((max(1, n4), 2, 4), device="cuda").double().cpu().numpy()
+    torch.manual_seed(123)
+    new3, new4 = tr.densify()
+    full = dict(train.DEFAULT_DENSIFY, **rule)
+    full = {k: float(np.float32(v)) for k, v in full.items()}
+    for four_d, fields, lo, hi, noise, n_new, s in ((False, F3, n4, n4 + n3, noise3, new3, tr.s3),
+                                                    (True, F4, 0, n4, noise4, new4, tr.s4)):
+        want_p, want_m, want_v = O.densify_set({k: snap[k] for k in fields}, {k: mom[k][0] for k in fields},
+                                               {k: mom[k][1] for k in fields}, acc[lo:hi], cnt[lo:hi], noise,
+                                               four_d=four_d, **full)
+        assert n_new == want_p[fields[0]].shape[0]
+        for k in fields:
+            got = tr.master.t[k][:n_new].double().cpu().numpy()
+            tol = 1e-6 if k in ("mean3", "mean4", "log_scale3", "log_scale4") else 0.0
+            np.testing.assert_allclose(got, want_p[k], rtol=tol, atol=tol, err_msg=k)
+            np.testing.assert_array_equal(s.m[k][:n_new].double().cpu().numpy(), want_m[k], err_msg=k)
+            assert torch.equal(tr.store.t[k][:n_new], tr.master.t[k][:n_new].to(torch.bfloat16)), k
+    assert (new3, new4) != (n3, n4)
+    # training goes on with the new counts
+    for _ in range(3):
+        tr.step(views, target)
+    torch.cuda.synchronize()
+    tr.R.check("after densification")
+    assert np.isfinite(float(tr.loss.item()))
