@@ -422,7 +422,10 @@ def run_train(args, hbm_peak, peak_src, dev, rank):
     rng = np.random.default_rng(500 + rank)
     scene = scenes.training_scene(seed=4, n=TRAIN_N, frac_static=0.7)
     views0 = scenes.random_arc_views(rng, TRAIN_VIEWS)
-    tr = train.Trainer(scene, views0, dtype=torch.bfloat16, tau=1.0, convert_every=TRAIN_STEPS)
+    # densification statistics gather every step (as in the paper's first 15k iterations);
+    # one densification pass is timed after the steps
+    tr = train.Trainer(scene, views0, dtype=torch.bfloat16, tau=1.0, convert_every=TRAIN_STEPS,
+                       densify_every=10 ** 9, densify_until=10 ** 9)
     gen = torch.Generator(device=dev)
     gen.manual_seed(77 + rank)
     target = torch.rand(tr.R.rgb.shape, generator=gen, device=dev)
@@ -440,9 +443,15 @@ def run_train(args, hbm_peak, peak_src, dev, rank):
     adam_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     t_before = tr.t
     ev0.record(stream)
+    import ctypes as C
+
+    from paper_2505_13215_gb300 import abi
+    from paper_2505_13215_gb300.raster import _ptr
     for k in range(steps):
         tr.R.set_views(batches[k % len(batches)])
         tr.R.step(tr.store, target)
+        abi.check(abi.splat_densify_stats(C.byref(tr.R.cproj), tr.R.cviews, tr.R.V, _ptr(tr.R.dproj),
+                                          _ptr(tr.accum), _ptr(tr.count), None), "splat_densify_stats")
         adam_ev[k][0].record(stream)
         tr.adam()
         adam_ev[k][1].record(stream)
@@ -452,19 +461,29 @@ def run_train(args, hbm_peak, peak_src, dev, rank):
     torch.cuda.synchronize()
     tr.R.check("training steps")
     total_ms = ev0.elapsed_time(ev1)
+    n_before = (tr.n3, tr.n4)
+    k_before = tr.R.instances()
+    t0 = time.perf_counter()
+    n_after = tr.densify()
+    torch.cuda.synchronize()
+    densify_ms = (time.perf_counter() - t0) * 1e3
     adam_ms = sum(a.elapsed_time(b) for a, b in adam_ev) / steps
     conversions = (tr.t // tr.convert_every) - (t_before // tr.convert_every)
-    floats = tr.n3 * (3 + 3 + 4 + 1 + 48) + tr.n4 * (4 + 4 + 4 + 4 + 1 + 48)
+    floats = n_before[0] * (3 + 3 + 4 + 1 + 48) + n_before[1] * (4 + 4 + 4 + 4 + 1 + 48)
     adam_bytes = floats * (4 + 12 + 12 + 2)  # gradient in; master, m, v in and out; BF16 copy out
     ach = adam_bytes / (adam_ms / 1e3) / 1e9
     return {
         "workload": "%d Gaussians starting 4D, %d random arc views/step at 1352x1014 over a 300-frame sequence, "
-                    "BF16 storage, L1 loss, fused Adam, 4D->3D conversion every %d steps" % (TRAIN_N, TRAIN_VIEWS,
+                    "BF16 storage, L1 loss, densification statistics, fused Adam, 4D->3D conversion every %d steps" % (TRAIN_N, TRAIN_VIEWS,
                                                                                           TRAIN_STEPS),
         "steps": steps, "ms_per_step": round(total_ms / steps, 3),
         "steps_per_s": round(1e3 * steps / total_ms, 2), "views_per_s": round(1e3 * steps * TRAIN_VIEWS / total_ms, 1),
         "conversions_timed": int(conversions), "moved_first_pass": int(moved0), "moved_total": int(tr.moved_total),
-        "n3": tr.n3, "n4": tr.n4, "share_4d": round(tr.n4 / (tr.n3 + tr.n4), 4), "instances_K": tr.R.instances(),
+        "n3": n_before[0], "n4": n_before[1], "share_4d": round(n_before[1] / sum(n_before), 4),
+        "instances_K": k_before,
+        "densify": {"ms": round(densify_ms, 2), "n3_after": n_after[0], "n4_after": n_after[1],
+                    "includes": "clone/split/prune of both sets, storage cast, a rasterizer for the new counts "
+                                "and its capacity tuning (one forward)"},
         "adam_ms": round(adam_ms, 4),
         "adam_roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                           "frac": round(ach / hbm_peak, 4), "algorithmic_bytes": int(adam_bytes),
