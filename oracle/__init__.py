@@ -35,7 +35,7 @@ class _G3(C.Structure):
 
 class _G4(C.Structure):
     _fields_ = [("n", C.c_int64), ("mean", _dp), ("log_scale", _dp), ("ql", _dp), ("qr", _dp),
-                ("opacity", _dp), ("sh", _dp)]
+                ("opacity", _dp), ("sh", _dp), ("n_time", C.c_int64)]
 
 
 class _View(C.Structure):
@@ -110,11 +110,15 @@ class _Packed:
         self.ql = _f64(_get(scene, "ql"), (-1, 4))
         self.qr = _f64(_get(scene, "qr"), (-1, 4))
         self.o4 = _f64(_get(scene, "opacity4"), (-1,))
-        self.s4 = _f64(_get(scene, "sh4"), (-1, 16, 3))
+        # sh4: [n][16 (T + 1)][3], the coefficient blocks of the T + 1 time frequencies
+        self.s4 = _f64(_get(scene, "sh4"))
+        self.n_time = self.s4.shape[1] // 16 - 1 if self.s4.ndim == 3 and self.s4.shape[0] else 0
+        self.s4 = self.s4.reshape(-1, 16 * (self.n_time + 1), 3)
         self.n3 = self.m3.shape[0]
         self.n4 = self.m4.shape[0]
         self.g3 = _G3(self.n3, _p(self.m3), _p(self.l3), _p(self.q3), _p(self.o3), _p(self.s3))
-        self.g4 = _G4(self.n4, _p(self.m4), _p(self.l4), _p(self.ql), _p(self.qr), _p(self.o4), _p(self.s4))
+        self.g4 = _G4(self.n4, _p(self.m4), _p(self.l4), _p(self.ql), _p(self.qr), _p(self.o4), _p(self.s4),
+                      self.n_time)
 
 
 def _view(v) -> _View:
@@ -251,7 +255,7 @@ def render_bwd(scene, view, dLdC):
         "mean3": np.zeros((pk.n3, 3)), "log_scale3": np.zeros((pk.n3, 3)), "quat3": np.zeros((pk.n3, 4)),
         "opacity3": np.zeros(pk.n3), "sh3": np.zeros((pk.n3, 16, 3)),
         "mean4": np.zeros((pk.n4, 4)), "log_scale4": np.zeros((pk.n4, 4)), "ql": np.zeros((pk.n4, 4)),
-        "qr": np.zeros((pk.n4, 4)), "opacity4": np.zeros(pk.n4), "sh4": np.zeros((pk.n4, 16, 3)),
+        "qr": np.zeros((pk.n4, 4)), "opacity4": np.zeros(pk.n4), "sh4": np.zeros((pk.n4, 16 * (pk.n_time + 1), 3)),
         "dproj": np.zeros((pk.n3 + pk.n4, 9)),
     }
     lib().oracle_render_bwd(C.byref(pk.g3), C.byref(pk.g4), C.byref(v), _p(g),

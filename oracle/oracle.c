@@ -61,7 +61,8 @@ typedef struct {
     const double *ql;        /* [n][4] left quaternion (a,b,c,d)             */
     const double *qr;        /* [n][4] right quaternion (p,q,r,s)            */
     const double *opacity;   /* [n]                                          */
-    const double *sh;        /* [n][16][3]                                   */
+    const double *sh;        /* [n][T+1][16][3]: coefficient block per time frequency */
+    int64_t n_time;          /* T: time frequencies of the colour, 0 = plain SH      */
 } og4;
 
 typedef struct {
@@ -336,9 +337,25 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 static int ifloor(double q) { return (int)floor(fmax(-1e9, fmin(1e9, q))); }
 static int iceil(double q) { return (int)ceil(fmax(-1e9, fmin(1e9, q))); }
 
-/* world mean/covariance of merged Gaussian i at the view's time (Eq. 2 or Eq. 5/6) */
+/* The 4D colour model with T > 0 time frequencies (4D spherindrical harmonics
+ * of 4DGS, which Sec. 3.2 defers to; reading N3): colour(d, t) = max(0, 0.5 +
+ * sum_n cos(2 pi n t) sum_k c_nk Y_k(d)), t in units of the sequence length.
+ * These are the effective degree-3 coefficients at t: sum_n cos(2 pi n t) c_n. */
+static void sh_at_time(const og4 *g4, int64_t i, double t, double out[48])
+{
+    const int64_t T = g4->n_time;
+    const double *c = g4->sh + 48 * (T + 1) * i;
+    for (int k = 0; k < 48; ++k) out[k] = 0.0;
+    for (int64_t n = 0; n <= T; ++n) {
+        const double w = cos(2.0 * M_PI * (double)n * t);
+        for (int k = 0; k < 48; ++k) out[k] += w * c[48 * n + k];
+    }
+}
+
+/* world mean/covariance of merged Gaussian i at the view's time (Eq. 2 or Eq. 5/6);
+ * sh points into the scene or, for a time-dependent 4D colour, to sh_buf */
 static void gaussian_world(const og3 *g3, const og4 *g4, int64_t i, double t,
-                           double mu[3], double cov[9], double *alpha_max, const double **sh)
+                           double mu[3], double cov[9], double *alpha_max, const double **sh, double sh_buf[48])
 {
     int64_t n4 = g4 ? g4->n : 0;
     if (i < n4) {
@@ -346,7 +363,12 @@ static void gaussian_world(const og3 *g3, const og4 *g4, int64_t i, double t,
         oracle_cov4(g4->ql + 4 * i, g4->qr + 4 * i, g4->log_scale + 4 * i, S4);
         oracle_slice(g4->mean + 4 * i, S4, t, mu, cov, &p);
         *alpha_max = sigmoid(g4->opacity[i]) * p;
-        *sh = g4->sh + 48 * i;
+        if (g4->n_time > 0) {
+            sh_at_time(g4, i, t, sh_buf);
+            *sh = sh_buf;
+        } else {
+            *sh = g4->sh + 48 * i;
+        }
     } else {
         int64_t j = i - n4;
         oracle_cov3(g3->quat + 4 * j, g3->log_scale + 3 * j, cov);
@@ -450,7 +472,8 @@ void oracle_project(const og3 *g3, const og4 *g4, const oview *v, oproj *out)
     for (int64_t i = 0; i < n4 + n3; ++i) {
         double mu[3], cov[9], am;
         const double *sh;
-        gaussian_world(g3, g4, i, v->time, mu, cov, &am, &sh);
+        double sh_buf[48];
+        gaussian_world(g3, g4, i, v->time, mu, cov, &am, &sh, sh_buf);
         project_one(mu, cov, am, sh, v, &out[i]);
     }
 }
@@ -919,7 +942,7 @@ static void slice_bwd(const double *mean4, const double *ql, const double *qr, c
  * be summed by calling once per view); dproj_out ([n][9], may be NULL) is
  * overwritten with the 2D gradients of this view.
  * 3D outputs: dmean3[n3][3], dlog3[n3][3], dquat3[n3][4], dop3[n3], dsh3[n3][48]
- * 4D outputs: dmean4[n4][4], dlog4[n4][4], dql[n4][4], dqr[n4][4], dop4[n4], dsh4[n4][48]
+ * 4D outputs: dmean4[n4][4], dlog4[n4][4], dql[n4][4], dqr[n4][4], dop4[n4], dsh4[n4][T+1][48]
  */
 void oracle_render_bwd(const og3 *g3, const og4 *g4, const oview *v, const double *dLdC,
                        double *dmean3, double *dlog3, double *dquat3, double *dop3, double *dsh3,
@@ -954,9 +977,9 @@ void oracle_render_bwd(const og3 *g3, const og4 *g4, const oview *v, const doubl
     for (int64_t i = 0; i < n; ++i) {
         if (!P[i].visible) continue;
         const double *dp = dproj + 9 * i;
-        double mu[3], cov[9], am, dmu[3], dcov[9], dam, dsh[48];
+        double mu[3], cov[9], am, dmu[3], dcov[9], dam, dsh[48], sh_buf[48];
         const double *sh;
-        gaussian_world(g3, g4, i, v->time, mu, cov, &am, &sh);
+        gaussian_world(g3, g4, i, v->time, mu, cov, &am, &sh, sh_buf);
         project_one_bwd(mu, cov, sh, v, dp, dmu, dcov, &dam, dsh);
         if (i < n4) {
             double S4[16], p_t, mu3[3], cov3[9];
@@ -975,7 +998,12 @@ void oracle_render_bwd(const og3 *g3, const og4 *g4, const oview *v, const doubl
                 dqr[4 * i + k] += gr[k];
                 dlog4[4 * i + k] += gs[k];
             }
-            for (int k = 0; k < 48; ++k) dsh4[48 * i + k] += dsh[k];
+            /* colour = sum_n cos(2 pi n t) (block n): block n gets cos(2 pi n t) dL/dsh_eff */
+            const int64_t T = g4->n_time;
+            for (int64_t n = 0; n <= T; ++n) {
+                const double w = cos(2.0 * M_PI * (double)n * v->time);
+                for (int k = 0; k < 48; ++k) dsh4[48 * ((T + 1) * i + n) + k] += w * dsh[k];
+            }
         } else {
             int64_t j = i - n4;
             double sg = sigmoid(g3->opacity[j]);
@@ -1058,7 +1086,8 @@ int64_t oracle_convert(const og4 *g4, double tau, int32_t *moved,
             log3[3 * nm + k] = g4->log_scale[4 * i + k];
         }
         op3[nm] = g4->opacity[i];
-        for (int k = 0; k < 48; ++k) sh3[48 * nm + k] = g4->sh[48 * i + k];
+        /* the colour keeps its time-constant block (the average over the sequence) */
+        for (int k = 0; k < 48; ++k) sh3[48 * nm + k] = g4->sh[48 * (g4->n_time + 1) * i + k];
         ++nm;
     }
     return nm;

@@ -113,3 +113,13 @@ def test_dproj_is_the_2d_gradient():
                       Pp["alpha"] - Pm["alpha"], *(Pp["rgb"] - Pm["rgb"])]) / (2 * h)
         acc[k] = d @ g["dproj"][n4 + j]
     np.testing.assert_allclose(acc, g["mean3"][j], rtol=1e-6, atol=1e-9)
+
+
+def test_gradients_with_time_dependent_colour():
+    """The 4D colour with two time frequencies (blocks of 16 x 3 coefficients
+    weighted by cos(2 pi n t)): every block's gradient, and all the others."""
+    sc, view = tiny_scene(3, t=0.3)
+    rng = np.random.default_rng(7)
+    extra = rng.normal(0, 0.2, (sc["sh4"].shape[0], 32, 3))
+    sc["sh4"] = np.concatenate([sc["sh4"], extra], 1)
+    assert check_fd(sc, view) > 300
