@@ -107,18 +107,23 @@ typedef struct {
     void *sh;         /* [capacity][16][3] SH coefficients, degree 3            */
 } splat_g3;
 
-/* Dynamic 4D Gaussians (Eq. 4 - Eq. 6). */
+/* Dynamic 4D Gaussians (Eq. 4 - Eq. 6).  The colour is degree-3 SH, or with
+ * sh_time = T > 0 the time-dependent model of 4D spherindrical harmonics that
+ * Sec. 3.2 defers to 4DGS for: colour(d, t) = max(0, 0.5 + sum_{n=0..T}
+ * cos(2 pi n t) sum_k c_nk Y_k(d)), t in units of the sequence length. */
 typedef struct {
     int64_t n;        /* N4                                                     */
     int32_t dtype;
-    int32_t reserved;
+    int32_t sh_time;  /* T, 0 .. SPLAT_MAX_SH_TIME (0: plain SH)                */
     void *mean;       /* [n][4] (x,y,z,t)                                       */
     void *log_scale;  /* [n][4] (s_x,s_y,s_z,s_t)                               */
     void *ql;         /* [n][4] left quaternion (a,b,c,d)                       */
     void *qr;         /* [n][4] right quaternion (p,q,r,s)                      */
     void *opacity;    /* [n]                                                    */
-    void *sh;         /* [n][16][3]                                             */
+    void *sh;         /* [n][T+1][16][3]: a coefficient block per time frequency */
 } splat_g4;
+
+#define SPLAT_MAX_SH_TIME 4
 
 /* One camera and timestamp (host memory; the library copies it into kernel
  * parameters).  x_cam = R x_world + T, R row major. */
@@ -375,6 +380,8 @@ typedef struct {
     const float *accum;    /* [n] statistics of splat_densify_stats (this set's rows)   */
     const float *count;    /* [n]                                                       */
     const float *noise;    /* [n][2][3] (3D set) or [n][2][4] (4D set) N(0, 1) draws    */
+    int32_t sh_time;       /* 4D set: the colour's time frequencies (splat_g4.sh_time); 3D: 0 */
+    int32_t reserved;
 } splat_densify_set;
 
 /*
@@ -397,8 +404,13 @@ typedef struct {
 splat_status splat_densify(const splat_densify_rule *rule, splat_densify_set *set3, splat_densify_set *set4,
                            int64_t *n_out, int32_t *status, void *workspace, size_t workspace_bytes, void *stream);
 
-/* Bytes of workspace splat_densify needs for sets of n rows and the given capacities. */
-size_t splat_densify_workspace_size(int64_t n3, int64_t capacity3, int64_t n4, int64_t capacity4);
+/* Bytes of workspace splat_densify needs for sets of n rows and the given capacities
+ * (sh_time4: the 4D set's colour time frequencies). */
+size_t splat_densify_workspace_size(int64_t n3, int64_t capacity3, int64_t n4, int64_t capacity4, int sh_time4);
+
+/* Workspace of SPLAT_OP_CONVERT / SPLAT_OP_CONVERT_STATE for a 4D set of N4 rows
+ * whose colour has sh_time time frequencies (splat_workspace_size assumes 0). */
+size_t splat_workspace_size_4d(int op, int64_t N4, int sh_time);
 
 /*
  * L1 photometric loss of a training step (Sec. 4.3 trains the rendered

@@ -24,6 +24,7 @@ SPLAT_BWD_STOP_2D = 1
 SPLAT_BWD_ADJOINT_ONLY = 2
 SPLAT_MAX_VIEWS = 16
 SPLAT_MAX_INSTANCES = 1 << 30
+SPLAT_MAX_SH_TIME = 4
 SPLAT_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STAGES = {1: "slice_project", 2: "depth_sort", 3: "scan", 4: "duplicate", 5: "tile_sort",
@@ -37,7 +38,7 @@ class splat_g3(C.Structure):
 
 
 class splat_g4(C.Structure):
-    _fields_ = [("n", C.c_int64), ("dtype", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("n", C.c_int64), ("dtype", C.c_int32), ("sh_time", C.c_int32),
                 ("mean", C.c_void_p), ("log_scale", C.c_void_p), ("ql", C.c_void_p), ("qr", C.c_void_p),
                 ("opacity", C.c_void_p), ("sh", C.c_void_p)]
 
@@ -89,7 +90,8 @@ class splat_densify_rule(C.Structure):
 
 class splat_densify_set(C.Structure):
     _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("state", C.POINTER(splat_adam_set)),
-                ("accum", C.c_void_p), ("count", C.c_void_p), ("noise", C.c_void_p)]
+                ("accum", C.c_void_p), ("count", C.c_void_p), ("noise", C.c_void_p), ("sh_time", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 _P = C.POINTER
@@ -129,7 +131,8 @@ EXPORTS = {
                                       C.c_void_p]),
     "splat_densify": (C.c_int, [_P(splat_densify_rule), _P(splat_densify_set), _P(splat_densify_set), C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
-    "splat_densify_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64, C.c_int64, C.c_int64]),
+    "splat_densify_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int]),
+    "splat_workspace_size_4d": (C.c_size_t, [C.c_int, C.c_int64, C.c_int]),
 }
 
 _lib = None
@@ -267,5 +270,9 @@ def splat_densify(rule, set3, set4, n_out, status, ws, ws_bytes, stream):
     return lib().splat_densify(rule, set3, set4, n_out, status, ws, ws_bytes, stream)
 
 
-def splat_densify_workspace_size(n3, cap3, n4, cap4):
-    return int(lib().splat_densify_workspace_size(int(n3), int(cap3), int(n4), int(cap4)))
+def splat_densify_workspace_size(n3, cap3, n4, cap4, sh_time4=0):
+    return int(lib().splat_densify_workspace_size(int(n3), int(cap3), int(n4), int(cap4), int(sh_time4)))
+
+
+def splat_workspace_size_4d(op, N4, sh_time):
+    return int(lib().splat_workspace_size_4d(int(op), int(N4), int(sh_time)))

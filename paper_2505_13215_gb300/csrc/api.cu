@@ -22,11 +22,11 @@ cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const Vie
 cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
                                  const float*, float*, int32_t*, int, unsigned long long*, const LaunchCtx&);
 cudaError_t launch_convert(const splat_g4&, const splat_g3&, float, int64_t*, int32_t*, void*, const LaunchCtx&);
-size_t convert_workspace(int64_t n4, int dtype_bytes);
+size_t convert_workspace(int64_t n4, int dtype_bytes, int sh_time);
 cudaError_t launch_l1_loss(const float*, const float*, int64_t, float, float*, float*, const LaunchCtx&);
 cudaError_t launch_convert_state(const splat_g4&, const splat_g3&, float, const splat_adam_set&,
                                  const splat_adam_set&, int32_t*, void*, const LaunchCtx&);
-size_t convert_state_workspace(int64_t n4);
+size_t convert_state_workspace(int64_t n4, int sh_time);
 
 constexpr int kMaxSegs = 11;
 struct OptSeg {
@@ -73,13 +73,14 @@ struct DensSet {
     float* tv[6];
     uint32_t* blocks;
     int64_t* n_out;
+    int wsh;
 };
 struct DensRule {
     float grad_threshold, dense_scale, min_opacity, split_shrink;
 };
 cudaError_t launch_dens_stats(const StatArgs&, const LaunchCtx&);
 cudaError_t launch_densify(const DensSet&, const DensSet&, const DensRule&, void*, int32_t*, const LaunchCtx&);
-size_t densify_workspace(int64_t n3, int64_t cap3, int64_t n4, int64_t cap4);
+size_t densify_workspace(int64_t n3, int64_t cap3, int64_t n4, int64_t cap4, int sh_time4);
 
 static std::atomic<int64_t> g_spin_limit{1ll << 22};
 std::atomic<int64_t> g_launches{0};
@@ -173,6 +174,7 @@ static bool valid_g4(const splat_g4& g)
     if (g.n < 0) return false;
     if (g.n == 0) return true;
     if (g.dtype < SPLAT_F32 || g.dtype > SPLAT_F16) return false;
+    if (g.sh_time < 0 || g.sh_time > SPLAT_MAX_SH_TIME) return false;
     return g.mean && g.log_scale && g.ql && g.qr && g.opacity && g.sh;
 }
 
@@ -261,9 +263,9 @@ size_t splat_workspace_size(int op, int64_t N3, int64_t N4, int V, const int32_t
         sort_b = bin_sort_workspace(N * V, capacity, V, TX, TY);
     }
     if (op == SPLAT_OP_COMPOSITE_BWD || op == SPLAT_OP_ALL) bwd_b = ((size_t)N * V * 48 + 255) & ~(size_t)255;
-    if (op == SPLAT_OP_CONVERT || op == SPLAT_OP_ALL) conv_b = convert_workspace(N4, 4);
+    if (op == SPLAT_OP_CONVERT || op == SPLAT_OP_ALL) conv_b = convert_workspace(N4, 4, 0);
     size_t state_b = 0;
-    if (op == SPLAT_OP_CONVERT_STATE || op == SPLAT_OP_ALL) state_b = convert_state_workspace(N4);
+    if (op == SPLAT_OP_CONVERT_STATE || op == SPLAT_OP_ALL) state_b = convert_state_workspace(N4, 0);
     if (op < SPLAT_OP_BIN_SORT || op > SPLAT_OP_CONVERT_STATE) return 0;
     size_t m = sort_b;
     if (bwd_b > m) m = bwd_b;
@@ -391,14 +393,15 @@ splat_status splat_convert_4d_to_3d(splat_g4* g4, splat_g3* g3, float tau, int64
     if (g4->n > 0 && g4->dtype == SPLAT_F32 && (!aligned(g4->ql, 16) || !aligned(g4->qr, 16)))
         return SPLAT_ERR_INVALID_ARG;
     const int bytes = g4->dtype == SPLAT_F32 ? 4 : 2;
-    const size_t need = convert_workspace(g4->n, bytes);
+    const size_t need = convert_workspace(g4->n, bytes, g4->sh_time);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
     const LaunchCtx ctx = launch_ctx(stream);
     return cuda_status(launch_convert(*g4, *g3, tau, n_moved_dev, status, workspace, ctx));
 }
 
 static const int kWidth3[5] = {3, 3, 4, 1, 48};
-static const int kWidth4[6] = {4, 4, 4, 4, 1, 48};
+// floats per row of a 4D field; sh holds a block of 48 per time frequency
+static int width4(int f, int sh_time) { return f < 4 ? 4 : (f == 4 ? 1 : 48 * (sh_time + 1)); }
 
 static bool valid_set(const splat_adam_set* s, int fields, int64_t rows, bool need_param, bool need_moments)
 {
@@ -427,6 +430,7 @@ splat_status splat_adam_step(const splat_adam_hyper* h, splat_adam_set* s3, cons
                              splat_adam_set* s4, const splat_grads4* dg4, splat_g4* g4, int32_t* status, void* stream)
 {
     if (!h || !g3 || !g4 || !status || h->step < 1) return SPLAT_ERR_INVALID_ARG;
+    if (g4->sh_time < 0 || g4->sh_time > SPLAT_MAX_SH_TIME) return SPLAT_ERR_INVALID_ARG;
     if (g3->n < 0 || g4->n < 0 || g3->capacity < g3->n || g3->dtype != g4->dtype) return SPLAT_ERR_INVALID_ARG;
     if (g3->dtype < SPLAT_F32 || g3->dtype > SPLAT_F16) return SPLAT_ERR_INVALID_ARG;
     if (!(h->beta1 >= 0.f && h->beta1 < 1.f) || !(h->beta2 >= 0.f && h->beta2 < 1.f) || !(h->eps > 0.f))
@@ -446,12 +450,13 @@ splat_status splat_adam_step(const splat_adam_hyper* h, splat_adam_set* s3, cons
     for (int f = 0; f < 5 && g3->n > 0; ++f) {
         if (!gr3[f] || !field3(*g3, f) || !std::isfinite(h->lr3[f])) return SPLAT_ERR_INVALID_ARG;
         a.seg[a.nseg++] = OptSeg{s3->param[f], s3->m[f], s3->v[f], gr3[f], field3(*g3, f), g3->n * kWidth3[f],
-                                 h->lr3[f], h->lr_sh_rest, f == 4};
+                                 h->lr3[f], h->lr_sh_rest, f == 4 ? 48 : 0};
     }
     for (int f = 0; f < 6 && g4->n > 0; ++f) {
         if (!gr4[f] || !field4(*g4, f) || !std::isfinite(h->lr4[f])) return SPLAT_ERR_INVALID_ARG;
-        a.seg[a.nseg++] = OptSeg{s4->param[f], s4->m[f], s4->v[f], gr4[f], field4(*g4, f), g4->n * kWidth4[f],
-                                 h->lr4[f], h->lr_sh_rest, f == 5};
+        a.seg[a.nseg++] = OptSeg{s4->param[f], s4->m[f], s4->v[f], gr4[f], field4(*g4, f),
+                                 g4->n * width4(f, g4->sh_time), h->lr4[f], h->lr_sh_rest,
+                                 f == 5 ? width4(5, g4->sh_time) : 0};
     }
     if (!std::isfinite(h->lr_sh_rest)) return SPLAT_ERR_INVALID_ARG;
     a.dtype = g3->dtype;
@@ -471,6 +476,8 @@ splat_status splat_cast_params(const splat_g3* src3, splat_g3* dst3, const splat
     if (!src3 || !dst3 || !src4 || !dst4) return SPLAT_ERR_INVALID_ARG;
     if (src3->dtype != SPLAT_F32 || src4->dtype != SPLAT_F32 || dst3->dtype != dst4->dtype) return SPLAT_ERR_INVALID_ARG;
     if (dst3->dtype < SPLAT_F32 || dst3->dtype > SPLAT_F16 || src3->n < 0 || src4->n < 0) return SPLAT_ERR_INVALID_ARG;
+    if (src4->sh_time != dst4->sh_time || src4->sh_time < 0 || src4->sh_time > SPLAT_MAX_SH_TIME)
+        return SPLAT_ERR_INVALID_ARG;
     if (src3->n > dst3->capacity) return SPLAT_ERR_INVALID_ARG;
     OptArgs a{};
     for (int f = 0; f < 5 && src3->n > 0; ++f) {
@@ -481,7 +488,7 @@ splat_status splat_cast_params(const splat_g3* src3, splat_g3* dst3, const splat
     for (int f = 0; f < 6 && src4->n > 0; ++f) {
         if (!field4(*src4, f) || !field4(*dst4, f)) return SPLAT_ERR_INVALID_ARG;
         a.seg[a.nseg++] = OptSeg{(float*)field4(*src4, f), nullptr, nullptr, nullptr, field4(*dst4, f),
-                                 src4->n * kWidth4[f], 0.f, 0.f, 0};
+                                 src4->n * width4(f, src4->sh_time), 0.f, 0.f, 0};
     }
     a.dtype = dst3->dtype;
     const LaunchCtx ctx = launch_ctx(stream);
@@ -496,7 +503,7 @@ splat_status splat_convert_adam_state(const splat_g4* g4, const splat_g3* g3, fl
     if (!valid_g4(*g4) || g3->n < 0 || g3->capacity < g3->n) return SPLAT_ERR_INVALID_ARG;
     if (!valid_set(s4, 6, g4->n, false, true)) return SPLAT_ERR_INVALID_ARG;
     if (g4->n > 0 && !valid_set(s3, 5, g3->capacity, false, true)) return SPLAT_ERR_INVALID_ARG;
-    const size_t need = convert_state_workspace(g4->n);
+    const size_t need = convert_state_workspace(g4->n, g4->sh_time);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
     const LaunchCtx ctx = launch_ctx(stream);
     const splat_adam_set empty{};
@@ -524,15 +531,24 @@ splat_status splat_densify_stats(const splat_proj* proj, const splat_view* views
     return cuda_status(launch_dens_stats(a, ctx));
 }
 
-size_t splat_densify_workspace_size(int64_t n3, int64_t capacity3, int64_t n4, int64_t capacity4)
+size_t splat_densify_workspace_size(int64_t n3, int64_t capacity3, int64_t n4, int64_t capacity4, int sh_time4)
 {
-    if (n3 < 0 || n4 < 0 || capacity3 < n3 || capacity4 < n4) return 0;
-    return densify_workspace(n3, capacity3, n4, capacity4);
+    if (n3 < 0 || n4 < 0 || capacity3 < n3 || capacity4 < n4 || sh_time4 < 0 || sh_time4 > SPLAT_MAX_SH_TIME) return 0;
+    return densify_workspace(n3, capacity3, n4, capacity4, sh_time4);
+}
+
+size_t splat_workspace_size_4d(int op, int64_t N4, int sh_time)
+{
+    if (N4 < 0 || sh_time < 0 || sh_time > SPLAT_MAX_SH_TIME) return 0;
+    if (op == SPLAT_OP_CONVERT) return convert_workspace(N4, 4, sh_time);
+    if (op == SPLAT_OP_CONVERT_STATE) return convert_state_workspace(N4, sh_time);
+    return 0;
 }
 
 static bool dens_set_ok(const splat_densify_set* s, int fields)
 {
-    if (!s || s->n < 0 || s->capacity < s->n) return false;
+    if (!s || s->n < 0 || s->capacity < s->n || s->sh_time < 0 || s->sh_time > SPLAT_MAX_SH_TIME) return false;
+    if (fields == 5 && s->sh_time != 0) return false;
     if (s->n == 0) return true;
     if (!s->accum || !s->count || !s->noise || !valid_set(s->state, fields, s->n, true, true)) return false;
     return true;
@@ -552,6 +568,7 @@ static DensSet dens_set_of(const splat_densify_set& s, int fields, int64_t* n_ou
     d.count = s.count;
     d.noise = s.noise;
     d.n_out = n_out;
+    d.wsh = 48 * (s.sh_time + 1);
     return d;
 }
 
@@ -562,7 +579,7 @@ splat_status splat_densify(const splat_densify_rule* rule, splat_densify_set* se
     if (!std::isfinite(rule->grad_threshold) || !std::isfinite(rule->dense_scale) ||
         !std::isfinite(rule->min_opacity) || !std::isfinite(rule->split_shrink))
         return SPLAT_ERR_INVALID_ARG;
-    const size_t need = densify_workspace(set3->n, set3->capacity, set4->n, set4->capacity);
+    const size_t need = densify_workspace(set3->n, set3->capacity, set4->n, set4->capacity, set4->sh_time);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
     const DensRule r{rule->grad_threshold, rule->dense_scale, rule->min_opacity, rule->split_shrink};
     const LaunchCtx ctx = launch_ctx(stream);

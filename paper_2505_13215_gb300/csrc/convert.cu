@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_scatter(splat_g4 g4, spla
         if (i >= g4.n) continue;
         const T* m = (const T*)g4.mean + i * 4;
         const T* ls = (const T*)g4.log_scale + i * 4;
-        const T* sh = (const T*)g4.sh + i * 48;
+        const int wsh = 48 * (g4.sh_time + 1);  // SH floats per 4D row
+        const T* sh = (const T*)g4.sh + i * wsh;
         if (st) {
             const int64_t d = g3.n + before;
             float ql[4], qr[4];
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_scatter(splat_g4 g4, spla
             for (int c = 0; c < 4; ++c) dq[c] = S::from(q[c]);
             ((T*)g3.opacity)[d] = ((const T*)g4.opacity)[i];
             T* dsh = (T*)g3.sh + d * 48;
-            for (int c = 0; c < 48; ++c) dsh[c] = sh[c];
+            for (int c = 0; c < 48; ++c) dsh[c] = sh[c];  // the time-constant block
         } else {
             const int64_t d = i - before;  // rows kept before i
             for (int c = 0; c < 4; ++c) {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_scatter(splat_g4 g4, spla
                 ((T*)tmp.qr)[d * 4 + c] = ((const T*)g4.qr)[i * 4 + c];
             }
             ((T*)tmp.opacity)[d] = ((const T*)g4.opacity)[i];
-            for (int c = 0; c < 48; ++c) ((T*)tmp.sh)[d * 48 + c] = sh[c];
+            for (int c = 0; c < wsh; ++c) ((T*)tmp.sh)[d * wsh + c] = sh[c];
         }
     }
 }
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_copyback(splat_g4 g4, Con
             ((T*)g4.qr)[i * 4 + c] = ((const T*)tmp.qr)[i * 4 + c];
         }
         ((T*)g4.opacity)[i] = ((const T*)tmp.opacity)[i];
-        for (int c = 0; c < 48; ++c) ((T*)g4.sh)[i * 48 + c] = ((const T*)tmp.sh)[i * 48 + c];
+        const int wsh = 48 * (g4.sh_time + 1);
+        for (int c = 0; c < wsh; ++c) ((T*)g4.sh)[i * wsh + c] = ((const T*)tmp.sh)[i * wsh + c];
     }
 }
 
@@ -215,7 +217,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_copyback(splat_g4 g4, Con
 // land in get zero moments.  The decision reads the parameter set g4, which
 // must still hold the values before the conversion.
 __host__ __device__ constexpr int width3(int f) { return f < 2 ? 3 : (f == 2 ? 4 : (f == 3 ? 1 : 48)); }
-__host__ __device__ constexpr int width4(int f) { return f < 4 ? 4 : (f == 4 ? 1 : 48); }
+// floats per 4D row of field f; sh holds a block of 48 per time frequency
+__host__ __device__ constexpr int width4(int f, int sh_time) { return f < 4 ? 4 : (f == 4 ? 1 : 48 * (sh_time + 1)); }
 
 struct StateTmp {  // workspace copy of the kept 4D rows' moments
     float* m[6];
@@ -227,6 +230,7 @@ __global__ void __launch_bounds__(kConvThreads) k_state_scatter(splat_g4 g4, flo
                                                                 const uint32_t* block_offsets, splat_adam_set s4,
                                                                 splat_adam_set s3, StateTmp tmp, int32_t* status)
 {
+    const int T = g4.sh_time;
     __shared__ uint32_t s_tmp[8];
     if (status_failed(status)) return;
     const int64_t base = (int64_t)blockIdx.x * kConvBlock;
@@ -260,15 +264,15 @@ __global__ void __launch_bounds__(kConvThreads) k_state_scatter(splat_g4 g4, flo
             const int64_t d = i - before;
 #pragma unroll
             for (int f = 0; f < 6; ++f)
-                for (int c = 0; c < width4(f); ++c) {
-                    tmp.m[f][d * width4(f) + c] = s4.m[f][i * width4(f) + c];
-                    tmp.v[f][d * width4(f) + c] = s4.v[f][i * width4(f) + c];
+                for (int c = 0; c < width4(f, T); ++c) {
+                    tmp.m[f][d * width4(f, T) + c] = s4.m[f][i * width4(f, T) + c];
+                    tmp.v[f][d * width4(f, T) + c] = s4.v[f][i * width4(f, T) + c];
                 }
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_state_copyback(int64_t n4, splat_adam_set s4, StateTmp tmp,
+__global__ void __launch_bounds__(256) k_state_copyback(int64_t n4, int T, splat_adam_set s4, StateTmp tmp,
                                                         const int64_t* n_moved, int32_t* status)
 {
     if (status_failed(status)) return;
@@ -276,20 +280,20 @@ __global__ void __launch_bounds__(256) k_state_copyback(int64_t n4, splat_adam_s
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < kept; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int f = 0; f < 6; ++f)
-            for (int c = 0; c < width4(f); ++c) {
-                s4.m[f][i * width4(f) + c] = tmp.m[f][i * width4(f) + c];
-                s4.v[f][i * width4(f) + c] = tmp.v[f][i * width4(f) + c];
+            for (int c = 0; c < width4(f, T); ++c) {
+                s4.m[f][i * width4(f, T) + c] = tmp.m[f][i * width4(f, T) + c];
+                s4.v[f][i * width4(f, T) + c] = tmp.v[f][i * width4(f, T) + c];
             }
     }
 }
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t convert_state_workspace(int64_t n4)
+size_t convert_state_workspace(int64_t n4, int T)
 {
     const int64_t nb = (n4 + kConvBlock - 1) / kConvBlock;
     size_t o = a256(4 * (size_t)(nb + 1)) + a256(8);
-    for (int f = 0; f < 6; ++f) o += 2 * a256(4 * (size_t)n4 * width4(f));
+    for (int f = 0; f < 6; ++f) o += 2 * a256(4 * (size_t)n4 * width4(f, T));
     return o;
 }
 
@@ -298,6 +302,7 @@ static cudaError_t convert_state_impl(const splat_g4& g4, const splat_g3& g3, fl
                                       const splat_adam_set& s3, int32_t* status, void* ws, const LaunchCtx& ctx)
 {
     const int64_t n4 = g4.n;
+    const int T = g4.sh_time;
     if (n4 == 0) return cudaSuccess;
     const int64_t nb = (n4 + kConvBlock - 1) / kConvBlock;
     char* w = (char*)ws;
@@ -308,9 +313,9 @@ static cudaError_t convert_state_impl(const splat_g4& g4, const splat_g3& g3, fl
     StateTmp tmp;
     for (int f = 0; f < 6; ++f) {
         tmp.m[f] = (float*)(w + o);
-        o += a256(4 * (size_t)n4 * width4(f));
+        o += a256(4 * (size_t)n4 * width4(f, T));
         tmp.v[f] = (float*)(w + o);
-        o += a256(4 * (size_t)n4 * width4(f));
+        o += a256(4 * (size_t)n4 * width4(f, T));
     }
     cudaStream_t s = ctx.stream;
     count_launch(4);
@@ -318,7 +323,7 @@ static cudaError_t convert_state_impl(const splat_g4& g4, const splat_g3& g3, fl
     k_conv_scan<<<1, 1024, 0, s>>>(counts, nb, g3.n, g3.capacity, n_moved, status);
     k_state_scatter<DT><<<(int)nb, kConvThreads, 0, s>>>(g4, tau, g3.n, counts, s4, s3, tmp, status);
     const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, (int64_t)ctx.num_sms * 8);
-    k_state_copyback<<<blocks, 256, 0, s>>>(n4, s4, tmp, n_moved, status);
+    k_state_copyback<<<blocks, 256, 0, s>>>(n4, T, s4, tmp, n_moved, status);
     return cudaGetLastError();
 }
 
@@ -332,11 +337,11 @@ cudaError_t launch_convert_state(const splat_g4& g4, const splat_g3& g3, float t
     }
 }
 
-size_t convert_workspace(int64_t n4, int dtype_bytes)
+size_t convert_workspace(int64_t n4, int dtype_bytes, int sh_time)
 {
     const int64_t nb = (n4 + kConvBlock - 1) / kConvBlock;
     return a256(4 * (size_t)(nb + 1)) + a256((size_t)dtype_bytes * n4 * 4) * 4 + a256((size_t)dtype_bytes * n4) +
-           a256((size_t)dtype_bytes * n4 * 48);
+           a256((size_t)dtype_bytes * n4 * 48 * (sh_time + 1));
 }
 
 template <int DT>

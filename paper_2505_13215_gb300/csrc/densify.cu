@@ -80,13 +80,14 @@ struct SetLayout;
 template <>
 struct SetLayout<3> {  // mean, log_scale, quat, opacity, sh
     static constexpr int F = 5;
-    __host__ __device__ static constexpr int width(int f) { return f < 2 ? 3 : (f == 2 ? 4 : (f == 3 ? 1 : 48)); }
+    // floats per row of field f; wsh: of the SH field
+    __host__ __device__ static constexpr int width(int f, int wsh) { return f < 2 ? 3 : (f == 2 ? 4 : (f == 3 ? 1 : wsh)); }
     static constexpr int kOpacity = 3;
 };
 template <>
-struct SetLayout<4> {  // mean, log_scale, ql, qr, opacity, sh
+struct SetLayout<4> {  // mean, log_scale, ql, qr, opacity, sh (a block of 48 per time frequency)
     static constexpr int F = 6;
-    __host__ __device__ static constexpr int width(int f) { return f < 4 ? 4 : (f == 4 ? 1 : 48); }
+    __host__ __device__ static constexpr int width(int f, int wsh) { return f < 4 ? 4 : (f == 4 ? 1 : wsh); }
     static constexpr int kOpacity = 4;
 };
 
@@ -103,6 +104,7 @@ struct DensSet {
     float* tv[6];
     uint32_t* blocks;    // per-block counts, then offsets: [nb][3]
     int64_t* n_out;      // new row count
+    int wsh;             // floats per row of the SH field
 };
 
 struct DensRule {
@@ -208,7 +210,7 @@ __device__ __forceinline__ void copy_row(const DensSet& s, int64_t src, int64_t 
 {
 #pragma unroll
     for (int f = 0; f < SetLayout<D>::F; ++f) {
-        const int w = SetLayout<D>::width(f);
+        const int w = SetLayout<D>::width(f, s.wsh);
         for (int c = 0; c < w; ++c) {
             s.tp[f][dst * w + c] = s.p[f][src * w + c];
             s.tm[f][dst * w + c] = moments ? s.m[f][src * w + c] : 0.f;
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(256) k_dens_copyback(DensSet s, int32_t* statu
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int f = 0; f < SetLayout<D>::F; ++f) {
-            const int w = SetLayout<D>::width(f);
+            const int w = SetLayout<D>::width(f, s.wsh);
             for (int c = 0; c < w; ++c) {
                 s.p[f][i * w + c] = s.tp[f][i * w + c];
                 s.m[f][i * w + c] = s.tm[f][i * w + c];
@@ -330,17 +332,17 @@ __global__ void __launch_bounds__(256) k_dens_copyback(DensSet s, int32_t* statu
 static size_t a256d(size_t x) { return (x + 255) & ~(size_t)255; }
 
 template <int D>
-size_t dens_set_workspace(int64_t n, int64_t capacity)
+size_t dens_set_workspace(int64_t n, int64_t capacity, int wsh)
 {
     const int64_t nb = (n + kDensBlock - 1) / kDensBlock + 1;
     size_t o = a256d(12 * (size_t)nb);
-    for (int f = 0; f < SetLayout<D>::F; ++f) o += 3 * a256d(4 * (size_t)capacity * SetLayout<D>::width(f));
+    for (int f = 0; f < SetLayout<D>::F; ++f) o += 3 * a256d(4 * (size_t)capacity * SetLayout<D>::width(f, wsh));
     return o;
 }
 
-size_t densify_workspace(int64_t n3, int64_t cap3, int64_t n4, int64_t cap4)
+size_t densify_workspace(int64_t n3, int64_t cap3, int64_t n4, int64_t cap4, int sh_time4)
 {
-    return dens_set_workspace<3>(n3, cap3) + dens_set_workspace<4>(n4, cap4);
+    return dens_set_workspace<3>(n3, cap3, 48) + dens_set_workspace<4>(n4, cap4, 48 * (sh_time4 + 1));
 }
 
 template <int D>
@@ -351,7 +353,7 @@ static DensSet carve_set(DensSet s, char* ws)
     s.blocks = (uint32_t*)(ws + o);
     o += a256d(12 * (size_t)(nb + 1));
     for (int f = 0; f < SetLayout<D>::F; ++f) {
-        const size_t b = a256d(4 * (size_t)s.capacity * SetLayout<D>::width(f));
+        const size_t b = a256d(4 * (size_t)s.capacity * SetLayout<D>::width(f, s.wsh));
         s.tp[f] = (float*)(ws + o);
         s.tm[f] = (float*)(ws + o + b);
         s.tv[f] = (float*)(ws + o + 2 * b);
@@ -367,7 +369,7 @@ cudaError_t launch_densify(const DensSet& s3in, const DensSet& s4in, const DensR
 {
     char* w = (char*)ws;
     const DensSet s3 = carve_set<3>(s3in, w);
-    const DensSet s4 = carve_set<4>(s4in, w + dens_set_workspace<3>(s3in.n, s3in.capacity));
+    const DensSet s4 = carve_set<4>(s4in, w + dens_set_workspace<3>(s3in.n, s3in.capacity, s3in.wsh));
     const int64_t nb3 = (s3.n + kDensBlock - 1) / kDensBlock, nb4 = (s4.n + kDensBlock - 1) / kDensBlock;
     cudaStream_t st = ctx.stream;
     cudaError_t e;

@@ -26,7 +26,8 @@ struct OptSeg {
     int64_t n;        // floats in the segment
     float lr;         // step size of the segment's floats
     float lr_rest;    // SH segments: step size of the coefficients of degree >= 1
-    int sh;           // 1: a [rows][16][3] SH field (the first 3 floats of a row are degree 0)
+    int sh;           // SH fields: floats per row (the first 3 of a row are the degree-0, time-constant
+                      // coefficients, which take lr); 0 for the other fields
 };
 
 struct OptArgs {
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kOptThreads) k_adam(OptArgs a)
         float4 p = ((float4*)s.p)[q];
         float lr[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) lr[k] = (s.sh && (4 * q + k) % 48 >= 3) ? s.lr_rest : s.lr;
+        for (int k = 0; k < 4; ++k) lr[k] = (s.sh && (4 * q + k) % s.sh >= 3) ? s.lr_rest : s.lr;
         p.x = adam_one(a, lr[0], g.x, m.x, v.x, p.x);
         p.y = adam_one(a, lr[1], g.y, m.y, v.y, p.y);
         p.z = adam_one(a, lr[2], g.z, m.z, v.z, p.z);
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kOptThreads) k_adam(OptArgs a)
     }
     // the floats a float4 walk does not cover (all of them when unaligned)
     for (int64_t i = (vec ? 4 * n4 : 0) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n; i += stride) {
-        const float lr = (s.sh && i % 48 >= 3) ? s.lr_rest : s.lr;
+        const float lr = (s.sh && i % s.sh >= 3) ? s.lr_rest : s.lr;
         float m = s.m[i], v = s.v[i];
         const float p = adam_one(a, lr, s.g[i], m, v, s.p[i]);
         s.m[i] = m;

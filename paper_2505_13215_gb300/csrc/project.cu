@@ -96,14 +96,12 @@ __device__ __forceinline__ void ewa_setup(const ViewParams& vp, const float mu[3
     e.det = e.s00 * e.s11 - e.s01 * e.s01;
 }
 
+// rgb += w sum_k c_k Y_k(d) for one block of 16 x 3 coefficients at p
 template <int DT>
-__device__ __forceinline__ void sh_rgb(const void* sh_base, int64_t row, const float dir[3], float rgb[3],
-                                       float Y[16])
+__device__ __forceinline__ void sh_block(const typename Storage<DT>::T* p, float w, const float Y[16], float& r,
+                                         float& g, float& b)
 {
     using S = Storage<DT>;
-    sh_basis(dir[0], dir[1], dir[2], Y);
-    const typename S::T* p = (const typename S::T*)sh_base + row * 48;
-    float r = 0.5f, g = 0.5f, b = 0.5f;
     if constexpr (DT == SPLAT_F32) {
         const float4* p4 = (const float4*)p;  // 48 floats = 12 float4
 #pragma unroll
@@ -113,6 +111,42 @@ __device__ __forceinline__ void sh_rgb(const void* sh_base, int64_t row, const f
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int idx = q * 4 + e;  // = k*3 + ch
+                const float term = w * cc[e] * Y[idx / 3];
+                if (idx % 3 == 0) r += term; else if (idx % 3 == 1) g += term; else b += term;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            r += w * S::ld(p + k * 3 + 0) * Y[k];
+            g += w * S::ld(p + k * 3 + 1) * Y[k];
+            b += w * S::ld(p + k * 3 + 2) * Y[k];
+        }
+    }
+}
+
+// weight of time frequency n at t: cos(2 pi n t), t in units of the sequence length
+__device__ __forceinline__ float time_weight(int n, float t) { return cospif(2.f * (float)n * t); }
+
+// rgb = 0.5 + sum_{n=0..T} cos(2 pi n t) sum_k c_nk Y_k(d) (unclamped); T = 0: plain SH.
+// Y receives the SH basis at d.
+template <int DT>
+__device__ __forceinline__ void sh_rgb(const void* sh_base, int64_t row, int T, float t, const float dir[3],
+                                       float rgb[3], float Y[16])
+{
+    using S = Storage<DT>;
+    sh_basis(dir[0], dir[1], dir[2], Y);
+    const typename S::T* p = (const typename S::T*)sh_base + row * 48 * (T + 1);
+    float r = 0.5f, g = 0.5f, b = 0.5f;
+    if constexpr (DT == SPLAT_F32) {
+        const float4* p4 = (const float4*)p;  // block 0 (weight 1), exactly the plain SH sum
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            float4 c = __ldg(p4 + q);
+            float cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int idx = q * 4 + e;
                 const float term = cc[e] * Y[idx / 3];
                 if (idx % 3 == 0) r += term; else if (idx % 3 == 1) g += term; else b += term;
             }
@@ -125,6 +159,7 @@ __device__ __forceinline__ void sh_rgb(const void* sh_base, int64_t row, const f
             b += S::ld(p + k * 3 + 2) * Y[k];
         }
     }
+    for (int n = 1; n <= T; ++n) sh_block<DT>(p + 48 * n, time_weight(n, t), Y, r, g, b);
     rgb[0] = r; rgb[1] = g; rgb[2] = b;
 }
 
@@ -283,7 +318,7 @@ __global__ void __launch_bounds__(128) k_slice_project(splat_g3 g3, splat_g4 g4,
                         const float id = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
                         d[0] *= id; d[1] *= id; d[2] *= id;
                         float rgb[3], Y[16];
-                        sh_rgb<DT>(sh_base, sh_row, d, rgb, Y);
+                        sh_rgb<DT>(sh_base, sh_row, is4 ? g4.sh_time : 0, vp.t, d, rgb, Y);
                         rd = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), e.z);
                     }
                 }
@@ -405,10 +440,17 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
         load_geo<DT>(g3, g4, i, is4, G);
         const void* sh_base = is4 ? g4.sh : g3.sh;
         const int64_t sh_row = is4 ? i : i - n4;
-        const typename St::T* shp = (const typename St::T*)sh_base + sh_row * 48;
+        const int Tn = is4 ? g4.sh_time : 0;  // time frequencies of the colour
+        const typename St::T* shp = (const typename St::T*)sh_base + sh_row * 48 * (Tn + 1);
+        // block 0's gradient in registers; blocks n >= 1 (weight cos(2 pi n t_v)) are summed in
+        // this thread's own rows of dg4.sh
         float dsh[48];
 #pragma unroll
         for (int k = 0; k < 48; ++k) dsh[k] = 0.f;
+        for (int n = 1; n <= Tn; ++n) {
+            float4* shg = (float4*)(dg4.sh + (i * (Tn + 1) + n) * 48);
+            for (int k = 0; k < 12; ++k) shg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         SymG GS = {0, 0, 0, 0, 0, 0};
         float gmu_sum[3] = {0, 0, 0};   // sum_v dL/dmu_v
         float gmu_dt[3] = {0, 0, 0};    // sum_v dL/dmu_v (t_v - mu_t)       (4D)
@@ -432,9 +474,9 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
             const float id = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             d[0] *= id; d[1] *= id; d[2] *= id;
             float rgb[3], Y[16];
-            sh_rgb<DT>(sh_base, sh_row, d, rgb, Y);
+            sh_rgb<DT>(sh_base, sh_row, Tn, vp.t, d, rgb, Y);
             const float gc[3] = {rgb[0] > 0.f ? dp[6] : 0.f, rgb[1] > 0.f ? dp[7] : 0.f, rgb[2] > 0.f ? dp[8] : 0.f};
-            float w[16];
+            float w[16];  // <dL/drgb, effective coefficients of Y_k at t>
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const float c0 = St::ld(shp + k * 3 + 0), c1 = St::ld(shp + k * 3 + 1), c2 = St::ld(shp + k * 3 + 2);
@@ -442,6 +484,18 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
                 dsh[k * 3 + 0] += gc[0] * Y[k];
                 dsh[k * 3 + 1] += gc[1] * Y[k];
                 dsh[k * 3 + 2] += gc[2] * Y[k];
+            }
+            for (int n = 1; n <= Tn; ++n) {
+                const float tw = time_weight(n, vp.t);
+                const typename St::T* pn = shp + 48 * n;
+                float* shg = dg4.sh + (i * (Tn + 1) + n) * 48;
+                for (int k = 0; k < 16; ++k) {
+                    w[k] += tw * (gc[0] * St::ld(pn + k * 3 + 0) + gc[1] * St::ld(pn + k * 3 + 1) +
+                                  gc[2] * St::ld(pn + k * 3 + 2));
+                    shg[k * 3 + 0] += tw * gc[0] * Y[k];
+                    shg[k * 3 + 1] += tw * gc[1] * Y[k];
+                    shg[k * 3 + 2] += tw * gc[2] * Y[k];
+                }
             }
             float gdir[3];
             sh_basis_grad(d[0], d[1], d[2], w, gdir);
@@ -570,7 +624,7 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
             ((float4*)dg4.ql)[i] = make_float4(gql[0], gql[1], gql[2], gql[3]);
             ((float4*)dg4.qr)[i] = make_float4(gqr[0], gqr[1], gqr[2], gqr[3]);
             dg4.opacity[i] = gal * sg * (1.f - sg);
-            float4* shg = (float4*)(dg4.sh + i * 48);
+            float4* shg = (float4*)(dg4.sh + i * (Tn + 1) * 48);
 #pragma unroll
             for (int k = 0; k < 12; ++k) shg[k] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
         } else {

@@ -22,6 +22,12 @@ FIELDS4 = ("mean4", "log_scale4", "ql", "qr", "opacity4", "sh4")
 SHAPES = {"mean3": (3,), "log_scale3": (3,), "quat3": (4,), "opacity3": (), "sh3": (16, 3),
           "mean4": (4,), "log_scale4": (4,), "ql": (4,), "qr": (4,), "opacity4": (), "sh4": (16, 3)}
 
+
+def shape_of(k: str, sh_time: int = 0):
+    """Per-row shape of field k; a 4D colour with sh_time time frequencies holds
+    a block of 16 x 3 coefficients per frequency."""
+    return (16 * (sh_time + 1), 3) if k == "sh4" else SHAPES[k]
+
 _DTYPES = {torch.float32: abi.SPLAT_F32, torch.bfloat16: abi.SPLAT_BF16, torch.float16: abi.SPLAT_F16}
 
 
@@ -47,6 +53,7 @@ class Gaussians:
             raise ValueError("all fields must share one dtype")
         self.dtype = dt
         self.code = _DTYPES[dt]
+        self.sh_time = int(t["sh4"].shape[1]) // 16 - 1 if t["sh4"].dim() == 3 else 0
 
     @property
     def capacity3(self) -> int:
@@ -70,7 +77,7 @@ class Gaussians:
             a = torch.from_numpy(np.ascontiguousarray(getattr(scene, k), dtype=np.float32))
             rows, n = (cap, scene.n3) if k in FIELDS3 else (cap4, scene.n4)
             if rows > n:
-                pad = torch.zeros((rows - n,) + tuple(SHAPES[k]), dtype=torch.float32)
+                pad = torch.zeros((rows - n,) + tuple(a.shape[1:]), dtype=torch.float32)
                 a = torch.cat([a, pad], 0)
             t[k] = a.to(device=device, dtype=dtype).contiguous()
         return cls(t, scene.n3, scene.n4)
@@ -91,7 +98,7 @@ class Gaussians:
 
     def c_g4(self) -> abi.splat_g4:
         t = self.t
-        return abi.splat_g4(self.n4, self.code, 0, t["mean4"].data_ptr(), t["log_scale4"].data_ptr(),
+        return abi.splat_g4(self.n4, self.code, self.sh_time, t["mean4"].data_ptr(), t["log_scale4"].data_ptr(),
                             t["ql"].data_ptr(), t["qr"].data_ptr(), t["opacity4"].data_ptr(), t["sh4"].data_ptr())
 
 
@@ -120,7 +127,7 @@ class Rasterizer:
     first render (see `autotune_capacity`)."""
 
     def __init__(self, n3: int, n4: int, views: Sequence, device="cuda", capacity: Optional[int] = None,
-                 headroom: float = 1.25, keep_keys: bool = True):
+                 headroom: float = 1.25, keep_keys: bool = True, sh_time: int = 0):
         self.keep_keys = keep_keys
         self.n3, self.n4 = int(n3), int(n4)
         self.N = self.n3 + self.n4
@@ -160,7 +167,9 @@ class Rasterizer:
         self.dL = torch.zeros_like(self.rgb)
         # gradient rows for N Gaussians in either set, so that the 3D / 4D split can
         # change (4D -> 3D conversion) without reallocating; self.grads views the first n
-        self._grad_buf = {k: torch.zeros((self.N,) + SHAPES[k], dtype=f32, device=d) for k in FIELDS3 + FIELDS4}
+        self.sh_time = int(sh_time)
+        self._grad_buf = {k: torch.zeros((self.N,) + shape_of(k, self.sh_time), dtype=f32, device=d)
+                          for k in FIELDS3 + FIELDS4}
         self.cg3 = abi.splat_grads3(*[self._grad_buf[k].data_ptr() for k in FIELDS3])
         self.cg4 = abi.splat_grads4(*[self._grad_buf[k].data_ptr() for k in FIELDS4])
         self._view_grads()
@@ -204,6 +213,8 @@ class Rasterizer:
     def slice_project(self, G: Gaussians, stream=None):
         if G.n3 != self.n3 or G.n4 != self.n4:
             raise ValueError("Gaussian counts differ from the rasterizer's")
+        if G.sh_time != self.sh_time:
+            raise ValueError("the 4D colour's time frequencies differ from the rasterizer's")
         g3, g4 = G.c_g3(), G.c_g4()
         abi.check(abi.splat_slice_project(C.byref(g3), C.byref(g4), self.cviews, self.V, C.byref(self.cproj),
                                           _ptr(self.status), _stream(stream)), "splat_slice_project")
@@ -393,7 +404,7 @@ class HybridRasterize(torch.autograd.Function):
 
 def render(G: Gaussians, views, capacity=None) -> List[torch.Tensor]:
     """Convenience: render the views, return [3, H, W] images (synchronises)."""
-    R = Rasterizer(G.n3, G.n4, views, device=G.t["mean3"].device, capacity=capacity)
+    R = Rasterizer(G.n3, G.n4, views, device=G.t["mean3"].device, capacity=capacity, sh_time=G.sh_time)
     R.autotune_capacity(G)
     R.forward(G)
     R.check("render")
@@ -405,9 +416,7 @@ def convert_4d_to_3d(G: Gaussians, tau: float, stream=None) -> int:
     3D set (appending within capacity3) and compacts the 4D set.  Synchronises
     once to read the moved count.  Returns the number moved."""
     dev = G.t["mean3"].device
-    bytes_ = abi.lib().splat_workspace_size(abi.SPLAT_OP_CONVERT, G.n3, G.n4, 0, None, None, 0)
-    if G.code != abi.SPLAT_F32:
-        bytes_ = max(bytes_, 256)
+    bytes_ = max(256, abi.splat_workspace_size_4d(abi.SPLAT_OP_CONVERT, G.n4, G.sh_time))
     ws = torch.empty((int(bytes_),), dtype=torch.uint8, device=dev)
     status = torch.zeros((4,), dtype=torch.int32, device=dev)
     n_moved = torch.zeros((1,), dtype=torch.int64, device=dev)

@@ -74,7 +74,8 @@ class Trainer:
                                                                                   capacity4=cap4)
         self.s3 = AdamState(self.master, FIELDS3)
         self.s4 = AdamState(self.master, FIELDS4)
-        self.R = Rasterizer(self.master.n3, self.master.n4, views, device=device, keep_keys=False, headroom=headroom)
+        self.R = Rasterizer(self.master.n3, self.master.n4, views, device=device, keep_keys=False, headroom=headroom,
+                            sh_time=self.master.sh_time)
         self.R.autotune_capacity(self.store)
         self.tau = float(tau)
         self.convert_every = int(convert_every)
@@ -90,8 +91,8 @@ class Trainer:
         self.hyper.beta1, self.hyper.beta2 = betas
         self.hyper.eps = eps
         dev = self.master.t["mean3"].device
-        wb = abi.splat_workspace_size(abi.SPLAT_OP_CONVERT_STATE, 0, self.master.n4, self.R.W, self.R.H, 0)
-        wb = max(wb, abi.splat_workspace_size(abi.SPLAT_OP_CONVERT, 0, self.master.n4, self.R.W, self.R.H, 0))
+        wb = max(abi.splat_workspace_size_4d(op, self.master.n4, self.master.sh_time)
+                 for op in (abi.SPLAT_OP_CONVERT_STATE, abi.SPLAT_OP_CONVERT))
         self.conv_ws = torch.empty((int(wb),), dtype=torch.uint8, device=dev)
         self.n_moved = torch.zeros((1,), dtype=torch.int64, device=dev)
         self.moved_total = 0
@@ -146,7 +147,7 @@ class Trainer:
         parameters, then the storage copy.  Synchronises once; returns the count."""
         m3, m4 = self.master.c_g3(), self.master.c_g4()
         st = _stream(stream)
-        need = max(abi.splat_workspace_size(op, 0, self.master.n4, self.R.W, self.R.H, 0)
+        need = max(abi.splat_workspace_size_4d(op, self.master.n4, self.master.sh_time)
                    for op in (abi.SPLAT_OP_CONVERT_STATE, abi.SPLAT_OP_CONVERT))
         if need > self.conv_ws.numel():  # the 4D set grew by densification
             self.conv_ws = torch.empty((int(need),), dtype=torch.uint8, device=self.conv_ws.device)
@@ -180,9 +181,11 @@ class Trainer:
         noise4 = torch.randn((max(1, n4), 2, 4), device=dev)
         a, c = self.accum.data_ptr(), self.count.data_ptr()
         d3 = abi.splat_densify_set(n3, self.master.capacity3, C.pointer(self.s3.c), a + 4 * n4, c + 4 * n4,
-                                   noise3.data_ptr())
-        d4 = abi.splat_densify_set(n4, self.master.capacity4, C.pointer(self.s4.c), a, c, noise4.data_ptr())
-        wb = abi.splat_densify_workspace_size(n3, self.master.capacity3, n4, self.master.capacity4)
+                                   noise3.data_ptr(), 0)
+        d4 = abi.splat_densify_set(n4, self.master.capacity4, C.pointer(self.s4.c), a, c, noise4.data_ptr(),
+                                   self.master.sh_time)
+        wb = abi.splat_densify_workspace_size(n3, self.master.capacity3, n4, self.master.capacity4,
+                                              self.master.sh_time)
         ws = torch.empty((wb,), dtype=torch.uint8, device=dev)
         st = _stream(stream)
         abi.check(abi.splat_densify(C.byref(self.rule), C.byref(d3), C.byref(d4), _ptr(self.n_out),
@@ -200,7 +203,7 @@ class Trainer:
         self.count.zero_()
         cap = self.R.capacity
         self.R = Rasterizer(n3, n4, self.views, device=dev, keep_keys=False, headroom=self.headroom,
-                            capacity=cap)
+                            capacity=cap, sh_time=self.master.sh_time)
         self.R.autotune_capacity(self.store)
         return n3, n4
 

@@ -37,7 +37,7 @@ class tile_cull:
 
 def make(scene, views, dtype=torch.float32, capacity3=None):
     G = raster.Gaussians.from_scene(scene, "cuda", dtype=dtype, capacity3=capacity3)
-    R = raster.Rasterizer(G.n3, G.n4, views)
+    R = raster.Rasterizer(G.n3, G.n4, views, sh_time=G.sh_time)
     R.autotune_capacity(G)
     R.forward(G)
     torch.cuda.synchronize()
