@@ -186,7 +186,8 @@ FLOPS_BLEND = {"composite_fwd": 17, "composite_bwd": 35}
 KERNEL_SOURCES = {"composite_fwd": ["composite.cu", "splat_internal.cuh"],
                   "composite_bwd": ["composite.cu", "splat_internal.cuh"],
                   "slice_project": ["project.cu", "splat_internal.cuh"],
-                  "adjoint": ["project.cu", "splat_internal.cuh"]}
+                  "adjoint": ["project.cu", "splat_internal.cuh"],
+                  "adam": ["optim.cu", "splat_internal.cuh"]}
 
 
 def source_digest(stage):
@@ -198,9 +199,10 @@ def source_digest(stage):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(stage, views):
-    """DRAM bytes per launch of `stage` from the committed ncu summary, scaled to
-    `views` views; None when the kernel's source changed since the capture."""
+def measured_traffic(stage, views=None):
+    """DRAM bytes per launch of `stage` from the committed ncu summary (per view,
+    scaled to `views` views, or per launch); None when the kernel's source changed
+    since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             t = json.load(fh)[stage]
@@ -208,7 +210,9 @@ def measured_traffic(stage, views):
         return None
     if t.get("source_digest") != source_digest(stage):
         return None
-    return int(t["dram_bytes_per_view"] * views)
+    if "dram_bytes_per_view" in t:
+        return int(t["dram_bytes_per_view"] * views)
+    return int(t["dram_bytes_per_launch"])
 
 
 # ---------------------------------------------------------------------------
@@ -509,6 +513,7 @@ def run_train(args, hbm_peak, peak_src, dev, rank):
         "adam_ms": round(adam_ms, 4),
         "adam_roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                           "frac": round(ach / hbm_peak, 4), "algorithmic_bytes": int(adam_bytes),
+                          "traffic": measured_traffic("adam"),
                           "peak_source": peak_src + " (copy bandwidth)"},
         "data": "synthetic",
     }
@@ -611,6 +616,26 @@ def run_profile(args):
     print("K", R.instances())
 
 
+def run_profile_train(args):
+    """Untimed training steps of the training workload (for profilers); prints the counts."""
+    import numpy as np
+    import torch
+
+    from paper_2505_13215_gb300 import scenes, train
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(500)
+    scene = scenes.training_scene(seed=4, n=TRAIN_N, frac_static=0.7)
+    tr = train.Trainer(scene, scenes.random_arc_views(rng, TRAIN_VIEWS), dtype=torch.bfloat16, tau=1.0,
+                       convert_every=0)
+    tr.convert()
+    target = torch.rand(tr.R.rgb.shape, device="cuda")
+    for _ in range(args.profile_train):
+        tr.step(scenes.random_arc_views(rng, TRAIN_VIEWS), target)
+    torch.cuda.synchronize()
+    tr.R.check("profile training steps")
+    print("n3", tr.n3, "n4", tr.n4)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -623,11 +648,15 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--profile", type=int, default=0, help="run this many untimed eager steps (for ncu) and exit")
+    ap.add_argument("--profile-train", type=int, default=0,
+                    help="run this many untimed steps of the training workload (for ncu) and exit")
     ap.add_argument("--dtype", choices=("bf16", "f32"), default="bf16", help="storage dtype of --profile")
     ap.add_argument("--ppl", default="2,4", help="pixels per lane (forward,backward) of --profile")
     args = ap.parse_args(argv)
     if args.profile:
         return run_profile(args)
+    if args.profile_train:
+        return run_profile_train(args)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank, local, world = dist_env()
