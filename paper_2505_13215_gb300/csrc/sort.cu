@@ -941,11 +941,20 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
     __shared__ float4 s_g0[COUNT ? 256 : 1], s_g1[COUNT ? 256 : 1], s_g2[COUNT ? 256 : 1];  // footprint constants
     __shared__ uint32_t s_row[COUNT ? 1 : 256];
     __shared__ uint2 s_mask[256];
+    // COUNT: coverage byte -> four words of two 16-bit column counters (columns 2q, 2q + 1),
+    // so that four warp reductions count all eight columns of 32 entries
+    __shared__ uint4 s_spread[COUNT ? 256 : 1];
     __shared__ int s_gs;
     if (status_failed(a.status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const uint32_t nseg = a.seg_base[a.total_super];
+    if (COUNT) {
+        const unsigned b = threadIdx.x;
+        s_spread[b] = make_uint4((b & 1u) | ((b >> 1 & 1u) << 16), (b >> 2 & 1u) | ((b >> 3 & 1u) << 16),
+                                 (b >> 4 & 1u) | ((b >> 5 & 1u) << 16), (b >> 6 & 1u) | ((b >> 7 & 1u) << 16));
+        __syncthreads();
+    }
     for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
         if (threadIdx.x == 0) {  // super-tile of segment g: last gs with seg_base[gs] <= g
             int lo = 0, hi = a.total_super - 1;
@@ -967,6 +976,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
         const int tx0 = sx * 8;
         const float vlo = (float)(ty * kTile), vhi = vlo + (float)(kTile - 1);
         uint32_t cur[8];
+        uint32_t packed[4] = {0u, 0u, 0u, 0u};  // COUNT: column counters, two per word
         const uint32_t* off = a.seg_cnt + (size_t)g * 64 + warp * 8;  // (after k_seg_prefix) segment offsets
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -1032,17 +1042,25 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                             m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu;
                         }
                     }
-                    const uint32_t row = COUNT ? 0u : s_row[e < n ? e : 0];
+                    if (COUNT) {
+                        const uint4 w = s_spread[m];
+                        packed[0] += __reduce_add_sync(0xffffffffu, w.x);
+                        packed[1] += __reduce_add_sync(0xffffffffu, w.y);
+                        packed[2] += __reduce_add_sync(0xffffffffu, w.z);
+                        packed[3] += __reduce_add_sync(0xffffffffu, w.w);
+                    } else {
+                        const uint32_t row = s_row[e < n ? e : 0];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const bool cov = (m >> k) & 1u;
-                        const unsigned bal = __ballot_sync(0xffffffffu, cov);
-                        if (!COUNT && cov) {
-                            const uint32_t pos = cur[k] + __popc(bal & lt);
-                            a.vals_out[pos] = row;
-                            if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
+                        for (int k = 0; k < 8; ++k) {
+                            const bool cov = (m >> k) & 1u;
+                            const unsigned bal = __ballot_sync(0xffffffffu, cov);
+                            if (cov) {
+                                const uint32_t pos = cur[k] + __popc(bal & lt);
+                                a.vals_out[pos] = row;
+                                if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
+                            }
+                            cur[k] += __popc(bal);
                         }
-                        cur[k] += __popc(bal);
                     }
                 }
             }
@@ -1051,10 +1069,10 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                 if (j < rg.y) a.mask[j] = s_mask[threadIdx.x];
             }
         }
-        if (COUNT) {
+        if (COUNT) {  // at most kFilterSeg entries per segment: the 16-bit counters do not overflow
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                if (lane == k) a.seg_cnt[(size_t)g * 64 + warp * 8 + k] = cur[k];
+                if (lane == k) a.seg_cnt[(size_t)g * 64 + warp * 8 + k] = (packed[k >> 1] >> (16 * (k & 1))) & 0xffffu;
         }
         __syncthreads();
     }
