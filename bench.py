@@ -409,6 +409,7 @@ def run_ours(args, rank, local, world):
                    "views_per_step": V, "gaussians": N3 + N4, "resolution": [W, H], "l2": "flushed before each step",
                    "instances_K": K_inst, "autotune": {k: tune[k] for k in ("ppl_fwd", "ppl_bwd", "capacity")},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "mpixel_per_s": round(value * W * H / 1e6, 1),
         "plain_fp32": {"value": round(plain_value, 2), "unit": UNIT, "path": "per-view launches, FP32 storage, eager"},
         "stage_ms": {k: round(v, 4) for k, v in stages.items()},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,

@@ -274,9 +274,23 @@ __global__ void __launch_bounds__(128) k_slice_project(splat_g3 g3, splat_g4 g4,
         load_geo<DT>(g3, g4, i, is4, G);
         const void* sh_base = is4 ? g4.sh : g3.sh;
         const int64_t sh_row = is4 ? i : i - n4;
+        // non-finite parameters: reported (row of the first view) and the Gaussian culled
+        const float gsum = G.mu[0] + G.mu[1] + G.mu[2] + G.S.xx + G.S.xy + G.S.xz + G.S.yy + G.S.yz + G.S.zz + G.op +
+                           (is4 ? G.mu_t + G.inv_n2 : 0.f);
+        const bool bad = !isfinite(gsum);
+        if (bad) set_status(status, SPLAT_ERR_NONFINITE, SPLAT_STAGE_SLICE_PROJECT, i);
         for (int v = 0; v < vb.V; ++v) {
             const ViewParams& vp = vb.v[v];
             const int64_t row = v * N + i;
+            if (bad) {
+                ((float2*)out.xy)[row] = make_float2(0.f, 0.f);
+                ((float4*)out.conic_opacity)[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ((float4*)out.rgb_depth)[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ((int4*)out.rect)[row] = make_int4(0, 0, 0, 0);
+                out.radius[row] = 0;
+                out.n_tiles[row] = 0;
+                continue;
+            }
             float mu[3], alpha, p_t, dt;
             at_time(G, is4, vp.t, mu, alpha, p_t, dt);
             Ewa e;
@@ -320,6 +334,10 @@ __global__ void __launch_bounds__(128) k_slice_project(splat_g3 g3, splat_g4 g4,
                         float rgb[3], Y[16];
                         sh_rgb<DT>(sh_base, sh_row, is4 ? g4.sh_time : 0, vp.t, d, rgb, Y);
                         rd = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), e.z);
+                        if (!isfinite(rgb[0] + rgb[1] + rgb[2])) {  // non-finite colour coefficients
+                            set_status(status, SPLAT_ERR_NONFINITE, SPLAT_STAGE_SLICE_PROJECT, row);
+                            culled = true;
+                        }
                     }
                 }
             }

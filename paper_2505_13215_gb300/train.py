@@ -207,6 +207,39 @@ class Trainer:
         self.R.autotune_capacity(self.store)
         return n3, n4
 
+    def state_dict(self) -> dict:
+        """Everything a resumed run needs: the step count, the set sizes, the FP32
+        master values and Adam's moments (rows in use only); torch.save-able."""
+        n3, n4 = self.master.n3, self.master.n4
+        rows = lambda k: n3 if k in FIELDS3 else n4  # noqa: E731
+        return {"t": self.t, "n3": n3, "n4": n4, "sh_time": self.master.sh_time,
+                "params": {k: self.master.t[k][: rows(k)].clone() for k in FIELDS3 + FIELDS4},
+                "m": {k: (self.s3 if k in FIELDS3 else self.s4).m[k][: rows(k)].clone() for k in FIELDS3 + FIELDS4},
+                "v": {k: (self.s3 if k in FIELDS3 else self.s4).v[k][: rows(k)].clone() for k in FIELDS3 + FIELDS4}}
+
+    def load_state_dict(self, sd: dict, stream=None):
+        """Resume from state_dict(): same N, views and capacities as the saved run."""
+        if sd["n3"] + sd["n4"] != self.R.N or sd["sh_time"] != self.master.sh_time:
+            raise ValueError("checkpoint of a different scene size or colour model")
+        if sd["n3"] > self.master.capacity3 or sd["n4"] > self.master.capacity4:
+            raise ValueError("checkpoint larger than this trainer's capacities")
+        n3, n4 = sd["n3"], sd["n4"]
+        for k in FIELDS3 + FIELDS4:
+            n = n3 if k in FIELDS3 else n4
+            st = self.s3 if k in FIELDS3 else self.s4
+            self.master.t[k][:n].copy_(sd["params"][k])
+            st.m[k][:n].copy_(sd["m"][k])
+            st.v[k][:n].copy_(sd["v"][k])
+        for G in {id(self.master): self.master, id(self.store): self.store}.values():
+            G.n3, G.n4 = n3, n4
+        if self.store is not self.master:
+            s3, s4 = self.master.c_g3(), self.master.c_g4()
+            d3, d4 = self.store.c_g3(), self.store.c_g4()
+            abi.check(abi.splat_cast_params(C.byref(s3), C.byref(d3), C.byref(s4), C.byref(d4), _stream(stream)),
+                      "splat_cast_params")
+        self.R.set_counts(n3, n4)
+        self.t = int(sd["t"])
+
     @property
     def loss(self) -> torch.Tensor:
         return self.R.loss

@@ -635,3 +635,28 @@ def test_autograd_function(small):
         for p in params:
             p.requires_grad_(False)
             p.grad = None
+
+
+def test_nonfinite_parameters_are_reported_and_culled(small):
+    """A NaN in a Gaussian's geometry or colour coefficients sets status NONFINITE with
+    its row and culls that Gaussian (fault injected on the host); the next call on
+    clean parameters renders exactly as before."""
+    scene, views, G0, R0, P, ref = small
+    G = raster.Gaussians.from_scene(scene, "cuda")
+    R = raster.Rasterizer(G.n3, G.n4, views, capacity=R0.capacity)
+    i = int(np.argmax(P["visible"][G.n4:] == 1))  # a visible 3D Gaussian
+    for field, idx, clean in (("log_scale3", (i, 0), float(scene.log_scale3[i, 0])),
+                              ("sh3", (i, 0, 1), float(scene.sh3[i, 0, 1]))):
+        G.t[field][idx] = float("nan")
+        R.forward(G)
+        torch.cuda.synchronize()
+        code, stage, aux = R.read_status()
+        assert code == abi.SPLAT_ERR_NONFINITE, field
+        assert abi.STAGES[stage] == "slice_project" and aux == G.n4 + i, field
+        assert R.n_tiles[G.n4 + i].item() == 0, field  # culled
+        assert torch.isfinite(R.rgb).all(), field
+        G.t[field][idx] = clean
+    R.forward(G)
+    torch.cuda.synchronize()
+    R.check()
+    assert torch.equal(R.rgb, R0.rgb)

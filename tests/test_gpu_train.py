@@ -239,3 +239,32 @@ def test_trainer_densification_matches_oracle():
     torch.cuda.synchronize()
     tr.R.check("after densification")
     assert np.isfinite(float(tr.loss.item()))
+
+
+def test_checkpoint_resume_continues_identically(tmp_path):
+    """state_dict after a few steps, a fresh Trainer loaded from it: the same state bit
+    for bit; one more step on both: the same parameters up to the order of the
+    gradient atomics."""
+    scene, views = _scene_with_time_scales(27, 700, 700, 1.0)
+    target = torch.rand((3 * 128 * 128,), device="cuda")
+    a = train.Trainer(scene, views, dtype=torch.bfloat16, convert_every=2)
+    for _ in range(3):  # includes a conversion
+        a.step(views, target)
+    path = tmp_path / "ckpt.pt"
+    torch.save(a.state_dict(), path)
+    b = train.Trainer(scene, views, dtype=torch.bfloat16, convert_every=2)
+    b.load_state_dict(torch.load(path))
+    assert (b.n3, b.n4, b.t) == (a.n3, a.n4, a.t)
+    for k in F3 + F4:
+        n = a.n3 if k in F3 else a.n4
+        assert torch.equal(a.master.t[k][:n], b.master.t[k][:n]), k
+        assert torch.equal(a.store.t[k][:n], b.store.t[k][:n]), k
+        st_a, st_b = (a.s3, b.s3) if k in F3 else (a.s4, b.s4)
+        assert torch.equal(st_a.m[k][:n], st_b.m[k][:n]) and torch.equal(st_a.v[k][:n], st_b.v[k][:n]), k
+    for tr in (a, b):
+        tr.step(views, target)
+    torch.cuda.synchronize()
+    for k in F3 + F4:
+        n = a.n3 if k in F3 else a.n4
+        pa, pb = a.master.t[k][:n].double().cpu().numpy(), b.master.t[k][:n].double().cpu().numpy()
+        assert np.abs(pa - pb).max() <= 1e-6 * max(1.0, np.abs(pa).max()), k
