@@ -94,6 +94,11 @@ enum {
 #define SPLAT_SH_COEFFS 16           /* degree 3, 3 channels each              */
 #define SPLAT_MAX_INSTANCES (1 << 30) /* upper bound of splat_bins.capacity    */
 
+/* Parameter arrays: FP32 arrays of 4-wide fields (quat, the 4D fields) and the
+ * SH arrays 16-byte aligned; with BF16 / FP16 storage the 4-wide fields 8-byte
+ * and the SH arrays 16-byte aligned (entry points return SPLAT_ERR_INVALID_ARG
+ * otherwise). */
+
 /* Static 3D Gaussians (Eq. 1, Eq. 2). */
 typedef struct {
     int64_t n;        /* N3                                                     */

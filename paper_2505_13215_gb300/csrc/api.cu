@@ -194,6 +194,16 @@ static bool valid_proj(const splat_proj* p, int V)
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// 16-bit storage: 4-wide rows are read as 8 bytes, SH blocks (96 bytes) as 16-byte vectors
+static bool half_storage_aligned(const splat_g3& g3, const splat_g4& g4, int dt)
+{
+    if (dt == SPLAT_F32) return true;
+    if (g4.n > 0 && (!aligned(g4.mean, 8) || !aligned(g4.log_scale, 8) || !aligned(g4.ql, 8) || !aligned(g4.qr, 8) ||
+                     !aligned(g4.sh, 16)))
+        return false;
+    return g3.n == 0 || (aligned(g3.quat, 8) && aligned(g3.sh, 16));
+}
+
 static splat_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SPLAT_OK : SPLAT_ERR_CUDA; }
 
 }  // namespace splat
@@ -291,6 +301,7 @@ splat_status splat_slice_project(const splat_g3* g3p, const splat_g4* g4p, const
                                         !aligned(g4.qr, 16) || !aligned(g4.sh, 16)))
         return SPLAT_ERR_INVALID_ARG;
     if (g3.n > 0 && dt == SPLAT_F32 && (!aligned(g3.quat, 16) || !aligned(g3.sh, 16))) return SPLAT_ERR_INVALID_ARG;
+    if (!half_storage_aligned(g3, g4, dt)) return SPLAT_ERR_INVALID_ARG;
     const LaunchCtx ctx = launch_ctx(stream);
     cudaError_t e = cudaMemsetAsync(status, 0, 4 * sizeof(int32_t), ctx.stream);
     if (e != cudaSuccess) return SPLAT_ERR_CUDA;
@@ -360,6 +371,7 @@ splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins,
                                             !aligned(g4.log_scale, 16) || !aligned(g4.sh, 16)))
             return SPLAT_ERR_INVALID_ARG;
         if (g3.n > 0 && dt == SPLAT_F32 && (!aligned(g3.quat, 16) || !aligned(g3.sh, 16))) return SPLAT_ERR_INVALID_ARG;
+        if (!half_storage_aligned(g3, g4, dt)) return SPLAT_ERR_INVALID_ARG;
     }
     const size_t dproj_bytes = (size_t)proj->n * V * 48;
     float* dp = dproj;

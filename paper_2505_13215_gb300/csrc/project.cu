@@ -96,70 +96,43 @@ __device__ __forceinline__ void ewa_setup(const ViewParams& vp, const float mu[3
     e.det = e.s00 * e.s11 - e.s01 * e.s01;
 }
 
-// rgb += w sum_k c_k Y_k(d) for one block of 16 x 3 coefficients at p
-template <int DT>
-__device__ __forceinline__ void sh_block(const typename Storage<DT>::T* p, float w, const float Y[16], float& r,
-                                         float& g, float& b)
-{
-    using S = Storage<DT>;
-    if constexpr (DT == SPLAT_F32) {
-        const float4* p4 = (const float4*)p;  // 48 floats = 12 float4
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            float4 c = __ldg(p4 + q);
-            float cc[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int idx = q * 4 + e;  // = k*3 + ch
-                const float term = w * cc[e] * Y[idx / 3];
-                if (idx % 3 == 0) r += term; else if (idx % 3 == 1) g += term; else b += term;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            r += w * S::ld(p + k * 3 + 0) * Y[k];
-            g += w * S::ld(p + k * 3 + 1) * Y[k];
-            b += w * S::ld(p + k * 3 + 2) * Y[k];
-        }
-    }
-}
-
 // weight of time frequency n at t: cos(2 pi n t), t in units of the sequence length
 __device__ __forceinline__ float time_weight(int n, float t) { return cospif(2.f * (float)n * t); }
 
+// rgb += w sum_k c_k Y_k for one block of coefficients c (16 x 3, k*3 + channel)
+__device__ __forceinline__ void sh_accumulate(const float c[48], float w, const float Y[16], float& r, float& g,
+                                              float& b)
+{
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        r += w * c[3 * k + 0] * Y[k];
+        g += w * c[3 * k + 1] * Y[k];
+        b += w * c[3 * k + 2] * Y[k];
+    }
+}
+
 // rgb = 0.5 + sum_{n=0..T} cos(2 pi n t) sum_k c_nk Y_k(d) (unclamped); T = 0: plain SH.
-// Y receives the SH basis at d.
+// Y receives the SH basis at d, c0 the coefficients of block 0.
 template <int DT>
 __device__ __forceinline__ void sh_rgb(const void* sh_base, int64_t row, int T, float t, const float dir[3],
-                                       float rgb[3], float Y[16])
+                                       float rgb[3], float Y[16], float c0[48])
 {
     using S = Storage<DT>;
     sh_basis(dir[0], dir[1], dir[2], Y);
     const typename S::T* p = (const typename S::T*)sh_base + row * 48 * (T + 1);
+    load_sh48<DT>(p, c0);
     float r = 0.5f, g = 0.5f, b = 0.5f;
-    if constexpr (DT == SPLAT_F32) {
-        const float4* p4 = (const float4*)p;  // block 0 (weight 1), exactly the plain SH sum
 #pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            float4 c = __ldg(p4 + q);
-            float cc[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int idx = q * 4 + e;
-                const float term = cc[e] * Y[idx / 3];
-                if (idx % 3 == 0) r += term; else if (idx % 3 == 1) g += term; else b += term;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            r += S::ld(p + k * 3 + 0) * Y[k];
-            g += S::ld(p + k * 3 + 1) * Y[k];
-            b += S::ld(p + k * 3 + 2) * Y[k];
-        }
+    for (int k = 0; k < 16; ++k) {  // block 0 (weight 1): exactly the plain SH sum
+        r += c0[3 * k + 0] * Y[k];
+        g += c0[3 * k + 1] * Y[k];
+        b += c0[3 * k + 2] * Y[k];
     }
-    for (int n = 1; n <= T; ++n) sh_block<DT>(p + 48 * n, time_weight(n, t), Y, r, g, b);
+    for (int n = 1; n <= T; ++n) {
+        float cn[48];
+        load_sh48<DT>(p + 48 * n, cn);
+        sh_accumulate(cn, time_weight(n, t), Y, r, g, b);
+    }
     rgb[0] = r; rgb[1] = g; rgb[2] = b;
 }
 
@@ -331,8 +304,8 @@ __global__ void __launch_bounds__(128) k_slice_project(splat_g3 g3, splat_g4 g4,
                         float d[3] = {mu[0] - vp.cam[0], mu[1] - vp.cam[1], mu[2] - vp.cam[2]};
                         const float id = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
                         d[0] *= id; d[1] *= id; d[2] *= id;
-                        float rgb[3], Y[16];
-                        sh_rgb<DT>(sh_base, sh_row, is4 ? g4.sh_time : 0, vp.t, d, rgb, Y);
+                        float rgb[3], Y[16], c0[48];
+                        sh_rgb<DT>(sh_base, sh_row, is4 ? g4.sh_time : 0, vp.t, d, rgb, Y, c0);
                         rd = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), e.z);
                         if (!isfinite(rgb[0] + rgb[1] + rgb[2])) {  // non-finite colour coefficients
                             set_status(status, SPLAT_ERR_NONFINITE, SPLAT_STAGE_SLICE_PROJECT, row);
@@ -491,25 +464,24 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
             float d[3] = {mu[0] - vp.cam[0], mu[1] - vp.cam[1], mu[2] - vp.cam[2]};
             const float id = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             d[0] *= id; d[1] *= id; d[2] *= id;
-            float rgb[3], Y[16];
-            sh_rgb<DT>(sh_base, sh_row, Tn, vp.t, d, rgb, Y);
+            float rgb[3], Y[16], c0[48];
+            sh_rgb<DT>(sh_base, sh_row, Tn, vp.t, d, rgb, Y, c0);
             const float gc[3] = {rgb[0] > 0.f ? dp[6] : 0.f, rgb[1] > 0.f ? dp[7] : 0.f, rgb[2] > 0.f ? dp[8] : 0.f};
             float w[16];  // <dL/drgb, effective coefficients of Y_k at t>
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                const float c0 = St::ld(shp + k * 3 + 0), c1 = St::ld(shp + k * 3 + 1), c2 = St::ld(shp + k * 3 + 2);
-                w[k] = gc[0] * c0 + gc[1] * c1 + gc[2] * c2;
+                w[k] = gc[0] * c0[3 * k + 0] + gc[1] * c0[3 * k + 1] + gc[2] * c0[3 * k + 2];
                 dsh[k * 3 + 0] += gc[0] * Y[k];
                 dsh[k * 3 + 1] += gc[1] * Y[k];
                 dsh[k * 3 + 2] += gc[2] * Y[k];
             }
             for (int n = 1; n <= Tn; ++n) {
                 const float tw = time_weight(n, vp.t);
-                const typename St::T* pn = shp + 48 * n;
+                float cn[48];
+                load_sh48<DT>(shp + 48 * n, cn);
                 float* shg = dg4.sh + (i * (Tn + 1) + n) * 48;
                 for (int k = 0; k < 16; ++k) {
-                    w[k] += tw * (gc[0] * St::ld(pn + k * 3 + 0) + gc[1] * St::ld(pn + k * 3 + 1) +
-                                  gc[2] * St::ld(pn + k * 3 + 2));
+                    w[k] += tw * (gc[0] * cn[3 * k + 0] + gc[1] * cn[3 * k + 1] + gc[2] * cn[3 * k + 2]);
                     shg[k * 3 + 0] += tw * gc[0] * Y[k];
                     shg[k * 3 + 1] += tw * gc[1] * Y[k];
                     shg[k * 3 + 2] += tw * gc[2] * Y[k];

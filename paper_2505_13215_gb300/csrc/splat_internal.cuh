@@ -133,6 +133,33 @@ __device__ __forceinline__ void load4(const void* base, int64_t row, float out[4
     }
 }
 
+// The 48 coefficients (16 x 3) of one SH block with 16-byte loads: 12 of them for
+// FP32, 6 for 16-bit storage.  Blocks are 192 / 96 bytes, so a block starts
+// 16-byte aligned whenever the array does.
+template <int DT>
+__device__ __forceinline__ void load_sh48(const typename Storage<DT>::T* p, float c[48])
+{
+    if constexpr (DT == SPLAT_F32) {
+        const float4* p4 = (const float4*)p;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const float4 v = __ldg(p4 + q);
+            c[4 * q + 0] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+        }
+    } else {
+        const uint4* p4 = (const uint4*)p;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const uint4 v = __ldg(p4 + q);
+            const typename Storage<DT>::T* h = (const typename Storage<DT>::T*)&v;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                c[8 * q + e] = (DT == SPLAT_BF16) ? __bfloat162float(((const __nv_bfloat16*)h)[e])
+                                                  : __half2float(((const __half*)h)[e]);
+        }
+    }
+}
+
 template <int DT>
 __device__ __forceinline__ void load3(const void* base, int64_t row, float out[3])
 {
