@@ -416,11 +416,14 @@ __device__ __forceinline__ void normalise_backward(const float q[4], const float
     for (int k = 0; k < 4; ++k) out[k] = (g[k] - qn[k] * dot) * in;
 }
 
+constexpr int kAdjThreads = 128;  // threads per block of the adjoint (its shared accumulators)
+
 template <int DT>
-__global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj proj,
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj proj,
                                                  const float* __restrict__ dproj, splat_grads3 dg3,
                                                  splat_grads4 dg4, int32_t* status)
 {
+    __shared__ float s_dsh[48 * kAdjThreads];  // SH gradient accumulators, thread-contiguous
     if (status_failed(status)) return;
     using St = Storage<DT>;
     const int64_t N = proj.n;
@@ -435,9 +438,9 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
         const typename St::T* shp = (const typename St::T*)sh_base + sh_row * 48 * (Tn + 1);
         // block 0's gradient in registers; blocks n >= 1 (weight cos(2 pi n t_v)) are summed in
         // this thread's own rows of dg4.sh
-        float dsh[48];
+        float* dsh = s_dsh + threadIdx.x;  // dsh[k * kAdjThreads]: this thread's 48 accumulators
 #pragma unroll
-        for (int k = 0; k < 48; ++k) dsh[k] = 0.f;
+        for (int k = 0; k < 48; ++k) dsh[k * kAdjThreads] = 0.f;
         for (int n = 1; n <= Tn; ++n) {
             float4* shg = (float4*)(dg4.sh + (i * (Tn + 1) + n) * 48);
             for (int k = 0; k < 12; ++k) shg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -471,9 +474,9 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 w[k] = gc[0] * c0[3 * k + 0] + gc[1] * c0[3 * k + 1] + gc[2] * c0[3 * k + 2];
-                dsh[k * 3 + 0] += gc[0] * Y[k];
-                dsh[k * 3 + 1] += gc[1] * Y[k];
-                dsh[k * 3 + 2] += gc[2] * Y[k];
+                dsh[(k * 3 + 0) * kAdjThreads] += gc[0] * Y[k];
+                dsh[(k * 3 + 1) * kAdjThreads] += gc[1] * Y[k];
+                dsh[(k * 3 + 2) * kAdjThreads] += gc[2] * Y[k];
             }
             for (int n = 1; n <= Tn; ++n) {
                 const float tw = time_weight(n, vp.t);
@@ -616,7 +619,9 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
             dg4.opacity[i] = gal * sg * (1.f - sg);
             float4* shg = (float4*)(dg4.sh + i * (Tn + 1) * 48);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) shg[k] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
+            for (int k = 0; k < 12; ++k)
+                shg[k] = make_float4(dsh[(4 * k) * kAdjThreads], dsh[(4 * k + 1) * kAdjThreads],
+                                     dsh[(4 * k + 2) * kAdjThreads], dsh[(4 * k + 3) * kAdjThreads]);
         } else {
             const int64_t j = i - n4;
             float q[4], ls[3];
@@ -663,7 +668,9 @@ __global__ void __launch_bounds__(128) k_adjoint(splat_g3 g3, splat_g4 g4, ViewB
             dg3.opacity[j] = gal * sg * (1.f - sg);
             float4* shg = (float4*)(dg3.sh + j * 48);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) shg[k] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
+            for (int k = 0; k < 12; ++k)
+                shg[k] = make_float4(dsh[(4 * k) * kAdjThreads], dsh[(4 * k + 1) * kAdjThreads],
+                                     dsh[(4 * k + 2) * kAdjThreads], dsh[(4 * k + 3) * kAdjThreads]);
         }
     }
 }
@@ -695,7 +702,7 @@ cudaError_t launch_adjoint(const splat_g3& g3, const splat_g4& g4, const ViewBat
 {
     const int64_t N = proj.n;
     if (N == 0) return cudaSuccess;
-    const int threads = 128;
+    const int threads = kAdjThreads;
     const int64_t want = (N + threads - 1) / threads;
     const int blocks = (int)(want < (int64_t)ctx.num_sms * 64 ? want : (int64_t)ctx.num_sms * 64);
     count_launch();
