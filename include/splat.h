@@ -460,9 +460,9 @@ const char *splat_status_string(int32_t code);
 void splat_set_spin_limit(int64_t iterations);
 
 /*
- * Tuning knob of the compositing kernels: pixels each lane owns (1, 2, 4 or
- * 8; one warp covers 32 x that many pixels of a 16x16 tile).  Other values
- * are ignored.  Default 8 / 8.  Host-side global; the results do not depend
+ * Tuning knob of the compositing kernels: pixels each lane owns (2, 4 or 8,
+ * evaluated in pairs; one warp covers 32 x that many pixels of a 16x16
+ * tile).  Other values are ignored.  Default 8 / 8.  Host-side global; the results do not depend
  * on it beyond floating-point summation order of the gradients.
  */
 void splat_set_pixels_per_lane(int fwd, int bwd);

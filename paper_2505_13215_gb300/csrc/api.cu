@@ -226,7 +226,7 @@ void splat_set_tile_cull(int on) { set_tile_cull(on); }
 
 void splat_set_pixels_per_lane(int fwd, int bwd)
 {
-    auto ok = [](int p) { return p == 1 || p == 2 || p == 4 || p == 8; };
+    auto ok = [](int p) { return p == 2 || p == 4 || p == 8; };
     if (ok(fwd)) g_ppl_fwd.store(fwd);
     if (ok(bwd)) g_ppl_bwd.store(bwd);
 }
