@@ -32,22 +32,36 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Projected features of one Gaussian as staged in shared memory.  The conic is
-// staged scaled by -log2(e)/2 (a2, c2) and -log2(e) (b2), so that
-// p2 = a2 dx^2 + b2 dx dy + c2 dy^2 is the power in base 2 and
-// alpha = alpha_max 2^p2 needs no extra multiply; pcut2 = log2(1/(255 alpha_max))
-// turns the alpha < 1/255 skip into a test on p2.  Forward and backward take
-// every decision (p2 > 0, p2 < pcut2, the clamp, the stop) on the same values.
+// Projected features of one Gaussian as staged in shared memory, every value
+// duplicated for the packed pixel-pair arithmetic (five float4):
+//   (px, px, py, py) (na2, na2, nb2, nb2) (nc2, nc2, -op, -op) (r, r, g, g) (b, b, lim, op)
+// The conic is staged scaled by log2(e)/2 (na2, nc2) and log2(e) (nb2), so that
+// np2 = na2 dx^2 + nb2 dx dy + nc2 dy^2 is minus the power in base 2 and
+// alpha = alpha_max 2^-np2 needs no extra multiply.  The skip tests power > 0
+// and alpha < 1/255 become 0 <= np2 <= -pcut2 with pcut2 = log2(1/(255 alpha_max)),
+// evaluated as one unsigned compare of the bits of np2 with lim, the bits of
+// 0 - pcut2 (non-negative floats order like their bit patterns; a NaN or a
+// negative np2 is above every lim).  np2 is +0, never -0, where the power
+// vanishes (dx = px - u is +0 there, and every product and sum of the
+// evaluation then gives +0).  Forward and backward take every decision (the
+// skip, the clamp, the stop) on the same values.
+constexpr int kFeat = 5;  // float4 per staged Gaussian
 struct Feat {
-    float px, py, a2, b2, c2, op, r, g, bl, pcut2;
+    float2 px, py, na2, nb2, nc2, nop, r, g, bl;
+    uint32_t lim;
+    float op;
 };
 
 __device__ __forceinline__ void load_feat(const float4* s, Feat& f)
 {
-    const float4 f0 = s[0], f1 = s[1], f2 = s[2];
-    f.px = f0.x; f.py = f0.y; f.a2 = f0.z; f.b2 = f0.w;
-    f.c2 = f1.x; f.op = f1.y; f.r = f1.z; f.g = f1.w;
-    f.bl = f2.x; f.pcut2 = f2.y;
+    const float4 f0 = s[0], f1 = s[1], f2 = s[2], f3 = s[3], f4 = s[4];
+    f.px = make_float2(f0.x, f0.y); f.py = make_float2(f0.z, f0.w);
+    f.na2 = make_float2(f1.x, f1.y); f.nb2 = make_float2(f1.z, f1.w);
+    f.nc2 = make_float2(f2.x, f2.y); f.nop = make_float2(f2.z, f2.w);
+    f.r = make_float2(f3.x, f3.y); f.g = make_float2(f3.z, f3.w);
+    f.bl = make_float2(f4.x, f4.y);
+    f.lim = __float_as_uint(f4.z);
+    f.op = f4.w;
 }
 
 __device__ __forceinline__ void stage_feat(const splat_proj& proj, uint32_t row, float4* s)
@@ -56,9 +70,16 @@ __device__ __forceinline__ void stage_feat(const splat_proj& proj, uint32_t row,
     const float4 co = ((const float4*)proj.conic_opacity)[row];
     const float4 rd = ((const float4*)proj.rgb_depth)[row];
     const float pcut2 = __log2f(kAlphaMin / co.w);
-    s[0] = make_float4(xy.x, xy.y, -0.5f * kLog2e * co.x, -kLog2e * co.y);
-    s[1] = make_float4(-0.5f * kLog2e * co.z, co.w, rd.x, rd.y);
-    s[2] = make_float4(rd.z, pcut2, 0.f, 0.f);
+    // alpha_max >= 1/255 for every listed Gaussian, so pcut2 <= 0; should the
+    // approximate logarithm round above 0, a NaN mean makes every test fail,
+    // as pcut2 <= p2 <= 0 would
+    const float px = pcut2 <= 0.f ? xy.x : __int_as_float(0x7fc00000);
+    const float na2 = 0.5f * kLog2e * co.x, nb2 = kLog2e * co.y, nc2 = 0.5f * kLog2e * co.z;
+    s[0] = make_float4(px, px, xy.y, xy.y);
+    s[1] = make_float4(na2, na2, nb2, nb2);
+    s[2] = make_float4(nc2, nc2, -co.w, -co.w);
+    s[3] = make_float4(rd.x, rd.x, rd.y, rd.y);
+    s[4] = make_float4(rd.z, rd.z, 0.f - pcut2, co.w);
 }
 
 __device__ __forceinline__ int find_view(const ViewBatch& vb, int tile)
@@ -72,7 +93,6 @@ __device__ __forceinline__ int find_view(const ViewBatch& vb, int tile)
 // Packed FP32 pairs: a lane evaluates its pixels two at a time with the
 // sm_100-family f32x2 instructions (each component rounds like the scalar
 // operation).
-__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -84,37 +104,115 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// One Gaussian seen from one lane's pixel column: the x-only terms of the
-// power, duplicated for the pixel pairs.  Forward and backward build them
+// One Gaussian seen from one lane's pixel column (-u in nu): the x-only terms
+// of minus the power for the pixel pairs.  Forward and backward build them
 // with the same operations, so both evaluate bit-identical powers.
 struct ColTerms {
-    float2 A2, Bx2, c2, py;
+    float2 nA2, nBx2, dx;
 };
 
-__device__ __forceinline__ ColTerms col_terms(const Feat& f, float uf)
+__device__ __forceinline__ ColTerms col_terms(const Feat& f, float2 nu)
 {
-    const float dx = f.px - uf;
     ColTerms c;
-    c.A2 = dup2(f.a2 * dx * dx);
-    c.Bx2 = dup2(f.b2 * dx);
-    c.c2 = dup2(f.c2);
-    c.py = dup2(f.py);
+    c.dx = add2(f.px, nu);
+    c.nA2 = mul2(mul2(f.na2, c.dx), c.dx);
+    c.nBx2 = mul2(f.nb2, c.dx);
     return c;
 }
 
-// base-2 power at a pixel pair whose rows are -nrow: A2 + dy (Bx2 + c2 dy),
-// dy = py - row.  A row of -inf (a finished pixel) gives dy = -inf and
-// p2 = -inf (c2 < 0), which the skip test rejects.
-__device__ __forceinline__ float2 pair_power(const ColTerms& c, float2 nrow)
+// Row of a pixel that is done (forward) or not yet reached (backward): dy is
+// then about -1e30 and np2 about nc2 1e60, +inf or far above any lim, so the
+// skip test rejects the pixel; dy stays finite, so the backward's moment sums
+// (dL/dpower = 0 times dy) stay 0.
+constexpr float kOffRow = 1e30f;
+
+// minus the base-2 power at a pixel pair whose rows are -nrow:
+// nA2 + dy (nBx2 + nc2 dy), dy = py - row.
+__device__ __forceinline__ float2 pair_npower(const Feat& f, const ColTerms& c, float2 dy)
 {
-    const float2 dy = add2(c.py, nrow);
-    return fma2(dy, fma2(c.c2, dy, c.Bx2), c.A2);
+    return fma2(dy, fma2(f.nc2, dy, c.nBx2), c.nA2);
+}
+
+__device__ __forceinline__ float2 pair_alpha_raw(const Feat& f, float2 np2)
+{
+    return mul2(f.nop, make_float2(ex2_approx(-np2.x), ex2_approx(-np2.y)));  // -alpha_max 2^p2
 }
 
 // A Gaussian with alpha_max below this never reaches the 0.99 clamp (p2 <= 0
 // makes 2^p2 <= 1, and ex2.approx overshoots 1 by far less than the margin),
 // so the clamp and its zero derivative are evaluated only above it.
 constexpr float kClampFree = 0.989f;
+
+// The forward's work for one staged Gaussian on all pixel pairs of the lane;
+// returns true once every pixel of the warp is done.  One vote skips a
+// Gaussian that no pixel of the warp passes; otherwise every pair is blended
+// in straight-line code, a skipped pixel with alpha = 0 (no effect).  The
+// saturation stop is rare and handled behind a second vote.
+template <int NP, bool CLAMP, bool STATS>
+__device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, float2 (&T)[NP],
+                                             float2 (&nC)[NP][3], float2 (&nrow)[NP], int (&last)[2 * NP],
+                                             unsigned& done, int pos, unsigned& n_eval, unsigned& n_blend)
+{
+    float2 np2[NP];
+    bool ox[NP], oy[NP], anyv = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        np2[p] = pair_npower(f, ct, add2(f.py, nrow[p]));
+        ox[p] = __float_as_uint(np2[p].x) <= f.lim;
+        oy[p] = __float_as_uint(np2[p].y) <= f.lim;
+        anyv |= ox[p] | oy[p];
+        if (STATS) n_eval += ((done >> (2 * p)) & 1u ^ 1u) + ((done >> (2 * p + 1)) & 1u ^ 1u);
+    }
+    if (!__any_sync(0xffffffffu, anyv)) return false;
+    float2 nw[NP], tT[NP];
+    bool stop = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float2 na = pair_alpha_raw(f, np2[p]);  // -alpha, 0 for a skipped pixel
+        if (CLAMP) {
+            na.x = fmaxf(na.x, -kAlphaClamp);
+            na.y = fmaxf(na.y, -kAlphaClamp);
+        }
+        na.x = ox[p] ? na.x : 0.f;
+        na.y = oy[p] ? na.y : 0.f;
+        nw[p] = mul2(na, T[p]);     // -alpha T
+        tT[p] = add2(T[p], nw[p]);  // T (1 - alpha); T itself for a skipped pixel (T >= 1e-4)
+        stop |= (tT[p].x < kTMin) | (tT[p].y < kTMin);
+    }
+    bool finished = false;
+    if (__any_sync(0xffffffffu, stop)) {
+        // a pixel saturates: this Gaussian does not contribute to it
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (tT[p].x < kTMin) {
+                done |= 1u << (2 * p);
+                nrow[p].x = -kOffRow;
+                nw[p].x = 0.f;
+                tT[p].x = T[p].x;
+                ox[p] = false;
+            }
+            if (tT[p].y < kTMin) {
+                done |= 2u << (2 * p);
+                nrow[p].y = -kOffRow;
+                nw[p].y = 0.f;
+                tT[p].y = T[p].y;
+                oy[p] = false;
+            }
+        }
+        finished = __all_sync(0xffffffffu, done == (1u << (2 * NP)) - 1);
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (STATS) n_blend += ox[p] + oy[p];
+        nC[p][0] = fma2(f.r, nw[p], nC[p][0]);
+        nC[p][1] = fma2(f.g, nw[p], nC[p][1]);
+        nC[p][2] = fma2(f.bl, nw[p], nC[p][2]);
+        T[p] = tT[p];
+        last[2 * p] = ox[p] ? pos : last[2 * p];
+        last[2 * p + 1] = oy[p] ? pos : last[2 * p + 1];
+    }
+    return finished;
+}
 
 // STATS: also count, per warp, the pixel-Gaussian pairs evaluated (power
 // computed) and blended, into stats[0..1] (diagnostic instantiation only).
@@ -126,7 +224,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
 {
     static_assert(PPL == 2 || PPL == 4 || PPL == 8, "pixels per lane come in pairs");
     constexpr int BANDS = 8 / PPL, NP = PPL / 2;
-    __shared__ float4 s_feat[kCompWarps][32][3];
+    __shared__ float4 s_feat[kCompWarps][32][kFeat];
     if (status_failed(status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
@@ -138,9 +236,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     const int ty = local / vp.TX, tx = local - ty * vp.TX;
     const int u = tx * kTile + (lane & 15);
     const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
-    const float uf = (float)u;
+    const float2 nu = make_float2(-(float)u, -(float)u);
     // pair p holds pixels k = 2p, 2p + 1 (rows y0 + 4p, y0 + 4p + 2).  nrow:
-    // minus the row, -inf once the pixel is done (outside the image or
+    // minus the row, -kOffRow once the pixel is done (outside the image or
     // saturated).  nC: minus the accumulated colour.
     float2 T[NP], nC[NP][3], nrow[NP];
     int last[PPL];
@@ -153,11 +251,11 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
         last[2 * p] = last[2 * p + 1] = 0;
         if (u >= vp.W || y0 + 4 * p >= vp.H) {
             done |= 1u << (2 * p);
-            nrow[p].x = __int_as_float(0xff800000);
+            nrow[p].x = -kOffRow;
         }
         if (u >= vp.W || y0 + 4 * p + 2 >= vp.H) {
             done |= 2u << (2 * p);
-            nrow[p].y = __int_as_float(0xff800000);
+            nrow[p].y = -kOffRow;
         }
     }
     const uint2 rg = ranges[tile];
@@ -167,59 +265,21 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     for (uint32_t b = rg.x; b < rg.y; b += 32) {
         if (__all_sync(0xffffffffu, done == all_done)) break;
         const uint32_t idx = b + lane;
-        if (idx < rg.y) stage_feat(proj, vals[idx], sf + lane * 3);
+        if (idx < rg.y) stage_feat(proj, vals[idx], sf + lane * kFeat);
         __syncwarp();
         const int n = (int)min(32u, rg.y - b);
-        if (done != all_done) {
-            const int pos0 = (int)(b - rg.x) + 1;
-            for (int j = 0; j < n; ++j) {
-                Feat f;
-                load_feat(sf + j * 3, f);
-                const ColTerms ct = col_terms(f, uf);
-                const float2 nop = dup2(-f.op), cr = dup2(f.r), cg = dup2(f.g), cb = dup2(f.bl);
-                const bool clamp = f.op >= kClampFree;  // same Gaussian on every lane
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const float2 p2 = pair_power(ct, nrow[p]);
-                    if (STATS) n_eval += ((done >> (2 * p)) & 1u ^ 1u) + ((done >> (2 * p + 1)) & 1u ^ 1u);
-                    // skip power > 0 and alpha < 1/255 (as p2 < pcut2); NaN and -inf skip too
-                    const bool ox = p2.x <= 0.f && p2.x >= f.pcut2, oy = p2.y <= 0.f && p2.y >= f.pcut2;
-                    if (!(ox || oy)) continue;
-                    // na = -alpha (0 for a skipped pixel of the pair)
-                    float2 na = mul2(nop, make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
-                    if (clamp) {
-                        na.x = fmaxf(na.x, -kAlphaClamp);
-                        na.y = fmaxf(na.y, -kAlphaClamp);
-                    }
-                    na.x = ox ? na.x : 0.f;
-                    na.y = oy ? na.y : 0.f;
-                    float2 nw = mul2(na, T[p]);  // -alpha T
-                    float2 tT = add2(T[p], nw);  // T (1 - alpha)
-                    const bool sx = ox && tT.x < kTMin, sy = oy && tT.y < kTMin;
-                    if (sx || sy) {  // the pixel saturates: this Gaussian does not contribute
-                        if (sx) {
-                            done |= 1u << (2 * p);
-                            nrow[p].x = __int_as_float(0xff800000);
-                            nw.x = 0.f;
-                            tT.x = T[p].x;
-                        }
-                        if (sy) {
-                            done |= 2u << (2 * p);
-                            nrow[p].y = __int_as_float(0xff800000);
-                            nw.y = 0.f;
-                            tT.y = T[p].y;
-                        }
-                    }
-                    if (STATS) n_blend += (ox && !sx) + (oy && !sy);
-                    nC[p][0] = fma2(cr, nw, nC[p][0]);
-                    nC[p][1] = fma2(cg, nw, nC[p][1]);
-                    nC[p][2] = fma2(cb, nw, nC[p][2]);
-                    T[p] = tT;
-                    if (ox && !sx) last[2 * p] = pos0 + j;
-                    if (oy && !sy) last[2 * p + 1] = pos0 + j;
-                }
-                if (done == all_done) break;
-            }
+        const int pos0 = (int)(b - rg.x) + 1;
+        // every lane walks the batch (finished pixels fail every test) so that
+        // the votes inside see the whole warp
+        for (int j = 0; j < n; ++j) {
+            Feat f;
+            load_feat(sf + j * kFeat, f);
+            const ColTerms ct = col_terms(f, nu);
+            const bool finished =
+                f.op < kClampFree  // same Gaussian on every lane
+                    ? fwd_gaussian<NP, false, STATS>(f, ct, T, nC, nrow, last, done, pos0 + j, n_eval, n_blend)
+                    : fwd_gaussian<NP, true, STATS>(f, ct, T, nC, nrow, last, done, pos0 + j, n_eval, n_blend);
+            if (finished) break;  // warp-uniform
         }
         __syncwarp();
     }
@@ -302,13 +362,13 @@ __device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint3
     const float b2 = __shfl_sync(0xffffffffu, s1.x, bl & 31), b3 = __shfl_sync(0xffffffffu, s1.y, bl & 31);
     if (q < nq) {
         if (h == 0) {
-            const float4 f0 = sf[jv * 3], f1 = sf[jv * 3 + 1];
+            const float4 f1 = sf[jv * kFeat + 1], f2 = sf[jv * kFeat + 2];
             float4 out;
             if ((gi & 1) == 0) {  // dpx, dpy, da, db with the natural-unit conic (a, b, c)
-                const float ca = -kLn2x2 * f0.z, cb = -0.5f * kLn2x2 * f0.w, cc = -kLn2x2 * f1.x;
+                const float ca = kLn2x2 * f1.x, cb = 0.5f * kLn2x2 * f1.z, cc = kLn2x2 * f2.x;
                 out = make_float4(ca * s0.x + cb * s0.y, cc * s0.y + cb * s0.x, 0.5f * s1.x, s1.y);
             } else {  // dc, dalpha_max = W0 / alpha_max (unclamped pairs only), dr, dg
-                out = make_float4(0.5f * s0.x, -s0.y / f1.y, -s1.x, -s1.y);
+                out = make_float4(0.5f * s0.x, s0.y / f2.z, -s1.x, -s1.y);
             }
             atomicAdd((float4*)(dproj + (int64_t)row * 12) + (gi & 1), out);
         } else {
@@ -318,6 +378,73 @@ __device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint3
         }
     }
     __syncwarp();
+}
+
+// Per-lane sums of one Gaussian over the lane's pixels, negated (the walk
+// accumulates minus each quantity): the moments of dL/dpower, 1, dy, dy^2
+// (W0, W1, W2) and dL/drgb, each as a pair of partial sums.
+struct BwdSums {
+    float2 W0, W1, W2, r, g, b;
+};
+
+// The backward's work for one staged Gaussian on all pixel pairs of the lane;
+// returns whether any lane of the warp blended it.  One vote skips a
+// Gaussian that no pixel of the warp passes; otherwise every pair runs in
+// straight-line code, a skipped pixel with alpha = 0.
+template <int NP, bool CLAMP, bool STATS>
+__device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, float2 (&T)[NP], float2 (&nQ)[NP],
+                                             const float2 (&G)[NP][3], const float2 (&nrow)[NP], BwdSums& S,
+                                             unsigned& n_blend)
+{
+    const float2 one = make_float2(1.f, 1.f);
+    float2 dy[NP], np2[NP];
+    bool ox[NP], oy[NP], anyv = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        dy[p] = add2(f.py, nrow[p]);
+        np2[p] = pair_npower(f, ct, dy[p]);
+        // the forward's skip, bit for bit, on the pixels that reached this Gaussian
+        ox[p] = __float_as_uint(np2[p].x) <= f.lim;
+        oy[p] = __float_as_uint(np2[p].y) <= f.lim;
+        anyv |= ox[p] | oy[p];
+    }
+    if (!__any_sync(0xffffffffu, anyv)) return false;
+    S.W0 = S.W1 = S.W2 = S.r = S.g = S.b = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (STATS) n_blend += ox[p] + oy[p];
+        const float2 nraw = pair_alpha_raw(f, np2[p]);
+        float2 na = nraw;  // -alpha, 0 for a skipped pixel of the pair
+        if (CLAMP) {
+            na.x = fmaxf(na.x, -kAlphaClamp);
+            na.y = fmaxf(na.y, -kAlphaClamp);
+        }
+        na.x = ox[p] ? na.x : 0.f;
+        na.y = oy[p] ? na.y : 0.f;
+        const float2 om = add2(one, na);  // 1 - alpha >= 0.01
+        // T_j = T + alpha T / (1 - alpha): exactly T for a skipped pixel
+        const float2 Tj = fma2(mul2(na, T[p]), make_float2(rcp_approx(-om.x), rcp_approx(-om.y)), T[p]);
+        const float2 nw = mul2(na, Tj);  // -alpha T_j
+        S.r = fma2(nw, G[p][0], S.r);
+        S.g = fma2(nw, G[p][1], S.g);
+        S.b = fma2(nw, G[p][2], S.b);
+        float2 d = fma2(G[p][0], f.r, nQ[p]);  // <G, c_j> - Q
+        d = fma2(G[p][1], f.g, d);
+        d = fma2(G[p][2], f.bl, d);
+        nQ[p] = fma2(na, d, nQ[p]);
+        T[p] = Tj;
+        // dL/dpower = dL/dalpha * alpha = w d where alpha is not clamped
+        float2 dp = mul2(nw, d);
+        if (CLAMP) {
+            dp.x = nraw.x > -kAlphaClamp ? dp.x : 0.f;
+            dp.y = nraw.y > -kAlphaClamp ? dp.y : 0.f;
+        }
+        const float2 dpy = mul2(dp, dy[p]);
+        S.W0 = add2(S.W0, dp);
+        S.W1 = add2(S.W1, dpy);
+        S.W2 = fma2(dpy, dy[p], S.W2);
+    }
+    return true;
 }
 
 // STATS: also count the pairs evaluated and blended into stats[2..3].
@@ -330,7 +457,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
 {
     static_assert(PPL == 2 || PPL == 4 || PPL == 8, "pixels per lane come in pairs");
     constexpr int BANDS = 8 / PPL, NP = PPL / 2;
-    __shared__ float4 s_feat[kCompWarps][32][3];
+    __shared__ float4 s_feat[kCompWarps][32][kFeat];
     __shared__ uint32_t s_row[kCompWarps][32];
     __shared__ float4 s_red[kCompWarps][kRedGroups][32];
     if (status_failed(status)) return;
@@ -344,13 +471,15 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     const int ty = local / vp.TX, tx = local - ty * vp.TX;
     const int u = tx * kTile + (lane & 15);
     const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
-    const float uf = (float)u;
+    const float2 nu = make_float2(-(float)u, -(float)u);
     const int64_t HW = (int64_t)vp.W * vp.H;
     // Per pixel: T = T_{j+1} (replayed transmittance behind the current Gaussian j),
     // G = dL/dC, and Q = <G, S_j> / T_{j+1} with S_j = sum_{i>j} c_i alpha_i T_i + T_final bg
     // the colour accumulated behind j.  Then dL/dalpha_j = T_j (<G, c_j> - Q) and
     // Q_{j-1} = Q + alpha_j (<G, c_j> - Q): S itself is never needed per channel, and
-    // Q starts at <G, bg>.  Pixels in pairs as in the forward; nQ = -Q.
+    // Q starts at <G, bg>.  Pixels in pairs as in the forward; nQ = -Q.  A pixel's
+    // row enters nrow (as minus the row) only once the walk reaches its last
+    // contributor; before that nrow is -kOffRow and every test fails.
     float2 T[NP], nQ[NP], G[NP][3], nrow[NP];
     int last[PPL];
     int maxlast = 0;
@@ -372,21 +501,22 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
         }
         if (k & 1) {
             T[k >> 1].y = t; nQ[k >> 1].y = q; G[k >> 1][0].y = g0; G[k >> 1][1].y = g1; G[k >> 1][2].y = g2;
-            nrow[k >> 1].y = -(float)y;
+            nrow[k >> 1].y = -kOffRow;
         } else {
             T[k >> 1].x = t; nQ[k >> 1].x = q; G[k >> 1][0].x = g0; G[k >> 1][1].x = g1; G[k >> 1][2].x = g2;
-            nrow[k >> 1].x = -(float)y;
+            nrow[k >> 1].x = -kOffRow;
         }
     }
     const float y0f = (float)y0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
+    maxlast = __reduce_max_sync(0xffffffffu, maxlast);
     if (maxlast == 0) return;
+    // act: the list position (0-based) at or below which one of the warp's
+    // pixels still has to switch on (its last contributor), -1 when none is left
+    int act = maxlast - 1;
     const uint2 rg = ranges[tile];
     float4* sf = &s_feat[warp][0][0];
     float4* red = &s_red[warp][0][0];
     const int nb = (maxlast + 31) / 32;
-    const float2 one = make_float2(1.f, 1.f);
     unsigned n_eval = 0, n_blend = 0;
     for (int bi = nb - 1; bi >= 0; --bi) {
         const uint32_t b = rg.x + 32u * bi;
@@ -395,7 +525,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
         if (idx < end) {
             const uint32_t row = vals[idx];
             s_row[warp][lane] = row;
-            stage_feat(proj, row, sf + lane * 3);
+            stage_feat(proj, row, sf + lane * kFeat);
         }
         __syncwarp();
         const int n = (int)min(32u, end - b);
@@ -403,67 +533,39 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
         uint32_t pend_row = 0; // lane q: row of waiting Gaussian q
         int pend_j = 0;        // lane q: its slot in the staged batch
         for (int j = n - 1; j >= 0; --j) {
-            Feat f;
-            load_feat(sf + j * 3, f);
             const int li = 32 * bi + j;  // position in the tile list
-            const ColTerms ct = col_terms(f, uf);
-            const float2 nop = dup2(-f.op), cr = dup2(f.r), cg = dup2(f.g), cb = dup2(f.bl);
-            const bool clamp = f.op >= kClampFree;  // same Gaussian on every lane
-            const float dx = f.px - uf;
-            const float pyr = f.py - y0f;  // dy of pixel k is pyr - 2 k (up to rounding)
-            // per lane, over its pixels, negated: dL/drgb and the moments of
-            // dL/dpower W0 = sum dpow, V1 = sum k dpow, V2 = sum k^2 dpow
-            float2 sW0 = make_float2(0.f, 0.f), sV1 = sW0, sV2 = sW0, sr = sW0, sg = sW0, sb = sW0;
-            bool any = false;
+            if (li <= act) {  // (warp-uniform) pixels whose last contributor is at li or later switch on
+                int nxt = -1;
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const float2 p2 = pair_power(ct, nrow[p]);
-                const bool ax = li < last[2 * p], ay = li < last[2 * p + 1];
-                if (STATS) n_eval += ax + ay;
-                // the forward's skip, bit for bit, on the pixels that reached this Gaussian
-                const bool ox = ax && p2.x <= 0.f && p2.x >= f.pcut2, oy = ay && p2.y <= 0.f && p2.y >= f.pcut2;
-                if (!(ox || oy)) continue;
-                if (STATS) n_blend += ox + oy;
-                any = true;
-                const float2 nraw = mul2(nop, make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
-                float2 na = nraw;  // -alpha, 0 for a skipped pixel of the pair
-                if (clamp) {
-                    na.x = fmaxf(na.x, -kAlphaClamp);
-                    na.y = fmaxf(na.y, -kAlphaClamp);
+                for (int k = 0; k < PPL; ++k) {
+                    const float nr = -(y0f + (float)(2 * k));
+                    if (li < last[k]) {
+                        if (k & 1) nrow[k >> 1].y = nr;
+                        else nrow[k >> 1].x = nr;
+                    } else {
+                        nxt = max(nxt, last[k] - 1);
+                    }
                 }
-                na.x = ox ? na.x : 0.f;
-                na.y = oy ? na.y : 0.f;
-                const float2 om = add2(one, na);  // 1 - alpha >= 0.01
-                const float2 rc = make_float2(ox ? rcp_approx(om.x) : 1.f, oy ? rcp_approx(om.y) : 1.f);
-                const float2 Tj = mul2(T[p], rc);
-                const float2 nw = mul2(na, Tj);  // -alpha T_j
-                sr = fma2(nw, G[p][0], sr);
-                sg = fma2(nw, G[p][1], sg);
-                sb = fma2(nw, G[p][2], sb);
-                float2 d = fma2(G[p][0], cr, nQ[p]);  // <G, c_j> - Q
-                d = fma2(G[p][1], cg, d);
-                d = fma2(G[p][2], cb, d);
-                nQ[p] = fma2(na, d, nQ[p]);
-                T[p] = Tj;
-                // dL/dpower = dL/dalpha * alpha = w d where alpha is not clamped
-                float2 dp = mul2(nw, d);
-                if (clamp) {
-                    dp.x = nraw.x > -kAlphaClamp ? dp.x : 0.f;
-                    dp.y = nraw.y > -kAlphaClamp ? dp.y : 0.f;
-                }
-                sW0 = add2(sW0, dp);
-                sV1 = fma2(make_float2((float)(2 * p), (float)(2 * p + 1)), dp, sV1);
-                sV2 = fma2(make_float2((float)(4 * p * p), (float)((2 * p + 1) * (2 * p + 1))), dp, sV2);
+                act = __reduce_max_sync(0xffffffffu, nxt);
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            const float W0 = sW0.x + sW0.y, V1 = sV1.x + sV1.y, V2 = sV2.x + sV2.y;
-            const float W1 = pyr * W0 - 2.f * V1;                     // sum dpow dy
-            const float W2 = pyr * (pyr * W0 - 4.f * V1) + 4.f * V2;  // sum dpow dy^2
+            if (STATS) {
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) n_eval += li < last[k];
+            }
+            Feat f;
+            load_feat(sf + j * kFeat, f);
+            const ColTerms ct = col_terms(f, nu);
+            BwdSums S;
+            const bool any = f.op < kClampFree  // same Gaussian on every lane
+                                 ? bwd_gaussian<NP, false, STATS>(f, ct, T, nQ, G, nrow, S, n_blend)
+                                 : bwd_gaussian<NP, true, STATS>(f, ct, T, nQ, G, nrow, S, n_blend);
+            if (!any) continue;  // warp-uniform
+            const float W0 = S.W0.x + S.W0.y, W1 = S.W1.x + S.W1.y;
             float4* slot = red + 2 * nq * 32 + lane;
-            const float dxW0 = dx * W0;
+            const float dx = ct.dx.x, dxW0 = dx * W0;
             slot[0] = make_float4(dxW0, W1, dx * dxW0, dx * W1);
-            slot[32] = make_float4(W2, W0, sr.x + sr.y, sg.x + sg.y);
-            ((float*)(red + (14 + (nq >> 2)) * 32 + lane))[nq & 3] = sb.x + sb.y;
+            slot[32] = make_float4(S.W2.x + S.W2.y, W0, S.r.x + S.r.y, S.g.x + S.g.y);
+            ((float*)(red + (14 + (nq >> 2)) * 32 + lane))[nq & 3] = S.b.x + S.b.y;
             if (lane == nq) {
                 pend_row = s_row[warp][j];
                 pend_j = j;
