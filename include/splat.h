@@ -171,8 +171,10 @@ typedef struct {
 typedef struct {
     float *rgb;            /* [sum_v 3 W_v H_v] planar per view                  */
     float *final_T;        /* [sum_v W_v H_v] transmittance after the last blend */
-    int32_t *last;         /* [sum_v W_v H_v] list entries walked up to and
-                              including the last contributing Gaussian          */
+    int32_t *last;         /* [sum_v W_v H_v] end of the pixel's walk: the
+                              index in its tile list of the entry that would
+                              bring T below 1e-4 (not blended), else the list
+                              length; the backward walks entries [0, last)   */
 } splat_image;
 
 /* FP32 gradients, same shapes as splat_g3 / splat_g4 (first n rows). */

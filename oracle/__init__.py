@@ -210,7 +210,9 @@ def project(scene, view):
 
 def render(scene, view, pixels=None):
     """Eq. 3 as the plain definition.  pixels: flat indices y*W+x (None = all).
-    Returns dict rgb [3, npix], T [npix], last [npix], the per-decision margins
+    Returns dict rgb [3, npix], T [npix], last [npix] (where the walk ends: the
+    list index of the entry that would take T below 1e-4, else the list
+    length), the per-decision margins
     (dict 'margins': power, alpha, stop, tie, clamp, tie3), margin_fwd (min of
     the first four) and margin_grad (the clamp).  'tie' is the relative depth gap
     of two touching Gaussians of which one is 4D; 'tie3' the distance of a 3D

@@ -548,7 +548,7 @@ static int64_t blend_pixel(const oproj *P, int64_t n4, const dkey *list, int64_t
 {
     double T = 1.0, C[3] = { 0, 0, 0 };
     double mgn[MG_COUNT] = { INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY };
-    int32_t last = 0;
+    int32_t last = (int32_t)m;  /* end of the walk: the list length unless T saturates */
     int64_t nt = 0;
     double prev_depth = -1.0;  /* depth, T, alpha, colour of the previous Gaussian that touched the pixel */
     int prev_3d = 0;
@@ -604,7 +604,10 @@ static int64_t blend_pixel(const oproj *P, int64_t n4, const dkey *list, int64_t
         if (alpha < ALPHA_MIN) continue;
         double test_T = T * (1.0 - alpha);
         mgn[MG_STOP] = dmin(mgn[MG_STOP], fabs(test_T - T_MIN) / T_MIN);
-        if (test_T < T_MIN) break;  /* this Gaussian does not contribute */
+        if (test_T < T_MIN) {  /* this Gaussian does not contribute; the walk ends here */
+            last = (int32_t)j;
+            break;
+        }
         if (tape) {
             tape[nt].idx = list[j].idx;
             tape[nt].G = G;
@@ -617,7 +620,6 @@ static int64_t blend_pixel(const oproj *P, int64_t n4, const dkey *list, int64_t
         ++nt;
         for (int ch = 0; ch < 3; ++ch) C[ch] += o->rgb[ch] * alpha * T;
         T = test_T;
-        last = (int32_t)(j + 1);
     }
     for (int ch = 0; ch < 3; ++ch) rgb[ch] = C[ch] + T * bg[ch];
     *T_out = T;

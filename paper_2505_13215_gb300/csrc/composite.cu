@@ -143,27 +143,31 @@ __device__ __forceinline__ float2 pair_alpha_raw(const Feat& f, float2 np2)
 // so the clamp and its zero derivative are evaluated only above it.
 constexpr float kClampFree = 0.989f;
 
-// The forward's work for one staged Gaussian on all pixel pairs of the lane;
-// returns true once every pixel of the warp is done.  One vote skips a
+// The forward's work for one staged Gaussian (list position pos, 1-based) on
+// all pixel pairs of the lane; returns true once every pixel of the warp is
+// done.  A pixel's walk ends at the entry that would bring T below 1e-4: its
+// `last` becomes that entry's 0-based index (pos - 1), the number of entries
+// the backward walks for it (the entries after its last contributor are
+// skipped for it there as here).  One vote skips a
 // Gaussian that no pixel of the warp passes; otherwise every pair is blended
 // in straight-line code, a skipped pixel with alpha = 0 (no effect).  The
-// saturation stop is rare and handled behind a second vote.
+// saturation stop is rare and handled behind a second vote.  No test result
+// is kept across the pairs (the skip test is one compare, redone where
+// needed), which keeps the predicate registers free.
 template <int NP, bool CLAMP, bool STATS>
 __device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, float2 (&T)[NP],
                                              float2 (&nC)[NP][3], float2 (&nrow)[NP], int (&last)[2 * NP],
                                              unsigned& done, int pos, unsigned& n_eval, unsigned& n_blend)
 {
     float2 np2[NP];
-    bool ox[NP], oy[NP], anyv = false;
+    uint32_t lo = 0xffffffffu;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         np2[p] = pair_npower(f, ct, add2(f.py, nrow[p]));
-        ox[p] = __float_as_uint(np2[p].x) <= f.lim;
-        oy[p] = __float_as_uint(np2[p].y) <= f.lim;
-        anyv |= ox[p] | oy[p];
+        lo = min(lo, min(__float_as_uint(np2[p].x), __float_as_uint(np2[p].y)));
         if (STATS) n_eval += ((done >> (2 * p)) & 1u ^ 1u) + ((done >> (2 * p + 1)) & 1u ^ 1u);
     }
-    if (!__any_sync(0xffffffffu, anyv)) return false;
+    if (!__any_sync(0xffffffffu, lo <= f.lim)) return false;
     float2 nw[NP], tT[NP];
     bool stop = false;
 #pragma unroll
@@ -173,9 +177,9 @@ __device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, 
             na.x = fmaxf(na.x, -kAlphaClamp);
             na.y = fmaxf(na.y, -kAlphaClamp);
         }
-        na.x = ox[p] ? na.x : 0.f;
-        na.y = oy[p] ? na.y : 0.f;
-        nw[p] = mul2(na, T[p]);     // -alpha T
+        na.x = __float_as_uint(np2[p].x) <= f.lim ? na.x : 0.f;
+        na.y = __float_as_uint(np2[p].y) <= f.lim ? na.y : 0.f;
+        nw[p] = mul2(na, T[p]);     // -alpha T: nonzero exactly for the blended pixels
         tT[p] = add2(T[p], nw[p]);  // T (1 - alpha); T itself for a skipped pixel (T >= 1e-4)
         stop |= (tT[p].x < kTMin) | (tT[p].y < kTMin);
     }
@@ -189,27 +193,25 @@ __device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, 
                 nrow[p].x = -kOffRow;
                 nw[p].x = 0.f;
                 tT[p].x = T[p].x;
-                ox[p] = false;
+                last[2 * p] = pos - 1;
             }
             if (tT[p].y < kTMin) {
                 done |= 2u << (2 * p);
                 nrow[p].y = -kOffRow;
                 nw[p].y = 0.f;
                 tT[p].y = T[p].y;
-                oy[p] = false;
+                last[2 * p + 1] = pos - 1;
             }
         }
         finished = __all_sync(0xffffffffu, done == (1u << (2 * NP)) - 1);
     }
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        if (STATS) n_blend += ox[p] + oy[p];
+        if (STATS) n_blend += (nw[p].x != 0.f) + (nw[p].y != 0.f);
         nC[p][0] = fma2(f.r, nw[p], nC[p][0]);
         nC[p][1] = fma2(f.g, nw[p], nC[p][1]);
         nC[p][2] = fma2(f.bl, nw[p], nC[p][2]);
         T[p] = tT[p];
-        last[2 * p] = ox[p] ? pos : last[2 * p];
-        last[2 * p + 1] = oy[p] ? pos : last[2 * p + 1];
     }
     return finished;
 }
@@ -240,25 +242,27 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     // pair p holds pixels k = 2p, 2p + 1 (rows y0 + 4p, y0 + 4p + 2).  nrow:
     // minus the row, -kOffRow once the pixel is done (outside the image or
     // saturated).  nC: minus the accumulated colour.
+    const uint2 rg = ranges[tile];
     float2 T[NP], nC[NP][3], nrow[NP];
-    int last[PPL];
+    int last[PPL];  // end of the walk: the list length unless the pixel saturates
     unsigned done = 0;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         T[p] = make_float2(1.f, 1.f);
         nC[p][0] = nC[p][1] = nC[p][2] = make_float2(0.f, 0.f);
         nrow[p] = make_float2(-(float)(y0 + 4 * p), -(float)(y0 + 4 * p + 2));
-        last[2 * p] = last[2 * p + 1] = 0;
+        last[2 * p] = last[2 * p + 1] = (int)(rg.y - rg.x);
         if (u >= vp.W || y0 + 4 * p >= vp.H) {
             done |= 1u << (2 * p);
             nrow[p].x = -kOffRow;
+            last[2 * p] = 0;
         }
         if (u >= vp.W || y0 + 4 * p + 2 >= vp.H) {
             done |= 2u << (2 * p);
             nrow[p].y = -kOffRow;
+            last[2 * p + 1] = 0;
         }
     }
-    const uint2 rg = ranges[tile];
     const unsigned all_done = (1u << PPL) - 1;
     float4* sf = &s_feat[warp][0][0];
     unsigned n_eval = 0, n_blend = 0;
@@ -398,29 +402,30 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
 {
     const float2 one = make_float2(1.f, 1.f);
     float2 dy[NP], np2[NP];
-    bool ox[NP], oy[NP], anyv = false;
+    bool anyv = false;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         dy[p] = add2(f.py, nrow[p]);
         np2[p] = pair_npower(f, ct, dy[p]);
-        // the forward's skip, bit for bit, on the pixels that reached this Gaussian
-        ox[p] = __float_as_uint(np2[p].x) <= f.lim;
-        oy[p] = __float_as_uint(np2[p].y) <= f.lim;
-        anyv |= ox[p] | oy[p];
+        // the forward's skip, bit for bit, on the pixels that reached this
+        // Gaussian (redone below rather than kept, which keeps the predicate
+        // registers free)
+        anyv |= (__float_as_uint(np2[p].x) <= f.lim) | (__float_as_uint(np2[p].y) <= f.lim);
     }
     if (!__any_sync(0xffffffffu, anyv)) return false;
     S.W0 = S.W1 = S.W2 = S.r = S.g = S.b = make_float2(0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        if (STATS) n_blend += ox[p] + oy[p];
+        const bool ox = __float_as_uint(np2[p].x) <= f.lim, oy = __float_as_uint(np2[p].y) <= f.lim;
+        if (STATS) n_blend += ox + oy;
         const float2 nraw = pair_alpha_raw(f, np2[p]);
         float2 na = nraw;  // -alpha, 0 for a skipped pixel of the pair
         if (CLAMP) {
             na.x = fmaxf(na.x, -kAlphaClamp);
             na.y = fmaxf(na.y, -kAlphaClamp);
         }
-        na.x = ox[p] ? na.x : 0.f;
-        na.y = oy[p] ? na.y : 0.f;
+        na.x = ox ? na.x : 0.f;
+        na.y = oy ? na.y : 0.f;
         const float2 om = add2(one, na);  // 1 - alpha >= 0.01
         // T_j = T + alpha T / (1 - alpha): exactly T for a skipped pixel
         const float2 Tj = fma2(mul2(na, T[p]), make_float2(rcp_approx(-om.x), rcp_approx(-om.y)), T[p]);

@@ -455,26 +455,42 @@ def test_depth_key_is_fp32_then_merged_index():
 
 def test_transmittance_stop_and_bounds():
     """Final T stays in [1e-4, 1], composite colour <= (1 - T) max c for a black
-    background, and 'last' counts the walk."""
+    background, and 'last' is where the walk ends: a stop needs T (1 - alpha) <
+    1e-4 with alpha <= 0.99, i.e. T < 0.01, so a pixel that kept T >= 0.01 walked
+    its whole tile list, and one that stopped early ended below 0.01."""
     scene, views = scenes.small_scene(seed=0)
-    r = O.render(scene, views[0])
-    P = O.project(scene, views[0])
+    v = views[0]
+    r = O.render(scene, v)
+    P = O.project(scene, v)
     cmax = P["rgb"][P["visible"] == 1].max(0)
     assert r["T"].min() >= 1e-4 and r["T"].max() <= 1.0
     assert np.all(r["rgb"] <= (1 - r["T"])[None] * cmax[:, None] + 1e-12)
-    assert np.all((r["last"] == 0) == (r["T"] == 1.0))
+    TX, TY = (v.W + 15) // 16, (v.H + 15) // 16
+    length = np.array([[len(O.tile_list(scene, v, tx, ty)) for tx in range(TX)] for ty in range(TY)])
+    yy, xx = np.divmod(np.arange(v.W * v.H), v.W)
+    m = length[yy // 16, xx // 16]
+    assert np.all(r["last"] <= m)
+    assert np.all(r["last"][r["T"] >= 0.01] == m[r["T"] >= 0.01])
+    assert np.all(r["T"][r["last"] < m] < 0.01)
+    assert np.any(r["last"] < m) and np.any(r["T"] >= 0.01)
 
 
-def test_transmittance_monotone_along_list():
-    scene, views = scenes.small_scene(seed=4, n3=300, n4=100)
+@pytest.mark.parametrize("seed,n3,n4,tiles", [(4, 300, 100, [(3, 3), (4, 2), (0, 7)]),
+                                              (0, 3072, 1024, [(3, 4), (4, 3)])])
+def test_transmittance_monotone_along_list(seed, n3, n4, tiles):
+    """Walk a pixel's tile list by hand: T never rises, the final T is the
+    renderer's, and the walk ends where 'last' says (the dense scene's pixels
+    saturate and stop early)."""
+    scene, views = scenes.small_scene(seed=seed, n3=n3, n4=n4)
     v = views[0]
     P = O.project(scene, v)
-    for (tx, ty) in [(3, 3), (4, 2), (0, 7)]:
+    stopped = 0
+    for (tx, ty) in tiles:
         ids = O.tile_list(scene, v, tx, ty)
         assert np.all(np.diff(P["depth"][ids].astype(np.float32)) >= 0)
         u, vv = tx * 16 + 5, ty * 16 + 9
-        T = 1.0
-        for i in ids:
+        T, end = 1.0, len(ids)
+        for j, i in enumerate(ids):
             p = P[i]
             dx, dy = p["px"] - u, p["py"] - vv
             a, b, c = p["conic"]
@@ -483,10 +499,15 @@ def test_transmittance_monotone_along_list():
             if pw > 0 or al < 1 / 255:
                 continue
             if T * (1 - al) < 1e-4:
+                end = j
                 break
             assert T * (1 - al) <= T
             T *= 1 - al
-        assert abs(T - O.render(scene, v, pixels=[vv * v.W + u])["T"][0]) < 1e-14
+        r = O.render(scene, v, pixels=[vv * v.W + u])
+        assert abs(T - r["T"][0]) < 1e-14
+        assert r["last"][0] == end
+        stopped += end < len(ids)
+    assert stopped == (len(tiles) if n3 > 1000 else 0)
 
 
 def test_stable_sort_against_numpy():
