@@ -178,11 +178,15 @@ def algorithmic_bytes(stage, n3, n4, V, pix, K, elem):
 
 
 # FP32 operations per pixel-Gaussian pair on each path of the compositing
-# kernels, counted from their source (FMA = 2): evaluating the power (dy and two
-# FMA) costs 5; a blended pair costs 17 in the forward (exp2, alpha, transmittance,
-# colour) and 35 in the backward (replayed T, colour and alpha gradients, moments).
+# kernels, counted from their source (FMA = 2, exp2 and reciprocal 1, compares
+# and selects 0): evaluating the power (dy and two FMA) costs 5; a blended pair
+# costs those 5 plus 10 in the forward (exp2, alpha, alpha T, transmittance,
+# three colour FMA) and plus 28 in the backward (exp2, alpha, 1 - alpha,
+# reciprocal, replayed T by a multiply and an FMA, alpha T, three
+# colour-gradient FMA, three FMA for <dL/dC, c> - Q, the Q update, dL/dpower and
+# its three moments).
 FLOPS_EVAL = 5
-FLOPS_BLEND = {"composite_fwd": 17, "composite_bwd": 35}
+FLOPS_BLEND = {"composite_fwd": 5 + 10, "composite_bwd": 5 + 28}
 KERNEL_SOURCES = {"composite_fwd": ["composite.cu", "splat_internal.cuh"],
                   "composite_bwd": ["composite.cu", "splat_internal.cuh"],
                   "slice_project": ["project.cu", "splat_internal.cuh"],

@@ -262,15 +262,21 @@ def test_footprint_culling_changes_nothing_but_the_lists(small):
         assert rel_l2(g1[k].cpu().numpy(), g0[k].cpu().numpy()) < 1e-5, k
 
 
-@pytest.mark.parametrize("ppl", [2, 4])
+@pytest.mark.parametrize("ppl", [(2, 2), (4, 4), (2, 8), (8, 4)])
 def test_composite_pixels_per_lane_variants(small, ppl):
+    """Every compositing variant (2, 4 or 8 pixels per lane, a warp per band of
+    the tile) against the oracle, forward and gradients, also with different
+    variants in the two passes (the backward reads where each pixel's walk
+    ended, whatever band shape wrote it)."""
     scene, views, G, R, P, ref = small
-    abi.splat_set_pixels_per_lane(ppl, ppl)
+    abi.splat_set_pixels_per_lane(*ppl)
     try:
         R.forward(G)
         torch.cuda.synchronize()
         R.check()
         check_image(R, P, ref, views[0])
+        dls = loss_grad(R, [ref], [P], views, seed=3)
+        check_grads(R, G, scene, [P], views, dls)
     finally:
         abi.splat_set_pixels_per_lane(8, 8)
         R.forward(G)
