@@ -389,6 +389,7 @@ def run_ours(args, rank, local, world):
     dom = max(stages, key=lambda s: stages[s])
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", clk.get("sm_max_mhz") or 2070.0))
+    fp32_peak_all = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     if dom in flops:
         # FP32 peak from unit counts and the maximum SM clock: SMs x 128 lanes x 2 (FMA)
         fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
@@ -403,6 +404,23 @@ def run_ours(args, rank, local, world):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(ach / hbm_peak, 4), "traffic": measured_traffic(dom, V),
                     "peak_source": peak_src + " (copy bandwidth)", "algorithmic_bytes": alg}
+
+    # every stage against its own bound: the compositing kernels in FP32
+    # operations, the others in algorithmic HBM bytes (inputs read once,
+    # outputs written once) against the measured copy bandwidth
+    stage_roof = {}
+    for st, ms in stages.items():
+        if ms <= 0:
+            continue
+        if st in flops:
+            a = flops[st] / (ms / 1e3) / 1e12
+            stage_roof[st] = {"bound": "alu", "achieved": round(a, 2), "unit": "TFLOP/s",
+                              "frac": round(a / fp32_peak_all, 4)}
+        else:
+            alg = algorithmic_bytes(st, G.n3, G.n4, V, pix, K_inst, 2)
+            a = alg / (ms / 1e3) / 1e9
+            stage_roof[st] = {"bound": "hbm", "achieved": round(a, 1), "unit": "GB/s", "frac": round(a / hbm_peak, 4),
+                              "algorithmic_bytes": int(alg)}
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -421,6 +439,7 @@ def run_ours(args, rank, local, world):
                             "loss and status read back after every step"},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "stage_roofline": stage_roof,
         "composite_pairs": pairs,
         "clocks": clk,
     }
