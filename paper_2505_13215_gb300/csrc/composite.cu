@@ -148,10 +148,10 @@ constexpr float kClampFree = 0.989f;
 // done.  A pixel's walk ends at the entry that would bring T below 1e-4: its
 // `last` becomes that entry's 0-based index (pos - 1), the number of entries
 // the backward walks for it (the entries after its last contributor are
-// skipped for it there as here).  One vote skips a
-// Gaussian that no pixel of the warp passes; otherwise every pair is blended
-// in straight-line code, a skipped pixel with alpha = 0 (no effect).  The
-// saturation stop is rare and handled behind a second vote.  No test result
+// skipped for it there as here).  Every pair is blended in straight-line code,
+// a skipped pixel with alpha = 0 (no effect): few listed Gaussians reach no
+// pixel of the band, and a block of independent pairs keeps the pipes fed.
+// The saturation stop is rare and handled behind a vote.  No test result
 // is kept across the pairs (the skip test is one compare, redone where
 // needed), which keeps the predicate registers free.
 template <int NP, bool CLAMP, bool STATS>
@@ -160,14 +160,11 @@ __device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, 
                                              unsigned& done, int pos, unsigned& n_eval, unsigned& n_blend)
 {
     float2 np2[NP];
-    uint32_t lo = 0xffffffffu;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         np2[p] = pair_npower(f, ct, add2(f.py, nrow[p]));
-        lo = min(lo, min(__float_as_uint(np2[p].x), __float_as_uint(np2[p].y)));
         if (STATS) n_eval += ((done >> (2 * p)) & 1u ^ 1u) + ((done >> (2 * p + 1)) & 1u ^ 1u);
     }
-    if (!__any_sync(0xffffffffu, lo <= f.lim)) return false;
     float2 nw[NP], tT[NP];
     bool stop = false;
 #pragma unroll
@@ -391,34 +388,27 @@ struct BwdSums {
     float2 W0, W1, W2, r, g, b;
 };
 
-// The backward's work for one staged Gaussian on all pixel pairs of the lane;
-// returns whether any lane of the warp blended it.  One vote skips a
-// Gaussian that no pixel of the warp passes; otherwise every pair runs in
-// straight-line code, a skipped pixel with alpha = 0.
+// The backward's work for one staged Gaussian on all pixel pairs of the lane,
+// in straight-line code (a skipped pixel with alpha = 0, no effect); returns
+// whether any lane of the warp blended it (one vote, after the work: few
+// listed Gaussians reach no pixel, and the block keeps the pairs independent).
 template <int NP, bool CLAMP, bool STATS>
 __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, float2 (&T)[NP], float2 (&nQ)[NP],
                                              const float2 (&G)[NP][3], const float2 (&nrow)[NP], BwdSums& S,
                                              unsigned& n_blend)
 {
     const float2 one = make_float2(1.f, 1.f);
-    float2 dy[NP], np2[NP];
     bool anyv = false;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        dy[p] = add2(f.py, nrow[p]);
-        np2[p] = pair_npower(f, ct, dy[p]);
-        // the forward's skip, bit for bit, on the pixels that reached this
-        // Gaussian (redone below rather than kept, which keeps the predicate
-        // registers free)
-        anyv |= (__float_as_uint(np2[p].x) <= f.lim) | (__float_as_uint(np2[p].y) <= f.lim);
-    }
-    if (!__any_sync(0xffffffffu, anyv)) return false;
     S.W0 = S.W1 = S.W2 = S.r = S.g = S.b = make_float2(0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const bool ox = __float_as_uint(np2[p].x) <= f.lim, oy = __float_as_uint(np2[p].y) <= f.lim;
+        const float2 dy = add2(f.py, nrow[p]);
+        const float2 np2 = pair_npower(f, ct, dy);
+        // the forward's skip, bit for bit, on the pixels that reached this Gaussian
+        const bool ox = __float_as_uint(np2.x) <= f.lim, oy = __float_as_uint(np2.y) <= f.lim;
+        anyv |= ox | oy;
         if (STATS) n_blend += ox + oy;
-        const float2 nraw = pair_alpha_raw(f, np2[p]);
+        const float2 nraw = pair_alpha_raw(f, np2);
         float2 na = nraw;  // -alpha, 0 for a skipped pixel of the pair
         if (CLAMP) {
             na.x = fmaxf(na.x, -kAlphaClamp);
@@ -444,12 +434,12 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
             dp.x = nraw.x > -kAlphaClamp ? dp.x : 0.f;
             dp.y = nraw.y > -kAlphaClamp ? dp.y : 0.f;
         }
-        const float2 dpy = mul2(dp, dy[p]);
+        const float2 dpy = mul2(dp, dy);
         S.W0 = add2(S.W0, dp);
         S.W1 = add2(S.W1, dpy);
-        S.W2 = fma2(dpy, dy[p], S.W2);
+        S.W2 = fma2(dpy, dy, S.W2);
     }
-    return true;
+    return __any_sync(0xffffffffu, anyv);
 }
 
 // STATS: also count the pairs evaluated and blended into stats[2..3].
@@ -492,7 +482,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     for (int k = 0; k < PPL; ++k) {
         const int y = y0 + 2 * k;
         float t = 1.f, q = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        last[k] = 0;
+        int lk = 0;
         if (u < vp.W && y < vp.H) {
             const int64_t p = (int64_t)y * vp.W + u;
             const float* g = dL + 3 * vp.pix_base;
@@ -500,10 +490,11 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
             g1 = g[HW + p];
             g2 = g[2 * HW + p];
             t = img.final_T[vp.pix_base + p];
-            last[k] = img.last[vp.pix_base + p];
+            lk = img.last[vp.pix_base + p];
             q = -(g0 * vp.bg[0] + g1 * vp.bg[1] + g2 * vp.bg[2]);
-            maxlast = max(maxlast, last[k]);
+            maxlast = max(maxlast, lk);
         }
+        last[k] = lk;
         if (k & 1) {
             T[k >> 1].y = t; nQ[k >> 1].y = q; G[k >> 1][0].y = g0; G[k >> 1][1].y = g1; G[k >> 1][2].y = g2;
             nrow[k >> 1].y = -kOffRow;
@@ -544,11 +535,12 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     const float nr = -(y0f + (float)(2 * k));
-                    if (li < last[k]) {
+                    const int lk = last[k];
+                    if (li < lk) {
                         if (k & 1) nrow[k >> 1].y = nr;
                         else nrow[k >> 1].x = nr;
                     } else {
-                        nxt = max(nxt, last[k] - 1);
+                        nxt = max(nxt, lk - 1);
                     }
                 }
                 act = __reduce_max_sync(0xffffffffu, nxt);
