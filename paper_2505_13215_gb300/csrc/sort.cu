@@ -941,6 +941,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
     __shared__ float4 s_g0[COUNT ? 256 : 1], s_g1[COUNT ? 256 : 1], s_g2[COUNT ? 256 : 1];  // footprint constants
     __shared__ uint32_t s_row[COUNT ? 1 : 256];
     __shared__ uint2 s_mask[256];
+    __shared__ unsigned char s_queue[8][256];  // per tile row: entries of the chunk it has work for
     // COUNT: coverage byte -> four words of two 16-bit column counters (columns 2q, 2q + 1),
     // so that four warp reductions count all eight columns of 32 entries
     __shared__ uint4 s_spread[COUNT ? 256 : 1];
@@ -1013,30 +1014,49 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
             __syncthreads();
             if (ty < TY) {
                 const int n = (int)min(256u, rg.y - b);
+                // the entries this tile row has work for (COUNT: rectangle covers the
+                // row; write pass: listed in some tile of the row), queued in order
+                // so that the work below runs on full warps
+                int nq = 0;
                 for (int sb = 0; sb < n; sb += 32) {
                     const int e = sb + lane;
-                    unsigned m = 0;  // tile columns of this tile row the entry is listed in
+                    bool take = false;
                     if (e < n) {
                         if (COUNT) {
                             const int4 rc = s_rect[e];
-                            if (rc.y <= ty && ty < rc.w) {
-                                int cx0 = rc.x, cx1 = rc.z;
-                                bool cy = true;
-                                if (a.cull) {
-                                    float ul, ur;
-                                    if (!ellipse_band_extent(s_g0[e], s_g1[e], s_g2[e], vlo, vhi, ul, ur)) {
-                                        cy = false;
-                                    } else {
-                                        // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
-                                        const float lo = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
-                                        const float hi = floorf(ur * (1.f / kTile));
-                                        cx0 = max(cx0, (int)fminf(fmaxf(lo, -1.f), 1.0e6f));
-                                        cx1 = min(cx1, (int)fminf(fmaxf(hi, -2.f), 1.0e6f) + 1);
-                                    }
+                            take = rc.y <= ty && ty < rc.w;
+                        } else {
+                            take = ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu) != 0u;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, take);
+                    if (take) s_queue[warp][nq + __popc(bal & lt)] = (unsigned char)e;
+                    nq += __popc(bal);
+                }
+                __syncwarp();
+                for (int sb = 0; sb < nq; sb += 32) {
+                    const int qi = sb + lane;
+                    const int e = qi < nq ? s_queue[warp][qi] : 0;
+                    unsigned m = 0;  // tile columns of this tile row the entry is listed in
+                    if (qi < nq) {
+                        if (COUNT) {
+                            const int4 rc = s_rect[e];
+                            int cx0 = rc.x, cx1 = rc.z;
+                            bool cy = true;
+                            if (a.cull) {
+                                float ul, ur;
+                                if (!ellipse_band_extent(s_g0[e], s_g1[e], s_g2[e], vlo, vhi, ul, ur)) {
+                                    cy = false;
+                                } else {
+                                    // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
+                                    const float lo = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
+                                    const float hi = floorf(ur * (1.f / kTile));
+                                    cx0 = max(cx0, (int)fminf(fmaxf(lo, -1.f), 1.0e6f));
+                                    cx1 = min(cx1, (int)fminf(fmaxf(hi, -2.f), 1.0e6f) + 1);
                                 }
-                                const int lo = max(cx0 - tx0, 0), hi = min(cx1 - tx0, 8);
-                                if (cy && hi > lo) m = (1u << hi) - (1u << lo);
                             }
+                            const int lo = max(cx0 - tx0, 0), hi = min(cx1 - tx0, 8);
+                            if (cy && hi > lo) m = (1u << hi) - (1u << lo);
                             reinterpret_cast<unsigned char*>(&s_mask[e])[warp] = (unsigned char)m;
                         } else {
                             m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu;
@@ -1049,7 +1069,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                         packed[2] += __reduce_add_sync(0xffffffffu, w.z);
                         packed[3] += __reduce_add_sync(0xffffffffu, w.w);
                     } else {
-                        const uint32_t row = s_row[e < n ? e : 0];
+                        const uint32_t row = s_row[e];
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
                             const bool cov = (m >> k) & 1u;
