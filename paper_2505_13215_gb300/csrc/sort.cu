@@ -137,6 +137,7 @@ struct PassArgs {
     int shift;
     int64_t spin_limit;
     int64_t view_div;      // > 0: write keys_out = value / view_div (the row's view) instead of the key
+    int ballot_rank;       // rank by digit-bit ballots (many distinct digits per warp) instead of match
 };
 
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
@@ -176,16 +177,28 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
             k[j] = ok ? a.keys_in[idx] : 0u;
             v[j] = ok ? a.vals_in[idx] : 0u;
         }
-        // warp-level stable ranking, items in (j, lane) order
+        // warp-level stable ranking, items in (j, lane) order.  The lanes holding
+        // the same digit: with ballot_rank, one ballot per digit bit (a constant
+        // cost, for digits that take many values in a warp); otherwise a match
+        // instruction (fast when the warp holds few distinct digits, slow with many)
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const int64_t idx = wbase + j * 32 + lane;
             const bool ok = idx < n;
+            const uint32_t dj = (k[j] >> a.shift) & 0xff;
             const unsigned valid = __ballot_sync(0xffffffffu, ok);
+            unsigned same = valid;
+            if (a.ballot_rank) {  // same for every thread
+#pragma unroll
+                for (int bit = 0; bit < 8; ++bit) {
+                    const unsigned bb = __ballot_sync(0xffffffffu, (dj >> bit) & 1u);
+                    same &= ((dj >> bit) & 1u) ? bb : ~bb;
+                }
+            }
             r[j] = 0;
             if (ok) {
-                const uint32_t d = (k[j] >> a.shift) & 0xff;
-                const unsigned peers = __match_any_sync(valid, d);
+                const uint32_t d = dj;
+                const unsigned peers = a.ballot_rank ? same : __match_any_sync(valid, d);
                 const int leader = __ffs(peers) - 1;
                 uint32_t prev = 0;
                 if (lane == leader) {
@@ -1369,6 +1382,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.shift = p < 4 ? 8 * p : 0;
         a.spin_limit = ctx.spin_limit;
         a.view_div = (by_view && p == 3) ? proj.n : 0;
+        a.ballot_rank = p < 3;  // the low depth digits take many values in a warp, the top one and the view few
         if ((err = run_pass(a, L.parts_d, resident, s)) != cudaSuccess) return err;
     }
     const uint32_t* rows = U(L.off_dvals[passes & 1]);
