@@ -1144,6 +1144,7 @@ __global__ void __launch_bounds__(32) k_bin_scatter(BinArgs a)
         const int tb = a.tile_base[c.v];
         const int T = a.tile_base[c.v + 1] - tb;
         const int TX = a.TX[c.v];
+        const int tbits = 32 - __clz(max(T - 1, 1));  // bits of a tile index of this view
         // absolute cursors of this chunk: one burst of 16-byte async copies (tmax % 4 == 0)
         const uint32_t* cnt = a.counts + (size_t)g * a.tmax;
         for (int t = lane * 4; t < T; t += 128) cp_async16(s_cur + t, cnt + t);
@@ -1204,7 +1205,14 @@ __global__ void __launch_bounds__(32) k_bin_scatter(BinArgs a)
                 const uint32_t ty = l / w;
                 tl = s_base[q] + ty * TX + (l - ty * w);
             }
-            const unsigned peers = __match_any_sync(0xffffffffu, tl);
+            // lanes holding the same tile: one ballot per bit of the view's
+            // tile index (constant cost; a warp holds many distinct tiles)
+            const unsigned actm = __ballot_sync(0xffffffffu, act);
+            unsigned peers = act ? actm : ~actm;
+            for (int bit = 0; bit < tbits; ++bit) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (tl >> bit) & 1u);
+                peers &= ((tl >> bit) & 1u) ? bb : ~bb;
+            }
             const int leader = __ffs(peers) - 1;
             uint32_t pos = 0;
             if (lane == leader && act) {
