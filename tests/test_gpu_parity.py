@@ -666,3 +666,82 @@ def test_nonfinite_parameters_are_reported_and_culled(small):
     torch.cuda.synchronize()
     R.check()
     assert torch.equal(R.rgb, R0.rgb)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases of the compositing decisions and of the batch
+# ---------------------------------------------------------------------------
+
+def test_clamped_opacity_matches_oracle():
+    """Gaussians whose alpha_max reaches the 0.99 clamp (opacity logits 4.6-8):
+    the forward's clamp and the backward's zero derivative where clamped, against
+    the oracle (the random scenes almost never reach the clamp)."""
+    scene, views = scenes.small_scene(seed=3, n3=1500, n4=500)
+    rng = np.random.default_rng(3)
+    for k in ("opacity3", "opacity4"):
+        o = getattr(scene, k)
+        hi = rng.random(o.shape[0]) < 0.4
+        o[hi] = rng.uniform(4.6, 8.0, int(hi.sum())).astype(np.float32)
+    G, R = make(scene, views)
+    P = O.project(scene, views[0])
+    vis = P["visible"] == 1
+    assert int((P["alpha"][vis] >= 0.99).sum()) > 100
+    ref = O.render(scene, views[0])
+    check_image(R, P, ref, views[0])
+    dls = loss_grad(R, [ref], [P], views, seed=4)
+    check_grads(R, G, scene, [P], views, dls)
+
+
+def test_power_zero_at_pixel_centres():
+    """Means that project exactly onto pixel centres (z = 4, f = 64, x = k / 16):
+    there the power is exactly 0, which passes the skip test (power > 0 skips)
+    and blends with alpha = alpha_max.  4D Gaussians sliced at their own mu_t
+    keep their mean exactly."""
+    rng = np.random.default_rng(12)
+    view = scenes.identity_view(64, 64, 64.0, 0.5)
+
+    def centred(n):
+        k = rng.integers(-28, 29, size=(n, 2))
+        return np.concatenate([k / 16.0, np.full((n, 1), 4.0)], axis=1)
+
+    n3, n4 = 120, 60
+    scene = scenes.random_scene(rng, n3, n4, centred(n3), centred(n4))
+    scene.mean4[:, 3] = 0.5
+    P = O.project(scene, view)
+    vis = P["visible"] == 1
+    assert np.all(P["px"][vis] == np.round(P["px"][vis])) and np.all(P["py"][vis] == np.round(P["py"][vis]))
+    G, R = make(scene, [view])
+    ref = O.render(scene, view)
+    check_image(R, P, ref, view)
+    # the centre pixels themselves take part in the comparison
+    frag = fragile_pixels(P, ref, view)
+    centres = (P["py"][vis].astype(int) * view.W + P["px"][vis].astype(int))
+    assert (~frag[centres]).mean() > 0.9
+    dls = loss_grad(R, [ref], [P], [view], seed=5)
+    check_grads(R, G, scene, [P], [view], dls)
+
+
+def test_max_batch_sixteen_views_mixed_sizes():
+    """The largest batch (16 views) in one launch per stage, sizes from 1x1 to
+    67x45 (ragged tiles), distinct cameras and timestamps, with a few Gaussians
+    larger than the image; every view against the oracle, gradients summed."""
+    rng = np.random.default_rng(21)
+    scene, _ = scenes.small_scene(seed=21, n3=600, n4=300)
+    for i in range(3):  # large splats covering every tile
+        scene.log_scale3[i] = np.float32(-0.3)
+        scene.mean3[i] = np.array([0.1 * i, -0.1 * i, 3.0], np.float32)
+    sizes = [(1, 1), (16, 16), (17, 9), (33, 31), (64, 48), (15, 17), (67, 45), (40, 40),
+             (31, 33), (2, 50), (50, 2), (48, 64), (23, 29), (32, 16), (9, 17), (45, 67)]
+    views = []
+    for W, H in sizes:
+        eye = np.array([rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), 0.0])
+        views.append(scenes.look_at_view(eye, np.array([0.0, 0.0, 4.0]), W, H, 0.9 * max(W, H),
+                                         float(rng.uniform(0, 1))))
+    assert len(views) == abi.SPLAT_MAX_VIEWS
+    G, R = make(scene, views)
+    Ps = [O.project(scene, v) for v in views]
+    refs = [O.render(scene, v) for v in views]
+    for v in range(len(views)):
+        check_image(R, Ps[v], refs[v], views[v], v)
+    dls = loss_grad(R, refs, Ps, views, seed=6)
+    check_grads(R, G, scene, Ps, views, dls)
