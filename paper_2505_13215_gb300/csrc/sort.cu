@@ -888,6 +888,15 @@ __global__ void __launch_bounds__(256) k_seg_prefix(TileArgs a)
 // Gaussian, computed once: g0 = (px, py, R2, Y) with Y the |dy| reach,
 // g1 = (X, yr, b/a, det/a) with X the |dx| reach and yr the dy of the rightmost
 // point, g2.x = 1/a.  Degenerate conics keep the whole band (Y = inf).
+// Square root by the PTX approximation (a few ulp): the footprint's squared
+// radius carries a margin of 1e-4 of itself, far above that error.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void ellipse_consts(float px, float py, float a, float b, float c, float R2, float4& g0,
                                                float4& g1, float4& g2)
 {
@@ -898,10 +907,12 @@ __device__ __forceinline__ void ellipse_consts(float px, float py, float a, floa
         g2 = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    const float ia = 1.f / a, idet = 1.f / det;
-    const float X = sqrtf(R2 * c * idet);
-    g0 = make_float4(px, py, R2, sqrtf(R2 * a * idet));
-    g1 = make_float4(X, -b / c * X, b * ia, det * ia);
+    // approximate quotients and roots (relative errors of a few 1e-7, inside
+    // the squared radius' 1e-4 margin)
+    const float ia = __fdividef(1.f, a), idet = __fdividef(1.f, det);
+    const float X = sqrt_approx(R2 * c * idet);
+    g0 = make_float4(px, py, R2, sqrt_approx(R2 * a * idet));
+    g1 = make_float4(X, -__fdividef(b, c) * X, b * ia, det * ia);
     g2 = make_float4(ia, 0.f, 0.f, 0.f);
 }
 
@@ -924,14 +935,14 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
         dxmax = X;
     } else {
         const float dy = fminf(fmaxf(yr, e0), e1);
-        dxmax = -ba * dy + sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
+        dxmax = -ba * dy + sqrt_approx(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
     }
     const float yl = -yr;  // leftmost point
     if (yl >= e0 && yl <= e1) {
         dxmin = -X;
     } else {
         const float dy = fminf(fmaxf(yl, e0), e1);
-        dxmin = -ba * dy - sqrtf(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
+        dxmin = -ba * dy - sqrt_approx(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
     }
     ul = px - dxmax;
     ur = px - dxmin;
@@ -1012,7 +1023,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                         const float2 xy = ((const float2*)a.proj.xy)[row];
                         const float4 co = ((const float4*)a.proj.conic_opacity)[row];
                         // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
-                        const float R2 = -2.f * __logf(kAlphaMin / co.w) * 1.0001f + 2e-3f;
+                        const float R2 = -2.f * __logf(__fdividef(kAlphaMin, co.w)) * 1.0001f + 2e-3f;
                         float4 g0, g1, g2;
                         ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1, g2);
                         s_g0[threadIdx.x] = g0;
