@@ -165,6 +165,13 @@ typedef struct {
     uint32_t *ranges;      /* [total_tiles][2] [start, end) of each tile in vals  */
     int64_t *n_instances;  /* [1] K, the number of (tile, Gaussian) instances;
                               on SPLAT_ERR_CAPACITY the count that was needed    */
+    uint32_t *tile_order;  /* optional (may be NULL), [total_tiles]: written by
+                              splat_bin_sort with the tiles in decreasing
+                              order of list length (powers of two; order inside
+                              a class unspecified); the compositing kernels
+                              take tiles in this order, the longest first, so
+                              that the last wave of warps is short.  Results
+                              do not depend on it.  NULL: raster order.      */
 } splat_bins;
 
 /* Rendered images and the per-pixel state the backward pass replays. */

@@ -57,8 +57,12 @@ def _time_steps(R, G, target, reps: int) -> float:
     return ev[0].elapsed_time(ev[1]) / reps
 
 
-def tune(R, G, target: torch.Tensor, reps: int = 3, use_cache: bool = True, candidates=CANDIDATES) -> Dict:
-    """Pick capacity and pixels-per-lane for (R, G); applies them and returns the choice."""
+def tune(R, G, target: torch.Tensor, reps: int = 6, rounds: int = 2, use_cache: bool = True,
+         candidates=CANDIDATES) -> Dict:
+    """Pick capacity and pixels-per-lane for (R, G); applies them and returns the choice.
+    Every candidate is timed in `rounds` interleaved rounds of `reps` steps and
+    keeps its fastest round, so that a transient slowdown of one trial does not
+    decide the choice."""
     key = _key(R, G)
     cache = _load() if use_cache else {}
     K = R.autotune_capacity(G)
@@ -67,12 +71,13 @@ def tune(R, G, target: torch.Tensor, reps: int = 3, use_cache: bool = True, cand
         abi.splat_set_pixels_per_lane(c["ppl_fwd"], c["ppl_bwd"])
         c = dict(c, K=K, capacity=R.capacity, cached=True)
         return c
-    best: Optional[Dict] = None
-    for fwd, bwd in candidates:
-        abi.splat_set_pixels_per_lane(fwd, bwd)
-        ms = _time_steps(R, G, target, reps)
-        if best is None or ms < best["ms"]:
-            best = {"ppl_fwd": fwd, "ppl_bwd": bwd, "ms": ms}
+    ms = {c: float("inf") for c in candidates}
+    for _ in range(rounds):
+        for fwd, bwd in candidates:
+            abi.splat_set_pixels_per_lane(fwd, bwd)
+            ms[(fwd, bwd)] = min(ms[(fwd, bwd)], _time_steps(R, G, target, reps))
+    (fwd, bwd), t = min(ms.items(), key=lambda kv: kv[1])
+    best = {"ppl_fwd": fwd, "ppl_bwd": bwd, "ms": t}
     abi.splat_set_pixels_per_lane(best["ppl_fwd"], best["ppl_bwd"])
     cache[key] = best
     if use_cache:

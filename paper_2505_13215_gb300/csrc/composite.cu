@@ -20,7 +20,7 @@
 
 namespace splat {
 
-constexpr int kCompWarps = 4;  // warps (units) per CTA
+constexpr int kCompWarps = 1;  // warps (units) per CTA
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2x2 = 1.3862943611198906f;  // 2 ln 2: converts the staged log2-scaled conic back
 
@@ -217,7 +217,8 @@ __device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, 
 // computed) and blended, into stats[0..1] (diagnostic instantiation only).
 template <int PPL, bool STATS>
 __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj proj, const uint32_t* __restrict__ vals,
-                                                                   const uint2* __restrict__ ranges, ViewBatch vb,
+                                                                   const uint2* __restrict__ ranges,
+                                                                   const uint32_t* __restrict__ order, ViewBatch vb,
                                                                    splat_image img, int32_t* status,
                                                                    unsigned long long* stats)
 {
@@ -228,7 +229,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
     if (unit >= (int64_t)vb.total_tiles * BANDS) return;
-    const int tile = (int)(unit / BANDS), band = (int)(unit % BANDS);
+    // tiles in the bin sort's order (longest list first) when it wrote one
+    const int slot = (int)(unit / BANDS), band = (int)(unit % BANDS);
+    const int tile = order ? (int)__ldg(order + slot) : slot;
     const int v = find_view(vb, tile);
     const ViewParams& vp = vb.v[v];
     const int local = tile - vp.tile_base;
@@ -328,7 +331,7 @@ constexpr int kRedGroups = 16;
 // holds 5 CTAs): PPL = 8 needs about 125 registers
 template <int PPL>
 struct BwdOccupancy {
-    static constexpr int kMinBlocks = PPL >= 8 ? 4 : 5;
+    static constexpr int kMinBlocks = PPL >= 8 ? 16 : 20;
 };
 
 __device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint32_t pend_row, int pend_j,
@@ -445,7 +448,8 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
 // STATS: also count the pairs evaluated and blended into stats[2..3].
 template <int PPL, bool STATS>
 __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks) k_composite_bwd(splat_proj proj, const uint32_t* __restrict__ vals,
-                                                                   const uint2* __restrict__ ranges, ViewBatch vb,
+                                                                   const uint2* __restrict__ ranges,
+                                                                   const uint32_t* __restrict__ order, ViewBatch vb,
                                                                    splat_image img, const float* __restrict__ dL,
                                                                    float* dproj, int32_t* status,
                                                                    unsigned long long* stats)
@@ -459,7 +463,9 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
     if (unit >= (int64_t)vb.total_tiles * BANDS) return;
-    const int tile = (int)(unit / BANDS), band = (int)(unit % BANDS);
+    // tiles in the bin sort's order (longest list first) when it wrote one
+    const int slot = (int)(unit / BANDS), band = (int)(unit % BANDS);
+    const int tile = order ? (int)__ldg(order + slot) : slot;
     const int v = find_view(vb, tile);
     const ViewParams& vp = vb.v[v];
     const int local = tile - vp.tile_base;
@@ -634,9 +640,9 @@ static void fwd_launch(int ppl, int blocks, cudaStream_t st, const splat_proj& p
 {
     const uint2* rg = (const uint2*)bins.ranges;
     switch (ppl) {
-    case 8: k_composite_fwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, status, stats); break;
-    case 4: k_composite_fwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, status, stats); break;
-    default: k_composite_fwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, status, stats); break;
+    case 8: k_composite_fwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, status, stats); break;
+    case 4: k_composite_fwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, status, stats); break;
+    default: k_composite_fwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, status, stats); break;
     }
 }
 
@@ -647,9 +653,9 @@ static void bwd_launch(int ppl, int blocks, cudaStream_t st, const splat_proj& p
 {
     const uint2* rg = (const uint2*)bins.ranges;
     switch (ppl) {
-    case 8: k_composite_bwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, dL, dproj, status, stats); break;
-    case 4: k_composite_bwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, dL, dproj, status, stats); break;
-    default: k_composite_bwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, vb, img, dL, dproj, status, stats); break;
+    case 8: k_composite_bwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, dL, dproj, status, stats); break;
+    case 4: k_composite_bwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, dL, dproj, status, stats); break;
+    default: k_composite_bwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, dL, dproj, status, stats); break;
     }
 }
 

@@ -805,6 +805,47 @@ __global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, i
     }
 }
 
+// Tiles in decreasing order of list length for the compositing kernels'
+// scheduling (the longest first, so that the last wave of warps is short):
+// classes of powers of two, counting sort over the classes in one block, the
+// order inside a class unspecified.  Lanes of a warp with the same class add to
+// its cursor once.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2* ranges, int n, uint32_t* order, int32_t* status)
+{
+    __shared__ uint32_t s_cls[33];
+    if (status_failed(status)) return;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 33) s_cls[tid] = 0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i0 = 0; i0 < n; i0 += blockDim.x) {  // warp-uniform
+            const int i = i0 + tid;
+            uint32_t cls = 33;  // none
+            if (i < n) {
+                const uint2 r = ranges[i];
+                const uint32_t c = r.y - r.x;
+                cls = c ? 32u - __clz(c) : 0u;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, cls);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (lane == leader && cls < 33) base = atomicAdd(&s_cls[cls], (uint32_t)__popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (pass == 1 && cls < 33) order[base + __popc(peers & lanemask_lt())] = (uint32_t)i;
+        }
+        __syncthreads();
+        if (pass == 0 && tid == 0) {  // class counts -> starts, the longest class first
+            uint32_t pos = 0;
+            for (int b = 32; b >= 0; --b) {
+                const uint32_t c = s_cls[b];
+                s_cls[b] = pos;
+                pos += c;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Tile level.  A counting pass of the per-super-tile filter gives every tile's
 // total, k_bin_ranges scans them into ranges (and K), and the writing pass of
@@ -1531,6 +1572,10 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_seg_prefix<<<(int)(((int64_t)sb * 64 + 255) / 256), 256, 0, s>>>(t);
         k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity);
         k_tile_filter<false><<<blocks_f, 256, 0, s>>>(t);
+        if (bins.tile_order && L.total_tiles > 0) {
+            count_launch();
+            k_tile_order<<<1, 1024, 0, s>>>((const uint2*)bins.ranges, (int)L.total_tiles, bins.tile_order, status);
+        }
         return cudaGetLastError();
     }
     // 4. radix path: duplicate, tile-digit passes, ranges
@@ -1589,6 +1634,11 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         const int blocks = ctx.num_sms * 8;
         count_launch();
         k_ranges<<<blocks, 256, 0, s>>>(bins.keys, bins.n_instances, bins.capacity, (uint2*)bins.ranges, status);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    if (bins.tile_order && L.total_tiles > 0) {
+        count_launch();
+        k_tile_order<<<1, 1024, 0, s>>>((const uint2*)bins.ranges, (int)L.total_tiles, bins.tile_order, status);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     return cudaSuccess;

@@ -162,6 +162,8 @@ class Rasterizer:
         self.status = torch.zeros((4,), dtype=i32, device=d)
         self.n_instances = torch.zeros((1,), dtype=torch.int64, device=d)
         self.ranges = torch.zeros((max(1, self.total_tiles) * 2,), dtype=i32, device=d)
+        # tiles longest list first, for the compositing kernels' scheduling
+        self.tile_order = torch.arange(max(1, self.total_tiles), dtype=i32, device=d)
         self.dproj = torch.zeros((rows * 12,), dtype=f32, device=d)
         self.loss = torch.zeros((1,), dtype=f32, device=d)
         self.dL = torch.zeros_like(self.rgb)
@@ -202,7 +204,7 @@ class Rasterizer:
         self.keys = torch.empty((capacity if self.keep_keys else 0,), dtype=torch.int32, device=self.device)
         self.vals = torch.empty((capacity,), dtype=torch.int32, device=self.device)
         self.cbins = abi.splat_bins(capacity, self.keys.data_ptr() if self.keep_keys else None, self.vals.data_ptr(),
-                                    self.ranges.data_ptr(), self.n_instances.data_ptr())
+                                    self.ranges.data_ptr(), self.n_instances.data_ptr(), self.tile_order.data_ptr())
         ws = abi.splat_workspace_size(abi.SPLAT_OP_ALL, self.n3, self.n4, self.W, self.H, capacity)
         if ws == 0:
             raise ValueError("invalid sizes for the workspace")

@@ -745,3 +745,38 @@ def test_max_batch_sixteen_views_mixed_sizes():
         check_image(R, Ps[v], refs[v], views[v], v)
     dls = loss_grad(R, refs, Ps, views, seed=6)
     check_grads(R, G, scene, Ps, views, dls)
+
+
+def test_tile_order_longest_first_changes_nothing(small):
+    """splat_bin_sort writes the tiles longest list first (classes of powers of
+    two); the compositing kernels take them in that order.  The order is a
+    permutation of the tiles, non-increasing by class, and rendering with it or
+    in raster order (NULL) gives the same images, T and ends of walks (gradients
+    up to the order of their float atomics)."""
+    scene, views = scenes.arc_scene(seed=5, n=20000, frac4=0.3, n_views=3, full=(256, 192, 280.0),
+                                    half=(120, 96, 130.0))
+    G, R = make(scene, views)
+    target = torch.rand(R.rgb.shape, generator=torch.Generator(device="cuda").manual_seed(13), device="cuda")
+    out = []
+    try:
+        for use in (True, False):
+            if not use:
+                R.cbins.tile_order = None
+            R.step(G, target)
+            torch.cuda.synchronize()
+            R.check()
+            out.append((R.rgb.clone(), R.final_T.clone(), R.last.clone(), {k: v.clone() for k, v in R.grads.items()}))
+            if use:
+                order = R.tile_order.cpu().numpy().astype(np.int64)
+                rg = R.ranges.cpu().numpy().astype(np.int64).reshape(-1, 2)
+    finally:
+        R.cbins.tile_order = R.tile_order.data_ptr()
+    T = R.total_tiles
+    assert np.array_equal(np.sort(order[:T]), np.arange(T))
+    length = rg[order[:T], 1] - rg[order[:T], 0]
+    cls = np.where(length > 0, np.floor(np.log2(np.maximum(length, 1))).astype(np.int64) + 1, 0)
+    assert np.all(np.diff(cls) <= 0) and cls[0] > cls[-1]
+    (rgb0, T0, l0, g0), (rgb1, T1, l1, g1) = out
+    assert torch.equal(rgb0, rgb1) and torch.equal(T0, T1) and torch.equal(l0, l1)
+    for k in g0:
+        assert rel_l2(g1[k].cpu().numpy(), g0[k].cpu().numpy()) < 1e-6, k
