@@ -807,43 +807,62 @@ __global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, i
 
 // Tiles in decreasing order of list length for the compositing kernels'
 // scheduling (the longest first, so that the last wave of warps is short):
-// classes of powers of two, counting sort over the classes in one block, the
-// order inside a class unspecified.  Lanes of a warp with the same class add to
-// its cursor once.
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2* ranges, int n, uint32_t* order, int32_t* status)
+// classes of powers of two, a counting sort over the classes in two grid-wide
+// passes (class counts, then each tile's slot from its class start and a
+// class cursor), the order inside a class unspecified.  cls[0..32]: counts,
+// cls[33..65]: cursors, both zero on entry.  Lanes of a warp in the same class
+// touch its counter once.
+__device__ __forceinline__ uint32_t tile_class(const uint2* ranges, int i)
 {
-    __shared__ uint32_t s_cls[33];
+    const uint2 r = ranges[i];
+    const uint32_t c = r.y - r.x;
+    return c ? 32u - __clz(c) : 0u;
+}
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_tile_order(const uint2* ranges, int n, uint32_t* cls, uint32_t* order,
+                                                    int32_t* status)
+{
+    __shared__ uint32_t s_start[33];
     if (status_failed(status)) return;
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < 33) s_cls[tid] = 0;
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int i0 = 0; i0 < n; i0 += blockDim.x) {  // warp-uniform
-            const int i = i0 + tid;
-            uint32_t cls = 33;  // none
-            if (i < n) {
-                const uint2 r = ranges[i];
-                const uint32_t c = r.y - r.x;
-                cls = c ? 32u - __clz(c) : 0u;
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, cls);
-            const int leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if (lane == leader && cls < 33) base = atomicAdd(&s_cls[cls], (uint32_t)__popc(peers));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (pass == 1 && cls < 33) order[base + __popc(peers & lanemask_lt())] = (uint32_t)i;
-        }
-        __syncthreads();
-        if (pass == 0 && tid == 0) {  // class counts -> starts, the longest class first
+    const int lane = threadIdx.x & 31;
+    if (SCATTER) {
+        if (threadIdx.x == 0) {  // class starts, the longest class first
             uint32_t pos = 0;
             for (int b = 32; b >= 0; --b) {
-                const uint32_t c = s_cls[b];
-                s_cls[b] = pos;
-                pos += c;
+                s_start[b] = pos;
+                pos += cls[b];
             }
         }
         __syncthreads();
     }
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {  // warp-uniform
+        const int i = i0 + lane;
+        const uint32_t c = i < n ? tile_class(ranges, i) : 33u;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader && c < 33) base = atomicAdd(&cls[SCATTER ? 33 + c : c], (uint32_t)__popc(peers));
+        if (SCATTER) {
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (c < 33) order[s_start[c] + base + __popc(peers & lanemask_lt())] = (uint32_t)i;
+        }
+    }
+}
+
+static cudaError_t launch_tile_order(const splat_bins& bins, int64_t total_tiles, uint32_t* cls, int32_t* status,
+                                     const LaunchCtx& ctx)
+{
+    if (!bins.tile_order || total_tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(cls, 0, 66 * sizeof(uint32_t), ctx.stream);
+    if (e != cudaSuccess) return e;
+    const int n = (int)total_tiles;
+    const int blocks = (int)std::min<int64_t>((total_tiles + 255) / 256, (int64_t)ctx.num_sms * 4);
+    count_launch(2);
+    k_tile_order<false><<<blocks, 256, 0, ctx.stream>>>((const uint2*)bins.ranges, n, cls, bins.tile_order, status);
+    k_tile_order<true><<<blocks, 256, 0, ctx.stream>>>((const uint2*)bins.ranges, n, cls, bins.tile_order, status);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -1300,7 +1319,7 @@ struct SortLayout {
     int64_t total_tiles, total_super;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
         off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
-    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_mask;
+    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_mask, off_tord;
     int64_t max_segs;
     size_t bytes;
 };
@@ -1364,6 +1383,7 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.off_segbase = take(4 * (size_t)(L.total_super + 1));
     L.off_segcnt = take(L.binned ? 4 * 64 * (size_t)L.max_segs : 4);
     L.off_mask = take(L.binned ? 8 * (size_t)capacity : 4);
+    L.off_tord = take(66 * 4);  // tile-order class counts and cursors
     L.bytes = o;
     return L;
 }
@@ -1572,11 +1592,8 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_seg_prefix<<<(int)(((int64_t)sb * 64 + 255) / 256), 256, 0, s>>>(t);
         k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity);
         k_tile_filter<false><<<blocks_f, 256, 0, s>>>(t);
-        if (bins.tile_order && L.total_tiles > 0) {
-            count_launch();
-            k_tile_order<<<1, 1024, 0, s>>>((const uint2*)bins.ranges, (int)L.total_tiles, bins.tile_order, status);
-        }
-        return cudaGetLastError();
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);
     }
     // 4. radix path: duplicate, tile-digit passes, ranges
     int bits = 1;
@@ -1636,12 +1653,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_ranges<<<blocks, 256, 0, s>>>(bins.keys, bins.n_instances, bins.capacity, (uint2*)bins.ranges, status);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    if (bins.tile_order && L.total_tiles > 0) {
-        count_launch();
-        k_tile_order<<<1, 1024, 0, s>>>((const uint2*)bins.ranges, (int)L.total_tiles, bins.tile_order, status);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
-    return cudaSuccess;
+    return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);
 }
 
 size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY)
