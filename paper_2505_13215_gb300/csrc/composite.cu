@@ -2,20 +2,22 @@
 //
 // Work decomposition: a "unit" is one tile (or a horizontal band of it, see
 // PPL) handled by ONE warp, independently of every other warp: no block
-// barriers.  Lane l owns pixel column l % 16 and rows (l / 16) + 2k, k < PPL,
-// of the band, so a warp covers 32 * PPL pixels (PPL = 8: the whole 16x16
-// tile).  The warp walks the tile's sorted list in batches of 32 Gaussians:
-// each lane gathers one Gaussian's projected features into the warp's
-// shared-memory slot, then every lane evaluates all its pixels against the
-// 32 staged Gaussians (broadcast reads).  The warp leaves the list as soon as
-// a vote shows every one of its pixels has saturated (T would drop below
-// 1e-4).
+// barriers, one warp per CTA (a CTA never waits for a slower tile), tiles
+// taken in the order splat_bin_sort wrote (longest list first) when it wrote
+// one.  Lane l owns pixel column l % 16 and rows (l / 16) + 2k, k < PPL, of
+// the band, so a warp covers 32 * PPL pixels (PPL = 8: the whole 16x16 tile);
+// it evaluates them in pairs with packed FP32x2 arithmetic.  The warp walks
+// the tile's sorted list in batches of 32 Gaussians: each lane gathers one
+// Gaussian's projected features into the warp's shared-memory slot, then
+// every lane evaluates all its pixels against the 32 staged Gaussians
+// (broadcast reads).  The warp leaves the list as soon as a vote shows every
+// one of its pixels has saturated (T would drop below 1e-4).
 //
-// The adjoint walks the same list back to front from each pixel's stored last
-// contributor, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
+// The adjoint walks the same list back to front from where each pixel's walk
+// ended, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
 // transmittance.  Per Gaussian each lane keeps 9 sums over its pixels; batches
 // of kRedBatch Gaussians are summed over the warp through shared memory and
-// added to the 2D gradients with one vector atomic per 4 components.
+// added to the 2D gradients with vector atomics.
 #include "splat_internal.cuh"
 
 namespace splat {
