@@ -15,7 +15,11 @@ loss.  L2 is flushed (a 512 MB write) before every timed step.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--views V] [--impl reference]
 
 Under torchrun each rank renders its own batch of views (independent
-replicas, weak scaling); rank 0 prints one JSON line.
+replicas, weak scaling); rank 0 prints one JSON line.  On one GPU the line
+also carries the training step (`train_step`), the other batched
+configurations (`workloads`: an 8-view arc of 500k Gaussians at mixed
+resolutions in FP32 and 1M Gaussians over 4 views at 2704x2028 in BF16) and
+the FP64 oracle timed on the host cores (`cpu_baseline`).
 """
 import argparse
 import json
@@ -447,10 +451,64 @@ def run_ours(args, rank, local, world):
         del gs, gs2, sets, R, G, G2, target2, G32, flush
         torch.cuda.empty_cache()
         out["train_step"] = run_train(args, hbm_peak, peak_src, dev, rank)
+    if rank == 0 and world == 1 and not args.no_extra:
+        out["workloads"] = run_workloads(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene, views, samples=args.cpu_samples)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# The other batched configurations, reported beside the headline (their
+# parity is checked by the workload tests): a 500k-Gaussian arc of 8 cameras
+# at mixed resolutions in FP32, and 1M Gaussians over 4 views at 2704x2028 with
+# BF16 storage.
+WORKLOADS = (
+    ("arc 500k (70% 3D), 8 views at 1352x1014 / 676x507, FP32",
+     dict(seed=2, n=500_000, frac4=0.3, n_views=8), "float32"),
+    ("arc 1M (60% 3D), 4 views at 2704x2028, BF16",
+     dict(seed=3, n=1_000_000, frac4=0.4, n_views=4, full=(2704, 2028, 2920.0), half=(2704, 2028, 2920.0)),
+     "bfloat16"),
+)
+
+
+def run_workloads(dev, steps=20, warmup=3):
+    """Each WORKLOADS entry autotuned and timed as its graphed training step
+    (forward, L1 loss, backward) with the L2 flushed before every step."""
+    import torch
+
+    from paper_2505_13215_gb300 import autotune, raster, scenes
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, kw, dt in WORKLOADS:
+        scene, views = scenes.arc_scene(**kw)
+        G = raster.Gaussians.from_scene(scene, dev, dtype=getattr(torch, dt))
+        R = raster.Rasterizer(G.n3, G.n4, views, device=dev, keep_keys=False)
+        target = torch.rand(R.rgb.shape, device=dev)
+        tune = autotune.tune(R, G, target)
+        gs = raster.GraphedStep(R, G, target, copies=1)
+        for _ in range(warmup):
+            flush.zero_()
+            gs.replay(0)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            gs.replay(0)
+            b.record(stream)
+        torch.cuda.synchronize()
+        R.check("workload: " + name)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        res[name] = {"views_per_s": round(R.V / (ms / 1e3), 2),
+                     "mpixel_per_s": round(sum(R.pix) / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 3),
+                     "views": R.V, "gaussians": G.n, "storage": dt, "instances_K": R.instances(),
+                     "autotune": {"ppl_fwd": tune["ppl_fwd"], "ppl_bwd": tune["ppl_bwd"]},
+                     "l2": "flushed before each step", "steps": steps}
+        del gs, R, G, target
+        torch.cuda.empty_cache()
+    return res
 
 
 TRAIN_N = 300_000
@@ -671,6 +729,7 @@ def main(argv=None):
     ap.add_argument("--ref-samples", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other batched workloads")
     ap.add_argument("--profile", type=int, default=0, help="run this many untimed eager steps (for ncu) and exit")
     ap.add_argument("--profile-train", type=int, default=0,
                     help="run this many untimed steps of the training workload (for ncu) and exit")
