@@ -291,6 +291,19 @@ splat_status splat_composite_fwd(const splat_proj *proj, const splat_bins *bins,
                                  splat_image *img, int32_t *status, void *stream);
 
 /*
+ * splat_composite_fwd with the L1 loss of splat_l1_loss fused into it: as
+ * each pixel's colour is written it is compared with target (device floats,
+ * the layout of img->rgb): *loss = sum |rgb - target| (device float,
+ * overwritten), dL_drgb = scale * sign(rgb - target) with sign(0) = 0.  The
+ * image and the gradient are the same as from the two calls, the loss up to
+ * the order of its float sum; the image is not read back.  When the status
+ * word already holds an error, nothing is rendered and dL_drgb is not written.
+ */
+splat_status splat_composite_fwd_l1(const splat_proj *proj, const splat_bins *bins, const splat_view *views, int V,
+                                    splat_image *img, const float *target, float scale, float *dL_drgb,
+                                    float *loss, int32_t *status, void *stream);
+
+/*
  * Reverse mode of the forward pipeline for a loss with pixel gradient
  * dL_drgb (same layout as img->rgb).  Replays each pixel back to front from
  * its stored final_T and last (T_i = T_{i+1} / (1 - alpha_i)); no per-splat

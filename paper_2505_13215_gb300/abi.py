@@ -113,6 +113,8 @@ EXPORTS = {
                                  C.c_size_t, C.c_void_p]),
     "splat_composite_fwd": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int, _P(splat_image),
                                       C.c_void_p, C.c_void_p]),
+    "splat_composite_fwd_l1": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int, _P(splat_image),
+                                         C.c_void_p, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "splat_composite_bwd": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int, _P(splat_image),
                                       C.c_void_p, _P(splat_g3), _P(splat_g4), _P(splat_grads3), _P(splat_grads4),
                                       C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -228,6 +230,10 @@ def splat_bin_sort(proj, views, V, bins, status, ws, ws_bytes, stream):
 
 def splat_composite_fwd(proj, bins, views, V, img, status, stream):
     return lib().splat_composite_fwd(proj, bins, views, V, img, status, stream)
+
+
+def splat_composite_fwd_l1(proj, bins, views, V, img, target, scale, dL, loss, status, stream):
+    return lib().splat_composite_fwd_l1(proj, bins, views, V, img, target, scale, dL, loss, status, stream)
 
 
 def splat_composite_bwd(proj, bins, views, V, img, dL, g3, g4, dg3, dg4, dproj, flags, status, ws, ws_bytes, stream):

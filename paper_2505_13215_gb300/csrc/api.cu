@@ -17,8 +17,8 @@ cudaError_t launch_bin_sort(const splat_proj&, const ViewBatch&, const splat_bin
 size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY);
 void set_tile_sort_mode(int mode);
 void set_tile_cull(int on);
-cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&, int32_t*,
-                                 int, unsigned long long*, const LaunchCtx&);
+cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
+                                 const L1Fuse*, int32_t*, int, unsigned long long*, const LaunchCtx&);
 cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
                                  const float*, float*, int32_t*, int, unsigned long long*, const LaunchCtx&);
 cudaError_t launch_convert(const splat_g4&, const splat_g3&, float, int64_t*, int32_t*, void*, const LaunchCtx&);
@@ -337,7 +337,23 @@ splat_status splat_composite_fwd(const splat_proj* proj, const splat_bins* bins,
         return SPLAT_ERR_INVALID_ARG;
     const LaunchCtx ctx = launch_ctx(stream);
     const ViewBatch vb = make_batch(views, V);
-    return cuda_status(launch_composite_fwd(*proj, *bins, vb, *img, status, g_ppl_fwd.load(), g_stats.load(), ctx));
+    return cuda_status(
+        launch_composite_fwd(*proj, *bins, vb, *img, nullptr, status, g_ppl_fwd.load(), g_stats.load(), ctx));
+}
+
+splat_status splat_composite_fwd_l1(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
+                                    splat_image* img, const float* target, float scale, float* dL_drgb, float* loss,
+                                    int32_t* status, void* stream)
+{
+    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !status) return SPLAT_ERR_INVALID_ARG;
+    if (!img->rgb || !img->final_T || !img->last || !bins->ranges || (bins->capacity > 0 && !bins->vals))
+        return SPLAT_ERR_INVALID_ARG;
+    if (!target || !dL_drgb || !loss || !std::isfinite(scale)) return SPLAT_ERR_INVALID_ARG;
+    const LaunchCtx ctx = launch_ctx(stream);
+    const ViewBatch vb = make_batch(views, V);
+    const L1Fuse l1{target, scale, dL_drgb, loss};
+    return cuda_status(
+        launch_composite_fwd(*proj, *bins, vb, *img, &l1, status, g_ppl_fwd.load(), g_stats.load(), ctx));
 }
 
 splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,

@@ -221,7 +221,7 @@ template <int PPL, bool STATS>
 __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj proj, const uint32_t* __restrict__ vals,
                                                                    const uint2* __restrict__ ranges,
                                                                    const uint32_t* __restrict__ order, ViewBatch vb,
-                                                                   splat_image img, int32_t* status,
+                                                                   splat_image img, L1Fuse l1, int32_t* status,
                                                                    unsigned long long* stats)
 {
     static_assert(PPL == 2 || PPL == 4 || PPL == 8, "pixels per lane come in pairs");
@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     }
     const int64_t HW = (int64_t)vp.W * vp.H;
     float* rgb = img.rgb + 3 * vp.pix_base;
+    float l1sum = 0.f;  // the lane's share of the fused L1 loss
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
         const int y = y0 + 2 * k;
@@ -307,11 +308,25 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
         const float c0 = (k & 1) ? nC[k >> 1][0].y : nC[k >> 1][0].x;
         const float c1 = (k & 1) ? nC[k >> 1][1].y : nC[k >> 1][1].x;
         const float c2 = (k & 1) ? nC[k >> 1][2].y : nC[k >> 1][2].x;
-        rgb[p] = Tk * vp.bg[0] - c0;
-        rgb[HW + p] = Tk * vp.bg[1] - c1;
-        rgb[2 * HW + p] = Tk * vp.bg[2] - c2;
+        const float out[3] = {Tk * vp.bg[0] - c0, Tk * vp.bg[1] - c1, Tk * vp.bg[2] - c2};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + p] = out[ch];
         img.final_T[vp.pix_base + p] = Tk;
         img.last[vp.pix_base + p] = last[k];
+        if (l1.target) {  // same for every lane
+            const int64_t q = 3 * vp.pix_base + p;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float d = out[ch] - l1.target[q + ch * HW];
+                l1sum += fabsf(d);
+                l1.dL[q + ch * HW] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * l1.scale;
+            }
+        }
+    }
+    if (l1.target) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1sum += __shfl_xor_sync(0xffffffffu, l1sum, o);
+        if (lane == 0) atomicAdd(l1.loss, l1sum);
     }
 }
 
@@ -638,13 +653,14 @@ cudaError_t launch_l1_loss(const float* img, const float* target, int64_t n, flo
 
 template <bool ST>
 static void fwd_launch(int ppl, int blocks, cudaStream_t st, const splat_proj& proj, const splat_bins& bins,
-                       const ViewBatch& vb, const splat_image& img, int32_t* status, unsigned long long* stats)
+                       const ViewBatch& vb, const splat_image& img, const L1Fuse& l1, int32_t* status,
+                       unsigned long long* stats)
 {
     const uint2* rg = (const uint2*)bins.ranges;
     switch (ppl) {
-    case 8: k_composite_fwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, status, stats); break;
-    case 4: k_composite_fwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, status, stats); break;
-    default: k_composite_fwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, status, stats); break;
+    case 8: k_composite_fwd<8, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, l1, status, stats); break;
+    case 4: k_composite_fwd<4, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, l1, status, stats); break;
+    default: k_composite_fwd<2, ST><<<blocks, kCompWarps * 32, 0, st>>>(proj, bins.vals, rg, bins.tile_order, vb, img, l1, status, stats); break;
     }
 }
 
@@ -662,16 +678,21 @@ static void bwd_launch(int ppl, int blocks, cudaStream_t st, const splat_proj& p
 }
 
 cudaError_t launch_composite_fwd(const splat_proj& proj, const splat_bins& bins, const ViewBatch& vb,
-                                 const splat_image& img, int32_t* status, int ppl, unsigned long long* stats,
-                                 const LaunchCtx& ctx)
+                                 const splat_image& img, const L1Fuse* l1p, int32_t* status, int ppl,
+                                 unsigned long long* stats, const LaunchCtx& ctx)
 {
+    const L1Fuse l1 = l1p ? *l1p : L1Fuse{nullptr, 0.f, nullptr, nullptr};
+    if (l1.loss) {
+        const cudaError_t e = cudaMemsetAsync(l1.loss, 0, sizeof(float), ctx.stream);
+        if (e != cudaSuccess) return e;
+    }
     if (vb.total_tiles == 0) return cudaSuccess;
     const int bands = 8 / ppl;
     const int64_t units = (int64_t)vb.total_tiles * bands;
     const int blocks = (int)((units + kCompWarps - 1) / kCompWarps);
     count_launch();
-    if (stats) fwd_launch<true>(ppl, blocks, ctx.stream, proj, bins, vb, img, status, stats);
-    else fwd_launch<false>(ppl, blocks, ctx.stream, proj, bins, vb, img, status, nullptr);
+    if (stats) fwd_launch<true>(ppl, blocks, ctx.stream, proj, bins, vb, img, l1, status, stats);
+    else fwd_launch<false>(ppl, blocks, ctx.stream, proj, bins, vb, img, l1, status, nullptr);
     return cudaGetLastError();
 }
 

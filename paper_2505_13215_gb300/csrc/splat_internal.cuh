@@ -276,6 +276,16 @@ __device__ __forceinline__ float inv_norm4(const float q[4])
 namespace splat {
 extern std::atomic<int64_t> g_launches;  // kernels launched or captured (diagnostic)
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// L1 loss fused into the forward compositing (all null when not fused):
+// *loss += sum |rgb - target|, dL = scale * sign(rgb - target), per pixel as
+// its colour is written.
+struct L1Fuse {
+    const float* target;
+    float scale;
+    float* dL;
+    float* loss;
+};
+
 struct LaunchCtx {
     cudaStream_t stream;
     int num_sms;

@@ -263,7 +263,18 @@ class Rasterizer:
                                     _ptr(self.loss), _stream(stream)), "splat_l1_loss")
         return self.loss
 
+    def composite_l1(self, target: torch.Tensor, stream=None):
+        """Composite all views with the L1 loss fused in (the same image, loss and
+        pixel gradient as composite() followed by l1_loss(); asynchronous)."""
+        n = self.rgb.numel()
+        abi.check(abi.splat_composite_fwd_l1(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
+                                             C.byref(self.cimg), _ptr(target), 1.0 / max(1, n), _ptr(self.dL),
+                                             _ptr(self.loss), _ptr(self.status), _stream(stream)),
+                  "splat_composite_fwd_l1")
+        return self.loss
+
     STAGES = ("slice_project", "bin_sort", "composite_fwd", "loss", "composite_bwd", "adjoint")
+    fuse_loss = True  # step(): the L1 loss inside the forward compositing (the "loss" stage is then empty)
 
     def step(self, G: Gaussians, target: torch.Tensor, stream=None, marks: Optional[dict] = None):
         """One training step of the rasterizer over the whole view batch: forward,
@@ -280,9 +291,13 @@ class Rasterizer:
         mark("slice_project")
         self.bin_sort(stream)
         mark("bin_sort")
-        self.composite(stream)
-        mark("composite_fwd")
-        self.l1_loss(target, stream)
+        if self.fuse_loss:
+            self.composite_l1(target, stream)
+            mark("composite_fwd")
+        else:
+            self.composite(stream)
+            mark("composite_fwd")
+            self.l1_loss(target, stream)
         mark("loss")
         self._bwd(G, self.dL, abi.SPLAT_BWD_STOP_2D, stream)
         mark("composite_bwd")

@@ -602,6 +602,38 @@ def test_l1_loss_kernel(small):
     np.testing.assert_array_equal(R.dL.cpu().numpy(), (torch.sign(d) / R.rgb.numel()).float().cpu().numpy())
 
 
+@pytest.mark.parametrize("ppl", [4, 8])
+def test_forward_with_fused_l1_loss(ppl):
+    """splat_composite_fwd_l1 against splat_composite_fwd + splat_l1_loss on a
+    3-view batch of mixed sizes: the same image, T and ends of walks, the same
+    pixel gradient bit for bit (including sign(0) = 0 where the target equals
+    the image), the loss up to the order of its sum."""
+    scene, views = scenes.arc_scene(seed=5, n=20000, frac4=0.3, n_views=3, full=(256, 192, 280.0),
+                                    half=(120, 96, 130.0))
+    G, R = make(scene, views)
+    abi.splat_set_pixels_per_lane(ppl, ppl)
+    try:
+        R.forward(G)
+        torch.cuda.synchronize()
+        target = torch.rand(R.rgb.shape, generator=torch.Generator(device="cuda").manual_seed(17), device="cuda")
+        target[::7] = R.rgb[::7]  # ties: sign(0) = 0
+        R.l1_loss(target)
+        torch.cuda.synchronize()
+        R.check()
+        ref = (R.rgb.clone(), R.final_T.clone(), R.last.clone(), R.dL.clone(), float(R.loss.item()))
+        R.dL.zero_()
+        R.rgb.zero_()
+        R.composite_l1(target)
+        torch.cuda.synchronize()
+        R.check()
+    finally:
+        abi.splat_set_pixels_per_lane(8, 8)
+    assert torch.equal(R.rgb, ref[0]) and torch.equal(R.final_T, ref[1]) and torch.equal(R.last, ref[2])
+    assert torch.equal(R.dL, ref[3])
+    assert int((R.dL == 0).sum()) >= R.rgb.numel() // 7
+    assert abs(float(R.loss.item()) - ref[4]) <= 1e-5 * ref[4]
+
+
 def test_graph_replay_matches_eager(small):
     scene, views, G, R0, P, ref = small
     R = raster.Rasterizer(G.n3, G.n4, views, capacity=R0.capacity)
