@@ -344,8 +344,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
 // blue-channel gradient (component 8).
 constexpr int kRedBatch = 7;
 constexpr int kRedGroups = 16;
-// resident CTAs per SM the backward is compiled for (registers; shared memory
-// holds 5 CTAs): PPL = 8 needs about 125 registers
+// resident one-warp CTAs per SM the backward is compiled for: 16 leave
+// PPL = 8 its 128 registers (fewer registers spill in the loop and measured
+// slower), 20 give the smaller variants 96
 template <int PPL>
 struct BwdOccupancy {
     static constexpr int kMinBlocks = PPL >= 8 ? 16 : 20;
