@@ -12,8 +12,9 @@
 //
 // Radix passes are single-pass "onesweep"-style: one 8-bit digit per pass,
 // partitions of 3840 keys taken in ticket order by persistent CTAs, local
-// ranking with warp match + shared-memory counters, and a decoupled look-back
-// across partitions whose waits are bounded (SPLAT_ERR_TIMEOUT on expiry).
+// ranking of the keys of a warp (digit-bit ballots or a match instruction)
+// with shared-memory counters, and a decoupled look-back across partitions
+// whose waits are bounded (SPLAT_ERR_TIMEOUT on expiry).
 #include <algorithm>
 
 #include "splat_internal.cuh"
@@ -1196,8 +1197,9 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 // One warp per chunk.  Slots are taken 32 at a time in order, across row
-// boundaries; lanes holding the same tile are ordered by lane (= slot order) with
-// match_any, and the group's lowest lane advances the tile's cursor.
+// boundaries; lanes holding the same tile (found by ballots over the tile
+// index bits) are ordered by lane (= slot order), and the group's lowest lane
+// advances the tile's cursor.
 __global__ void __launch_bounds__(32) k_bin_scatter(BinArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
