@@ -97,7 +97,14 @@ __global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int64_t n_r
     if (threadIdx.x < SPLAT_MAX_VIEWS) s_view[threadIdx.x] = 0;
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows; r += stride) {
+    const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int v = 0;  // view of row r, advanced with r (no division in the loop)
+    int64_t vend = proj.n;
+    if (r0 < n_rows) {
+        v = (int)(r0 / proj.n);
+        vend = (int64_t)(v + 1) * proj.n;
+    }
+    for (int64_t r = r0; r < n_rows; r += stride) {
         const uint32_t nt = proj.n_tiles[r];
         const float depth = ((const float4*)proj.rgb_depth)[r].w;
         const uint32_t k = nt > 0 ? __float_as_uint(depth) : 0xffffffffu;
@@ -105,7 +112,11 @@ __global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int64_t n_r
         vals[r] = (uint32_t)r;
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xff], 1u);
-        atomicAdd(&s_view[r / proj.n], 1u);
+        while (r >= vend) {
+            ++v;
+            vend += proj.n;
+        }
+        atomicAdd(&s_view[v], 1u);
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_a; i += stride) zero_a[i] = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_b; i += stride) zero_b[i] = 0;
@@ -893,6 +904,7 @@ struct TileArgs {
     uint32_t* seg_base;               // [total_super + 1] first segment of each super-tile's list
     uint32_t* seg_cnt;                // [segments][64] per-segment tile counts, then offsets
     uint2* mask;                      // per super-tile list entry: byte w = its tile columns in tile row w
+    uint32_t* ticket;                 // [2] segment tickets of the write and count passes (zeroed)
     int32_t* status;
 };
 
@@ -959,30 +971,31 @@ __device__ __forceinline__ float sqrt_approx(float x)
 }
 
 __device__ __forceinline__ void ellipse_consts(float px, float py, float a, float b, float c, float R2, float4& g0,
-                                               float4& g1, float4& g2)
+                                               float4& g1)
 {
     const float det = a * c - b * b;
     if (!(det > 0.f) || !(a > 0.f) || !(c > 0.f)) {
-        g0 = make_float4(px, py, R2, __int_as_float(0x7f800000));
+        g0 = make_float4(px, py, 0.f, __int_as_float(0x7f800000));
         g1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        g2 = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     // approximate quotients and roots (relative errors of a few 1e-7, inside
     // the squared radius' 1e-4 margin)
     const float ia = __fdividef(1.f, a), idet = __fdividef(1.f, det);
     const float X = sqrt_approx(R2 * c * idet);
-    g0 = make_float4(px, py, R2, sqrt_approx(R2 * a * idet));
-    g1 = make_float4(X, -__fdividef(b, c) * X, b * ia, det * ia);
-    g2 = make_float4(ia, 0.f, 0.f, 0.f);
+    // g0 = (centre, R2 / a, reach in y); g1 = (reach in x, dy of the rightmost
+    // point, b / a, det / a^2)
+    g0 = make_float4(px, py, R2 * ia, sqrt_approx(R2 * a * idet));
+    g1 = make_float4(X, -__fdividef(b, c) * X, b * ia, det * ia * ia);
 }
 
 // Horizontal pixel extent [ul, ur] of the footprint inside the pixel band
-// v in [vlo, vhi]; false when the footprint misses the band.
-__device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const float4& g1, const float4& g2, float vlo,
-                                                    float vhi, float& ul, float& ur)
+// v in [vlo, vhi]; false when the footprint misses the band.  At offset dy the
+// footprint spans dx = -(b/a) dy +- sqrt(R2/a - (det/a^2) dy^2).
+__device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const float4& g1, float vlo, float vhi,
+                                                    float& ul, float& ur)
 {
-    const float px = g0.x, py = g0.y, R2 = g0.z, Y = g0.w;
+    const float px = g0.x, py = g0.y, Ra = g0.z, Y = g0.w;
     if (isinf(Y)) {
         ul = -3.0e38f;
         ur = 3.0e38f;
@@ -990,20 +1003,20 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
     }
     const float e0 = fmaxf(py - vhi, -Y), e1 = fminf(py - vlo, Y);  // dy range of the band inside the reach
     if (e0 > e1) return false;
-    const float X = g1.x, yr = g1.y, ba = g1.z, ha = g1.w, ia = g2.x;
+    const float X = g1.x, yr = g1.y, ba = g1.z, hq = g1.w;
     float dxmax, dxmin;
     if (yr >= e0 && yr <= e1) {
         dxmax = X;
     } else {
         const float dy = fminf(fmaxf(yr, e0), e1);
-        dxmax = -ba * dy + sqrt_approx(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
+        dxmax = -ba * dy + sqrt_approx(fmaxf(0.f, Ra - hq * dy * dy));
     }
     const float yl = -yr;  // leftmost point
     if (yl >= e0 && yl <= e1) {
         dxmin = -X;
     } else {
         const float dy = fminf(fmaxf(yl, e0), e1);
-        dxmin = -ba * dy - sqrt_approx(fmaxf(0.f, (R2 - ha * dy * dy) * ia));
+        dxmin = -ba * dy - sqrt_approx(fmaxf(0.f, Ra - hq * dy * dy));
     }
     ul = px - dxmax;
     ur = px - dxmin;
@@ -1022,8 +1035,10 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
 {
-    __shared__ int4 s_rect[COUNT ? 256 : 1];
-    __shared__ float4 s_g0[COUNT ? 256 : 1], s_g1[COUNT ? 256 : 1], s_g2[COUNT ? 256 : 1];  // footprint constants
+    // COUNT: rectangle relative to the super-tile, clamped to [0, 8], one byte
+    // per bound (x0, y0, x1, y1); footprint constants
+    __shared__ uint32_t s_rect[COUNT ? 256 : 1];
+    __shared__ float4 s_g0[COUNT ? 256 : 1], s_g1[COUNT ? 256 : 1];
     __shared__ uint32_t s_row[COUNT ? 1 : 256];
     __shared__ uint2 s_mask[256];
     __shared__ unsigned char s_queue[8][256];  // per tile row: entries of the chunk it has work for
@@ -1031,6 +1046,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
     // so that four warp reductions count all eight columns of 32 entries
     __shared__ uint4 s_spread[COUNT ? 256 : 1];
     __shared__ int s_gs;
+    __shared__ uint32_t s_g;
     if (status_failed(a.status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
@@ -1041,16 +1057,24 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                                  (b >> 4 & 1u) | ((b >> 5 & 1u) << 16), (b >> 6 & 1u) | ((b >> 7 & 1u) << 16));
         __syncthreads();
     }
-    for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
-        if (threadIdx.x == 0) {  // super-tile of segment g: last gs with seg_base[gs] <= g
-            int lo = 0, hi = a.total_super - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.seg_base[mid] <= g) lo = mid; else hi = mid - 1;
+    for (;;) {
+        // segments are taken from a ticket counter: their costs differ, so a
+        // fixed assignment leaves SMs idle while others finish
+        if (threadIdx.x == 0) {
+            const uint32_t g = atomicAdd(a.ticket + (COUNT ? 1 : 0), 1u);
+            s_g = g;
+            if (g < nseg) {  // super-tile of segment g: last gs with seg_base[gs] <= g
+                int lo = 0, hi = a.total_super - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.seg_base[mid] <= g) lo = mid; else hi = mid - 1;
+                }
+                s_gs = lo;
             }
-            s_gs = lo;
         }
         __syncthreads();
+        const uint32_t g = s_g;
+        if (g >= nseg) break;
         const int gs = s_gs;
         int v = 0;
         for (int w = 1; w < a.V; ++w)
@@ -1078,18 +1102,20 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
             if (j < rg.y) {
                 const uint32_t row = a.list[j];
                 if (COUNT) {
-                    s_rect[threadIdx.x] = ((const int4*)a.proj.rect)[row];
+                    const int4 rc = ((const int4*)a.proj.rect)[row];
+                    auto rel = [](int c, int o) { return (uint32_t)min(max(c - o, 0), 8); };
+                    s_rect[threadIdx.x] = rel(rc.x, tx0) | rel(rc.y, sy * 8) << 8 | rel(rc.z, tx0) << 16 |
+                                          rel(rc.w, sy * 8) << 24;
                     s_mask[threadIdx.x] = make_uint2(0u, 0u);
                     if (a.cull) {
                         const float2 xy = ((const float2*)a.proj.xy)[row];
                         const float4 co = ((const float4*)a.proj.conic_opacity)[row];
                         // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
                         const float R2 = -2.f * __logf(__fdividef(kAlphaMin, co.w)) * 1.0001f + 2e-3f;
-                        float4 g0, g1, g2;
-                        ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1, g2);
+                        float4 g0, g1;
+                        ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1);
                         s_g0[threadIdx.x] = g0;
                         s_g1[threadIdx.x] = g1;
-                        s_g2[threadIdx.x] = g2;
                     }
                 } else {
                     s_row[threadIdx.x] = row;
@@ -1108,8 +1134,8 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                     bool take = false;
                     if (e < n) {
                         if (COUNT) {
-                            const int4 rc = s_rect[e];
-                            take = rc.y <= ty && ty < rc.w;
+                            const uint32_t rc = s_rect[e];
+                            take = (int)(rc >> 8 & 0xffu) <= warp && warp < (int)(rc >> 24);
                         } else {
                             take = ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu) != 0u;
                         }
@@ -1125,23 +1151,21 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                     unsigned m = 0;  // tile columns of this tile row the entry is listed in
                     if (qi < nq) {
                         if (COUNT) {
-                            const int4 rc = s_rect[e];
-                            int cx0 = rc.x, cx1 = rc.z;
-                            bool cy = true;
+                            const uint32_t rc = s_rect[e];
+                            int lo = (int)(rc & 0xffu), hi = (int)(rc >> 16 & 0xffu);  // columns of the super-tile
                             if (a.cull) {
                                 float ul, ur;
-                                if (!ellipse_band_extent(s_g0[e], s_g1[e], s_g2[e], vlo, vhi, ul, ur)) {
-                                    cy = false;
+                                if (!ellipse_band_extent(s_g0[e], s_g1[e], vlo, vhi, ul, ur)) {
+                                    hi = lo;
                                 } else {
                                     // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
-                                    const float lo = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
-                                    const float hi = floorf(ur * (1.f / kTile));
-                                    cx0 = max(cx0, (int)fminf(fmaxf(lo, -1.f), 1.0e6f));
-                                    cx1 = min(cx1, (int)fminf(fmaxf(hi, -2.f), 1.0e6f) + 1);
+                                    const float fl = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
+                                    const float fh = floorf(ur * (1.f / kTile));
+                                    lo = max(lo, (int)fminf(fmaxf(fl, -1.f), 1.0e6f) - tx0);
+                                    hi = min(hi, (int)fminf(fmaxf(fh, -2.f), 1.0e6f) + 1 - tx0);
                                 }
                             }
-                            const int lo = max(cx0 - tx0, 0), hi = min(cx1 - tx0, 8);
-                            if (cy && hi > lo) m = (1u << hi) - (1u << lo);
+                            if (hi > lo) m = (1u << hi) - (1u << lo);
                             reinterpret_cast<unsigned char*>(&s_mask[e])[warp] = (unsigned char)m;
                         } else {
                             m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu;
@@ -1390,6 +1414,15 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     return L;
 }
 
+// resident CTAs per SM of a kernel (grid-stride kernels launch one wave of them)
+template <typename Kernel>
+static int ctas_per_sm(Kernel kernel, int threads)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
 static int sort_ctas_per_sm()
 {
     static int cached = 0;
@@ -1437,7 +1470,8 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
 
     // 1. depth keys + digit histograms (+ rows per view); zero the first depth look-back buffer and the scan's
     {
-        const int blocks = (int)std::min<int64_t>((n_rows + 255) / 256, (int64_t)ctx.num_sms * 8);
+        static const int per_sm = ctas_per_sm(k_depth_keys, 256);
+        const int blocks = (int)std::min<int64_t>((n_rows + 255) / 256, (int64_t)ctx.num_sms * per_sm);
         count_launch();
         k_depth_keys<<<blocks, 256, 0, s>>>(proj, n_rows, U(L.off_dkeys[0]), U(L.off_dvals[0]), hist,
                                             U(L.off_dlb[0]), L.parts_d * kRadix,
@@ -1523,6 +1557,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.seg_base = U(L.off_segbase);
         t.seg_cnt = U(L.off_segcnt);
         t.mask = (uint2*)(w + L.off_mask);
+        t.ticket = tickets + 10;
         BinArgs tr{};
         tr.total_tiles = vb.total_tiles;
         tr.tile_total = U(L.off_total);
@@ -1587,13 +1622,15 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_bin_scatter<<<blocks_s, 32, smem_scatter, s>>>(a);
         // tile level: segment the super-tile lists, count each (segment, tile),
         // prefix over segments, ranges + K + capacity check, then write the lists
-        const int blocks_f = (int)std::min<int64_t>(L.max_segs, (int64_t)ctx.num_sms * 8);
+        // one wave of resident CTAs, which take the segments from a ticket counter
+        static const int per_sm_f[2] = {ctas_per_sm(k_tile_filter<false>, 256), ctas_per_sm(k_tile_filter<true>, 256)};
+        auto blocks_f = [&](int c) { return (int)std::min<int64_t>(L.max_segs, (int64_t)ctx.num_sms * per_sm_f[c]); };
         count_launch(5);
         k_seg_plan<<<1, 256, 0, s>>>(t);
-        k_tile_filter<true><<<blocks_f, 256, 0, s>>>(t);
+        k_tile_filter<true><<<blocks_f(1), 256, 0, s>>>(t);
         k_seg_prefix<<<(int)(((int64_t)sb * 64 + 255) / 256), 256, 0, s>>>(t);
         k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity);
-        k_tile_filter<false><<<blocks_f, 256, 0, s>>>(t);
+        k_tile_filter<false><<<blocks_f(0), 256, 0, s>>>(t);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);
     }
