@@ -172,6 +172,11 @@ typedef struct {
                               take tiles in this order, the longest first, so
                               that the last wave of warps is short.  Results
                               do not depend on it.  NULL: raster order.      */
+    int64_t *n_needed;     /* optional (may be NULL), [1]: the capacity the call
+                              needed, K or, on the binned path, the larger of K
+                              and the super-tile list length (which shares the
+                              capacity-sized buffers and, with the saturation
+                              cut, is often the larger)                      */
 } splat_bins;
 
 /* Rendered images and the per-pixel state the backward pass replays. */
@@ -506,10 +511,16 @@ void splat_set_tile_sort(int mode);
  * Binned tile sort only: when on (default), a Gaussian is listed for a tile of
  * its rectangle only if its opacity footprint -- the ellipse where alpha_max
  * exp(power) can reach 1/255, enlarged by a margin covering FP32 rounding --
- * meets the tile.  Every pixel skips the dropped pairs anyway, so images and
- * gradients do not change; the lists (and so `last`) are shorter.  Off: every
- * tile of the rectangle, as in splat_bin_sort's key definition.  Host-side
- * global.
+ * meets the tile; and each tile's list ends once the entries so far certify
+ * that every pixel of the tile has stopped its walk (T below 1e-4): a lower
+ * bound of each entry's alpha over the tile (alpha_max exp(-q/2), q the
+ * largest quadratic form over the tile's corners, with margins for FP32
+ * rounding) enters a fixed-point sum of -ln(1 - alpha), and the list ends
+ * after the batch of 32 entries that takes the sum past -ln(1e-4) plus a
+ * margin.  Every pixel skips the dropped pairs, or stops before reaching
+ * them, so images and gradients do not change; the lists (and so `last`) are
+ * shorter.  Off: every tile of the rectangle, as in splat_bin_sort's key
+ * definition.  Host-side global.
  */
 void splat_set_tile_cull(int on);
 

@@ -57,7 +57,7 @@ class splat_proj(C.Structure):
 
 class splat_bins(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("keys", C.c_void_p), ("vals", C.c_void_p), ("ranges", C.c_void_p),
-                ("n_instances", C.c_void_p), ("tile_order", C.c_void_p)]
+                ("n_instances", C.c_void_p), ("tile_order", C.c_void_p), ("n_needed", C.c_void_p)]
 
 
 class splat_image(C.Structure):

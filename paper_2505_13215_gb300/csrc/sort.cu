@@ -302,6 +302,7 @@ struct ScanArgs {
     unsigned long long* lb;    // [parts] look-back words (zeroed)
     uint32_t* ticket;
     int64_t* n_instances;      // out: K
+    int64_t* n_needed;         // out (may be null): K as the capacity needed
     int64_t capacity;
     int32_t* status;
     int64_t spin_limit;
@@ -387,6 +388,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
             if (ticket == parts - 1) {
                 const int64_t K = (int64_t)(excl + agg);
                 *a.n_instances = K;
+                if (a.n_needed) *a.n_needed = K;
                 if (K > a.capacity) set_status(a.status, SPLAT_ERR_CAPACITY, SPLAT_STAGE_SCAN, K);
             }
         }
@@ -769,7 +771,8 @@ constexpr int kRangeRound = 256 * kRangeItems;
 
 __device__ __forceinline__ int range_pad(int i) { return i + (i >> 5); }  // conflict-free strided reads
 
-__global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, int64_t capacity)
+__global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, int64_t capacity,
+                                                    const int64_t* K_super = nullptr, int64_t* needed = nullptr)
 {
     __shared__ uint32_t s_c[kRangeRound + kRangeRound / 32], s_st[kRangeRound + kRangeRound / 32];
     __shared__ unsigned long long s_tmp64[8];
@@ -814,6 +817,8 @@ __global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, i
     if (K_out && threadIdx.x == 0) {
         *K_out = (int64_t)carry;
         if ((int64_t)carry > capacity) set_status(a.status, SPLAT_ERR_CAPACITY, SPLAT_STAGE_DUPLICATE, (int64_t)carry);
+        // the capacity the call needed: the super-tile lists share the buffers' size
+        if (needed) *needed = K_super ? max((int64_t)carry, *K_super) : (int64_t)carry;
     }
 }
 
@@ -901,16 +906,55 @@ struct TileArgs {
     uint32_t* vals_out;
     uint32_t* keys_out;               // may be null
     int cull;                         // drop tiles the opacity footprint cannot reach
-    uint32_t* seg_base;               // [total_super + 1] first segment of each super-tile's list
+    int W[SPLAT_MAX_VIEWS], H[SPLAT_MAX_VIEWS];
+    uint32_t* n_head;                 // [total_super] rows of each list the head pass went through
+    uint2* sat_head;                  // [total_super] tiles (bit 8 r + c) whose lists ended in the head
+    uint32_t* seg_base;               // [total_super + 1] first tail segment of each super-tile
     uint32_t* seg_cnt;                // [segments][64] per-segment tile counts, then offsets
     uint2* mask;                      // per super-tile list entry: byte w = its tile columns in tile row w
-    uint32_t* ticket;                 // [2] segment tickets of the write and count passes (zeroed)
+    uint32_t* ticket;                 // [4] tickets of the tail write / count and head write / count passes (zeroed)
     int32_t* status;
 };
 
-constexpr int kFilterSeg = 1024;  // list entries per filter segment (one CTA)
+// Tile saturation.  Every pixel of a tile stops its walk before the first
+// entry that would take its transmittance T below 1e-4 (Alg. 1), so the
+// entries of a tile list that come after the point where T is certainly below
+// that bound at every pixel of the tile are never read.  For each (entry,
+// tile) the count pass takes a lower bound of the alpha the compositing
+// kernels compute at every pixel of the tile (clipped to the image):
+// alpha_max exp(-q/2) with q the largest value of the conic's quadratic form
+// over the tile's corners (the form is convex), q enlarged to cover FP32
+// rounding, provided the bound passes the 1/255 skip with a margin and the
+// conic is far enough from singular that the kernels' evaluation of the power
+// cannot round to the wrong side of 0.  It sums -ln(1 - alpha) per (segment,
+// tile) in fixed point (rounded down); the prefix over the segments ends the
+// tile's list after the segment that takes the sum past -ln(1e-4) with a
+// margin for the rounding of the T products.  The sums are exact integers, so
+// the cut does not depend on the order of any reduction.
+constexpr float kSatScale = 65536.f;                       // fixed point of -ln(1 - alpha)
+constexpr uint32_t kSatThreshold = (uint32_t)(9.25 * 65536);  // -ln(1e-4) = 9.2103 plus the margin
 
-// one block: segments per super-tile list, exclusive scan -> seg_base
+__device__ __forceinline__ uint32_t sat_weight(const float4& co, float px, float py, float xlo, float xhi,
+                                               float ylo, float yhi)
+{
+    const float a = co.x, b = co.y, c = co.z;
+    const float dx0 = px - xlo, dx1 = px - xhi, dy0 = py - ylo, dy1 = py - yhi;
+    auto q = [&](float dx, float dy) { return fmaf(dx, fmaf(a, dx, 2.f * b * dy), c * dy * dy); };
+    const float qmax = fmaxf(fmaxf(q(dx0, dy0), q(dx0, dy1)), fmaxf(q(dx1, dy0), q(dx1, dy1)));
+    const float mx = fmaxf(fabsf(dx0), fabsf(dx1)), my = fmaxf(fabsf(dy0), fabsf(dy1));
+    const float qabs = fmaf(mx, fmaf(a, mx, 2.f * fabsf(b) * my), c * my * my);
+    const float qhi = fmaf(1e-5f, qabs, qmax) + 1e-6f;
+    const float alpha = fminf(co.w * __expf(-0.5f * qhi) * (1.f - 1e-5f), 0.98999f);
+    if (!(alpha >= kAlphaMin * 1.002f)) return 0u;
+    const float nl = -__log2f(1.f - alpha) * 0.69314718f;  // -ln(1 - alpha)
+    const float w = fmaf(nl, 1.f - 1e-4f, -2e-5f);
+    return w > 0.f ? (uint32_t)(w * kSatScale) : 0u;
+}
+
+constexpr int kFilterSeg = 1024;  // list entries per tail segment (one CTA)
+constexpr int kHeadChunks = 4;    // 256-row chunks of each list the head pass takes in order
+
+// one block: tail segments per super-tile list, exclusive scan -> seg_base
 __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
 {
     __shared__ uint32_t s_tmp[8];
@@ -919,9 +963,10 @@ __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
     for (int base = 0; base < a.total_super; base += 256) {
         const int gs = base + threadIdx.x;
         uint32_t c = 0;
-        if (gs < a.total_super) {
-            const uint2 rg = a.sranges[gs];
-            c = (rg.y - rg.x + kFilterSeg - 1) / kFilterSeg;
+        if (gs < a.total_super) {  // the tail: what the head pass left, unless every list ended in it
+            const uint2 rg = a.sranges[gs], sat = a.sat_head[gs];
+            const uint32_t rest = (sat.x & sat.y) == 0xffffffffu ? 0u : rg.y - rg.x - a.n_head[gs];
+            c = (rest + kFilterSeg - 1) / kFilterSeg;
         }
         uint32_t tot;
         const uint32_t ex = block_excl_scan256(c, s_tmp, &tot);
@@ -932,7 +977,7 @@ __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
 }
 
 // thread per (super-tile, tile of its 8x8 block): exclusive sum of the tile's
-// counts over the super-tile's segments; the tile's total
+// counts over the head and the super-tile's tail segments; the tile's total
 __global__ void __launch_bounds__(256) k_seg_prefix(TileArgs a)
 {
     if (status_failed(a.status)) return;
@@ -945,14 +990,16 @@ __global__ void __launch_bounds__(256) k_seg_prefix(TileArgs a)
     const int ls = gs - a.super_base[v];
     const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
     const int ty = sy * 8 + (lt >> 3), tx = sx * 8 + (lt & 7);
-    uint32_t run = 0;
+    if (ty >= a.TY[v] || tx >= a.TX[v]) return;
+    uint32_t* total = a.tile_total + a.tile_base[v] + ty * a.TX[v] + tx;
+    uint32_t run = *total;  // the head's count: the tail segments follow it
     for (uint32_t g = a.seg_base[gs]; g < a.seg_base[gs + 1]; ++g) {
         uint32_t* p = a.seg_cnt + (size_t)g * 64 + lt;
         const uint32_t c = *p;
         *p = run;
         run += c;
     }
-    if (ty < a.TY[v] && tx < a.TX[v]) a.tile_total[a.tile_base[v] + ty * a.TX[v] + tx] = run;
+    *total = run;
 }
 
 // Opacity footprint of one projected Gaussian: the ellipse {power >= pcut},
@@ -1023,15 +1070,237 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
     return true;
 }
 
-// One CTA per segment (kFilterSeg entries) of a super-tile's row list (8x8
-// tiles): it streams the rows in depth order through shared memory; warp w
-// serves tile row w (8 tiles).
+// Head pass: one CTA per super-tile (8x8 tiles), taken from a ticket counter:
+// it streams the first kHeadChunks x 256 rows of the super-tile's row list in
+// depth order through shared memory, 256 rows at a time; warp w serves tile
+// row w (8 tiles).
 // COUNT: warp w keeps a row for the tiles of its rectangle in tile row w that
 // its opacity footprint reaches (the footprint enlarged by a margin that covers
 // FP32 rounding, so no pixel result changes), records them as byte w of the
-// entry's coverage word (bit k: tile column k of the super-tile) and counts
-// per (segment, tile).  Write pass: each tile's list is written contiguously,
-// in order, from the segment's offsets, driven by the coverage words alone.
+// entry's coverage word (bit k: tile column k of the super-tile), counts per
+// tile and, with culling on, ends each tile's list once the tile saturates;
+// the CTA stops when all its tiles have.  The tail pass takes the rest of the
+// lists of the tiles that did not saturate.  Write pass: each tile's list
+// starts at the tile's range start, driven by the coverage words of the rows
+// the count pass went through.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_tile_head(TileArgs a)
+{
+    // COUNT: rectangle relative to the super-tile, clamped to [0, 8], one byte
+    // per bound (x0, y0, x1, y1); footprint constants; conic and alpha_max
+    // (0 when the row does not enter the saturation bound)
+    __shared__ uint32_t s_rect[COUNT ? 256 : 1];
+    __shared__ float4 s_g0[COUNT ? 256 : 1], s_g1[COUNT ? 256 : 1], s_co[COUNT ? 256 : 1];
+    __shared__ uint32_t s_row[COUNT ? 1 : 256];
+    __shared__ uint2 s_mask[256];
+    __shared__ unsigned char s_queue[8][256];  // per tile row: entries of the chunk it has work for
+    // COUNT: coverage byte -> four words of two 16-bit column counters (columns 2q, 2q + 1),
+    // so that four warp reductions count all eight columns of 32 entries
+    __shared__ uint4 s_spread[COUNT ? 256 : 1];
+    __shared__ uint32_t s_gs;
+    __shared__ uint32_t s_sat[8];
+    if (status_failed(a.status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    if (COUNT) {
+        const unsigned b = threadIdx.x;
+        s_spread[b] = make_uint4((b & 1u) | ((b >> 1 & 1u) << 16), (b >> 2 & 1u) | ((b >> 3 & 1u) << 16),
+                                 (b >> 4 & 1u) | ((b >> 5 & 1u) << 16), (b >> 6 & 1u) | ((b >> 7 & 1u) << 16));
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_gs = atomicAdd(a.ticket + (COUNT ? 3 : 2), 1u);
+        __syncthreads();
+        const uint32_t gs = s_gs;
+        if (gs >= (uint32_t)a.total_super) break;
+        int v = 0;
+        for (int w = 1; w < a.V; ++w)
+            if ((int)gs >= a.super_base[w]) v = w;
+        const int ls = (int)gs - a.super_base[v];
+        const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
+        const int TX = a.TX[v], TY = a.TY[v];
+        const int ty = sy * 8 + warp;
+        const int tx0 = sx * 8;
+        const float vlo = (float)(ty * kTile), vhi = vlo + (float)(kTile - 1);
+        const float vhi_img = fminf(vhi, (float)(a.H[v] - 1)), xmax_img = (float)(a.W[v] - 1);
+        const uint2 rgs = a.sranges[gs];
+        // COUNT: sat = columns whose list has ended (warp-uniform; columns and
+        // rows outside the grid from the start); lane k < 8 holds tile k's
+        // count and saturation sum
+        uint32_t sat = 0u, cnt = 0u, wsum = 0u;
+        uint32_t cur[8];  // write pass: next slot of each tile's list
+        uint32_t end = min(rgs.y, rgs.x + (uint32_t)(kHeadChunks * 256));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool ok = ty < TY && tx0 + k < TX;
+            if (!ok) sat |= 1u << k;
+            cur[k] = (!COUNT && ok) ? a.ranges[a.tile_base[v] + ty * TX + tx0 + k].x : 0u;
+        }
+        if (!COUNT) end = rgs.x + a.n_head[gs];
+        uint32_t b = rgs.x;
+        for (; b < end; b += 256) {
+            __syncthreads();
+            const uint32_t j = b + threadIdx.x;
+            if (j < end) {
+                const uint32_t row = a.list[j];
+                if (COUNT) {
+                    const int4 rc = ((const int4*)a.proj.rect)[row];
+                    auto rel = [](int c, int o) { return (uint32_t)min(max(c - o, 0), 8); };
+                    s_rect[threadIdx.x] = rel(rc.x, tx0) | rel(rc.y, sy * 8) << 8 | rel(rc.z, tx0) << 16 |
+                                          rel(rc.w, sy * 8) << 24;
+                    s_mask[threadIdx.x] = make_uint2(0u, 0u);
+                    if (a.cull) {
+                        const float2 xy = ((const float2*)a.proj.xy)[row];
+                        const float4 co = ((const float4*)a.proj.conic_opacity)[row];
+                        // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
+                        const float R2 = -2.f * __logf(__fdividef(kAlphaMin, co.w)) * 1.0001f + 2e-3f;
+                        float4 g0, g1;
+                        ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1);
+                        s_g0[threadIdx.x] = g0;
+                        s_g1[threadIdx.x] = g1;
+                        // the saturation bound needs a*c - b^2 >= 1e-3 a c: the
+                        // relative rounding of the power stays far below its size
+                        const bool ok = co.x > 0.f && co.z > 0.f && co.x * co.z - co.y * co.y >= 1e-3f * co.x * co.z &&
+                                        co.w <= 1.f;
+                        s_co[threadIdx.x] = make_float4(co.x, co.y, co.z, ok ? co.w : 0.f);
+                    }
+                } else {
+                    s_row[threadIdx.x] = row;
+                    s_mask[threadIdx.x] = a.mask[j];
+                }
+            }
+            __syncthreads();
+            if (!COUNT || sat != 0xffu) {
+                const int n = (int)min(256u, end - b);
+                // the entries this tile row has work for (COUNT: rectangle covers the
+                // row; write pass: listed in some tile of the row), queued in order
+                // so that the work below runs on full warps
+                int nq = 0;
+                if (ty < TY) {
+                    for (int sb = 0; sb < n; sb += 32) {
+                        const int e = sb + lane;
+                        bool take = false;
+                        if (e < n) {
+                            if (COUNT) {
+                                const uint32_t rc = s_rect[e];
+                                take = (int)(rc >> 8 & 0xffu) <= warp && warp < (int)(rc >> 24);
+                            } else {
+                                take = ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) &
+                                        0xffu) != 0u;
+                            }
+                        }
+                        const unsigned bal = __ballot_sync(0xffffffffu, take);
+                        if (take) s_queue[warp][nq + __popc(bal & lt)] = (unsigned char)e;
+                        nq += __popc(bal);
+                    }
+                }
+                __syncwarp();
+                uint32_t packed[4] = {0u, 0u, 0u, 0u};  // COUNT: column counters of this chunk, two per word
+                for (int sb = 0; sb < nq; sb += 32) {
+                    if (COUNT && sat == 0xffu) break;  // warp-uniform: the row's lists have all ended
+                    const int qi = sb + lane;
+                    const int e = qi < nq ? s_queue[warp][qi] : 0;
+                    unsigned m = 0;  // tile columns of this tile row the entry is listed in
+                    if (qi < nq) {
+                        if (COUNT) {
+                            const uint32_t rc = s_rect[e];
+                            int lo = (int)(rc & 0xffu), hi = (int)(rc >> 16 & 0xffu);  // columns of the super-tile
+                            if (a.cull) {
+                                float ul, ur;
+                                if (!ellipse_band_extent(s_g0[e], s_g1[e], vlo, vhi, ul, ur)) {
+                                    hi = lo;
+                                } else {
+                                    // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
+                                    const float fl = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
+                                    const float fh = floorf(ur * (1.f / kTile));
+                                    lo = max(lo, (int)fminf(fmaxf(fl, -1.f), 1.0e6f) - tx0);
+                                    hi = min(hi, (int)fminf(fmaxf(fh, -2.f), 1.0e6f) + 1 - tx0);
+                                }
+                            }
+                            if (hi > lo) m = ((1u << hi) - (1u << lo)) & ~sat;
+                            reinterpret_cast<unsigned char*>(&s_mask[e])[warp] = (unsigned char)m;
+                        } else {
+                            m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu;
+                        }
+                    }
+                    if (COUNT) {
+                        const uint4 w = s_spread[m];
+                        packed[0] += __reduce_add_sync(0xffffffffu, w.x);
+                        packed[1] += __reduce_add_sync(0xffffffffu, w.y);
+                        packed[2] += __reduce_add_sync(0xffffffffu, w.z);
+                        packed[3] += __reduce_add_sync(0xffffffffu, w.w);
+                        if (a.cull) {
+                            // saturation sums of this batch, column by column
+                            unsigned cols = __reduce_or_sync(0xffffffffu, m);
+                            const float4 co = s_co[e];
+                            const float px = s_g0[e].x, py = s_g0[e].y;
+                            while (cols) {
+                                const int k = __ffs(cols) - 1;
+                                cols &= cols - 1;
+                                uint32_t wt = 0u;
+                                if (((m >> k) & 1u) && co.w > 0.f) {
+                                    const float xlo = (float)((tx0 + k) * kTile);
+                                    wt = sat_weight(co, px, py, xlo, fminf(xlo + (float)(kTile - 1), xmax_img), vlo,
+                                                    vhi_img);
+                                }
+                                const uint32_t r = __reduce_add_sync(0xffffffffu, wt);
+                                if (lane == k) wsum += r;
+                            }
+                            sat |= __ballot_sync(0xffffffffu, lane < 8 && wsum >= kSatThreshold) & 0xffu;
+                        }
+                    } else {
+                        const uint32_t row = s_row[e];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const bool cov = (m >> k) & 1u;
+                            const unsigned bal = __ballot_sync(0xffffffffu, cov);
+                            if (cov) {
+                                const uint32_t pos = cur[k] + __popc(bal & lt);
+                                a.vals_out[pos] = row;
+                                if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
+                            }
+                            cur[k] += __popc(bal);
+                        }
+                    }
+                }
+                if (COUNT) {  // at most 256 rows per chunk: the 16-bit counters do not overflow
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (lane == k) cnt += (packed[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                }
+            }
+            if (COUNT) {
+                __syncthreads();
+                if (j < end) a.mask[j] = s_mask[threadIdx.x];
+                if (__syncthreads_and(sat == 0xffu)) {  // every list of the super-tile has ended
+                    b += 256;
+                    break;
+                }
+            }
+        }
+        if (COUNT) {
+            if (lane == 0) s_sat[warp] = sat;
+            if (lane < 8 && ty < TY && tx0 + lane < TX) a.tile_total[a.tile_base[v] + ty * TX + tx0 + lane] = cnt;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                a.n_head[gs] = min(b, end) - rgs.x;
+                a.sat_head[gs] = make_uint2(s_sat[0] | s_sat[1] << 8 | s_sat[2] << 16 | s_sat[3] << 24,
+                                            s_sat[4] | s_sat[5] << 8 | s_sat[6] << 16 | s_sat[7] << 24);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Tail pass: one CTA per segment (kFilterSeg entries) of what the head pass
+// left of a super-tile's row list (8x8 tiles): it streams the rows in depth
+// order through shared memory; warp w serves tile row w (8 tiles).
+// COUNT: warp w keeps a row for the tiles of its rectangle in tile row w that
+// its opacity footprint reaches (the footprint enlarged by a margin that covers
+// FP32 rounding, so no pixel result changes) and whose list did not end in the
+// head, records them as byte w of the entry's coverage word (bit k: tile column
+// k of the super-tile) and counts per (segment, tile).  Write pass: each tile's
+// list continues contiguously, in order, from the segment's offsets, driven by
+// the coverage words alone.
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
 {
@@ -1087,6 +1356,9 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
         const float vlo = (float)(ty * kTile), vhi = vlo + (float)(kTile - 1);
         uint32_t cur[8];
         uint32_t packed[4] = {0u, 0u, 0u, 0u};  // COUNT: column counters, two per word
+        // columns whose lists ended in the head (none are added to them here)
+        const uint2 sat = a.sat_head[gs];
+        const uint32_t done = ((warp < 4 ? sat.x >> (8 * warp) : sat.y >> (8 * (warp - 4))) & 0xffu);
         const uint32_t* off = a.seg_cnt + (size_t)g * 64 + warp * 8;  // (after k_seg_prefix) segment offsets
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -1094,7 +1366,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
             cur[k] = (!COUNT && ok) ? a.tile_total[a.tile_base[v] + ty * TX + tx0 + k] + off[k] : 0u;
         }
         const uint2 rgs = a.sranges[gs];
-        const uint32_t sb0 = rgs.x + (g - a.seg_base[gs]) * kFilterSeg;
+        const uint32_t sb0 = rgs.x + a.n_head[gs] + (g - a.seg_base[gs]) * kFilterSeg;
         const uint2 rg = make_uint2(sb0, min(sb0 + kFilterSeg, rgs.y));
         for (uint32_t b = rg.x; b < rg.y; b += 256) {
             __syncthreads();
@@ -1137,7 +1409,8 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                             const uint32_t rc = s_rect[e];
                             take = (int)(rc >> 8 & 0xffu) <= warp && warp < (int)(rc >> 24);
                         } else {
-                            take = ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu) != 0u;
+                            take = ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu &
+                                    ~done) != 0u;
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, take);
@@ -1165,10 +1438,10 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                                     hi = min(hi, (int)fminf(fmaxf(fh, -2.f), 1.0e6f) + 1 - tx0);
                                 }
                             }
-                            if (hi > lo) m = (1u << hi) - (1u << lo);
+                            if (hi > lo) m = ((1u << hi) - (1u << lo)) & ~done;
                             reinterpret_cast<unsigned char*>(&s_mask[e])[warp] = (unsigned char)m;
                         } else {
-                            m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu;
+                            m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu & ~done;
                         }
                     }
                     if (COUNT) {
@@ -1345,7 +1618,8 @@ struct SortLayout {
     int64_t total_tiles, total_super;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
         off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
-    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_mask, off_tord;
+    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_nhead, off_sathead, off_mask,
+        off_tord;
     int64_t max_segs;
     size_t bytes;
 };
@@ -1408,6 +1682,8 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.max_segs = L.binned ? (capacity + kFilterSeg - 1) / kFilterSeg + L.total_super : 1;
     L.off_segbase = take(4 * (size_t)(L.total_super + 1));
     L.off_segcnt = take(L.binned ? 4 * 64 * (size_t)L.max_segs : 4);
+    L.off_nhead = take(4 * (size_t)std::max<int64_t>(L.total_super, 1));
+    L.off_sathead = take(8 * (size_t)std::max<int64_t>(L.total_super, 1));
     L.off_mask = take(L.binned ? 8 * (size_t)capacity : 4);
     L.off_tord = take(66 * 4);  // tile-order class counts and cursors
     L.bytes = o;
@@ -1462,6 +1738,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     if ((err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)vb.total_tiles, s)) != cudaSuccess)
         return err;
     if ((err = cudaMemsetAsync(bins.n_instances, 0, sizeof(int64_t), s)) != cudaSuccess) return err;
+    if (bins.n_needed && (err = cudaMemsetAsync(bins.n_needed, 0, sizeof(int64_t), s)) != cudaSuccess) return err;
     if (n_rows == 0) return cudaSuccess;
     uint32_t* hist = U(L.off_hist);
     uint32_t* tickets = U(L.off_tickets);
@@ -1516,7 +1793,8 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.lb = (unsigned long long*)(w + L.off_scan_lb);
         a.ticket = tickets + 4;
         a.n_instances = L.binned ? (int64_t*)(w + L.off_ninst1) : bins.n_instances;
-        // binned: the super-tile list (K1 <= K entries) lives in a capacity-sized
+        a.n_needed = L.binned ? nullptr : bins.n_needed;
+        // binned: the super-tile list (K1 entries) lives in a capacity-sized
         // buffer, so K1 is checked here, before anything is written; K itself is
         // checked by the tile ranges once the lists are counted
         a.capacity = bins.capacity;
@@ -1539,6 +1817,8 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
             t.tile_base[v] = vb.v[v].tile_base;
             t.TX[v] = vb.v[v].TX;
             t.TY[v] = vb.v[v].TY;
+            t.W[v] = vb.v[v].W;
+            t.H[v] = vb.v[v].H;
             t.super_base[v] = sb;
             t.STX[v] = (vb.v[v].TX + 7) >> kSuperShift;
             sb += t.STX[v] * ((vb.v[v].TY + 7) >> kSuperShift);
@@ -1556,6 +1836,8 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.cull = g_tile_cull;
         t.seg_base = U(L.off_segbase);
         t.seg_cnt = U(L.off_segcnt);
+        t.n_head = U(L.off_nhead);
+        t.sat_head = (uint2*)(w + L.off_sathead);
         t.mask = (uint2*)(w + L.off_mask);
         t.ticket = tickets + 10;
         BinArgs tr{};
@@ -1620,16 +1902,23 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_bin_ranges<<<1, 256, 0, s>>>(a, nullptr, 0);
         k_bin_prefix<1><<<(sb + 31) / 32, 32 * kPrefixSegs, 0, s>>>(a);
         k_bin_scatter<<<blocks_s, 32, smem_scatter, s>>>(a);
-        // tile level: segment the super-tile lists, count each (segment, tile),
-        // prefix over segments, ranges + K + capacity check, then write the lists
-        // one wave of resident CTAs, which take the segments from a ticket counter
+        // tile level: the head of each super-tile list in order (each tile's list
+        // up to its saturation), the tail in parallel segments, the prefix over
+        // head and segments, ranges + K + capacity check, then the lists are
+        // written; one wave of resident CTAs per pass, which take super-tiles or
+        // segments from ticket counters
         static const int per_sm_f[2] = {ctas_per_sm(k_tile_filter<false>, 256), ctas_per_sm(k_tile_filter<true>, 256)};
+        static const int per_sm_h[2] = {ctas_per_sm(k_tile_head<false>, 256), ctas_per_sm(k_tile_head<true>, 256)};
         auto blocks_f = [&](int c) { return (int)std::min<int64_t>(L.max_segs, (int64_t)ctx.num_sms * per_sm_f[c]); };
-        count_launch(5);
+        auto blocks_h = [&](int c) { return (int)std::min<int64_t>(sb, (int64_t)ctx.num_sms * per_sm_h[c]); };
+        count_launch(7);
+        k_tile_head<true><<<blocks_h(1), 256, 0, s>>>(t);
         k_seg_plan<<<1, 256, 0, s>>>(t);
         k_tile_filter<true><<<blocks_f(1), 256, 0, s>>>(t);
         k_seg_prefix<<<(int)(((int64_t)sb * 64 + 255) / 256), 256, 0, s>>>(t);
-        k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity);
+        k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity, (const int64_t*)(w + L.off_ninst1),
+                                       bins.n_needed);
+        k_tile_head<false><<<blocks_h(0), 256, 0, s>>>(t);
         k_tile_filter<false><<<blocks_f(0), 256, 0, s>>>(t);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);

@@ -161,6 +161,7 @@ class Rasterizer:
         self.cimg = abi.splat_image(self.rgb.data_ptr(), self.final_T.data_ptr(), self.last.data_ptr())
         self.status = torch.zeros((4,), dtype=i32, device=d)
         self.n_instances = torch.zeros((1,), dtype=torch.int64, device=d)
+        self.n_needed = torch.zeros((1,), dtype=torch.int64, device=d)  # capacity the last sort needed
         self.ranges = torch.zeros((max(1, self.total_tiles) * 2,), dtype=i32, device=d)
         # tiles longest list first, for the compositing kernels' scheduling
         self.tile_order = torch.arange(max(1, self.total_tiles), dtype=i32, device=d)
@@ -204,7 +205,8 @@ class Rasterizer:
         self.keys = torch.empty((capacity if self.keep_keys else 0,), dtype=torch.int32, device=self.device)
         self.vals = torch.empty((capacity,), dtype=torch.int32, device=self.device)
         self.cbins = abi.splat_bins(capacity, self.keys.data_ptr() if self.keep_keys else None, self.vals.data_ptr(),
-                                    self.ranges.data_ptr(), self.n_instances.data_ptr(), self.tile_order.data_ptr())
+                                    self.ranges.data_ptr(), self.n_instances.data_ptr(), self.tile_order.data_ptr(),
+                                    self.n_needed.data_ptr())
         ws = abi.splat_workspace_size(abi.SPLAT_OP_ALL, self.n3, self.n4, self.W, self.H, capacity)
         if ws == 0:
             raise ValueError("invalid sizes for the workspace")
@@ -331,7 +333,8 @@ class Rasterizer:
             if code != abi.SPLAT_OK:
                 raise SplatError(code, "autotune_capacity", stage, aux)
             K = self.instances()
-            want = int(math.ceil(K * self.headroom)) + 1024
+            # the super-tile lists of the binned sort share the capacity
+            want = int(math.ceil(max(K, int(self.n_needed.item())) * self.headroom)) + 1024
             if want < self.capacity // 2 or want > self.capacity:
                 self.set_capacity(want)
             return K

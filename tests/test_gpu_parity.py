@@ -262,6 +262,50 @@ def test_footprint_culling_changes_nothing_but_the_lists(small):
         assert rel_l2(g1[k].cpu().numpy(), g0[k].cpu().numpy()) < 1e-5, k
 
 
+def test_saturation_cut_changes_nothing_but_the_lists():
+    """The 300k-Gaussian video view, dense enough that every tile saturates
+    early: with culling on, each tile's list ends once the alpha lower bounds
+    certify T < 1e-4 at every pixel of the tile, so the lists shrink to a
+    fraction of the footprint lists, while the images, the transmittance and the
+    gradients are those of the full rectangle lists (the walks end before the
+    cut)."""
+    scene, views = scenes.video_scene()
+    G = raster.Gaussians.from_scene(scene, "cuda")
+    target = torch.rand((3 * views[0].W * views[0].H,), generator=torch.Generator(device="cuda").manual_seed(4),
+                        device="cuda")
+    out = []
+    for on in (False, True):
+        with tile_cull(on):
+            R = raster.Rasterizer(G.n3, G.n4, views, keep_keys=False)
+            R.autotune_capacity(G)
+            R.step(G, target)
+            torch.cuda.synchronize()
+            R.check()
+            K = R.instances()
+            need = int(R.n_needed.item())
+            # every tile list ends at or after its last read entry
+            lens = (R.ranges.view(-1, 2)[:, 1] - R.ranges.view(-1, 2)[:, 0]).cpu().numpy()
+            tiles_last = R.last.view(views[0].H, views[0].W).cpu().numpy()
+            out.append((K, need, lens, tiles_last, R.rgb.clone(), R.final_T.clone(),
+                        {k: v.clone() for k, v in R.grads.items()}))
+            del R
+    (k0, n0, len0, last0, rgb0, T0, g0), (k1, n1, len1, last1, rgb1, T1, g1) = out
+    assert k1 < 0.2 * k0, (k0, k1)
+    assert n1 >= k1 and n0 == k0
+    assert torch.equal(rgb0, rgb1) and torch.equal(T0, T1)
+    for k in g0:
+        assert rel_l2(g1[k].cpu().numpy(), g0[k].cpu().numpy()) < 1e-5, k
+    # no walk reaches the end of a cut list: last < list length at every pixel of a cut tile
+    H, W = last1.shape
+    TX = (W + 15) // 16
+    for (ty, tx) in [(0, 0), (10, 20), (31, 42), ((H - 1) // 16, TX - 1)]:
+        t = ty * TX + tx
+        blk = last1[16 * ty: 16 * ty + 16, 16 * tx: 16 * tx + 16]
+        assert len1[t] <= len0[t]
+        if len1[t] < len0[t]:
+            assert blk.max() < len1[t], (ty, tx)
+
+
 @pytest.mark.parametrize("ppl", [(2, 2), (4, 4), (2, 8), (8, 4)])
 def test_composite_pixels_per_lane_variants(small, ppl):
     """Every compositing variant (2, 4 or 8 pixels per lane, a warp per band of
