@@ -934,17 +934,42 @@ struct TileArgs {
 constexpr float kSatScale = 65536.f;                       // fixed point of -ln(1 - alpha)
 constexpr uint32_t kSatThreshold = (uint32_t)(9.25 * 65536);  // -ln(1e-4) = 9.2103 plus the margin
 
-__device__ __forceinline__ uint32_t sat_weight(const float4& co, float px, float py, float xlo, float xhi,
-                                               float ylo, float yhi)
+// Terms of an entry's quadratic form that depend only on the tile row's pixel
+// rows [ylo, yhi] (shared by the tiles of the row).
+struct SatRow {
+    float a, B0, B1, C0, C1, Bm, Cm, px, amax;
+};
+
+__device__ __forceinline__ SatRow sat_row(const float4& co, float px, float py, float ylo, float yhi)
 {
-    const float a = co.x, b = co.y, c = co.z;
-    const float dx0 = px - xlo, dx1 = px - xhi, dy0 = py - ylo, dy1 = py - yhi;
-    auto q = [&](float dx, float dy) { return fmaf(dx, fmaf(a, dx, 2.f * b * dy), c * dy * dy); };
-    const float qmax = fmaxf(fmaxf(q(dx0, dy0), q(dx0, dy1)), fmaxf(q(dx1, dy0), q(dx1, dy1)));
-    const float mx = fmaxf(fabsf(dx0), fabsf(dx1)), my = fmaxf(fabsf(dy0), fabsf(dy1));
-    const float qabs = fmaf(mx, fmaf(a, mx, 2.f * fabsf(b) * my), c * my * my);
+    const float b2 = 2.f * co.y, dy0 = py - ylo, dy1 = py - yhi, my = fmaxf(fabsf(dy0), fabsf(dy1));
+    SatRow r;
+    r.a = co.x;
+    r.B0 = b2 * dy0;
+    r.B1 = b2 * dy1;
+    r.C0 = co.z * dy0 * dy0;
+    r.C1 = co.z * dy1 * dy1;
+    r.Bm = fabsf(b2) * my;
+    r.Cm = co.z * my * my;
+    r.px = px;
+    r.amax = co.w;
+    return r;
+}
+
+// Saturation weight of one (entry, tile): -ln(1 - alpha_lb) in fixed point,
+// rounded down, for the tile's pixel columns [xlo, xhi]; 0 when the bound does
+// not pass the 1/255 skip with a margin.
+__device__ __forceinline__ uint32_t sat_weight(const SatRow& r, float xlo, float xhi)
+{
+    const float dx0 = r.px - xlo, dx1 = r.px - xhi;
+    // q = a dx^2 + 2 b dx dy + c dy^2 at the four corners
+    const float q00 = fmaf(dx0, fmaf(r.a, dx0, r.B0), r.C0), q01 = fmaf(dx0, fmaf(r.a, dx0, r.B1), r.C1);
+    const float q10 = fmaf(dx1, fmaf(r.a, dx1, r.B0), r.C0), q11 = fmaf(dx1, fmaf(r.a, dx1, r.B1), r.C1);
+    const float qmax = fmaxf(fmaxf(q00, q01), fmaxf(q10, q11));
+    const float mx = fmaxf(fabsf(dx0), fabsf(dx1));
+    const float qabs = fmaf(mx, fmaf(r.a, mx, r.Bm), r.Cm);  // bounds |a dx^2| + |2 b dx dy| + |c dy^2|
     const float qhi = fmaf(1e-5f, qabs, qmax) + 1e-6f;
-    const float alpha = fminf(co.w * __expf(-0.5f * qhi) * (1.f - 1e-5f), 0.98999f);
+    const float alpha = fminf(r.amax * __expf(-0.5f * qhi) * (1.f - 1e-5f), 0.98999f);
     if (!(alpha >= kAlphaMin * 1.002f)) return 0u;
     const float nl = -__log2f(1.f - alpha) * 0.69314718f;  // -ln(1 - alpha)
     const float w = fmaf(nl, 1.f - 1e-4f, -2e-5f);
@@ -952,7 +977,7 @@ __device__ __forceinline__ uint32_t sat_weight(const float4& co, float px, float
 }
 
 constexpr int kFilterSeg = 1024;  // list entries per tail segment (one CTA)
-constexpr int kHeadChunks = 4;    // 256-row chunks of each list the head pass takes in order
+constexpr int kHeadChunks = 2;    // 256-row chunks of each list the head pass takes in order
 
 // one block: tail segments per super-tile list, exclusive scan -> seg_base
 __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
@@ -1230,22 +1255,23 @@ __global__ void __launch_bounds__(256) k_tile_head(TileArgs a)
                         packed[3] += __reduce_add_sync(0xffffffffu, w.w);
                         if (a.cull) {
                             // saturation sums of this batch, column by column
-                            unsigned cols = __reduce_or_sync(0xffffffffu, m);
                             const float4 co = s_co[e];
-                            const float px = s_g0[e].x, py = s_g0[e].y;
-                            while (cols) {
-                                const int k = __ffs(cols) - 1;
-                                cols &= cols - 1;
-                                uint32_t wt = 0u;
-                                if (((m >> k) & 1u) && co.w > 0.f) {
-                                    const float xlo = (float)((tx0 + k) * kTile);
-                                    wt = sat_weight(co, px, py, xlo, fminf(xlo + (float)(kTile - 1), xmax_img), vlo,
-                                                    vhi_img);
+                            unsigned cols = __reduce_or_sync(0xffffffffu, co.w > 0.f ? m : 0u);
+                            if (cols) {
+                                const SatRow sr = sat_row(co, s_g0[e].x, s_g0[e].y, vlo, vhi_img);
+                                while (cols) {
+                                    const int k = __ffs(cols) - 1;
+                                    cols &= cols - 1;
+                                    uint32_t wt = 0u;
+                                    if (((m >> k) & 1u) && co.w > 0.f) {
+                                        const float xlo = (float)((tx0 + k) * kTile);
+                                        wt = sat_weight(sr, xlo, fminf(xlo + (float)(kTile - 1), xmax_img));
+                                    }
+                                    const uint32_t r = __reduce_add_sync(0xffffffffu, wt);
+                                    if (lane == k) wsum += r;
                                 }
-                                const uint32_t r = __reduce_add_sync(0xffffffffu, wt);
-                                if (lane == k) wsum += r;
+                                sat |= __ballot_sync(0xffffffffu, lane < 8 && wsum >= kSatThreshold) & 0xffu;
                             }
-                            sat |= __ballot_sync(0xffffffffu, lane < 8 && wsum >= kSatThreshold) & 0xffu;
                         }
                     } else {
                         const uint32_t row = s_row[e];
