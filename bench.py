@@ -158,9 +158,11 @@ def param_bytes(n3, n4, elem):
     return elem * (n3 * (3 + 3 + 4 + 1 + 48) + n4 * (4 + 4 + 4 + 4 + 1 + 48))
 
 
-def algorithmic_bytes(stage, n3, n4, V, pix, K, elem):
+def algorithmic_bytes(stage, n3, n4, V, pix, K, elem, K_super=0):
     """Bytes each stage must move to/from HBM once (inputs read once, outputs
-    written once), per launch over the batch."""
+    written once), per launch over the batch.  K: entries of the per-tile lists
+    (after the footprint culling and the saturation cut); K_super: entries of
+    the binned sort's super-tile lists (0 on the radix path)."""
     N = n3 + n4
     rows = V * N
     proj_row = 8 + 16 + 16 + 16 + 4 + 4       # xy, conic/opacity, rgb/depth, rect, radius, n_tiles
@@ -175,6 +177,10 @@ def algorithmic_bytes(stage, n3, n4, V, pix, K, elem):
     if stage == "loss":
         return pix * 12 * 3
     if stage == "bin_sort":
+        if K_super:
+            # depth keys of the rows; the super-tile lists written once and read
+            # once with their coverage words; the per-tile lists written once
+            return rows * (4 + 4 + 16) + K_super * (4 + 8) * 2 + K * 4
         # depth keys of the rows, instances written once by the duplication and
         # read once by the (tile-digit) sort, sorted ids and tile keys written once
         return rows * (4 + 4 + 16) + K * 8 * 2
@@ -259,6 +265,7 @@ def run_ours(args, rank, local, world):
     target = torch.rand(R.rgb.shape, generator=gen, device=dev)
     tune = autotune.tune(R, G, target)
     K_inst = R.instances()
+    K_super = int(R.n_needed.item())  # binned sort: the larger of K and the super-tile list length
     copies = min(args.steps, 8)
     try:
         gs = raster.GraphedStep(R, G, target, copies=copies, with_marks=True)
@@ -424,7 +431,7 @@ def run_ours(args, rank, local, world):
             stage_roof[st] = {"bound": "alu", "achieved": round(a, 2), "unit": "TFLOP/s",
                               "frac": round(a / fp32_peak_all, 4)}
         else:
-            alg = algorithmic_bytes(st, G.n3, G.n4, V, pix, K_inst, 2)
+            alg = algorithmic_bytes(st, G.n3, G.n4, V, pix, K_inst, 2, K_super if K_super > K_inst else 0)
             a = alg / (ms / 1e3) / 1e9
             stage_roof[st] = {"bound": "hbm", "achieved": round(a, 1), "unit": "GB/s", "frac": round(a / hbm_peak, 4),
                               "algorithmic_bytes": int(alg)}
@@ -436,7 +443,7 @@ def run_ours(args, rank, local, world):
         "config": {"workload": "video scene 200k 3D + 100k 4D Gaussians, %d views/step at %dx%d, BF16 storage, "
                                "one CUDA graph per step" % (V, W, H),
                    "views_per_step": V, "gaussians": N3 + N4, "resolution": [W, H], "l2": "flushed before each step",
-                   "instances_K": K_inst, "autotune": {k: tune[k] for k in ("ppl_fwd", "ppl_bwd", "capacity")},
+                   "instances_K": K_inst, "capacity_needed": K_super, "autotune": {k: tune[k] for k in ("ppl_fwd", "ppl_bwd", "capacity")},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "mpixel_per_s": round(value * W * H / 1e6, 1),
         "plain_fp32": {"value": round(plain_value, 2), "unit": UNIT, "path": "per-view launches, FP32 storage, eager"},

@@ -15,6 +15,13 @@
 // ranking of the keys of a warp (digit-bit ballots or a match instruction)
 // with shared-memory counters, and a decoupled look-back across partitions
 // whose waits are bounded (SPLAT_ERR_TIMEOUT on expiry).
+//
+// The binned path (the default up to 40960 tiles per view) orders by tile
+// without tile-digit passes: the depth-ordered rows are partitioned stably by
+// 8x8-tile super-tile, then each super-tile's rows are filtered into its
+// tiles' lists in order.  With culling on, a list holds only the tiles the
+// opacity footprint reaches and ends where every pixel of the tile has
+// certainly saturated (tile saturation, below); neither changes a result.
 #include <algorithm>
 
 #include "splat_internal.cuh"
