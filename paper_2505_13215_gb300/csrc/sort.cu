@@ -1131,6 +1131,7 @@ __global__ void __launch_bounds__(256) k_tile_head(TileArgs a)
     __shared__ uint4 s_spread[COUNT ? 256 : 1];
     __shared__ uint32_t s_gs;
     __shared__ uint32_t s_sat[8];
+    __shared__ uint32_t s_w[COUNT ? 8 : 1][8][32];  // COUNT: per tile row, saturation weights [column][lane]
     if (status_failed(a.status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
@@ -1261,22 +1262,33 @@ __global__ void __launch_bounds__(256) k_tile_head(TileArgs a)
                         packed[2] += __reduce_add_sync(0xffffffffu, w.z);
                         packed[3] += __reduce_add_sync(0xffffffffu, w.w);
                         if (a.cull) {
-                            // saturation sums of this batch, column by column
+                            // saturation sums of this batch: each lane weighs its own
+                            // columns into shared memory, then one warp sum per column
                             const float4 co = s_co[e];
-                            unsigned cols = __reduce_or_sync(0xffffffffu, co.w > 0.f ? m : 0u);
+                            unsigned mine = co.w > 0.f ? m : 0u;
+                            const unsigned cols = __reduce_or_sync(0xffffffffu, mine);
                             if (cols) {
-                                const SatRow sr = sat_row(co, s_g0[e].x, s_g0[e].y, vlo, vhi_img);
-                                while (cols) {
-                                    const int k = __ffs(cols) - 1;
-                                    cols &= cols - 1;
-                                    uint32_t wt = 0u;
-                                    if (((m >> k) & 1u) && co.w > 0.f) {
+                                uint32_t* sw = &s_w[warp][0][lane];  // [column][lane]
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) sw[32 * k] = 0u;
+                                if (mine) {
+                                    const SatRow sr = sat_row(co, s_g0[e].x, s_g0[e].y, vlo, vhi_img);
+                                    do {
+                                        const int k = __ffs(mine) - 1;
+                                        mine &= mine - 1;
                                         const float xlo = (float)((tx0 + k) * kTile);
-                                        wt = sat_weight(sr, xlo, fminf(xlo + (float)(kTile - 1), xmax_img));
-                                    }
-                                    const uint32_t r = __reduce_add_sync(0xffffffffu, wt);
+                                        sw[32 * k] = sat_weight(sr, xlo, fminf(xlo + (float)(kTile - 1), xmax_img));
+                                    } while (mine);
+                                }
+                                __syncwarp();
+                                unsigned left = cols;
+                                while (left) {
+                                    const int k = __ffs(left) - 1;
+                                    left &= left - 1;
+                                    const uint32_t r = __reduce_add_sync(0xffffffffu, sw[32 * k]);
                                     if (lane == k) wsum += r;
                                 }
+                                __syncwarp();
                                 sat |= __ballot_sync(0xffffffffu, lane < 8 && wsum >= kSatThreshold) & 0xffu;
                             }
                         }

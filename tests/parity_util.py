@@ -177,3 +177,31 @@ def oracle_grads_views(scene, views, dLdC_per_view):
             for k in tot:
                 tot[k] = tot[k] + r[k]
     return tot
+
+
+EPS32 = 2.0 ** -24
+
+
+def split_mean_tol(mean, log_scale, noise, shrink):
+    """Per-element bound of the FP32 error of a densified Gaussian's mean.
+
+    A split child sits at mean + sum_c M_rc z_c with M = R diag(exp(s)) built
+    from the normalised quaternion(s) in FP32: each entry of M carries at most
+    about 15 roundings relative to exp(s_c) (|R_rc| <= 1), the dot product D
+    more and the final add one, so |error_r| <= (16 + D) eps sum_c exp(s_c)
+    |z_c| + eps |result_r|.  Bounded here by 32 eps (|result_r| + D max|z|
+    max_c exp(s_c)), with the parent's exp(s_c) = exp(child log-scale + shrink).
+    Kept and cloned rows are copies (error 0), below any bound."""
+    mean = np.asarray(mean, np.float64)
+    D = mean.shape[1]
+    zmax = float(np.max(np.abs(noise))) if np.size(noise) else 0.0
+    smax = np.exp(np.max(np.asarray(log_scale, np.float64), axis=1) + shrink)
+    return 32 * EPS32 * (np.abs(mean) + (D * zmax * smax)[:, None])
+
+
+def assert_split_means(got, want, want_log_scale, noise, shrink, name):
+    tol = split_mean_tol(want, want_log_scale, noise, shrink)
+    err = np.abs(np.asarray(got, np.float64) - want)
+    bad = err > tol
+    assert not bad.any(), "%s: %d elements beyond the FP32 bound, worst %s (bound %s)" % (
+        name, int(bad.sum()), err[bad].max(), tol[bad][np.argmax(err[bad])])
