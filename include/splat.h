@@ -517,7 +517,9 @@ void splat_set_tile_sort(int mode);
  * largest quadratic form over the tile's corners, with margins for FP32
  * rounding) enters a fixed-point sum of -ln(1 - alpha), and the list ends
  * after the batch of 32 entries that takes the sum past -ln(1e-4) plus a
- * margin.  Every pixel skips the dropped pairs, or stops before reaching
+ * margin (checked over the first 512 entries of the tile's 8x8-tile block in
+ * depth order; a tile not saturated by then keeps its whole list).  Every
+ * pixel skips the dropped pairs, or stops before reaching
  * them, so images and gradients do not change; the lists (and so `last`) are
  * shorter.  Off: every tile of the rectangle, as in splat_bin_sort's key
  * definition.  Host-side global.

@@ -933,11 +933,13 @@ struct TileArgs {
 // over the tile's corners (the form is convex), q enlarged to cover FP32
 // rounding, provided the bound passes the 1/255 skip with a margin and the
 // conic is far enough from singular that the kernels' evaluation of the power
-// cannot round to the wrong side of 0.  It sums -ln(1 - alpha) per (segment,
-// tile) in fixed point (rounded down); the prefix over the segments ends the
-// tile's list after the segment that takes the sum past -ln(1e-4) with a
-// margin for the rounding of the T products.  The sums are exact integers, so
-// the cut does not depend on the order of any reduction.
+// cannot round to the wrong side of 0.  The head pass sums -ln(1 - alpha)
+// over each tile's list in order, in fixed point (rounded down), and ends the
+// list after the batch of 32 entries that takes the sum past -ln(1e-4) with a
+// margin for the rounding of the T products (a product of (1 - alpha) below
+// e^-9.25 at every pixel; the kernels' T rounds by about 2^-23 a step, which
+// the margin covers for 2e5 steps).  The sums are exact integers, so the cut
+// does not depend on the order of any reduction.
 constexpr float kSatScale = 65536.f;                       // fixed point of -ln(1 - alpha)
 constexpr uint32_t kSatThreshold = (uint32_t)(9.25 * 65536);  // -ln(1e-4) = 9.2103 plus the margin
 
