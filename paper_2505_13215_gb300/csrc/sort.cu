@@ -1423,10 +1423,19 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                 if (COUNT) {
                     const int4 rc = ((const int4*)a.proj.rect)[row];
                     auto rel = [](int c, int o) { return (uint32_t)min(max(c - o, 0), 8); };
-                    s_rect[threadIdx.x] = rel(rc.x, tx0) | rel(rc.y, sy * 8) << 8 | rel(rc.z, tx0) << 16 |
-                                          rel(rc.w, sy * 8) << 24;
+                    const uint32_t x0 = rel(rc.x, tx0), y0 = rel(rc.y, sy * 8), x1 = rel(rc.z, tx0),
+                                   y1 = rel(rc.w, sy * 8);
+                    // does the rectangle reach a tile whose list is still open?
+                    const uint32_t cols = (1u << x1) - (1u << x0);
+                    bool open = false;
+#pragma unroll
+                    for (uint32_t r = 0; r < 8; ++r)
+                        if (r >= y0 && r < y1)
+                            open |= (cols & ~((r < 4 ? sat.x >> (8 * r) : sat.y >> (8 * (r - 4))) & 0xffu)) != 0u;
+                    // a row that reaches no open tile is queued by no tile row (y0 = 8, y1 = 0)
+                    s_rect[threadIdx.x] = open ? x0 | y0 << 8 | x1 << 16 | y1 << 24 : 8u << 8;
                     s_mask[threadIdx.x] = make_uint2(0u, 0u);
-                    if (a.cull) {
+                    if (a.cull && open) {
                         const float2 xy = ((const float2*)a.proj.xy)[row];
                         const float4 co = ((const float4*)a.proj.conic_opacity)[row];
                         // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
@@ -1442,7 +1451,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
                 }
             }
             __syncthreads();
-            if (ty < TY) {
+            if (ty < TY && done != 0xffu) {  // tile rows whose lists all ended in the head have no work
                 const int n = (int)min(256u, rg.y - b);
                 // the entries this tile row has work for (COUNT: rectangle covers the
                 // row; write pass: listed in some tile of the row), queued in order
