@@ -917,6 +917,7 @@ struct TileArgs {
     uint32_t* n_head;                 // [total_super] rows of each list the head pass went through
     uint2* sat_head;                  // [total_super] tiles (bit 8 r + c) whose lists ended in the head
     uint32_t* seg_base;               // [total_super + 1] first tail segment of each super-tile
+    uint32_t* seg_super;              // [segments] super-tile of each tail segment
     uint32_t* seg_cnt;                // [segments][64] per-segment tile counts, then offsets
     uint2* mask;                      // per super-tile list entry: byte w = its tile columns in tile row w
     uint32_t* ticket;                 // [4] tickets of the tail write / count and head write / count passes (zeroed)
@@ -1004,7 +1005,10 @@ __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
         }
         uint32_t tot;
         const uint32_t ex = block_excl_scan256(c, s_tmp, &tot);
-        if (gs < a.total_super) a.seg_base[gs] = carry + ex;
+        if (gs < a.total_super) {
+            a.seg_base[gs] = carry + ex;
+            for (uint32_t q = 0; q < c; ++q) a.seg_super[carry + ex + q] = (uint32_t)gs;
+        }
         carry += tot;
     }
     if (threadIdx.x == 0) a.seg_base[a.total_super] = carry;
@@ -1379,14 +1383,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
         if (threadIdx.x == 0) {
             const uint32_t g = atomicAdd(a.ticket + (COUNT ? 1 : 0), 1u);
             s_g = g;
-            if (g < nseg) {  // super-tile of segment g: last gs with seg_base[gs] <= g
-                int lo = 0, hi = a.total_super - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (a.seg_base[mid] <= g) lo = mid; else hi = mid - 1;
-                }
-                s_gs = lo;
-            }
+            if (g < nseg) s_gs = (int)a.seg_super[g];  // super-tile of segment g
         }
         __syncthreads();
         const uint32_t g = s_g;
@@ -1674,8 +1671,8 @@ struct SortLayout {
     int64_t total_tiles, total_super;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
         off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
-    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_nhead, off_sathead, off_mask,
-        off_tord;
+    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_segsuper, off_nhead, off_sathead,
+        off_mask, off_tord;
     int64_t max_segs;
     size_t bytes;
 };
@@ -1738,6 +1735,7 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.max_segs = L.binned ? (capacity + kFilterSeg - 1) / kFilterSeg + L.total_super : 1;
     L.off_segbase = take(4 * (size_t)(L.total_super + 1));
     L.off_segcnt = take(L.binned ? 4 * 64 * (size_t)L.max_segs : 4);
+    L.off_segsuper = take(L.binned ? 4 * (size_t)L.max_segs : 4);
     L.off_nhead = take(4 * (size_t)std::max<int64_t>(L.total_super, 1));
     L.off_sathead = take(8 * (size_t)std::max<int64_t>(L.total_super, 1));
     L.off_mask = take(L.binned ? 8 * (size_t)capacity : 4);
@@ -1892,6 +1890,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.cull = g_tile_cull;
         t.seg_base = U(L.off_segbase);
         t.seg_cnt = U(L.off_segcnt);
+        t.seg_super = U(L.off_segsuper);
         t.n_head = U(L.off_nhead);
         t.sat_head = (uint2*)(w + L.off_sathead);
         t.mask = (uint2*)(w + L.off_mask);
