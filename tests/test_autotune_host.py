@@ -69,3 +69,51 @@ def test_choice_is_cached_per_workload_shape(monkeypatch, fake):
     G2 = types.SimpleNamespace(n3=11, n4=5, dtype="bfloat16")
     monkeypatch.setattr(autotune, "_time_steps", lambda *a, **k: 1.0)
     assert not autotune.tune(FakeR(), G2, target=None, reps=1)["cached"]
+
+
+class FakeSort:
+    """A rasterizer whose sort needs `need_super` entries for the super-tile
+    lists and `K` for the tile lists (the saturation cut can make the tile
+    lists the shorter), with the capacity checks of the binned path: the
+    super-tile list is checked first and reports its own count."""
+
+    headroom = 1.25
+
+    def __init__(self, capacity, K, need_super):
+        self.capacity, self.K, self.need_super = capacity, K, need_super
+        self.calls = 0
+        self._status = (abi.SPLAT_OK, 0, 0)
+        self.n_needed = types.SimpleNamespace(item=lambda: max(self.K, self.need_super))
+
+    def set_capacity(self, c):
+        self.capacity = int(c)
+
+    def forward(self, G):
+        self.calls += 1
+        if self.need_super > self.capacity:
+            self._status = (abi.SPLAT_ERR_CAPACITY, 0, self.need_super)
+        elif self.K > self.capacity:
+            self._status = (abi.SPLAT_ERR_CAPACITY, 0, self.K)
+        else:
+            self._status = (abi.SPLAT_OK, 0, 0)
+
+    def read_status(self):
+        return self._status
+
+    def instances(self):
+        return self.K
+
+
+@pytest.mark.parametrize("K,need_super", [(6_000_000, 3_000_000), (1_000_000, 4_000_000)])
+def test_capacity_covers_the_larger_of_the_two_lists(K, need_super):
+    """The capacity settles at the headroom over the larger of K and the
+    super-tile list, whichever overflowed first, and a later call at that
+    capacity passes both checks."""
+    from paper_2505_13215_gb300 import raster
+    R = FakeSort(capacity=100_000, K=K, need_super=need_super)
+    got = raster.Rasterizer.autotune_capacity(R, None)
+    assert got == K
+    big = max(K, need_super)
+    assert big <= R.capacity <= int(big * R.headroom) + 1024 + 1
+    R.forward(None)
+    assert R.read_status()[0] == abi.SPLAT_OK
