@@ -938,9 +938,10 @@ struct TileArgs {
 // over each tile's list in order, in fixed point (rounded down), and ends the
 // list after the batch of 32 entries that takes the sum past -ln(1e-4) with a
 // margin for the rounding of the T products (a product of (1 - alpha) below
-// e^-9.25 at every pixel; the kernels' T rounds by about 2^-23 a step, which
-// the margin covers for 2e5 steps).  The sums are exact integers, so the cut
-// does not depend on the order of any reduction.
+// e^-9.25 at every pixel; the kernels' T rounds by about 2^-23 an update, which
+// the margin covers for 2e5 updates, and a cut falls within the first
+// kHeadChunks x 256 entries of a list).  The sums are exact integers, so the
+// cut does not depend on the order of any reduction.
 constexpr float kSatScale = 65536.f;                       // fixed point of -ln(1 - alpha)
 constexpr uint32_t kSatThreshold = (uint32_t)(9.25 * 65536);  // -ln(1e-4) = 9.2103 plus the margin
 
