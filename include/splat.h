@@ -466,7 +466,9 @@ splat_status splat_l1_loss(const float *img, const float *target, int64_t n, flo
  *    rejected on the host with SPLAT_ERR_CAPACITY, before any device work.
  *  - The first call on each device looks up the array's device address with
  *    the device current (cudaGetSymbolAddress); make that first call before
- *    any stream capture.
+ *    any stream capture.  The address is kept for the life of the process: a
+ *    cudaDeviceReset (or a reset of the primary context) unloads the array and
+ *    voids this entry point on that device until the process restarts.
  *  - All calls share the array and its contents persist between calls (the
  *    sort clears what must start at zero); calls that overlap on the GPU --
  *    other streams, or other host threads without ordering -- race on it.
@@ -534,6 +536,23 @@ void splat_set_tile_cull(int on);
  * Host-side global; the caller zeroes the counters.
  */
 void splat_set_stats(unsigned long long *dev_counters);
+
+/*
+ * Diagnostic: throughput probe of one SM pipe, for the roofline of the
+ * compositing kernels (bound by FP32 arithmetic and the multi-function unit,
+ * not by memory).  Launches `blocks` CTAs of 256 threads on `stream`, each
+ * thread running 8 independent chains of `iters` steps of one instruction:
+ *   SPLAT_PROBE_FFMA   fma.rn.f32            2 FP32 operations per step
+ *   SPLAT_PROBE_FFMA2  fma.rn.f32x2 (packed) 4 FP32 operations per step
+ *   SPLAT_PROBE_EX2    ex2.approx.ftz.f32    1 operation per step
+ *   SPLAT_PROBE_RCP    rcp.approx.ftz.f32    1 operation per step
+ * Returns the number of operations the launch performs (the caller times it
+ * with CUDA events), or -1 on invalid arguments or a launch failure.  `out`:
+ * device float[256], written only to keep the chains from being optimised
+ * away (its contents are meaningless).
+ */
+enum { SPLAT_PROBE_FFMA = 0, SPLAT_PROBE_FFMA2 = 1, SPLAT_PROBE_EX2 = 2, SPLAT_PROBE_RCP = 3 };
+double splat_peak_probe(int kind, int blocks, int iters, float *out, void *stream);
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int32_t splat_version(void);

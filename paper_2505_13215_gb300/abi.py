@@ -135,6 +135,7 @@ EXPORTS = {
                                 C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "splat_densify_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int]),
     "splat_workspace_size_4d": (C.c_size_t, [C.c_int, C.c_int64, C.c_int]),
+    "splat_peak_probe": (C.c_double, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -282,3 +283,11 @@ def splat_densify_workspace_size(n3, cap3, n4, cap4, sh_time4=0):
 
 def splat_workspace_size_4d(op, N4, sh_time):
     return int(lib().splat_workspace_size_4d(int(op), int(N4), int(sh_time)))
+
+
+SPLAT_PROBE_FFMA, SPLAT_PROBE_FFMA2, SPLAT_PROBE_EX2, SPLAT_PROBE_RCP = 0, 1, 2, 3
+
+
+def splat_peak_probe(kind, blocks, iters, out, stream):
+    """Launches one pipe-throughput probe; returns its operation count (-1 on error)."""
+    return float(lib().splat_peak_probe(int(kind), int(blocks), int(iters), out, stream))

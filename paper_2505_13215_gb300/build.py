@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsplat.so")
-SOURCES = ["api.cu", "project.cu", "sort.cu", "composite.cu", "convert.cu", "noalloc.cu", "optim.cu", "densify.cu"]
+SOURCES = ["api.cu", "project.cu", "sort.cu", "composite.cu", "convert.cu", "noalloc.cu", "optim.cu", "densify.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -105,17 +105,7 @@ LaunchCtx launch_ctx(void* stream)
     return c;
 }
 
-static bool valid_views(const splat_view* views, int V)
-{
-    if (!views || V < 1 || V > SPLAT_MAX_VIEWS) return false;
-    for (int v = 0; v < V; ++v) {
-        const splat_view& s = views[v];
-        if (s.W < 1 || s.H < 1 || s.W > 16384 || s.H > 16384) return false;
-        if (!(s.fx > 0.f) || !(s.fy > 0.f) || !std::isfinite(s.cx) || !std::isfinite(s.cy)) return false;
-        if (!(s.z_near > 0.f) || !std::isfinite(s.t)) return false;
-    }
-    return true;
-}
+static bool valid_views(const splat_view* views, int V) { return host_valid_views(views, V); }
 
 static ViewBatch make_batch(const splat_view* views, int V)
 {
@@ -185,14 +175,9 @@ static int common_dtype(const splat_g3& g3, const splat_g4& g4, bool* ok)
     return g4.n > 0 ? g4.dtype : (g3.n > 0 ? g3.dtype : SPLAT_F32);
 }
 
-static bool valid_proj(const splat_proj* p, int V)
-{
-    return p && p->views == V && p->n >= 0 && (p->n == 0 || (p->xy && p->conic_opacity && p->rgb_depth && p->rect &&
-                                                              p->radius && p->n_tiles)) &&
-           (int64_t)V * p->n < (1ll << 32);
-}
+static bool valid_proj(const splat_proj* p, int V) { return host_valid_proj(p, V); }
 
-static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+static bool aligned(const void* p, size_t a) { return host_aligned(p, a); }
 
 // 16-bit storage: 4-wide rows are read as 8 bytes, SH blocks (96 bytes) as 16-byte vectors
 static bool half_storage_aligned(const splat_g3& g3, const splat_g4& g4, int dt)
@@ -312,11 +297,8 @@ splat_status splat_slice_project(const splat_g3* g3p, const splat_g4* g4p, const
 splat_status splat_bin_sort(const splat_proj* proj, const splat_view* views, int V, splat_bins* bins,
                             int32_t* status, void* workspace, size_t workspace_bytes, void* stream)
 {
-    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !status) return SPLAT_ERR_INVALID_ARG;
-    if (bins->capacity < 0 || bins->capacity > SPLAT_MAX_INSTANCES || !bins->ranges || !bins->n_instances)
+    if (!valid_views(views, V) || !valid_proj(proj, V) || !host_valid_bins(bins) || !status)
         return SPLAT_ERR_INVALID_ARG;
-    if (bins->capacity > 0 && !bins->vals) return SPLAT_ERR_INVALID_ARG;
-    if (!aligned(bins->ranges, 8) || !aligned(bins->n_instances, 8)) return SPLAT_ERR_INVALID_ARG;
     int TX[SPLAT_MAX_VIEWS], TY[SPLAT_MAX_VIEWS];
     for (int v = 0; v < V; ++v) {
         TX[v] = (views[v].W + kTile - 1) / kTile;

@@ -50,15 +50,6 @@ static void* scratch_for_current_device(cudaError_t* err)
     return g_scratch_ptr[dev];
 }
 
-// the same view packing as the other entry points
-static bool noalloc_views_ok(const splat_view* views, int V)
-{
-    if (!views || V < 1 || V > SPLAT_MAX_VIEWS) return false;
-    for (int v = 0; v < V; ++v)
-        if (views[v].W < 1 || views[v].H < 1 || views[v].W > 16384 || views[v].H > 16384) return false;
-    return true;
-}
-
 }  // namespace splat
 
 using namespace splat;
@@ -66,13 +57,9 @@ using namespace splat;
 extern "C" splat_status splat_bin_sort_noalloc(const splat_proj* proj, const splat_view* views, int V,
                                                splat_bins* bins, int32_t* status, void* stream)
 {
-    if (!noalloc_views_ok(views, V) || !proj || proj->views != V || proj->n < 0 || !bins || !status)
+    // the argument checks of splat_bin_sort, so both entry points reject the same calls
+    if (!host_valid_views(views, V) || !host_valid_proj(proj, V) || !host_valid_bins(bins) || !status)
         return SPLAT_ERR_INVALID_ARG;
-    if ((int64_t)V * proj->n >= (1ll << 32)) return SPLAT_ERR_INVALID_ARG;
-    if (bins->capacity < 0 || bins->capacity > SPLAT_MAX_INSTANCES || !bins->ranges || !bins->n_instances ||
-        (bins->capacity > 0 && !bins->vals))
-        return SPLAT_ERR_INVALID_ARG;
-    if (proj->n > 0 && (!proj->rect || !proj->n_tiles || !proj->rgb_depth)) return SPLAT_ERR_INVALID_ARG;
     int TX[SPLAT_MAX_VIEWS], TY[SPLAT_MAX_VIEWS];
     for (int v = 0; v < V; ++v) {
         TX[v] = (views[v].W + kTile - 1) / kTile;

@@ -273,6 +273,7 @@ __device__ __forceinline__ float inv_norm4(const float q[4])
 
 // Host-side launch helpers shared by the .cu files (defined in api.cu).
 #include <atomic>
+#include <cmath>
 namespace splat {
 extern std::atomic<int64_t> g_launches;  // kernels launched or captured (diagnostic)
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -292,4 +293,36 @@ struct LaunchCtx {
     int64_t spin_limit;
 };
 LaunchCtx launch_ctx(void* stream);
+
+// Host-side argument checks shared by the entry points that take the same
+// arguments (splat_bin_sort and its allocation-free variant reject the same
+// calls).
+inline bool host_aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+inline bool host_valid_views(const splat_view* views, int V)
+{
+    if (!views || V < 1 || V > SPLAT_MAX_VIEWS) return false;
+    for (int v = 0; v < V; ++v) {
+        const splat_view& s = views[v];
+        if (s.W < 1 || s.H < 1 || s.W > 16384 || s.H > 16384) return false;
+        if (!(s.fx > 0.f) || !(s.fy > 0.f) || !std::isfinite(s.cx) || !std::isfinite(s.cy)) return false;
+        if (!(s.z_near > 0.f) || !std::isfinite(s.t)) return false;
+    }
+    return true;
+}
+
+inline bool host_valid_proj(const splat_proj* p, int V)
+{
+    return p && p->views == V && p->n >= 0 &&
+           (p->n == 0 || (p->xy && p->conic_opacity && p->rgb_depth && p->rect && p->radius && p->n_tiles)) &&
+           (int64_t)V * p->n < (1ll << 32);
+}
+
+// splat_bins as splat_bin_sort reads and writes it
+inline bool host_valid_bins(const splat_bins* b)
+{
+    if (!b || b->capacity < 0 || b->capacity > SPLAT_MAX_INSTANCES || !b->ranges || !b->n_instances) return false;
+    if (b->capacity > 0 && !b->vals) return false;
+    return host_aligned(b->ranges, 8) && host_aligned(b->n_instances, 8);
+}
 }  // namespace splat

@@ -100,3 +100,38 @@ def test_knobs_are_host_side(lib):
     abi.splat_set_pixels_per_lane(3, 5)  # ignored
     abi.splat_set_pixels_per_lane(8, 8)
     assert abi.splat_version() == 0x000100
+
+
+@pytest.mark.parametrize("missing", ["xy", "conic_opacity", "rgb_depth", "rect", "radius", "n_tiles"])
+def test_both_bin_sorts_reject_the_same_projected_rows(lib, missing):
+    """splat_bin_sort and splat_bin_sort_noalloc check their arguments alike:
+    a projected-row array left NULL with rows present (the tile passes read xy
+    and conic_opacity when footprint culling is on) is rejected on the host,
+    before any device work; so are misaligned ranges / n_instances."""
+    v = (abi.splat_view * 1)()
+    v[0].W, v[0].H, v[0].fx, v[0].fy, v[0].z_near = 64, 64, 50.0, 50.0, 0.2
+    fields = {f: 4096 for f in ("xy", "conic_opacity", "rgb_depth", "rect", "radius", "n_tiles")}
+    fields[missing] = None
+    proj = abi.splat_proj(10, 1, 0, fields["xy"], fields["conic_opacity"], fields["rgb_depth"], fields["rect"],
+                          fields["radius"], fields["n_tiles"])
+    bins = abi.splat_bins(1024, 4096, 4096, 4096, 4096)
+    st = C.c_void_p(4096)
+    assert abi.splat_bin_sort_noalloc(C.byref(proj), v, 1, C.byref(bins), st, None) == abi.SPLAT_ERR_INVALID_ARG
+    assert abi.splat_bin_sort(C.byref(proj), v, 1, C.byref(bins), st, C.c_void_p(4096), 1 << 30, None) == \
+        abi.SPLAT_ERR_INVALID_ARG
+
+
+def test_both_bin_sorts_reject_misaligned_bins(lib):
+    v = (abi.splat_view * 1)()
+    v[0].W, v[0].H, v[0].fx, v[0].fy, v[0].z_near = 64, 64, 50.0, 50.0, 0.2
+    proj = abi.splat_proj(10, 1, 0, 4096, 4096, 4096, 4096, 4096, 4096)
+    st = C.c_void_p(4096)
+    for ranges, n_inst in ((4100, 4096), (4096, 4100)):
+        bins = abi.splat_bins(1024, 4096, 4096, ranges, n_inst)
+        assert abi.splat_bin_sort_noalloc(C.byref(proj), v, 1, C.byref(bins), st, None) == abi.SPLAT_ERR_INVALID_ARG
+        assert abi.splat_bin_sort(C.byref(proj), v, 1, C.byref(bins), st, C.c_void_p(4096), 1 << 30, None) == \
+            abi.SPLAT_ERR_INVALID_ARG
+    # a non-positive focal length is rejected by both, as by every entry point
+    v[0].fx = 0.0
+    bins = abi.splat_bins(1024, 4096, 4096, 4096, 4096)
+    assert abi.splat_bin_sort_noalloc(C.byref(proj), v, 1, C.byref(bins), st, None) == abi.SPLAT_ERR_INVALID_ARG
