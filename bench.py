@@ -197,6 +197,9 @@ def algorithmic_bytes(stage, n3, n4, V, pix, K, elem, K_super=0):
 # its three moments).
 FLOPS_EVAL = 5
 FLOPS_BLEND = {"composite_fwd": 5 + 10, "composite_bwd": 5 + 28}
+# the round per-pair figures of the method's cost model: about 15 FP32
+# operations and one exponential per evaluated pair forward, about 60 backward
+SURVEY_OPS = {"composite_fwd": 15, "composite_bwd": 60}
 KERNEL_SOURCES = {"composite_fwd": ["composite.cu", "splat_internal.cuh"],
                   "composite_bwd": ["composite.cu", "splat_internal.cuh"],
                   "slice_project": ["project.cu", "splat_internal.cuh"],
@@ -227,6 +230,55 @@ def measured_traffic(stage, views=None):
     if "dram_bytes_per_view" in t:
         return int(t["dram_bytes_per_view"] * views)
     return int(t["dram_bytes_per_launch"])
+
+
+# ---------------------------------------------------------------------------
+# measured ceilings of the SM pipes the compositing kernels use
+# ---------------------------------------------------------------------------
+
+PROBE_ITERS = {0: 40000, 1: 20000, 2: 2500, 3: 2500}
+
+
+def measure_pipe_peaks(dev, local, reps=12):
+    """FP32 (scalar fma.rn.f32 and packed fma.rn.f32x2) and MUFU (ex2, rcp)
+    throughput of this GPU, from splat_peak_probe launches of a few ms timed
+    with CUDA events (best of `reps` after two warm-up launches), with the SM
+    clock sampled while they run.  Returns TFLOP/s for the FMA probes and
+    T operations/s for the MUFU probes."""
+    import torch
+
+    from paper_2505_13215_gb300 import abi
+    props = torch.cuda.get_device_properties(dev)
+    blocks = props.multi_processor_count * 8
+    out = torch.zeros(256, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    res = {}
+    clocks = ClockSampler(local)
+    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ex2"), (3, "rcp")):
+        for _ in range(2):
+            abi.splat_peak_probe(kind, blocks, PROBE_ITERS[kind], out.data_ptr(), sp)
+        best = None
+        ops = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ops = abi.splat_peak_probe(kind, blocks, PROBE_ITERS[kind], out.data_ptr(), sp)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if ops <= 0:
+                raise RuntimeError("splat_peak_probe failed")
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        res[name] = round(ops / (best / 1e3) / 1e12, 3)
+        res[name + "_ms"] = round(best, 3)
+    clk = clocks.stop()
+    res["fp32_peak_tflops"] = max(res["ffma"], res["ffma2"])
+    res["mufu_peak_tops"] = min(res["ex2"], res["rcp"])
+    res["clocks"] = clk
+    res["how"] = ("splat_peak_probe: %d CTAs x 256 threads x 8 independent chains of one instruction, best of %d "
+                  "launches (CUDA events); FMA counted as 2 FP32 operations, f32x2 as 4" % (blocks, reps))
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -312,7 +364,9 @@ def run_ours(args, rank, local, world):
         tv = torch.rand(Rv.rgb.shape, generator=gen, device=dev)
         Rv.autotune_capacity(G32)
         plain.append((Rv, tv))
-    abi.splat_set_pixels_per_lane(8, 8)
+    # the plain path gets its own tuned launch shape (pixels per lane of the
+    # compositing kernels), chosen on its first view like the batched path's
+    plain_tune = autotune.tune(plain[0][0], G32, plain[0][1])
     plain_steps = max(2, args.steps // 2)
     for Rv, tv in plain:
         Rv.step(G32, tv)
@@ -398,17 +452,30 @@ def run_ours(args, rank, local, world):
     # ---- roofline of the dominant stage ----
     pix = int(sum(R.pix))
     dom = max(stages, key=lambda s: stages[s])
-    props = torch.cuda.get_device_properties(dev)
-    sm_max = float(peaks.get("sm_max_mhz", clk.get("sm_max_mhz") or 2070.0))
-    fp32_peak_all = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    pipes = measure_pipe_peaks(dev, local)
+    fp32_peak = pipes["fp32_peak_tflops"]
+    mufu_peak = pipes["mufu_peak_tops"]
+    # operation counts per pair: the kernels' own source (FLOPS_EVAL / FLOPS_BLEND)
+    # and the survey's round figures (about 15 FP32 operations per evaluated pair
+    # in the forward, about 60 in the backward)
+    survey_flops = {"composite_fwd": SURVEY_OPS["composite_fwd"] * fe, "composite_bwd": SURVEY_OPS["composite_bwd"] * be}
+    # MUFU operations: one base-2 exponential per evaluated pair in both kernels,
+    # plus one reciprocal per evaluated pair in the backward
+    mufu_ops = {"composite_fwd": fe, "composite_bwd": 2 * be}
+
+    def alu_entry(st, ms):
+        a = flops[st] / (ms / 1e3) / 1e12
+        a_s = survey_flops[st] / (ms / 1e3) / 1e12
+        m = mufu_ops[st] / (ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": round(a, 2), "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": round(a / fp32_peak, 4), "achieved_survey_count": round(a_s, 2),
+                "frac_survey_count": round(a_s / fp32_peak, 4), "mufu_tops": round(m, 3),
+                "mufu_frac": round(m / mufu_peak, 4)}
+
     if dom in flops:
-        # FP32 peak from unit counts and the maximum SM clock: SMs x 128 lanes x 2 (FMA)
-        fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-        ach = flops[dom] / (stages[dom] / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(fp32_peak, 1),
-                    "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
-                    "traffic": measured_traffic(dom, V), "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz"
-                    % (props.multi_processor_count, sm_max), "algorithmic_flops": flops[dom]}
+        roofline = dict(alu_entry(dom, stages[dom]), kernel=dom, traffic=measured_traffic(dom, V),
+                        peak_source="measured: splat_peak_probe, max of fma.rn.f32 and fma.rn.f32x2 chains",
+                        algorithmic_flops=flops[dom], algorithmic_flops_survey_count=survey_flops[dom])
     else:
         alg = algorithmic_bytes(dom, G.n3, G.n4, V, pix, K_inst, 2)
         ach = alg / (stages[dom] / 1e3) / 1e9
@@ -417,8 +484,9 @@ def run_ours(args, rank, local, world):
                     "peak_source": peak_src + " (copy bandwidth)", "algorithmic_bytes": alg}
 
     # every stage against its own bound: the compositing kernels in FP32
-    # operations, the others in algorithmic HBM bytes (inputs read once,
-    # outputs written once) against the measured copy bandwidth
+    # operations against the measured FP32 ceiling, the others in algorithmic
+    # HBM bytes (inputs read once, outputs written once) against the measured
+    # copy bandwidth
     stage_roof = {}
     for st, ms in stages.items():
         if ms <= 0:
@@ -427,9 +495,7 @@ def run_ours(args, rank, local, world):
             stage_roof[st] = {"fused": "computed inside composite_fwd's pixel epilogue (splat_composite_fwd_l1)"}
             continue
         if st in flops:
-            a = flops[st] / (ms / 1e3) / 1e12
-            stage_roof[st] = {"bound": "alu", "achieved": round(a, 2), "unit": "TFLOP/s",
-                              "frac": round(a / fp32_peak_all, 4)}
+            stage_roof[st] = alu_entry(st, ms)
         else:
             alg = algorithmic_bytes(st, G.n3, G.n4, V, pix, K_inst, 2, K_super if K_super > K_inst else 0)
             a = alg / (ms / 1e3) / 1e9
@@ -446,7 +512,8 @@ def run_ours(args, rank, local, world):
                    "instances_K": K_inst, "capacity_needed": K_super, "autotune": {k: tune[k] for k in ("ppl_fwd", "ppl_bwd", "capacity")},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "mpixel_per_s": round(value * W * H / 1e6, 1),
-        "plain_fp32": {"value": round(plain_value, 2), "unit": UNIT, "path": "per-view launches, FP32 storage, eager"},
+        "plain_fp32": {"value": round(plain_value, 2), "unit": UNIT, "path": "per-view launches, FP32 storage, eager",
+                       "autotune": {k: plain_tune[k] for k in ("ppl_fwd", "ppl_bwd")}},
         "stage_ms": {k: round(v, 4) for k, v in stages.items()},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
                 "pipeline": "pinned host parameters and targets copied on a second stream one step ahead; "
@@ -455,6 +522,9 @@ def run_ours(args, rank, local, world):
         "roofline": roofline,
         "stage_roofline": stage_roof,
         "composite_pairs": pairs,
+        "pipe_peaks": pipes,
+        "fp32_peak_measured": {"tflops": fp32_peak, "sm_mhz": pipes["clocks"].get("sm_mhz"),
+                               "ffma_tflops": pipes["ffma"], "ffma2_tflops": pipes["ffma2"]},
         "clocks": clk,
     }
     if not args.no_train:
@@ -629,13 +699,12 @@ def eager_stage_ms(R, G, target, reps):
 # CPU baseline: the FP64 oracle, as it stands, on a bounded sample
 # ---------------------------------------------------------------------------
 
-def cpu_baseline(scene, views, samples=1500, seed=0):
-    """Oracle forward at `samples` random pixels of view 0 plus the backward of a
-    loss on those pixels, scaled to views/s by the fraction of the view sampled."""
+def _oracle_sample(scene, v, samples, seed):
+    """Oracle forward at `samples` random pixels of view v plus the backward of
+    a loss on those pixels; returns (seconds, sampled fraction of the view)."""
     import numpy as np
 
     import oracle as O
-    v = views[0]
     rng = np.random.default_rng(seed)
     npix = v.W * v.H
     pix = rng.choice(npix, size=min(samples, npix), replace=False)
@@ -644,12 +713,64 @@ def cpu_baseline(scene, views, samples=1500, seed=0):
     g = np.zeros((3, npix))
     g[:, pix] = np.sign(ref["rgb"] - 0.5)
     O.render_bwd(scene, v, g.reshape(3, v.H, v.W))
-    dt = time.perf_counter() - t0
-    frac = len(pix) / npix
-    return {"value": round(frac / dt, 6), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": "FP64 oracle forward at %d random pixels of one %dx%d view (of %d Gaussians) plus the "
-                      "backward of a loss on them: %.1f s; scaled by the sampled fraction %.2e of a view"
-                      % (len(pix), v.W, v.H, scene.n, dt, frac)}
+    return time.perf_counter() - t0, len(pix) / npix
+
+
+def _oracle_full_small():
+    """The 128x128 workload (3,072 3D + 1,024 4D Gaussians, one view) rendered in
+    full by the oracle: seconds of the forward and of forward + backward (L1
+    sign gradient against 0.5)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2505_13215_gb300 import scenes
+    scene, views = scenes.small_scene(seed=0)
+    v = views[0]
+    t0 = time.perf_counter()
+    O.render(scene, v)
+    t1 = time.perf_counter()
+    ref = O.render(scene, v)
+    O.render_bwd(scene, v, np.sign(ref["rgb"] - 0.5).reshape(3, v.H, v.W))
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def cpu_baseline(scene, views, samples=1500, seed=0, full_small=True):
+    """The FP64 oracle as it stands on the host cores.  Headline value: the
+    1352x1014 video workload, forward at `samples` random pixels of view 0 plus
+    the backward of a loss on them, all threads, scaled to views/s by the
+    sampled fraction.  Also: the same sample single-threaded (fewer pixels),
+    and the 128x128 workload rendered in full, forward and forward + backward,
+    single-threaded and on all threads."""
+    import oracle as O
+    v = views[0]
+    n_all = O.num_threads()
+    dt, frac = _oracle_sample(scene, v, samples, seed)
+    out = {"value": round(frac / dt, 6), "unit": UNIT, "cores": n_all, "kind": "oracle",
+           "sample": "FP64 oracle forward at %d random pixels of one %dx%d view (of %d Gaussians) plus the "
+                     "backward of a loss on them: %.1f s on %d threads; scaled by the sampled fraction %.2e of a view"
+                     % (int(round(frac * v.W * v.H)), v.W, v.H, scene.n, dt, n_all, frac)}
+    if not full_small:
+        return out
+    configs = {}
+    O.set_num_threads(1)
+    try:
+        dt1, frac1 = _oracle_sample(scene, v, max(100, samples // 5), seed + 1)
+        f1, fb1 = _oracle_full_small()
+    finally:
+        O.set_num_threads(n_all)
+    fN, fbN = _oracle_full_small()
+    configs["%dx%d, %d Gaussians, fwd+bwd, sampled pixels" % (v.W, v.H, scene.n)] = {
+        "views_per_s": {"1": round(frac1 / dt1, 6), str(n_all): out["value"]},
+        "sample": "%d / %d pixels (1 thread), %d (%d threads)" % (int(round(frac1 * v.W * v.H)), v.W * v.H,
+                                                                   int(round(frac * v.W * v.H)), n_all)}
+    configs["128x128, 4096 Gaussians, full image"] = {
+        "fwd_views_per_s": {"1": round(1.0 / f1, 3), str(n_all): round(1.0 / fN, 3)},
+        "fwd_bwd_views_per_s": {"1": round(1.0 / fb1, 3), str(n_all): round(1.0 / fbN, 3)},
+        "seconds": {"fwd_1": round(f1, 3), "fwd_bwd_1": round(fb1, 3), "fwd_%d" % n_all: round(fN, 3),
+                    "fwd_bwd_%d" % n_all: round(fbN, 3)}}
+    out["configs"] = configs
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -667,10 +788,10 @@ def run_reference(args, rank, local, world):
     scene, base = scenes.video_scene(seed=1, n3=N3, n4=N4, W=W, H=H)
     views = scenes.jittered_views(base[0], args.views, seed=rank_seed(0))
     for i in range(args.warmup):
-        cpu_baseline(scene, views, samples=args.ref_samples // 4, seed=1000 + i)
+        cpu_baseline(scene, views, samples=args.ref_samples // 4, seed=1000 + i, full_small=False)
     vals, total, cores, sample = [], 0.0, None, None
     for k in range(args.steps):
-        r = cpu_baseline(scene, [views[k % len(views)]], samples=args.ref_samples, seed=k)
+        r = cpu_baseline(scene, [views[k % len(views)]], samples=args.ref_samples, seed=k, full_small=False)
         vals.append(r["value"])
         cores, sample = r["cores"], r["sample"]
     value = len(vals) / sum(1.0 / x for x in vals)  # views per total second
