@@ -8,16 +8,21 @@
 // the band, so a warp covers 32 * PPL pixels (PPL = 8: the whole 16x16 tile);
 // it evaluates them in pairs with packed FP32x2 arithmetic.  The warp walks
 // the tile's sorted list in batches of 32 Gaussians: each lane gathers one
-// Gaussian's projected features into the warp's shared-memory slot, then
-// every lane evaluates all its pixels against the 32 staged Gaussians
-// (broadcast reads).  The warp leaves the list as soon as a vote shows every
-// one of its pixels has saturated (T would drop below 1e-4).
+// Gaussian's projected rows into shared memory with cp.async one batch ahead
+// (they land while the previous batch is composited) and turns them into the
+// staged features, then every lane evaluates all its pixels against the 32
+// staged Gaussians (broadcast reads).  The warp leaves the list as soon as a
+// vote shows every one of its pixels has saturated (T would drop below 1e-4).
 //
 // The adjoint walks the same list back to front from where each pixel's walk
 // ended, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
 // transmittance.  Per Gaussian each lane keeps 9 sums over its pixels; batches
 // of kRedBatch Gaussians are summed over the warp through shared memory and
-// added to the 2D gradients with vector atomics.
+// added to the 2D gradients with vector atomics.  Whether the 0.99 opacity
+// clamp needs evaluating is decided once per staged batch (one vote over its
+// 32 Gaussians), so the walk runs one of two straight-line loop bodies.
+#include <type_traits>
+
 #include "splat_internal.cuh"
 
 namespace splat {
@@ -66,11 +71,46 @@ __device__ __forceinline__ void load_feat(const float4* s, Feat& f)
     f.op = f4.w;
 }
 
-__device__ __forceinline__ void stage_feat(const splat_proj& proj, uint32_t row, float4* s)
+// The projected rows of the next batch are gathered while the current batch
+// is composited: each lane copies its entry's three rows (xy, conic/opacity,
+// rgb/depth; 40 bytes) into its own slot of a per-warp buffer with cp.async,
+// and turns them into staged features when the walk reaches that batch.  The
+// slot is private to the lane, so only the features need a warp barrier.
+struct RawRows {
+    float4 co[32];
+    float4 rd[32];
+    float2 xy[32];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
-    const float2 xy = ((const float2*)proj.xy)[row];
-    const float4 co = ((const float4*)proj.conic_opacity)[row];
-    const float4 rd = ((const float4*)proj.rgb_depth)[row];
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void gather_rows(const splat_proj& proj, uint32_t row, RawRows& raw, int lane)
+{
+    cp_async16(&raw.co[lane], (const float4*)proj.conic_opacity + row);
+    cp_async16(&raw.rd[lane], (const float4*)proj.rgb_depth + row);
+    cp_async8(&raw.xy[lane], (const float2*)proj.xy + row);
+}
+
+// The staged features (Feat) of the lane's gathered rows, after its copies
+// have landed.
+__device__ __forceinline__ void stage_feat(const RawRows& raw, int lane, float4* s)
+{
+    const float2 xy = raw.xy[lane];
+    const float4 co = raw.co[lane];
+    const float4 rd = raw.rd[lane];
     const float pcut2 = __log2f(kAlphaMin / co.w);
     // alpha_max >= 1/255 for every listed Gaussian, so pcut2 <= 0; should the
     // approximate logarithm round above 0, a NaN mean makes every test fail,
@@ -227,6 +267,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     static_assert(PPL == 2 || PPL == 4 || PPL == 8, "pixels per lane come in pairs");
     constexpr int BANDS = 8 / PPL, NP = PPL / 2;
     __shared__ float4 s_feat[kCompWarps][32][kFeat];
+    __shared__ RawRows s_raw[kCompWarps];
     if (status_failed(status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
@@ -267,12 +308,22 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     }
     const unsigned all_done = (1u << PPL) - 1;
     float4* sf = &s_feat[warp][0][0];
+    RawRows& raw = s_raw[warp];
     unsigned n_eval = 0, n_blend = 0;
+    // the rows of batch 0 in flight, the list entries of batch 1 in a register
+    if (rg.x + lane < rg.y) gather_rows(proj, vals[rg.x + lane], raw, lane);
+    cp_async_commit();
+    uint32_t next_row = rg.x + 32 + lane < rg.y ? vals[rg.x + 32 + lane] : 0u;
     for (uint32_t b = rg.x; b < rg.y; b += 32) {
         if (__all_sync(0xffffffffu, done == all_done)) break;
         const uint32_t idx = b + lane;
-        if (idx < rg.y) stage_feat(proj, vals[idx], sf + lane * kFeat);
+        cp_async_wait_all();
+        if (idx < rg.y) stage_feat(raw, lane, sf + lane * kFeat);
         __syncwarp();
+        // the next batch's rows land while this one is composited
+        if (idx + 32 < rg.y) gather_rows(proj, next_row, raw, lane);
+        cp_async_commit();
+        next_row = idx + 64 < rg.y ? vals[idx + 64] : 0u;
         const int n = (int)min(32u, rg.y - b);
         const int pos0 = (int)(b - rg.x) + 1;
         // every lane walks the batch (finished pixels fail every test) so that
@@ -289,6 +340,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
         }
         __syncwarp();
     }
+    cp_async_wait_all();  // no copy may land in shared memory after the CTA has left
     if (STATS) {
         const unsigned e = __reduce_add_sync(0xffffffffu, n_eval), bl = __reduce_add_sync(0xffffffffu, n_blend);
         if (lane == 0) {
@@ -438,8 +490,9 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
         na.x = ox ? na.x : 0.f;
         na.y = oy ? na.y : 0.f;
         const float2 om = add2(one, na);  // 1 - alpha >= 0.01
-        // T_j = T + alpha T / (1 - alpha): exactly T for a skipped pixel
-        const float2 Tj = fma2(mul2(na, T[p]), make_float2(rcp_approx(-om.x), rcp_approx(-om.y)), T[p]);
+        // T_j = T / (1 - alpha), one reciprocal and one multiply (a skipped
+        // pixel multiplies T by the reciprocal of exactly 1)
+        const float2 Tj = mul2(T[p], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
         const float2 nw = mul2(na, Tj);  // -alpha T_j
         S.r = fma2(nw, G[p][0], S.r);
         S.g = fma2(nw, G[p][1], S.g);
@@ -477,6 +530,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     __shared__ float4 s_feat[kCompWarps][32][kFeat];
     __shared__ uint32_t s_row[kCompWarps][32];
     __shared__ float4 s_red[kCompWarps][kRedGroups][32];
+    __shared__ RawRows s_raw[kCompWarps];
     if (status_failed(status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
@@ -536,69 +590,96 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     const uint2 rg = ranges[tile];
     float4* sf = &s_feat[warp][0][0];
     float4* red = &s_red[warp][0][0];
-    const int nb = (maxlast + 31) / 32;
+    // entries walked: [rg.x, end); batches 0 .. nb - 2 are full
+    const uint32_t end = min(rg.x + (uint32_t)maxlast, rg.y);
+    if (end <= rg.x) return;
+    const int nb = (int)((end - rg.x + 31) / 32);
+    RawRows& raw = s_raw[warp];
     unsigned n_eval = 0, n_blend = 0;
+    // the walk goes back to front: the last (possibly partial) batch's rows in
+    // flight first, the list entries of the one before it in a register; every
+    // earlier batch is full
+    uint32_t cur_row = 0, next_row = 0;
+    {
+        const uint32_t idx = rg.x + 32u * (nb - 1) + lane;
+        if (idx < end) {
+            cur_row = vals[idx];
+            gather_rows(proj, cur_row, raw, lane);
+        }
+        cp_async_commit();
+        if (nb >= 2) next_row = vals[rg.x + 32u * (nb - 2) + lane];
+    }
     for (int bi = nb - 1; bi >= 0; --bi) {
         const uint32_t b = rg.x + 32u * bi;
-        const uint32_t end = min(rg.x + (uint32_t)maxlast, rg.y);
         const uint32_t idx = b + lane;
+        cp_async_wait_all();
         if (idx < end) {
-            const uint32_t row = vals[idx];
-            s_row[warp][lane] = row;
-            stage_feat(proj, row, sf + lane * kFeat);
+            s_row[warp][lane] = cur_row;
+            stage_feat(raw, lane, sf + lane * kFeat);
         }
         __syncwarp();
+        // the previous batch's rows land while this one is walked
+        if (bi >= 1) gather_rows(proj, next_row, raw, lane);
+        cp_async_commit();
+        cur_row = next_row;
+        if (bi >= 2) next_row = vals[b - 64u + lane];
         const int n = (int)min(32u, end - b);
         int nq = 0;            // Gaussians waiting in the reduction buffer
         uint32_t pend_row = 0; // lane q: row of waiting Gaussian q
         int pend_j = 0;        // lane q: its slot in the staged batch
-        for (int j = n - 1; j >= 0; --j) {
-            const int li = 32 * bi + j;  // position in the tile list
-            if (li <= act) {  // (warp-uniform) pixels whose last contributor is at li or later switch on
-                int nxt = -1;
+        // one vote per batch: does any staged Gaussian reach the 0.99 clamp
+        const bool clamp_batch = __any_sync(0xffffffffu, lane < n && sf[lane * kFeat + 4].w >= kClampFree);
+        auto walk = [&](auto clamp_tag) {
+            constexpr bool CL = decltype(clamp_tag)::value;
+            for (int j = n - 1; j >= 0; --j) {
+                const int li = 32 * bi + j;  // position in the tile list
+                if (li <= act) {  // (warp-uniform) pixels whose last contributor is at li or later switch on
+                    int nxt = -1;
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) {
-                    const float nr = -(y0f + (float)(2 * k));
-                    const int lk = last[k];
-                    if (li < lk) {
-                        if (k & 1) nrow[k >> 1].y = nr;
-                        else nrow[k >> 1].x = nr;
-                    } else {
-                        nxt = max(nxt, lk - 1);
+                    for (int k = 0; k < PPL; ++k) {
+                        const float nr = -(y0f + (float)(2 * k));
+                        const int lk = last[k];
+                        if (li < lk) {
+                            if (k & 1) nrow[k >> 1].y = nr;
+                            else nrow[k >> 1].x = nr;
+                        } else {
+                            nxt = max(nxt, lk - 1);
+                        }
                     }
+                    act = __reduce_max_sync(0xffffffffu, nxt);
                 }
-                act = __reduce_max_sync(0xffffffffu, nxt);
-            }
-            if (STATS) {
+                if (STATS) {
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) n_eval += li < last[k];
+                    for (int k = 0; k < PPL; ++k) n_eval += li < last[k];
+                }
+                Feat f;
+                load_feat(sf + j * kFeat, f);
+                const ColTerms ct = col_terms(f, nu);
+                BwdSums S;
+                const bool any = bwd_gaussian<NP, CL, STATS>(f, ct, T, nQ, G, nrow, S, n_blend);
+                if (!any) continue;  // warp-uniform
+                const float W0 = S.W0.x + S.W0.y, W1 = S.W1.x + S.W1.y;
+                float4* slot = red + 2 * nq * 32 + lane;
+                const float dx = ct.dx.x, dxW0 = dx * W0;
+                slot[0] = make_float4(dxW0, W1, dx * dxW0, dx * W1);
+                slot[32] = make_float4(S.W2.x + S.W2.y, W0, S.r.x + S.r.y, S.g.x + S.g.y);
+                ((float*)(red + (14 + (nq >> 2)) * 32 + lane))[nq & 3] = S.b.x + S.b.y;
+                if (lane == nq) {
+                    pend_row = s_row[warp][j];
+                    pend_j = j;
+                }
+                if (++nq == kRedBatch) {
+                    flush_reduction(red, nq, pend_row, pend_j, sf, dproj, lane);
+                    nq = 0;
+                }
             }
-            Feat f;
-            load_feat(sf + j * kFeat, f);
-            const ColTerms ct = col_terms(f, nu);
-            BwdSums S;
-            const bool any = f.op < kClampFree  // same Gaussian on every lane
-                                 ? bwd_gaussian<NP, false, STATS>(f, ct, T, nQ, G, nrow, S, n_blend)
-                                 : bwd_gaussian<NP, true, STATS>(f, ct, T, nQ, G, nrow, S, n_blend);
-            if (!any) continue;  // warp-uniform
-            const float W0 = S.W0.x + S.W0.y, W1 = S.W1.x + S.W1.y;
-            float4* slot = red + 2 * nq * 32 + lane;
-            const float dx = ct.dx.x, dxW0 = dx * W0;
-            slot[0] = make_float4(dxW0, W1, dx * dxW0, dx * W1);
-            slot[32] = make_float4(S.W2.x + S.W2.y, W0, S.r.x + S.r.y, S.g.x + S.g.y);
-            ((float*)(red + (14 + (nq >> 2)) * 32 + lane))[nq & 3] = S.b.x + S.b.y;
-            if (lane == nq) {
-                pend_row = s_row[warp][j];
-                pend_j = j;
-            }
-            if (++nq == kRedBatch) {
-                flush_reduction(red, nq, pend_row, pend_j, sf, dproj, lane);
-                nq = 0;
-            }
-        }
+        };
+        if (clamp_batch) walk(std::integral_constant<bool, true>());
+        else walk(std::integral_constant<bool, false>());
         if (nq) flush_reduction(red, nq, pend_row, pend_j, sf, dproj, lane);
         __syncwarp();
     }
+    cp_async_wait_all();  // no copy may land in shared memory after the CTA has left
     if (STATS) {
         const unsigned e = __reduce_add_sync(0xffffffffu, n_eval), bl = __reduce_add_sync(0xffffffffu, n_blend);
         if (lane == 0) {

@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(256) k_probe_ffma2(int iters, float a, float b
     if (s == 12345.f) out[threadIdx.x] = s;
 }
 
-// ex2.approx.ftz.f32 chains: x = 2^x, which reaches +inf after a few steps
-// and stays there (the unit's throughput does not depend on the value).
+// ex2.approx.ftz.f32 chains: x = 2^-|x| (the sign bit set by a logic
+// operation on the ALU pipe), which stays in (0, 1].
 __global__ void __launch_bounds__(256) k_probe_ex2(int iters, float* out)
 {
     float x[kProbeChains];
@@ -57,9 +57,15 @@ __global__ void __launch_bounds__(256) k_probe_ex2(int iters, float* out)
     for (int c = 0; c < kProbeChains; ++c) x[c] = 0.1f * (float)c + 1e-3f * (float)(threadIdx.x & 31);
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int c = 0; c < kProbeChains; ++c) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(x[c]));
+        for (int c = 0; c < kProbeChains; ++c) {
+            const float nx = __uint_as_float(__float_as_uint(x[c]) | 0x80000000u);
+            asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(x[c]) : "f"(nx));
+        }
 #pragma unroll
-        for (int c = 0; c < kProbeChains; ++c) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(x[c]));
+        for (int c = 0; c < kProbeChains; ++c) {
+            const float nx = __uint_as_float(__float_as_uint(x[c]) | 0x80000000u);
+            asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(x[c]) : "f"(nx));
+        }
     }
     float s = 0.f;
 #pragma unroll
@@ -67,7 +73,9 @@ __global__ void __launch_bounds__(256) k_probe_ex2(int iters, float* out)
     if (s == 12345.f) out[threadIdx.x] = s;
 }
 
-// rcp.approx.ftz.f32 chains: x alternates between x0 and 1 / x0.
+// rcp.approx.ftz.f32 chains: x = 1 / x', x' = x with its lowest mantissa bit
+// flipped by a logic operation (two reciprocals in a row could otherwise be
+// simplified away); x stays near x0 and 1 / x0.
 __global__ void __launch_bounds__(256) k_probe_rcp(int iters, float* out)
 {
     float x[kProbeChains];
@@ -75,9 +83,15 @@ __global__ void __launch_bounds__(256) k_probe_rcp(int iters, float* out)
     for (int c = 0; c < kProbeChains; ++c) x[c] = 1.5f + 0.1f * (float)c + 1e-3f * (float)(threadIdx.x & 31);
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int c = 0; c < kProbeChains; ++c) asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(x[c]));
+        for (int c = 0; c < kProbeChains; ++c) {
+            const float nx = __uint_as_float(__float_as_uint(x[c]) ^ 1u);
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(x[c]) : "f"(nx));
+        }
 #pragma unroll
-        for (int c = 0; c < kProbeChains; ++c) asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(x[c]));
+        for (int c = 0; c < kProbeChains; ++c) {
+            const float nx = __uint_as_float(__float_as_uint(x[c]) ^ 1u);
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(x[c]) : "f"(nx));
+        }
     }
     float s = 0.f;
 #pragma unroll
