@@ -30,7 +30,7 @@ namespace splat {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 15;
+constexpr int kSortItems = 16;
 constexpr int kSortPart = kSortThreads * kSortItems;  // keys per partition
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
@@ -38,6 +38,7 @@ constexpr int kScanPart = kScanThreads * kScanItems;
 constexpr int kDupChunk = 2048;  // instance slots per duplicate work item
 constexpr int kDupThreads = 256;
 
+constexpr int kLookWindow = 8;  // predecessors a look-back thread reads per step
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
@@ -243,25 +244,42 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
         st_relaxed(my, (ticket == 0 ? kFlagPrefix : kFlagAgg) | cnt);
         if (a.lb_next) a.lb_next[ticket * kRadix + d] = 0;
         s_dstart[d] = block_excl_scan256(cnt, s_tmp, nullptr);
-        // decoupled look-back for digit d
+        // decoupled look-back for digit d, kLookWindow predecessors per step
+        // (independent loads): all partitions of a pass usually run in one wave,
+        // so a walk of one predecessor per L2 round trip would make the last
+        // partition wait for about half the partition count of round trips
         uint32_t excl = 0;
         if (ticket > 0) {
-            int64_t j = ticket - 1;
+            int64_t j = ticket - 1;  // nearest predecessor not yet added
             int64_t spins = 0;
             for (;;) {
-                const uint32_t s = ld_relaxed(a.lb + j * kRadix + d);
-                const uint32_t flag = s & ~kValMask;
-                if (flag == 0) {
+                uint32_t w[kLookWindow];
+#pragma unroll
+                for (int q = 0; q < kLookWindow; ++q)
+                    w[q] = j - q >= 0 ? ld_relaxed(a.lb + (j - q) * kRadix + d) : kFlagPrefix;
+                // add the published words from the nearest one back, up to and
+                // including the first inclusive prefix, or up to the first word
+                // not yet published
+                int q = 0;
+                bool found = false;
+#pragma unroll
+                for (int t = 0; t < kLookWindow; ++t) {
+                    if (found || q < t) continue;  // stopped at an earlier word
+                    const uint32_t flag = w[t] & ~kValMask;
+                    if (flag == 0) continue;       // not yet published: q stays at t
+                    excl += w[t] & kValMask;
+                    q = t + 1;
+                    found = flag == kFlagPrefix;
+                }
+                if (found) break;
+                j -= q;
+                if (q == 0) {
                     if (++spins > a.spin_limit) {
                         set_status(a.status, SPLAT_ERR_TIMEOUT, a.stage, ticket);
                         break;
                     }
                     if (spins > 64) __nanosleep(64);
-                    continue;
                 }
-                excl += s & kValMask;
-                if (flag == kFlagPrefix || j == 0) break;
-                --j;
             }
             st_relaxed(my, kFlagPrefix | ((excl + cnt) & kValMask));
         }
@@ -369,30 +387,47 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(ScanArgs a)
         unsigned long long running;
         const unsigned long long texcl = block_excl_scan256_u64(tsum, s_tmp64, &running);
         const unsigned long long agg = running;
-        if (tid == 0) {
+        if (tid < 32) {
+            // decoupled look-back by one warp: lane l reads predecessor j - l, so
+            // one round trip covers 32 of them (all partitions usually run in one
+            // wave, and a walk of one predecessor per round trip would make the
+            // last partition wait for about half the partition count of them)
+            const int lane = tid;
             unsigned long long excl = 0;
-            st_relaxed64(a.lb + ticket, (ticket == 0 ? kP : kA) | agg);
+            if (lane == 0) st_relaxed64(a.lb + ticket, (ticket == 0 ? kP : kA) | agg);
             if (ticket > 0) {
-                int64_t j = ticket - 1, spins = 0;
+                int64_t j = ticket - 1, spins = 0;  // nearest predecessor not yet added
                 for (;;) {
-                    const unsigned long long s = ld_relaxed64(a.lb + j);
+                    const bool in = j - lane >= 0;
+                    const unsigned long long s = in ? ld_relaxed64(a.lb + (j - lane)) : kP;
                     const unsigned long long flag = s & ~kM;
-                    if (flag == 0) {
+                    // the published words from the nearest one back, up to and
+                    // including the first inclusive prefix or up to the first
+                    // word not yet published
+                    const unsigned pend = __ballot_sync(0xffffffffu, flag == 0);
+                    const unsigned pref = __ballot_sync(0xffffffffu, flag == kP);
+                    const int first_pend = pend ? __ffs(pend) - 1 : 32;
+                    const int first_pref = pref ? __ffs(pref) - 1 : 32;
+                    const bool found = first_pref < first_pend;
+                    const int take = found ? first_pref + 1 : first_pend;
+                    unsigned long long v = lane < take ? (s & kM) : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    excl += v;
+                    if (found) break;
+                    j -= take;
+                    if (take == 0) {
                         if (++spins > a.spin_limit) {
-                            set_status(a.status, SPLAT_ERR_TIMEOUT, SPLAT_STAGE_SCAN, ticket);
+                            if (lane == 0) set_status(a.status, SPLAT_ERR_TIMEOUT, SPLAT_STAGE_SCAN, ticket);
                             break;
                         }
                         if (spins > 64) __nanosleep(64);
-                        continue;
                     }
-                    excl += s & kM;
-                    if (flag == kP || j == 0) break;
-                    --j;
                 }
-                st_relaxed64(a.lb + ticket, kP | ((excl + agg) & kM));
+                if (lane == 0) st_relaxed64(a.lb + ticket, kP | ((excl + agg) & kM));
             }
-            s_excl = excl;
-            if (ticket == parts - 1) {
+            if (lane == 0) s_excl = excl;
+            if (lane == 0 && ticket == parts - 1) {
                 const int64_t K = (int64_t)(excl + agg);
                 *a.n_instances = K;
                 if (a.n_needed) *a.n_needed = K;
