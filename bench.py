@@ -453,23 +453,25 @@ def run_ours(args, rank, local, world):
     dom = max(stages, key=lambda s: stages[s])
     pipes = measure_pipe_peaks(dev, local)
     fp32_peak = pipes["fp32_peak_tflops"]
-    mufu_peak = pipes["mufu_peak_tops"]
     # operation counts per pair: the kernels' own source (FLOPS_EVAL / FLOPS_BLEND)
     # and the survey's round figures (about 15 FP32 operations per evaluated pair
     # in the forward, about 60 in the backward)
     survey_flops = {"composite_fwd": SURVEY_OPS["composite_fwd"] * fe, "composite_bwd": SURVEY_OPS["composite_bwd"] * be}
-    # MUFU operations: one base-2 exponential per evaluated pair in both kernels,
-    # plus one reciprocal per evaluated pair in the backward
-    mufu_ops = {"composite_fwd": fe, "composite_bwd": 2 * be}
+    # MUFU work: one base-2 exponential per evaluated pair in both kernels, plus
+    # one reciprocal per evaluated pair in the backward, each at its own
+    # measured rate; mufu_frac is the share of the kernel's time the unit needs
+    mufu_ops = {"composite_fwd": (fe, 0), "composite_bwd": (be, be)}
 
     def alu_entry(st, ms):
         a = flops[st] / (ms / 1e3) / 1e12
         a_s = survey_flops[st] / (ms / 1e3) / 1e12
-        m = mufu_ops[st] / (ms / 1e3) / 1e12
+        n_ex2, n_rcp = mufu_ops[st]
+        mufu_s = n_ex2 / (pipes["ex2"] * 1e12) + n_rcp / (pipes["rcp"] * 1e12)
         return {"bound": "alu", "achieved": round(a, 2), "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": round(a / fp32_peak, 4), "achieved_survey_count": round(a_s, 2),
-                "frac_survey_count": round(a_s / fp32_peak, 4), "mufu_tops": round(m, 3),
-                "mufu_frac": round(m / mufu_peak, 4)}
+                "frac_survey_count": round(a_s / fp32_peak, 4),
+                "mufu_tops": round((n_ex2 + n_rcp) / (ms / 1e3) / 1e12, 3),
+                "mufu_frac": round(mufu_s / (ms / 1e3), 4)}
 
     if dom in flops:
         roofline = dict(alu_entry(dom, stages[dom]), kernel=dom, traffic=measured_traffic(dom, V),
@@ -522,6 +524,7 @@ def run_ours(args, rank, local, world):
         "stage_roofline": stage_roof,
         "composite_pairs": pairs,
         "pipe_peaks": pipes,
+        "error_vs_oracle": workload_errors("headline"),
         "fp32_peak_measured": {"tflops": fp32_peak, "sm_mhz": pipes["clocks"].get("sm_mhz"),
                                "ffma_tflops": pipes["ffma"], "ffma2_tflops": pipes["ffma2"]},
         "clocks": clk,
@@ -541,14 +544,30 @@ def run_ours(args, rank, local, world):
 # The other batched configurations, reported beside the headline (their
 # parity is checked by the workload tests): a 500k-Gaussian arc of 8 cameras
 # at mixed resolutions in FP32, and 1M Gaussians over 4 views at 2704x2028 with
-# BF16 storage.
+# BF16 and with FP16 storage.
 WORKLOADS = (
     ("arc 500k (70% 3D), 8 views at 1352x1014 / 676x507, FP32",
      dict(seed=2, n=500_000, frac4=0.3, n_views=8), "float32"),
     ("arc 1M (60% 3D), 4 views at 2704x2028, BF16",
      dict(seed=3, n=1_000_000, frac4=0.4, n_views=4, full=(2704, 2028, 2920.0), half=(2704, 2028, 2920.0)),
      "bfloat16"),
+    ("arc 1M (60% 3D), 4 views at 2704x2028, FP16",
+     dict(seed=3, n=1_000_000, frac4=0.4, n_views=4, full=(2704, 2028, 2920.0), half=(2704, 2028, 2920.0)),
+     "float16"),
 )
+
+
+def workload_errors(name):
+    """The errors against the FP64 oracle that the GPU parity test of this
+    workload measured (profiles/precision_workloads.json, written from its
+    report): per view RGB max-abs and per tensor gradient rel-L2 on the stored
+    values, and for half storage also against the FP32 originals."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "precision_workloads.json")) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    return d.get("workloads", {}).get(name)
 
 
 def run_workloads(dev, steps=20, warmup=3):
@@ -584,7 +603,8 @@ def run_workloads(dev, steps=20, warmup=3):
                      "mpixel_per_s": round(sum(R.pix) / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 3),
                      "views": R.V, "gaussians": G.n, "storage": dt, "instances_K": R.instances(),
                      "autotune": {"ppl_fwd": tune["ppl_fwd"], "ppl_bwd": tune["ppl_bwd"]},
-                     "l2": "flushed before each step", "steps": steps}
+                     "l2": "flushed before each step", "steps": steps,
+                     "error_vs_oracle": workload_errors(name)}
         del gs, R, G, target
         torch.cuda.empty_cache()
     return res

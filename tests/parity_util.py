@@ -8,7 +8,9 @@ relative distance of every decision to its threshold; these helpers turn that
 into masks of pixels / Gaussians whose result is not unique at FP32 and
 count them.  Everything else must match within the stated tolerance.
 """
+import json
 import math
+import os
 
 import numpy as np
 
@@ -33,6 +35,19 @@ EPS_PIXEL = {"power": 1e-5, "alpha": 5e-5, "stop": 5e-5, "tie": 1e-6, "tie3": 1e
 EPS_CLAMP = 5e-5      # alpha clamp at 0.99: a kink of the gradient only
 EPS_GRAD_GAUSS = 3e-5  # Jacobian clamp, rgb clamp: kinks of one Gaussian's gradient
 RGB_TOL = 2e-4        # max-abs on colours in [0, 1]
+# Bound of the pixels set aside as not unique at FP32 among n compared:
+# FRAGILE_FRAC n + FRAGILE_SLACK.  A pixel is set aside when one of the
+# decisions along its walk lies within its window (a few times that decision's
+# FP32 error) of its threshold, so the expected count grows with the
+# decisions per walk: measured 0.04-0.09% of the small scenes' images and up
+# to about 1% of the dense full-size samples.  The bounds are about three
+# times that, so that an oracle margin that sets aside too much fails.
+FRAGILE_FRAC = {"small": 0.003, "dense": 0.01}
+FRAGILE_SLACK = 3
+
+
+def fragile_bound(n, kind="small"):
+    return FRAGILE_FRAC[kind] * n + FRAGILE_SLACK
 GRAD_RTOL = 1e-3      # relative L2 per gradient tensor
 
 
@@ -154,6 +169,17 @@ def grad_fragile_pixels(ref):
 def grad_fragile_gaussians(P):
     """Gaussians whose own gradient has a kink within its window (Jacobian clamp, rgb clamp)."""
     return P["margin_grad"] < EPS_GRAD_GAUSS
+
+
+def report(case, **rec):
+    """Prints one JSON record of a parity measurement (fragile counts, errors)
+    and appends it to the file named by SPLAT_PARITY_REPORT when that is set."""
+    line = json.dumps(dict(case=case, **rec))
+    print(line)
+    path = os.environ.get("SPLAT_PARITY_REPORT")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(line + "\n")
 
 
 def rel_l2(a, b):

@@ -5,6 +5,7 @@ result is unique at FP32; parameter gradients 1e-3 relative L2 per tensor;
 sorted per-tile instance lists bit-exact when both sides sort the same keys.
 """
 import ctypes as C
+import os
 
 import numpy as np
 import pytest
@@ -13,8 +14,8 @@ import torch
 import oracle as O
 from paper_2505_13215_gb300 import abi, raster, scenes
 
-from parity_util import (GRAD_RTOL, RGB_TOL, fragile_gaussians, fragile_pixels, grad_fragile_gaussians,
-                         grad_fragile_pixels, rel_l2)
+from parity_util import (GRAD_RTOL, RGB_TOL, fragile_bound, fragile_gaussians, fragile_pixels, grad_fragile_gaussians,
+                         grad_fragile_pixels, rel_l2, report)
 
 pytestmark = pytest.mark.gpu
 
@@ -212,23 +213,27 @@ def test_bin_sort_end_to_end_lists(small):
 
 def check_image(R, P, ref, view, v=0, check_last=False):
     """RGB and final T against the oracle on the pixels unique at FP32; `last` (an
-    index into the tile list) only when the lists are the oracle's full rectangles."""
+    index into the tile list) only when the lists are the oracle's full rectangles.
+    The pixels set aside are counted, reported and bounded (fragile_bound)."""
     img = R.image(v).cpu().numpy().reshape(3, -1).astype(np.float64)
     T = R.plane(v, R.final_T).cpu().numpy().reshape(-1)
     last = R.plane(v, R.last).cpu().numpy().reshape(-1)
     frag = fragile_pixels(P, ref, view)
     err = np.abs(img - ref["rgb"])[:, ~frag]
-    assert err.max() <= RGB_TOL, "rgb max-abs %.3g" % err.max()
+    note = "fragile pixels %d of %d" % (int(frag.sum()), frag.size)
+    report(os.environ.get("PYTEST_CURRENT_TEST", "check_image").split(" ")[0], view=v, pixels=int(frag.size),
+           fragile=int(frag.sum()), rgb_maxabs=float(err.max()))
+    assert frag.sum() <= fragile_bound(frag.size), note
+    assert err.max() <= RGB_TOL, "rgb max-abs %.3g; %s" % (err.max(), note)
     if check_last:
-        np.testing.assert_array_equal(last[~frag], ref["last"][~frag])
-    np.testing.assert_allclose(T[~frag], ref["T"][~frag], rtol=1e-4, atol=1e-6)
+        np.testing.assert_array_equal(last[~frag], ref["last"][~frag], err_msg=note)
+    np.testing.assert_allclose(T[~frag], ref["T"][~frag], rtol=1e-4, atol=1e-6, err_msg=note)
     return frag.mean(), err.max()
 
 
 def test_composite_fwd_matches_oracle(small):
     scene, views, G, R, P, ref = small
     frac, err = check_image(R, P, ref, views[0])
-    assert frac < 0.01, "fragile pixels %.4f" % frac
 
 
 def test_composite_fwd_full_rectangles_last_index(small):
@@ -451,8 +456,7 @@ def test_batched_views_match_oracle():
     refs = [O.render(scene, v) for v in views]
     for v in range(3):
         check_projection(R, Ps[v], v)
-        frac, _ = check_image(R, Ps[v], refs[v], views[v], v)
-        assert frac < 0.02
+        check_image(R, Ps[v], refs[v], views[v], v)
     dls = loss_grad(R, refs, Ps, views, seed=4)
     check_grads(R, G, scene, Ps, views, dls)
 
@@ -483,9 +487,11 @@ def test_full_size_sampled_pixels_and_gradients(big):
     ref = O.render(scene, view, pixels=pix)
     img = R.image(0).cpu().numpy().reshape(3, -1)[:, pix]
     frag = fragile_pixels(P, ref, view, pix)
-    assert frag.mean() < 0.05
     err = np.abs(img - ref["rgb"])[:, ~frag]
-    assert err.max() <= RGB_TOL, err.max()
+    note = "fragile pixels %d of %d" % (int(frag.sum()), len(pix))
+    report("full size sampled", pixels=len(pix), fragile=int(frag.sum()), rgb_maxabs=float(err.max()))
+    assert frag.sum() <= fragile_bound(len(pix), "dense"), note
+    assert err.max() <= RGB_TOL, "rgb max-abs %.3g; %s" % (err.max(), note)
     # gradient of a loss on the sampled, unique pixels only
     sel = pix[~frag & ~grad_fragile_pixels(ref)]
     g = np.zeros((3, view.W * view.H))

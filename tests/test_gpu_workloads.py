@@ -30,7 +30,8 @@ import bench
 import oracle as O
 from paper_2505_13215_gb300 import abi, autotune, raster, scenes
 
-from parity_util import (GRAD_RTOL, RGB_TOL, fragile_pixels, grad_fragile_gaussians, grad_fragile_pixels,
+from parity_util import (GRAD_RTOL, RGB_TOL, fragile_bound, fragile_pixels, grad_fragile_gaussians, grad_fragile_pixels,
+                         report,
                          rel_l2)
 
 pytestmark = pytest.mark.gpu
@@ -39,13 +40,25 @@ F3 = raster.FIELDS3
 F4 = raster.FIELDS4
 
 
-def _report(name, rec):
-    path = os.environ.get("SPLAT_PARITY_REPORT")
-    line = json.dumps(dict(case=name, **rec))
-    print(line)
-    if path:
-        with open(path, "a") as fh:
-            fh.write(line + "\n")
+def _report(name, rec, bench_name=None):
+    """Prints and records the measurement; with SPLAT_PRECISION_DIGEST set, also
+    files it under the bench's name of the workload in that JSON digest (the
+    errors bench.py attaches to its workload entries)."""
+    report(name, **rec)
+    path = os.environ.get("SPLAT_PRECISION_DIGEST")
+    if path and bench_name:
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+        except (OSError, ValueError):
+            d = {}
+        d.setdefault("how", "tests/test_gpu_workloads.py: the workload's graphed step against the FP64 oracle at "
+                            "seeded sample pixels of every view (RGB max-abs over the pixels unique at FP32) and "
+                            "the gradients of a loss on those pixels (rel-L2 per tensor); half storage also "
+                            "against the oracle on the FP32 originals")
+        d.setdefault("workloads", {})[bench_name] = rec
+        with open(path, "w") as fh:
+            json.dump(d, fh, indent=1, sort_keys=True)
 
 
 @pytest.fixture(autouse=True)
@@ -54,7 +67,7 @@ def _restore_launch_shape():
     abi.splat_set_pixels_per_lane(8, 8)
 
 
-def graph_parity(name, scene, views, dtype, n_pix, seed, fragile_max, quant_ref=False):
+def graph_parity(name, scene, views, dtype, n_pix, seed, quant_ref=False, bench_name=None):
     G = raster.Gaussians.from_scene(scene, "cuda", dtype=dtype)
     R = raster.Rasterizer(G.n3, G.n4, views, keep_keys=False)
     target = torch.zeros_like(R.rgb)
@@ -84,7 +97,7 @@ def graph_parity(name, scene, views, dtype, n_pix, seed, fragile_max, quant_ref=
             ref32 = O.render(scene, view, pixels=pix)
             rec["rgb_maxabs_vs_fp32_params"] = float(np.abs(got - ref32["rgb"]).max())
         per_view.append(rec)
-        assert frag.mean() < fragile_max, rec
+        assert frag.sum() <= fragile_bound(len(pix), "dense"), rec
         assert rec["rgb_maxabs"] <= RGB_TOL, rec
         # loss on the sampled pixels whose value and gradient are unique at FP32
         sel = pix[~frag & ~grad_fragile_pixels(ref)]
@@ -119,8 +132,20 @@ def graph_parity(name, scene, views, dtype, n_pix, seed, fragile_max, quant_ref=
         keep = ~(bad3 if k in F3 else bad4)
         if keep.sum():
             grads[k] = rel_l2(a[keep], tot[k][keep])
-    _report(name, {"dtype": str(dtype).replace("torch.", ""), "instances": R.instances(),
-                   "ppl": [tune["ppl_fwd"], tune["ppl_bwd"]], "views": per_view, "grad_rel_l2": grads})
+    rec = {"dtype": str(dtype).replace("torch.", ""), "instances": R.instances(),
+           "ppl": [tune["ppl_fwd"], tune["ppl_bwd"]], "views": per_view, "grad_rel_l2": grads}
+    if quant_ref:
+        # the error of the storage rounding itself: the same loss against the
+        # oracle on the FP32 originals (a statement, not a tolerance)
+        tot32 = None
+        for view, g in zip(views, dls):
+            r = O.render_bwd(scene, view, g)
+            r.pop("dproj")
+            tot32 = r if tot32 is None else {k: tot32[k] + r[k] for k in tot32}
+        rec["grad_rel_l2_vs_fp32_params"] = {
+            k: rel_l2(R.grads[k].cpu().numpy().astype(np.float64)[~(bad3 if k in F3 else bad4)],
+                      tot32[k][~(bad3 if k in F3 else bad4)]) for k in grads}
+    _report(name, rec, bench_name)
     for k, e in grads.items():
         assert e <= GRAD_RTOL, "%s rel-L2 %.3g (all: %s)" % (k, e, grads)
 
@@ -131,13 +156,13 @@ def test_bench_workload_in_its_graph():
     scene, base = scenes.video_scene(seed=1, n3=bench.N3, n4=bench.N4, W=bench.W, H=bench.H)
     views = scenes.jittered_views(base[0], 4, seed=bench.rank_seed(0))
     graph_parity("video 300k, 4 views 1352x1014, bf16", scene, views, torch.bfloat16, n_pix=400, seed=11,
-                 fragile_max=0.06)
+                 quant_ref=True, bench_name="headline")
 
 
 def test_arc_500k_eight_mixed_views_fp32():
     scene, views = scenes.arc_scene(seed=2, n=500_000, frac4=0.3, n_views=8)
     graph_parity("arc 500k, 8 views 1352x1014 / 676x507, fp32", scene, views, torch.float32, n_pix=200,
-                 seed=12, fragile_max=0.06)
+                 seed=12, bench_name=bench.WORKLOADS[0][0])
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
@@ -145,4 +170,5 @@ def test_1m_gaussians_4k_four_views_half_storage(dtype):
     full = (2704, 2028, 2920.0)
     scene, views = scenes.arc_scene(seed=3, n=1_000_000, frac4=0.4, n_views=4, full=full, half=full)
     graph_parity("arc 1M, 4 views 2704x2028, %s" % str(dtype).replace("torch.", ""), scene, views, dtype,
-                 n_pix=200, seed=13, fragile_max=0.08, quant_ref=True)
+                 n_pix=200, seed=13, quant_ref=True,
+                 bench_name=bench.WORKLOADS[1 if dtype == torch.bfloat16 else 2][0])
