@@ -382,8 +382,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     }
 }
 
-// Gradient sums over the warp's 32 lanes of a batch of up to kRedBatch = 7
-// Gaussians.  Each lane leaves its sums (negated: the walk accumulates minus
+// Gradient sums over the warp's 32 lanes of a group of up to kRedBatch = 7
+// consecutive Gaussians of the walk (Gaussian q of the group in slot q, a
+// compile-time index of the unrolled group).  Each lane leaves its sums (negated: the walk accumulates minus
 // each quantity) in shared memory as 16 float4 groups of 32 lanes:
 //   group 2 q     = (S dx W0, W1, S dx^2 W0, S dx W1)   of Gaussian q
 //   group 2 q + 1 = (W2, W0, dr, dg)                    of Gaussian q
@@ -404,14 +405,16 @@ struct BwdOccupancy {
     static constexpr int kMinBlocks = PPL >= 8 ? 16 : 20;
 };
 
-__device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint32_t pend_row, int pend_j,
-                                                const float4* sf, float* dproj, int lane)
+// Reduction of a group of consecutive staged Gaussians j0, j0 - 1, ..,
+// j0 - nq + 1 held in slots 0 .. nq - 1; slot q is added to dproj when bit q of
+// `used` is set (some pixel of the warp blended that Gaussian).
+__device__ __forceinline__ void flush_group(const float4* red, int nq, unsigned used, int j0, const float4* sf,
+                                            const uint32_t* srow, float* dproj, int lane)
 {
     __syncwarp();
     const int gi = lane >> 1, h = lane & 1;
     float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
     if (gi < 2 * nq || gi == 14 || (gi == 15 && nq > 4)) {
-        // source lane 16 h + (i ^ x): the quarter-warp's loads fall in distinct banks
         const float4* col = red + gi * 32 + 16 * h;
         const int x = lane & 7;
 #pragma unroll
@@ -425,23 +428,20 @@ __device__ __forceinline__ void flush_reduction(const float4* red, int nq, uint3
     s0.y += __shfl_xor_sync(0xffffffffu, s0.y, 1);
     s1.x += __shfl_xor_sync(0xffffffffu, s1.x, 1);
     s1.y += __shfl_xor_sync(0xffffffffu, s1.y, 1);
-    // Gaussian of this lane: gi / 2 for the h = 0 (group) lanes, gi for the
-    // h = 1 (blue-channel) lanes
     const int q = h ? gi : gi >> 1;
-    const int src = q < kRedBatch ? q : 0;
-    const uint32_t row = __shfl_sync(0xffffffffu, pend_row, src);
-    const int jv = __shfl_sync(0xffffffffu, pend_j, src);
-    const int bl = 28 + 2 * (q >> 2);  // a lane holding the blue sums of Gaussians 4 (q / 4) ..
+    const int bl = 28 + 2 * (q >> 2);
     const float b0 = __shfl_sync(0xffffffffu, s0.x, bl & 31), b1 = __shfl_sync(0xffffffffu, s0.y, bl & 31);
     const float b2 = __shfl_sync(0xffffffffu, s1.x, bl & 31), b3 = __shfl_sync(0xffffffffu, s1.y, bl & 31);
-    if (q < nq) {
+    if (q < nq && ((used >> q) & 1u)) {
+        const int jv = j0 - q;
+        const uint32_t row = srow[jv];
         if (h == 0) {
             const float4 f1 = sf[jv * kFeat + 1], f2 = sf[jv * kFeat + 2];
             float4 out;
-            if ((gi & 1) == 0) {  // dpx, dpy, da, db with the natural-unit conic (a, b, c)
+            if ((gi & 1) == 0) {
                 const float ca = kLn2x2 * f1.x, cb = 0.5f * kLn2x2 * f1.z, cc = kLn2x2 * f2.x;
                 out = make_float4(ca * s0.x + cb * s0.y, cc * s0.y + cb * s0.x, 0.5f * s1.x, s1.y);
-            } else {  // dc, dalpha_max = W0 / alpha_max (unclamped pairs only), dr, dg
+            } else {
                 out = make_float4(0.5f * s0.x, s0.y / f2.z, -s1.x, -s1.y);
             }
             atomicAdd((float4*)(dproj + (int64_t)row * 12) + (gi & 1), out);
@@ -624,59 +624,56 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
         cur_row = next_row;
         if (bi >= 2) next_row = vals[b - 64u + lane];
         const int n = (int)min(32u, end - b);
-        int nq = 0;            // Gaussians waiting in the reduction buffer
-        uint32_t pend_row = 0; // lane q: row of waiting Gaussian q
-        int pend_j = 0;        // lane q: its slot in the staged batch
         // one vote per batch: does any staged Gaussian reach the 0.99 clamp
         const bool clamp_batch = __any_sync(0xffffffffu, lane < n && sf[lane * kFeat + 4].w >= kClampFree);
         auto walk = [&](auto clamp_tag) {
             constexpr bool CL = decltype(clamp_tag)::value;
-            for (int j = n - 1; j >= 0; --j) {
-                const int li = 32 * bi + j;  // position in the tile list
-                if (li <= act) {  // (warp-uniform) pixels whose last contributor is at li or later switch on
-                    int nxt = -1;
+            // groups of kRedBatch consecutive Gaussians, back to front; Gaussian
+            // j0 - q of a group sums into reduction slot q
+            for (int j0 = n - 1; j0 >= 0; j0 -= kRedBatch) {
+                unsigned used = 0;
 #pragma unroll
-                    for (int k = 0; k < PPL; ++k) {
-                        const float nr = -(y0f + (float)(2 * k));
-                        const int lk = last[k];
-                        if (li < lk) {
-                            if (k & 1) nrow[k >> 1].y = nr;
-                            else nrow[k >> 1].x = nr;
-                        } else {
-                            nxt = max(nxt, lk - 1);
+                for (int q = 0; q < kRedBatch; ++q) {
+                    const int j = j0 - q;
+                    if (j < 0) break;  // warp-uniform: the last group of a batch may be short
+                    const int li = 32 * bi + j;  // position in the tile list
+                    if (li <= act) {  // (warp-uniform) pixels whose last contributor is at li or later switch on
+                        int nxt = -1;
+#pragma unroll
+                        for (int k = 0; k < PPL; ++k) {
+                            const float nr = -(y0f + (float)(2 * k));
+                            const int lk = last[k];
+                            if (li < lk) {
+                                if (k & 1) nrow[k >> 1].y = nr;
+                                else nrow[k >> 1].x = nr;
+                            } else {
+                                nxt = max(nxt, lk - 1);
+                            }
                         }
+                        act = __reduce_max_sync(0xffffffffu, nxt);
                     }
-                    act = __reduce_max_sync(0xffffffffu, nxt);
-                }
-                if (STATS) {
+                    if (STATS) {
 #pragma unroll
-                    for (int k = 0; k < PPL; ++k) n_eval += li < last[k];
+                        for (int k = 0; k < PPL; ++k) n_eval += li < last[k];
+                    }
+                    Feat f;
+                    load_feat(sf + j * kFeat, f);
+                    const ColTerms ct = col_terms(f, nu);
+                    BwdSums S;
+                    const bool any = bwd_gaussian<NP, CL, STATS>(f, ct, T, nQ, G, nrow, S, n_blend);
+                    used |= (unsigned)any << q;
+                    const float W0 = S.W0.x + S.W0.y, W1 = S.W1.x + S.W1.y;
+                    float4* slot = red + 2 * q * 32 + lane;
+                    const float dx = ct.dx.x, dxW0 = dx * W0;
+                    slot[0] = make_float4(dxW0, W1, dx * dxW0, dx * W1);
+                    slot[32] = make_float4(S.W2.x + S.W2.y, W0, S.r.x + S.r.y, S.g.x + S.g.y);
+                    ((float*)(red + (14 + (q >> 2)) * 32 + lane))[q & 3] = S.b.x + S.b.y;
                 }
-                Feat f;
-                load_feat(sf + j * kFeat, f);
-                const ColTerms ct = col_terms(f, nu);
-                BwdSums S;
-                const bool any = bwd_gaussian<NP, CL, STATS>(f, ct, T, nQ, G, nrow, S, n_blend);
-                if (!any) continue;  // warp-uniform
-                const float W0 = S.W0.x + S.W0.y, W1 = S.W1.x + S.W1.y;
-                float4* slot = red + 2 * nq * 32 + lane;
-                const float dx = ct.dx.x, dxW0 = dx * W0;
-                slot[0] = make_float4(dxW0, W1, dx * dxW0, dx * W1);
-                slot[32] = make_float4(S.W2.x + S.W2.y, W0, S.r.x + S.r.y, S.g.x + S.g.y);
-                ((float*)(red + (14 + (nq >> 2)) * 32 + lane))[nq & 3] = S.b.x + S.b.y;
-                if (lane == nq) {
-                    pend_row = s_row[warp][j];
-                    pend_j = j;
-                }
-                if (++nq == kRedBatch) {
-                    flush_reduction(red, nq, pend_row, pend_j, sf, dproj, lane);
-                    nq = 0;
-                }
+                if (used) flush_group(red, min(kRedBatch, j0 + 1), used, j0, sf, s_row[warp], dproj, lane);
             }
         };
         if (clamp_batch) walk(std::integral_constant<bool, true>());
         else walk(std::integral_constant<bool, false>());
-        if (nq) flush_reduction(red, nq, pend_row, pend_j, sf, dproj, lane);
         __syncwarp();
     }
     cp_async_wait_all();  // no copy may land in shared memory after the CTA has left
