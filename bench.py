@@ -366,6 +366,8 @@ def run_ours(args, rank, local, world):
     # the plain path gets its own tuned launch shape (pixels per lane of the
     # compositing kernels), chosen on its first view like the batched path's
     plain_tune = autotune.tune(plain[0][0], G32, plain[0][1])
+    for Rv, _ in plain[1:]:
+        Rv.set_options(ppl_fwd=plain_tune["ppl_fwd"], ppl_bwd=plain_tune["ppl_bwd"])
     plain_steps = max(2, args.steps // 2)
     for Rv, tv in plain:
         Rv.step(G32, tv)
@@ -382,7 +384,6 @@ def run_ours(args, rank, local, world):
         Rv.check("plain FP32 path")
     plain_s = sum(a.elapsed_time(b) for a, b in pe) / 1e3
     plain_value = aggregate(V * plain_steps, plain_s, dev)[0]
-    abi.splat_set_pixels_per_lane(tune["ppl_fwd"], tune["ppl_bwd"])
     del plain
 
     # ---- end to end: pinned host inputs in, loss out, every step.  Two input sets
@@ -437,12 +438,12 @@ def run_ours(args, rank, local, world):
 
     # ---- pair counts of the compositing kernels (one instrumented step, untimed) ----
     counters = torch.zeros(4, dtype=torch.int64, device=dev)
-    abi.splat_set_stats(counters.data_ptr())
+    R.set_options(stats=counters.data_ptr())
     try:
         R.step(G, target)
         torch.cuda.synchronize()
     finally:
-        abi.splat_set_stats(None)
+        R.set_options(stats=None)
     fe, fb, be, bb = [int(x) for x in counters.cpu().tolist()]
     pairs = {"fwd_evaluated": fe, "fwd_blended": fb, "bwd_evaluated": be, "bwd_blended": bb}
     flops = {"composite_fwd": FLOPS_EVAL * fe + (FLOPS_BLEND["composite_fwd"] - FLOPS_EVAL) * fb,
@@ -838,7 +839,7 @@ def run_profile(args):
     G = raster.Gaussians.from_scene(scene, "cuda", dtype=dt)
     R = raster.Rasterizer(G.n3, G.n4, views, keep_keys=False)
     ppl_f, ppl_b = (int(x) for x in args.ppl.split(","))
-    abi.splat_set_pixels_per_lane(ppl_f, ppl_b)
+    R.set_options(ppl_fwd=ppl_f, ppl_bwd=ppl_b)
     R.autotune_capacity(G)
     target = torch.rand(R.rgb.shape, device="cuda")
     for _ in range(args.profile):

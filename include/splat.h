@@ -478,20 +478,69 @@ splat_status splat_l1_loss(const float *img, const float *target, int64_t n, flo
 splat_status splat_bin_sort_noalloc(const splat_proj *proj, const splat_view *views, int V, splat_bins *bins,
                                     int32_t *status, void *stream);
 
+/*
+ * Per-call tuning (host memory), for callers that run several rasterizers
+ * with different settings in one process, or from several threads: the
+ * *_opts entry points below take it as their second-to-last argument and
+ * otherwise behave exactly as the entry point of the same name without the
+ * suffix.  Each field at its "library default" value (0, -1 or NULL as noted)
+ * takes the library-wide setting of the matching splat_set_* call, so a
+ * zero-initialised struct with tile_sort = tile_cull = spin_limit = -1 (or a
+ * NULL pointer) changes nothing.  Out-of-range values are rejected with
+ * SPLAT_ERR_INVALID_ARG (splat_workspace_size_opts returns 0).  The struct is
+ * read during the call only.
+ */
+typedef struct {
+    int32_t pixels_per_lane_fwd;  /* 2, 4 or 8; 0: library default (splat_set_pixels_per_lane) */
+    int32_t pixels_per_lane_bwd;  /* 2, 4 or 8; 0: library default                           */
+    int32_t tile_sort;            /* 0 automatic, 1 radix, 2 binned; -1: splat_set_tile_sort */
+    int32_t tile_cull;            /* 0 off, 1 on; -1: splat_set_tile_cull                    */
+    int64_t spin_limit;           /* >= 0; -1: splat_set_spin_limit                          */
+    unsigned long long *stats;    /* device uint64[4] (see splat_set_stats); NULL: library default */
+} splat_options;
+
+/* splat_workspace_size for a call made with the given options (the sort's
+ * workspace depends on the tile sort mode). */
+size_t splat_workspace_size_opts(int op, int64_t N3, int64_t N4, int V, const int32_t *W, const int32_t *H,
+                                 int64_t capacity, const splat_options *opt);
+
+/* splat_bin_sort with per-call options (tile_sort, tile_cull, spin_limit). */
+splat_status splat_bin_sort_opts(const splat_proj *proj, const splat_view *views, int V, splat_bins *bins,
+                                 int32_t *status, void *workspace, size_t workspace_bytes, const splat_options *opt,
+                                 void *stream);
+
+/* splat_composite_fwd with per-call options (pixels_per_lane_fwd, stats). */
+splat_status splat_composite_fwd_opts(const splat_proj *proj, const splat_bins *bins, const splat_view *views, int V,
+                                      splat_image *img, int32_t *status, const splat_options *opt, void *stream);
+
+/* splat_composite_fwd_l1 with per-call options (pixels_per_lane_fwd, stats). */
+splat_status splat_composite_fwd_l1_opts(const splat_proj *proj, const splat_bins *bins, const splat_view *views,
+                                         int V, splat_image *img, const float *target, float scale, float *dL_drgb,
+                                         float *loss, int32_t *status, const splat_options *opt, void *stream);
+
+/* splat_composite_bwd with per-call options (pixels_per_lane_bwd, stats). */
+splat_status splat_composite_bwd_opts(const splat_proj *proj, const splat_bins *bins, const splat_view *views, int V,
+                                      const splat_image *img, const float *dL_drgb, const splat_g3 *g3,
+                                      const splat_g4 *g4, splat_grads3 *dg3, splat_grads4 *dg4, float *dproj,
+                                      uint32_t flags, int32_t *status, void *workspace, size_t workspace_bytes,
+                                      const splat_options *opt, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *splat_status_string(int32_t code);
 
 /*
  * Test knob: maximum polling iterations of every bounded device-side wait
  * (decoupled look-back of the scans and sorts).  0 gives up at the first
- * not-yet-published predecessor.  Default 1 << 22.  Host-side global.
+ * not-yet-published predecessor.  Default 1 << 22.  Host-side global: the
+ * library default that splat_options.spin_limit = -1 takes.
  */
 void splat_set_spin_limit(int64_t iterations);
 
 /*
  * Tuning knob of the compositing kernels: pixels each lane owns (2, 4 or 8,
  * evaluated in pairs; one warp covers 32 x that many pixels of a 16x16
- * tile).  Other values are ignored.  Default 8 / 8.  Host-side global; the results do not depend
+ * tile).  Other values are ignored.  Default 8 / 8.  Host-side global (the library default
+ * of splat_options.pixels_per_lane_*); the results do not depend
  * on it beyond floating-point summation order of the gradients.
  */
 void splat_set_pixels_per_lane(int fwd, int bwd);
@@ -505,7 +554,8 @@ int64_t splat_launch_count(void);
  * same):  0 = automatic (default), 1 = tile-digit radix passes over the
  * instance list, 2 = binned partition with per-tile shared-memory counters
  * (used automatically when every view has at most 40960 tiles).  Host-side
- * global; splat_workspace_size depends on it.
+ * global (the library default of splat_options.tile_sort); splat_workspace_size
+ * depends on it.
  */
 void splat_set_tile_sort(int mode);
 
@@ -524,7 +574,7 @@ void splat_set_tile_sort(int mode);
  * pixel skips the dropped pairs, or stops before reaching
  * them, so images and gradients do not change; the lists (and so `last`) are
  * shorter.  Off: every tile of the rectangle, as in splat_bin_sort's key
- * definition.  Host-side global.
+ * definition.  Host-side global (the library default of splat_options.tile_cull).
  */
 void splat_set_tile_cull(int on);
 
@@ -533,7 +583,8 @@ void splat_set_tile_cull(int on);
  * compositing launches use an instrumented variant that adds the numbers of
  * pixel-Gaussian pairs evaluated (power computed) and blended by the forward
  * (counters 0, 1) and by the backward (2, 3).  NULL (default) turns it off.
- * Host-side global; the caller zeroes the counters.
+ * Host-side global (the library default of splat_options.stats); the caller
+ * zeroes the counters.
  */
 void splat_set_stats(unsigned long long *dev_counters);
 

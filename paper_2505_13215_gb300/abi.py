@@ -83,6 +83,16 @@ class splat_adam_hyper(C.Structure):
                 ("beta2", C.c_float), ("eps", C.c_float), ("step", C.c_int32)]
 
 
+class splat_options(C.Structure):
+    _fields_ = [("pixels_per_lane_fwd", C.c_int32), ("pixels_per_lane_bwd", C.c_int32), ("tile_sort", C.c_int32),
+                ("tile_cull", C.c_int32), ("spin_limit", C.c_int64), ("stats", C.c_void_p)]
+
+
+def options(ppl_fwd=0, ppl_bwd=0, tile_sort=-1, tile_cull=-1, spin_limit=-1, stats=None) -> splat_options:
+    """A splat_options whose unset fields take the library-wide defaults."""
+    return splat_options(int(ppl_fwd), int(ppl_bwd), int(tile_sort), int(tile_cull), int(spin_limit), stats)
+
+
 class splat_densify_rule(C.Structure):
     _fields_ = [("grad_threshold", C.c_float), ("dense_scale", C.c_float), ("min_opacity", C.c_float),
                 ("split_shrink", C.c_float)]
@@ -136,6 +146,19 @@ EXPORTS = {
     "splat_densify_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int]),
     "splat_workspace_size_4d": (C.c_size_t, [C.c_int, C.c_int64, C.c_int]),
     "splat_peak_probe": (C.c_double, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "splat_workspace_size_opts": (C.c_size_t, [C.c_int, C.c_int64, C.c_int64, C.c_int, _P(C.c_int32), _P(C.c_int32),
+                                               C.c_int64, _P(splat_options)]),
+    "splat_bin_sort_opts": (C.c_int, [_P(splat_proj), _P(splat_view), C.c_int, _P(splat_bins), C.c_void_p, C.c_void_p,
+                                      C.c_size_t, _P(splat_options), C.c_void_p]),
+    "splat_composite_fwd_opts": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int, _P(splat_image),
+                                           C.c_void_p, _P(splat_options), C.c_void_p]),
+    "splat_composite_fwd_l1_opts": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int,
+                                              _P(splat_image), C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, _P(splat_options), C.c_void_p]),
+    "splat_composite_bwd_opts": (C.c_int, [_P(splat_proj), _P(splat_bins), _P(splat_view), C.c_int, _P(splat_image),
+                                           C.c_void_p, _P(splat_g3), _P(splat_g4), _P(splat_grads3),
+                                           _P(splat_grads4), C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
+                                           C.c_size_t, _P(splat_options), C.c_void_p]),
 }
 
 _lib = None
@@ -291,3 +314,26 @@ SPLAT_PROBE_FFMA, SPLAT_PROBE_FFMA2, SPLAT_PROBE_EX2, SPLAT_PROBE_RCP = 0, 1, 2,
 def splat_peak_probe(kind, blocks, iters, out, stream):
     """Launches one pipe-throughput probe; returns its operation count (-1 on error)."""
     return float(lib().splat_peak_probe(int(kind), int(blocks), int(iters), out, stream))
+
+
+def splat_workspace_size_opts(op, N3, N4, W, H, capacity, opt):
+    return lib().splat_workspace_size_opts(int(op), int(N3), int(N4), len(W), _i32arr(W), _i32arr(H), int(capacity),
+                                           opt)
+
+
+def splat_bin_sort_opts(proj, views, V, bins, status, ws, ws_bytes, opt, stream):
+    return lib().splat_bin_sort_opts(proj, views, V, bins, status, ws, ws_bytes, opt, stream)
+
+
+def splat_composite_fwd_opts(proj, bins, views, V, img, status, opt, stream):
+    return lib().splat_composite_fwd_opts(proj, bins, views, V, img, status, opt, stream)
+
+
+def splat_composite_fwd_l1_opts(proj, bins, views, V, img, target, scale, dL, loss, status, opt, stream):
+    return lib().splat_composite_fwd_l1_opts(proj, bins, views, V, img, target, scale, dL, loss, status, opt, stream)
+
+
+def splat_composite_bwd_opts(proj, bins, views, V, img, dL, g3, g4, dg3, dg4, dproj, flags, status, ws, ws_bytes, opt,
+                             stream):
+    return lib().splat_composite_bwd_opts(proj, bins, views, V, img, dL, g3, g4, dg3, dg4, dproj, flags, status, ws,
+                                          ws_bytes, opt, stream)

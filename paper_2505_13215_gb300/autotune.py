@@ -3,7 +3,8 @@
 Chooses the tile-instance capacity (the measured instance count K times a
 headroom) and the pixels-per-lane of the two compositing kernels (which sets
 how many warps share a 16x16 tile), by timing full training steps of the
-actual workload with CUDA events.  Results are cached in a JSON file keyed by
+actual workload with CUDA events.  The choice is applied to the tuned
+rasterizer only (its splat_options), and cached in a JSON file keyed by
 (views, resolutions, Gaussian counts, storage dtype).
 """
 from __future__ import annotations
@@ -13,8 +14,6 @@ import os
 from typing import Dict, Optional
 
 import torch
-
-from . import abi
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 CANDIDATES = ((8, 8), (8, 4), (4, 8), (4, 4), (2, 4))
@@ -68,17 +67,17 @@ def tune(R, G, target: torch.Tensor, reps: int = 6, rounds: int = 2, use_cache: 
     K = R.autotune_capacity(G)
     if key in cache:
         c = cache[key]
-        abi.splat_set_pixels_per_lane(c["ppl_fwd"], c["ppl_bwd"])
+        R.set_options(ppl_fwd=c["ppl_fwd"], ppl_bwd=c["ppl_bwd"])
         c = dict(c, K=K, capacity=R.capacity, cached=True)
         return c
     ms = {c: float("inf") for c in candidates}
     for _ in range(rounds):
         for fwd, bwd in candidates:
-            abi.splat_set_pixels_per_lane(fwd, bwd)
+            R.set_options(ppl_fwd=fwd, ppl_bwd=bwd)
             ms[(fwd, bwd)] = min(ms[(fwd, bwd)], _time_steps(R, G, target, reps))
     (fwd, bwd), t = min(ms.items(), key=lambda kv: kv[1])
     best = {"ppl_fwd": fwd, "ppl_bwd": bwd, "ms": t}
-    abi.splat_set_pixels_per_lane(best["ppl_fwd"], best["ppl_bwd"])
+    R.set_options(ppl_fwd=best["ppl_fwd"], ppl_bwd=best["ppl_bwd"])
     cache[key] = best
     if use_cache:
         _save(cache)

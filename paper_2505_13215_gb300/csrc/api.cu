@@ -14,9 +14,7 @@ cudaError_t launch_slice_project(const splat_g3&, const splat_g4&, const ViewBat
 cudaError_t launch_adjoint(const splat_g3&, const splat_g4&, const ViewBatch&, const splat_proj&, const float*,
                            const splat_grads3&, const splat_grads4&, int32_t*, int, const LaunchCtx&);
 cudaError_t launch_bin_sort(const splat_proj&, const ViewBatch&, const splat_bins&, int32_t*, void*, const LaunchCtx&);
-size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY);
-void set_tile_sort_mode(int mode);
-void set_tile_cull(int on);
+size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY, int tile_sort);
 cudaError_t launch_composite_fwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
                                  const L1Fuse*, int32_t*, int, unsigned long long*, const LaunchCtx&);
 cudaError_t launch_composite_bwd(const splat_proj&, const splat_bins&, const ViewBatch&, const splat_image&,
@@ -82,13 +80,28 @@ cudaError_t launch_dens_stats(const StatArgs&, const LaunchCtx&);
 cudaError_t launch_densify(const DensSet&, const DensSet&, const DensRule&, void*, int32_t*, const LaunchCtx&);
 size_t densify_workspace(int64_t n3, int64_t cap3, int64_t n4, int64_t cap4, int sh_time4);
 
+// Library-wide defaults of the tuning (splat_set_*); a call's splat_options
+// overrides them field by field.
 static std::atomic<int64_t> g_spin_limit{1ll << 22};
 std::atomic<int64_t> g_launches{0};
 static std::atomic<int> g_ppl_fwd{8}, g_ppl_bwd{8};
+static std::atomic<int> g_tile_sort{0}, g_tile_cull{1};
 static std::atomic<unsigned long long*> g_stats{nullptr};
 static int g_num_sms[64];
 
-LaunchCtx launch_ctx(void* stream)
+static bool ppl_ok(int p) { return p == 2 || p == 4 || p == 8; }
+
+// A caller's options are valid when every field is its "default" value or in range.
+static bool valid_options(const splat_options* o)
+{
+    if (!o) return true;
+    return (o->pixels_per_lane_fwd == 0 || ppl_ok(o->pixels_per_lane_fwd)) &&
+           (o->pixels_per_lane_bwd == 0 || ppl_ok(o->pixels_per_lane_bwd)) &&
+           o->tile_sort >= -1 && o->tile_sort <= 2 && o->tile_cull >= -1 && o->tile_cull <= 1 &&
+           o->spin_limit >= -1;
+}
+
+LaunchCtx launch_ctx(void* stream, const splat_options* opt)
 {
     LaunchCtx c;
     c.stream = (cudaStream_t)stream;
@@ -102,6 +115,19 @@ LaunchCtx launch_ctx(void* stream)
     }
     c.num_sms = g_num_sms[dev];
     c.spin_limit = g_spin_limit.load();
+    c.tile_sort = g_tile_sort.load();
+    c.tile_cull = g_tile_cull.load();
+    c.ppl_fwd = g_ppl_fwd.load();
+    c.ppl_bwd = g_ppl_bwd.load();
+    c.stats = g_stats.load();
+    if (opt) {
+        if (opt->pixels_per_lane_fwd) c.ppl_fwd = opt->pixels_per_lane_fwd;
+        if (opt->pixels_per_lane_bwd) c.ppl_bwd = opt->pixels_per_lane_bwd;
+        if (opt->tile_sort >= 0) c.tile_sort = opt->tile_sort;
+        if (opt->tile_cull >= 0) c.tile_cull = opt->tile_cull;
+        if (opt->spin_limit >= 0) c.spin_limit = opt->spin_limit;
+        if (opt->stats) c.stats = opt->stats;
+    }
     return c;
 }
 
@@ -203,17 +229,16 @@ int64_t splat_launch_count(void) { return g_launches.load(); }
 
 void splat_set_spin_limit(int64_t iterations) { g_spin_limit.store(iterations < 0 ? 0 : iterations); }
 
-void splat_set_tile_sort(int mode) { set_tile_sort_mode(mode); }
+void splat_set_tile_sort(int mode) { g_tile_sort.store((mode >= 0 && mode <= 2) ? mode : 0); }
 
 void splat_set_stats(unsigned long long* dev_counters) { g_stats.store(dev_counters); }
 
-void splat_set_tile_cull(int on) { set_tile_cull(on); }
+void splat_set_tile_cull(int on) { g_tile_cull.store(on ? 1 : 0); }
 
 void splat_set_pixels_per_lane(int fwd, int bwd)
 {
-    auto ok = [](int p) { return p == 2 || p == 4 || p == 8; };
-    if (ok(fwd)) g_ppl_fwd.store(fwd);
-    if (ok(bwd)) g_ppl_bwd.store(bwd);
+    if (ppl_ok(fwd)) g_ppl_fwd.store(fwd);
+    if (ppl_ok(bwd)) g_ppl_bwd.store(bwd);
 }
 
 const char* splat_status_string(int32_t code)
@@ -243,7 +268,14 @@ int64_t splat_total_tiles(int V, const int32_t* W, const int32_t* H)
 size_t splat_workspace_size(int op, int64_t N3, int64_t N4, int V, const int32_t* W, const int32_t* H,
                             int64_t capacity)
 {
-    if (N3 < 0 || N4 < 0 || capacity < 0 || capacity > SPLAT_MAX_INSTANCES) return 0;
+    return splat_workspace_size_opts(op, N3, N4, V, W, H, capacity, nullptr);
+}
+
+size_t splat_workspace_size_opts(int op, int64_t N3, int64_t N4, int V, const int32_t* W, const int32_t* H,
+                                 int64_t capacity, const splat_options* opt)
+{
+    if (N3 < 0 || N4 < 0 || capacity < 0 || capacity > SPLAT_MAX_INSTANCES || !valid_options(opt)) return 0;
+    const int tile_sort = (opt && opt->tile_sort >= 0) ? opt->tile_sort : g_tile_sort.load();
     const int64_t N = N3 + N4;
     size_t sort_b = 0, bwd_b = 0, conv_b = 0;
     if (op == SPLAT_OP_BIN_SORT || op == SPLAT_OP_ALL || op == SPLAT_OP_COMPOSITE_BWD) {
@@ -255,7 +287,7 @@ size_t splat_workspace_size(int op, int64_t N3, int64_t N4, int V, const int32_t
             TX[v] = (W[v] + kTile - 1) / kTile;
             TY[v] = (H[v] + kTile - 1) / kTile;
         }
-        sort_b = bin_sort_workspace(N * V, capacity, V, TX, TY);
+        sort_b = bin_sort_workspace(N * V, capacity, V, TX, TY, tile_sort);
     }
     if (op == SPLAT_OP_COMPOSITE_BWD || op == SPLAT_OP_ALL) bwd_b = ((size_t)N * V * 48 + 255) & ~(size_t)255;
     if (op == SPLAT_OP_CONVERT || op == SPLAT_OP_ALL) conv_b = convert_workspace(N4, 4, 0);
@@ -297,16 +329,23 @@ splat_status splat_slice_project(const splat_g3* g3p, const splat_g4* g4p, const
 splat_status splat_bin_sort(const splat_proj* proj, const splat_view* views, int V, splat_bins* bins,
                             int32_t* status, void* workspace, size_t workspace_bytes, void* stream)
 {
-    if (!valid_views(views, V) || !valid_proj(proj, V) || !host_valid_bins(bins) || !status)
+    return splat_bin_sort_opts(proj, views, V, bins, status, workspace, workspace_bytes, nullptr, stream);
+}
+
+splat_status splat_bin_sort_opts(const splat_proj* proj, const splat_view* views, int V, splat_bins* bins,
+                                 int32_t* status, void* workspace, size_t workspace_bytes, const splat_options* opt,
+                                 void* stream)
+{
+    if (!valid_views(views, V) || !valid_proj(proj, V) || !host_valid_bins(bins) || !status || !valid_options(opt))
         return SPLAT_ERR_INVALID_ARG;
     int TX[SPLAT_MAX_VIEWS], TY[SPLAT_MAX_VIEWS];
     for (int v = 0; v < V; ++v) {
         TX[v] = (views[v].W + kTile - 1) / kTile;
         TY[v] = (views[v].H + kTile - 1) / kTile;
     }
-    const size_t need = bin_sort_workspace(proj->n * V, bins->capacity, V, TX, TY);
+    const LaunchCtx ctx = launch_ctx(stream, opt);
+    const size_t need = bin_sort_workspace(proj->n * V, bins->capacity, V, TX, TY, ctx.tile_sort);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return SPLAT_ERR_INVALID_ARG;
-    const LaunchCtx ctx = launch_ctx(stream);
     const ViewBatch vb = make_batch(views, V);
     return cuda_status(launch_bin_sort(*proj, vb, *bins, status, workspace, ctx));
 }
@@ -314,28 +353,42 @@ splat_status splat_bin_sort(const splat_proj* proj, const splat_view* views, int
 splat_status splat_composite_fwd(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
                                  splat_image* img, int32_t* status, void* stream)
 {
-    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !status) return SPLAT_ERR_INVALID_ARG;
+    return splat_composite_fwd_opts(proj, bins, views, V, img, status, nullptr, stream);
+}
+
+splat_status splat_composite_fwd_opts(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
+                                      splat_image* img, int32_t* status, const splat_options* opt, void* stream)
+{
+    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !status || !valid_options(opt))
+        return SPLAT_ERR_INVALID_ARG;
     if (!img->rgb || !img->final_T || !img->last || !bins->ranges || (bins->capacity > 0 && !bins->vals))
         return SPLAT_ERR_INVALID_ARG;
-    const LaunchCtx ctx = launch_ctx(stream);
+    const LaunchCtx ctx = launch_ctx(stream, opt);
     const ViewBatch vb = make_batch(views, V);
-    return cuda_status(
-        launch_composite_fwd(*proj, *bins, vb, *img, nullptr, status, g_ppl_fwd.load(), g_stats.load(), ctx));
+    return cuda_status(launch_composite_fwd(*proj, *bins, vb, *img, nullptr, status, ctx.ppl_fwd, ctx.stats, ctx));
 }
 
 splat_status splat_composite_fwd_l1(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
                                     splat_image* img, const float* target, float scale, float* dL_drgb, float* loss,
                                     int32_t* status, void* stream)
 {
-    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !status) return SPLAT_ERR_INVALID_ARG;
+    return splat_composite_fwd_l1_opts(proj, bins, views, V, img, target, scale, dL_drgb, loss, status, nullptr,
+                                       stream);
+}
+
+splat_status splat_composite_fwd_l1_opts(const splat_proj* proj, const splat_bins* bins, const splat_view* views,
+                                         int V, splat_image* img, const float* target, float scale, float* dL_drgb,
+                                         float* loss, int32_t* status, const splat_options* opt, void* stream)
+{
+    if (!valid_views(views, V) || !valid_proj(proj, V) || !bins || !img || !status || !valid_options(opt))
+        return SPLAT_ERR_INVALID_ARG;
     if (!img->rgb || !img->final_T || !img->last || !bins->ranges || (bins->capacity > 0 && !bins->vals))
         return SPLAT_ERR_INVALID_ARG;
     if (!target || !dL_drgb || !loss || !std::isfinite(scale)) return SPLAT_ERR_INVALID_ARG;
-    const LaunchCtx ctx = launch_ctx(stream);
+    const LaunchCtx ctx = launch_ctx(stream, opt);
     const ViewBatch vb = make_batch(views, V);
     const L1Fuse l1{target, scale, dL_drgb, loss};
-    return cuda_status(
-        launch_composite_fwd(*proj, *bins, vb, *img, &l1, status, g_ppl_fwd.load(), g_stats.load(), ctx));
+    return cuda_status(launch_composite_fwd(*proj, *bins, vb, *img, &l1, status, ctx.ppl_fwd, ctx.stats, ctx));
 }
 
 splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
@@ -343,6 +396,17 @@ splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins,
                                  splat_grads3* dg3, splat_grads4* dg4, float* dproj, uint32_t flags, int32_t* status,
                                  void* workspace, size_t workspace_bytes, void* stream)
 {
+    return splat_composite_bwd_opts(proj, bins, views, V, img, dL_drgb, g3p, g4p, dg3, dg4, dproj, flags, status,
+                                    workspace, workspace_bytes, nullptr, stream);
+}
+
+splat_status splat_composite_bwd_opts(const splat_proj* proj, const splat_bins* bins, const splat_view* views, int V,
+                                      const splat_image* img, const float* dL_drgb, const splat_g3* g3p,
+                                      const splat_g4* g4p, splat_grads3* dg3, splat_grads4* dg4, float* dproj,
+                                      uint32_t flags, int32_t* status, void* workspace, size_t workspace_bytes,
+                                      const splat_options* opt, void* stream)
+{
+    if (!valid_options(opt)) return SPLAT_ERR_INVALID_ARG;
     const splat_g3 g3 = g3_or_empty(g3p);
     const splat_g4 g4 = g4_or_empty(g4p);
     bool same = true;
@@ -379,12 +443,12 @@ splat_status splat_composite_bwd(const splat_proj* proj, const splat_bins* bins,
     } else if (!aligned(dp, 16)) {
         return SPLAT_ERR_INVALID_ARG;
     }
-    const LaunchCtx ctx = launch_ctx(stream);
+    const LaunchCtx ctx = launch_ctx(stream, opt);
     const ViewBatch vb = make_batch(views, V);
     if (!adj_only) {
         cudaError_t e = cudaMemsetAsync(dp, 0, dproj_bytes, ctx.stream);
         if (e != cudaSuccess) return SPLAT_ERR_CUDA;
-        e = launch_composite_bwd(*proj, *bins, vb, *img, dL_drgb, dp, status, g_ppl_bwd.load(), g_stats.load(), ctx);
+        e = launch_composite_bwd(*proj, *bins, vb, *img, dL_drgb, dp, status, ctx.ppl_bwd, ctx.stats, ctx);
         if (e != cudaSuccess) return SPLAT_ERR_CUDA;
     }
     if (stop2d) return SPLAT_OK;

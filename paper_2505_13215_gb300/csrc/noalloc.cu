@@ -20,7 +20,7 @@
 namespace splat {
 
 cudaError_t launch_bin_sort(const splat_proj&, const ViewBatch&, const splat_bins&, int32_t*, void*, const LaunchCtx&);
-size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY);
+size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY, int tile_sort);
 
 constexpr size_t kSplatNoallocScratchBytes = SPLAT_NOALLOC_SCRATCH_BYTES;
 
@@ -65,7 +65,8 @@ extern "C" splat_status splat_bin_sort_noalloc(const splat_proj* proj, const spl
         TX[v] = (views[v].W + kTile - 1) / kTile;
         TY[v] = (views[v].H + kTile - 1) / kTile;
     }
-    const size_t need = bin_sort_workspace(proj->n * V, bins->capacity, V, TX, TY);
+    const LaunchCtx ctx = launch_ctx(stream);  // the library-wide tuning (splat_set_*)
+    const size_t need = bin_sort_workspace(proj->n * V, bins->capacity, V, TX, TY, ctx.tile_sort);
     if (need > kSplatNoallocScratchBytes) return SPLAT_ERR_CAPACITY;  // larger than the fixed scratch
     cudaError_t err;
     void* scratch = scratch_for_current_device(&err);
@@ -87,6 +88,5 @@ extern "C" splat_status splat_bin_sort_noalloc(const splat_proj* proj, const spl
         pix += (int64_t)views[v].W * views[v].H;
     }
     vb.total_tiles = tiles;
-    const LaunchCtx ctx = launch_ctx(stream);
     return launch_bin_sort(*proj, vb, *bins, status, scratch, ctx) == cudaSuccess ? SPLAT_OK : SPLAT_ERR_CUDA;
 }

@@ -1,6 +1,6 @@
 // project.cu -- slice + cull + EWA projection + SH colour (forward, one thread
-// per Gaussian, all views) and its adjoint (one thread per Gaussian, summed
-// over views without atomics).
+// per Gaussian, all views) and its adjoint (a group of lanes per Gaussian, one
+// per view, summed over views without atomics).
 //
 // Forward follows Alg. 1 CullGaussian / ProjGaussian4D / ProjGaussian3D:
 //   4D: R = R_l R_r (Eq. 4), M = R diag(exp s), Sigma_4D = M M^T.  With m_t the
@@ -136,6 +136,34 @@ __device__ __forceinline__ void sh_rgb(const void* sh_base, int64_t row, int T, 
     rgb[0] = r; rgb[1] = g; rgb[2] = b;
 }
 
+// w[k] += tw sum_c gc[c] c_kc for one block of coefficients (16 x 3, k*3 + c),
+// streamed from storage 16 bytes at a time (never all 48 in registers).
+template <int DT>
+__device__ __forceinline__ void sh_weights(const typename Storage<DT>::T* p, const float gc[3], float tw, float w[16])
+{
+    const float g0 = tw * gc[0], g1 = tw * gc[1], g2 = tw * gc[2];
+    auto add = [&](int e, float c) { w[e / 3] += (e % 3 == 0 ? g0 : (e % 3 == 1 ? g1 : g2)) * c; };
+    if constexpr (DT == SPLAT_F32) {
+        const float4* p4 = (const float4*)p;
+#pragma unroll
+        for (int qq = 0; qq < 12; ++qq) {
+            const float4 v = __ldg(p4 + qq);
+            add(4 * qq, v.x); add(4 * qq + 1, v.y); add(4 * qq + 2, v.z); add(4 * qq + 3, v.w);
+        }
+    } else {
+        const uint4* p4 = (const uint4*)p;
+#pragma unroll
+        for (int qq = 0; qq < 6; ++qq) {
+            const uint4 v = __ldg(p4 + qq);
+            const typename Storage<DT>::T* h = (const typename Storage<DT>::T*)&v;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                add(8 * qq + e, DT == SPLAT_BF16 ? __bfloat162float(((const __nv_bfloat16*)h)[e])
+                                                 : __half2float(((const __half*)h)[e]));
+        }
+    }
+}
+
 // View-independent geometry of one merged Gaussian.
 struct Geo {
     float mu[3];   // world mean (3D) or mu_x (4D)
@@ -236,7 +264,7 @@ __device__ __forceinline__ void at_time(const Geo& G, bool is4, float t, float m
 }
 
 template <int DT>
-__global__ void __launch_bounds__(128) k_slice_project(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj out,
+__global__ void __launch_bounds__(128, 7) k_slice_project(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj out,
                                                        int32_t* status)
 {
     const int64_t N = out.n;
@@ -416,44 +444,72 @@ __device__ __forceinline__ void normalise_backward(const float q[4], const float
     for (int k = 0; k < 4; ++k) out[k] = (g[k] - qn[k] * dot) * in;
 }
 
-constexpr int kAdjThreads = 128;  // threads per block of the adjoint (its shared accumulators)
+constexpr int kAdjThreads = 128;  // threads per block of the adjoint
 
-template <int DT>
-__global__ void __launch_bounds__(kAdjThreads) k_adjoint(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj proj,
+// One lane's share of the colour gradient, staged for its group: the view's
+// dL/drgb where the colour is not clamped (gc), the view's timestamp, and the
+// SH basis at the view direction.  The group sums dsh_n[k][c] = sum_v
+// cos(2 pi n t_v) gc_v[c] Y_v[k] from these.
+struct ShPart {
+    float4 gct;   // (gc_r, gc_g, gc_b, t_v); zero when the lane's view does not see the Gaussian
+    float4 Y[4];  // Y_0 .. Y_15
+};
+
+// View-parallel adjoint.  A warp takes 32 consecutive Gaussians at a time.
+// First, in L sub-batches of 32 / L Gaussians, a group of L lanes (L: the
+// view count rounded up to a power of two) per Gaussian, lane q chaining view
+// q's 2D gradients through the colour and the EWA projection; the group sums
+// its views -- the 15 view-summed quantities by shuffles, the SH gradient from
+// the staged ShPart (each lane writes 16 / L of the 16 SH functions, all time
+// blocks) -- and parks the 15 sums in shared memory.  Then every lane chains
+// one Gaussian's sums through the slicing / covariance and writes its other
+// gradients.  No atomics; the views' memory requests are independent of one
+// another, and the heavy view-independent chain runs on full warps.
+template <int DT, int L>
+__global__ void __launch_bounds__(kAdjThreads, 5) k_adjoint(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj proj,
                                                  const float* __restrict__ dproj, splat_grads3 dg3,
                                                  splat_grads4 dg4, int32_t* status)
 {
-    __shared__ float s_dsh[48 * kAdjThreads];  // SH gradient accumulators, thread-contiguous
+    static_assert(L == 1 || L == 2 || L == 4 || L == 8 || L == 16, "lanes per Gaussian");
+    constexpr int KPL = 16 / L;  // SH functions whose gradient a lane writes
+    constexpr int GPS = 32 / L;  // Gaussians per sub-batch of a warp
+    __shared__ ShPart s_part[kAdjThreads];
+    __shared__ float s_sum[kAdjThreads / 32][15][32];  // per warp: the 15 view sums of its 32 Gaussians
+    __shared__ ViewParams s_view[SPLAT_MAX_VIEWS];  // lanes of one warp read different views
     if (status_failed(status)) return;
-    using St = Storage<DT>;
+    for (int v = threadIdx.x; v < vb.V; v += blockDim.x) s_view[v] = vb.v[v];
+    __syncthreads();
     const int64_t N = proj.n;
     const int64_t n4 = g4.n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, q = threadIdx.x % L, warp = threadIdx.x >> 5;
+    const int gbase = threadIdx.x - q;  // first lane of the group
+    float (*sums)[32] = s_sum[warp];
+    // every lane of a warp takes the same number of trips (the group sums are warp collectives)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + warp * 32; c0 < N; c0 += stride) {
+      for (int sb = 0; sb < L; ++sb) {
+        const int slot = sb * GPS + lane / L;  // the Gaussian's lane in the chain phase
+        const int64_t i = c0 + slot;
+        const bool valid = i < N;
         const bool is4 = i < n4;
-        Geo G;
-        load_geo<DT>(g3, g4, i, is4, G);
-        const void* sh_base = is4 ? g4.sh : g3.sh;
-        const int64_t sh_row = is4 ? i : i - n4;
         const int Tn = is4 ? g4.sh_time : 0;  // time frequencies of the colour
-        const typename St::T* shp = (const typename St::T*)sh_base + sh_row * 48 * (Tn + 1);
-        // block 0's gradient in registers; blocks n >= 1 (weight cos(2 pi n t_v)) are summed in
-        // this thread's own rows of dg4.sh
-        float* dsh = s_dsh + threadIdx.x;  // dsh[k * kAdjThreads]: this thread's 48 accumulators
-#pragma unroll
-        for (int k = 0; k < 48; ++k) dsh[k * kAdjThreads] = 0.f;
-        for (int n = 1; n <= Tn; ++n) {
-            float4* shg = (float4*)(dg4.sh + (i * (Tn + 1) + n) * 48);
-            for (int k = 0; k < 12; ++k) shg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
         SymG GS = {0, 0, 0, 0, 0, 0};
         float gmu_sum[3] = {0, 0, 0};   // sum_v dL/dmu_v
         float gmu_dt[3] = {0, 0, 0};    // sum_v dL/dmu_v (t_v - mu_t)       (4D)
         float gal = 0.f;                // sum_v dL/dalpha_v p_v            (opacity)
         float gp_dt = 0.f, gp_dt2 = 0.f;// sum_v g_p p dt, sum_v g_p p dt^2/2 (4D)
-        for (int v = 0; v < vb.V; ++v) {
-            const int64_t row = v * N + i;
-            if (proj.radius[row] == 0) continue;
-            const ViewParams& vp = vb.v[v];
+        ShPart part;
+        part.gct = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) part.Y[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        Geo G;
+        const int v = q;
+        const int64_t row = (int64_t)v * N + i;
+        if (valid && v < vb.V && proj.radius[row] != 0) {
+            load_geo<DT>(g3, g4, i, is4, G);
+            const typename Storage<DT>::T* shp =
+                (const typename Storage<DT>::T*)(is4 ? g4.sh : g3.sh) + (is4 ? i : i - n4) * 48 * (Tn + 1);
+            const ViewParams& vp = s_view[v];
             const float4* dq = (const float4*)(dproj + row * 12);
             const float4 d0 = dq[0], d1 = dq[1], d2 = dq[2];
             const float dp[9] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w, d2.x};
@@ -463,33 +519,24 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(splat_g3 g3, splat_g4 g
             ewa_setup(vp, mu, G.S, e);
             float gmu[3] = {0.f, 0.f, 0.f};
             ewa_backward(vp, e, G.S, dp, gmu, GS);
-            // colour: rgb = max(0, 0.5 + sum_k sh_k Y_k(d)), d = (mu - cam)/|mu - cam|
+            // colour: rgb = max(0, 0.5 + sum_k sh_k Y_k(d)), d = (mu - cam)/|mu - cam|.  The
+            // forward stored max(0, rgb) from the same evaluation, so a channel is clamped
+            // exactly where its stored value is 0
             float d[3] = {mu[0] - vp.cam[0], mu[1] - vp.cam[1], mu[2] - vp.cam[2]};
             const float id = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             d[0] *= id; d[1] *= id; d[2] *= id;
-            float rgb[3], Y[16], c0[48];
-            sh_rgb<DT>(sh_base, sh_row, Tn, vp.t, d, rgb, Y, c0);
-            const float gc[3] = {rgb[0] > 0.f ? dp[6] : 0.f, rgb[1] > 0.f ? dp[7] : 0.f, rgb[2] > 0.f ? dp[8] : 0.f};
+            const float4 rd = ((const float4*)proj.rgb_depth)[row];
+            const float gc[3] = {rd.x > 0.f ? dp[6] : 0.f, rd.y > 0.f ? dp[7] : 0.f, rd.z > 0.f ? dp[8] : 0.f};
             float w[16];  // <dL/drgb, effective coefficients of Y_k at t>
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                w[k] = gc[0] * c0[3 * k + 0] + gc[1] * c0[3 * k + 1] + gc[2] * c0[3 * k + 2];
-                dsh[(k * 3 + 0) * kAdjThreads] += gc[0] * Y[k];
-                dsh[(k * 3 + 1) * kAdjThreads] += gc[1] * Y[k];
-                dsh[(k * 3 + 2) * kAdjThreads] += gc[2] * Y[k];
-            }
-            for (int n = 1; n <= Tn; ++n) {
-                const float tw = time_weight(n, vp.t);
-                float cn[48];
-                load_sh48<DT>(shp + 48 * n, cn);
-                float* shg = dg4.sh + (i * (Tn + 1) + n) * 48;
-                for (int k = 0; k < 16; ++k) {
-                    w[k] += tw * (gc[0] * cn[3 * k + 0] + gc[1] * cn[3 * k + 1] + gc[2] * cn[3 * k + 2]);
-                    shg[k * 3 + 0] += tw * gc[0] * Y[k];
-                    shg[k * 3 + 1] += tw * gc[1] * Y[k];
-                    shg[k * 3 + 2] += tw * gc[2] * Y[k];
-                }
-            }
+            for (int k = 0; k < 16; ++k) w[k] = 0.f;
+            sh_weights<DT>(shp, gc, 1.f, w);
+            for (int n = 1; n <= Tn; ++n) sh_weights<DT>(shp + 48 * n, gc, time_weight(n, vp.t), w);
+            float Y[16];
+            sh_basis(d[0], d[1], d[2], Y);
+            part.gct = make_float4(gc[0], gc[1], gc[2], vp.t);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) part.Y[k] = make_float4(Y[4 * k], Y[4 * k + 1], Y[4 * k + 2], Y[4 * k + 3]);
             float gdir[3];
             sh_basis_grad(d[0], d[1], d[2], w, gdir);
             const float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
@@ -497,181 +544,240 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(splat_g3 g3, splat_g4 g
             for (int k = 0; k < 3; ++k) gmu[k] += (gdir[k] - d[k] * dd) * id;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                gmu_sum[k] += gmu[k];
-                gmu_dt[k] += gmu[k] * dt;
+                gmu_sum[k] = gmu[k];
+                gmu_dt[k] = gmu[k] * dt;
             }
-            gal += dp[5] * p_t;
+            gal = dp[5] * p_t;
             const float gp = dp[5] * G.op * p_t;  // dL/dp times p
-            gp_dt += gp * dt;
-            gp_dt2 += gp * 0.5f * dt * dt;
+            gp_dt = gp * dt;
+            gp_dt2 = gp * 0.5f * dt * dt;
         }
+        // sums over the group's views
+        if (L > 1) {
+#pragma unroll
+            for (int o = 1; o < L; o <<= 1) {
+                auto add = [&](float& x) { x += __shfl_xor_sync(0xffffffffu, x, o); };
+                add(GS.xx); add(GS.xy); add(GS.xz); add(GS.yy); add(GS.yz); add(GS.zz);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    add(gmu_sum[k]);
+                    add(gmu_dt[k]);
+                }
+                add(gal); add(gp_dt); add(gp_dt2);
+            }
+        }
+        s_part[threadIdx.x] = part;
+        __syncwarp();
+        if (valid) {
+            // SH gradient of functions k0 .. k0 + KPL - 1, every time block
+            const int k0 = q * KPL;
+            float* shrow = (is4 ? dg4.sh + i * (Tn + 1) * 48 : dg3.sh + (i - n4) * 48) + 3 * k0;
+            for (int n = 0; n <= Tn; ++n) {
+                float acc[3 * KPL];
+#pragma unroll
+                for (int e = 0; e < 3 * KPL; ++e) acc[e] = 0.f;
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    const ShPart& pj = s_part[gbase + j];
+                    const float4 g = pj.gct;
+                    const float tw = n == 0 ? 1.f : time_weight(n, g.w);
+                    const float gr = tw * g.x, gg = tw * g.y, gb = tw * g.z;
+#pragma unroll
+                    for (int kk = 0; kk < KPL; ++kk) {
+                        const float4 y4 = pj.Y[(k0 + kk) >> 2];
+                        const int c = (k0 + kk) & 3;
+                        const float y = c == 0 ? y4.x : (c == 1 ? y4.y : (c == 2 ? y4.z : y4.w));
+                        acc[3 * kk + 0] += gr * y;
+                        acc[3 * kk + 1] += gg * y;
+                        acc[3 * kk + 2] += gb * y;
+                    }
+                }
+                float* out = shrow + n * 48;
+                if constexpr ((3 * KPL) % 4 == 0) {
+#pragma unroll
+                    for (int e = 0; e < 3 * KPL; e += 4)
+                        *(float4*)(out + e) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 3 * KPL; ++e) out[e] = acc[e];
+                }
+            }
+        }
+        if (q == 0) {
+            const float v15[15] = {GS.xx, GS.xy, GS.xz, GS.yy, GS.yz, GS.zz, gmu_sum[0], gmu_sum[1], gmu_sum[2],
+                                   gmu_dt[0], gmu_dt[1], gmu_dt[2], gal, gp_dt, gp_dt2};
+#pragma unroll
+            for (int e = 0; e < 15; ++e) sums[e][slot] = v15[e];
+        }
+        __syncwarp();  // s_part is rewritten in the next sub-batch, sums are read below
+      }
+        // every lane: the view-independent chain of one Gaussian's summed gradients
+        const int64_t i = c0 + lane;
+        if (i < N) {
+        const bool is4 = i < n4;
+        const SymG GS = {sums[0][lane], sums[1][lane], sums[2][lane], sums[3][lane], sums[4][lane], sums[5][lane]};
+        const float gmu_sum[3] = {sums[6][lane], sums[7][lane], sums[8][lane]};
+        const float gmu_dt[3] = {sums[9][lane], sums[10][lane], sums[11][lane]};
+        const float gal = sums[12][lane], gp_dt = sums[13][lane], gp_dt2 = sums[14][lane];
         if (is4) {
-            // Rebuild the 4D factors (view independent).
-            float m[4], ls[4], ql[4], qr[4];
-            load4<DT>(g4.mean, i, m);
-            load4<DT>(g4.log_scale, i, ls);
-            load4<DT>(g4.ql, i, ql);
-            load4<DT>(g4.qr, i, qr);
-            const float o = load1<DT>(g4.opacity, i);
-            float qln[4], qrn[4];
-            const float il = inv_norm4(ql), ir = inv_norm4(qr);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { qln[k] = ql[k] * il; qrn[k] = qr[k] * ir; }
-            float R[16], s[4], M[16];
-            rot4(qln, qrn, R);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s[k] = expf(ls[k]);
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) M[r * 4 + k] = R[r * 4 + k] * s[k];
-            const float* mt = &M[12];
-            const float n2 = mt[0] * mt[0] + mt[1] * mt[1] + mt[2] * mt[2] + mt[3] * mt[3];
-            const float in = rsqrtf(n2), in2 = 1.f / n2;
-            const float u[4] = {mt[0] * in, mt[1] * in, mt[2] * in, mt[3] * in};
-            float vx[3], B[12], b[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                vx[r] = M[r * 4 + 0] * u[0] + M[r * 4 + 1] * u[1] + M[r * 4 + 2] * u[2] + M[r * 4 + 3] * u[3];
-                b[r] = M[r * 4 + 0] * mt[0] + M[r * 4 + 1] * mt[1] + M[r * 4 + 2] * mt[2] + M[r * 4 + 3] * mt[3];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) B[r * 4 + k] = M[r * 4 + k] - vx[r] * u[k];
-            }
-            // Sigma3 = B B^T: G_B = 2 G_S B
-            const float Gs[9] = {GS.xx, GS.xy, GS.xz, GS.xy, GS.yy, GS.yz, GS.xz, GS.yz, GS.zz};
-            float GB[12];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    GB[r * 4 + k] = 2.f * (Gs[r * 3 + 0] * B[0 * 4 + k] + Gs[r * 3 + 1] * B[1 * 4 + k] +
-                                           Gs[r * 3 + 2] * B[2 * 4 + k]);
-            // B = M_x - (M_x u) u^T
-            float GBu[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) GBu[r] = GB[r * 4 + 0] * u[0] + GB[r * 4 + 1] * u[1] + GB[r * 4 + 2] * u[2] + GB[r * 4 + 3] * u[3];
-            float GM[16];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) GM[r * 4 + k] = GB[r * 4 + k] - GBu[r] * u[k];
-            float gu[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                gu[k] = -(M[0 * 4 + k] * GBu[0] + M[1 * 4 + k] * GBu[1] + M[2 * 4 + k] * GBu[2]) -
-                        (GB[0 * 4 + k] * vx[0] + GB[1 * 4 + k] * vx[1] + GB[2 * 4 + k] * vx[2]);
-            // mu3 = mu_x + M_x m_t dt / n2 (summed over views through gmu_dt)
-            const float a_b = gmu_dt[0] * b[0] + gmu_dt[1] * b[1] + gmu_dt[2] * b[2];
-            float gmt[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-#pragma unroll
-                for (int r = 0; r < 3; ++r) GM[r * 4 + k] += gmu_dt[r] * mt[k] * in2;
-                gmt[k] = (M[0 * 4 + k] * gmu_dt[0] + M[1 * 4 + k] * gmu_dt[1] + M[2 * 4 + k] * gmu_dt[2]) * in2;
-            }
-            float gn2 = -a_b * in2 * in2 + gp_dt2 * in2 * in2;
-            const float gmu_t = -(gmu_sum[0] * b[0] + gmu_sum[1] * b[1] + gmu_sum[2] * b[2]) * in2 + gp_dt * in2;
-            // u = m_t / |m_t|
-            const float ugu = u[0] * gu[0] + u[1] * gu[1] + u[2] * gu[2] + u[3] * gu[3];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) gmt[k] += (gu[k] - u[k] * ugu) * in + 2.f * mt[k] * gn2;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) GM[12 + k] = gmt[k];
-            // M = R diag(s)
-            float GR[16], gls[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float acc = 0.f;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    GR[r * 4 + k] = GM[r * 4 + k] * s[k];
-                    acc += GM[r * 4 + k] * R[r * 4 + k];
-                }
-                gls[k] = acc * s[k];
-            }
-            // R = L Rr:  G_L = G_R Rr^T,  G_Rr = L^T G_R
-            const float a = qln[0], bb = qln[1], c = qln[2], dd = qln[3];
-            const float p = qrn[0], q = qrn[1], rr = qrn[2], ss = qrn[3];
-            const float L[16] = {a, -bb, -c, -dd, bb, a, -dd, c, c, dd, a, -bb, dd, -c, bb, a};
-            const float Q[16] = {p, -q, -rr, -ss, q, p, ss, -rr, rr, -ss, p, q, ss, rr, -q, p};
-            float GL[16], GQ[16];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    GL[r * 4 + k] = GR[r * 4 + 0] * Q[k * 4 + 0] + GR[r * 4 + 1] * Q[k * 4 + 1] +
-                                    GR[r * 4 + 2] * Q[k * 4 + 2] + GR[r * 4 + 3] * Q[k * 4 + 3];
-                    GQ[r * 4 + k] = L[0 * 4 + r] * GR[0 * 4 + k] + L[1 * 4 + r] * GR[1 * 4 + k] +
-                                    L[2 * 4 + r] * GR[2 * 4 + k] + L[3 * 4 + r] * GR[3 * 4 + k];
-                }
-            const float gan[4] = {GL[0] + GL[5] + GL[10] + GL[15], -GL[1] + GL[4] - GL[11] + GL[14],
-                                  -GL[2] + GL[7] + GL[8] - GL[13], -GL[3] - GL[6] + GL[9] + GL[12]};
-            const float gbn[4] = {GQ[0] + GQ[5] + GQ[10] + GQ[15], -GQ[1] + GQ[4] + GQ[11] - GQ[14],
-                                  -GQ[2] - GQ[7] + GQ[8] + GQ[13], -GQ[3] + GQ[6] - GQ[9] + GQ[12]};
-            float gql[4], gqr[4];
-            normalise_backward(ql, gan, gql);
-            normalise_backward(qr, gbn, gqr);
-            const float sg = sigmoidf_(o);
-            ((float4*)dg4.mean)[i] = make_float4(gmu_sum[0], gmu_sum[1], gmu_sum[2], gmu_t);
-            ((float4*)dg4.log_scale)[i] = make_float4(gls[0], gls[1], gls[2], gls[3]);
-            ((float4*)dg4.ql)[i] = make_float4(gql[0], gql[1], gql[2], gql[3]);
-            ((float4*)dg4.qr)[i] = make_float4(gqr[0], gqr[1], gqr[2], gqr[3]);
-            dg4.opacity[i] = gal * sg * (1.f - sg);
-            float4* shg = (float4*)(dg4.sh + i * (Tn + 1) * 48);
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-                shg[k] = make_float4(dsh[(4 * k) * kAdjThreads], dsh[(4 * k + 1) * kAdjThreads],
-                                     dsh[(4 * k + 2) * kAdjThreads], dsh[(4 * k + 3) * kAdjThreads]);
-        } else {
-            const int64_t j = i - n4;
-            float q[4], ls[3];
-            load4<DT>(g3.quat, j, q);
-            load3<DT>(g3.log_scale, j, ls);
-            const float o = load1<DT>(g3.opacity, j);
-            const float iq = inv_norm4(q);
-            const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
-            float R[9], s[3], M[9];
-            quat_to_rot(w, x, y, z, R);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) s[k] = expf(ls[k]);
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) M[r * 3 + k] = R[r * 3 + k] * s[k];
-            const float Gs[9] = {GS.xx, GS.xy, GS.xz, GS.xy, GS.yy, GS.yz, GS.xz, GS.yz, GS.zz};
-            float GR[9], gls[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float acc = 0.f;
-#pragma unroll
+                // Rebuild the 4D factors (view independent).
+                float m[4], ls[4], ql[4], qr[4];
+                load4<DT>(g4.mean, i, m);
+                load4<DT>(g4.log_scale, i, ls);
+                load4<DT>(g4.ql, i, ql);
+                load4<DT>(g4.qr, i, qr);
+                const float o = load1<DT>(g4.opacity, i);
+                float qln[4], qrn[4];
+                const float il = inv_norm4(ql), ir = inv_norm4(qr);
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) { qln[k] = ql[k] * il; qrn[k] = qr[k] * ir; }
+                float R[16], s[4], M[16];
+                rot4(qln, qrn, R);
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) s[k] = expf(ls[k]);
+    #pragma unroll
+                for (int r = 0; r < 4; ++r)
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) M[r * 4 + k] = R[r * 4 + k] * s[k];
+                const float* mt = &M[12];
+                const float n2 = mt[0] * mt[0] + mt[1] * mt[1] + mt[2] * mt[2] + mt[3] * mt[3];
+                const float in = rsqrtf(n2), in2 = 1.f / n2;
+                const float u[4] = {mt[0] * in, mt[1] * in, mt[2] * in, mt[3] * in};
+                float vx[3], B[12], b[3];
+    #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    const float gm = 2.f * (Gs[r * 3 + 0] * M[0 * 3 + k] + Gs[r * 3 + 1] * M[1 * 3 + k] +
-                                            Gs[r * 3 + 2] * M[2 * 3 + k]);
-                    GR[r * 3 + k] = gm * s[k];
-                    acc += gm * R[r * 3 + k];
+                    vx[r] = M[r * 4 + 0] * u[0] + M[r * 4 + 1] * u[1] + M[r * 4 + 2] * u[2] + M[r * 4 + 3] * u[3];
+                    b[r] = M[r * 4 + 0] * mt[0] + M[r * 4 + 1] * mt[1] + M[r * 4 + 2] * mt[2] + M[r * 4 + 3] * mt[3];
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) B[r * 4 + k] = M[r * 4 + k] - vx[r] * u[k];
                 }
-                gls[k] = acc * s[k];
-            }
-            float g4v[4];
-            g4v[0] = GR[1] * (-2.f * z) + GR[2] * (2.f * y) + GR[3] * (2.f * z) + GR[5] * (-2.f * x) + GR[6] * (-2.f * y) + GR[7] * (2.f * x);
-            g4v[1] = GR[1] * (2.f * y) + GR[2] * (2.f * z) + GR[3] * (2.f * y) + GR[4] * (-4.f * x) + GR[5] * (-2.f * w) + GR[6] * (2.f * z) + GR[7] * (2.f * w) + GR[8] * (-4.f * x);
-            g4v[2] = GR[0] * (-4.f * y) + GR[1] * (2.f * x) + GR[2] * (2.f * w) + GR[3] * (2.f * x) + GR[5] * (2.f * z) + GR[6] * (-2.f * w) + GR[7] * (2.f * z) + GR[8] * (-4.f * y);
-            g4v[3] = GR[0] * (-4.f * z) + GR[1] * (-2.f * w) + GR[2] * (2.f * x) + GR[3] * (2.f * w) + GR[4] * (-4.f * z) + GR[5] * (2.f * y) + GR[6] * (2.f * x) + GR[7] * (2.f * y);
-            float gq[4];
-            normalise_backward(q, g4v, gq);
-            const float sg = sigmoidf_(o);
-            float* dm = dg3.mean + j * 3;
-            dm[0] = gmu_sum[0]; dm[1] = gmu_sum[1]; dm[2] = gmu_sum[2];
-            float* dl = dg3.log_scale + j * 3;
-            dl[0] = gls[0]; dl[1] = gls[1]; dl[2] = gls[2];
-            ((float4*)dg3.quat)[j] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-            dg3.opacity[j] = gal * sg * (1.f - sg);
-            float4* shg = (float4*)(dg3.sh + j * 48);
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-                shg[k] = make_float4(dsh[(4 * k) * kAdjThreads], dsh[(4 * k + 1) * kAdjThreads],
-                                     dsh[(4 * k + 2) * kAdjThreads], dsh[(4 * k + 3) * kAdjThreads]);
+                // Sigma3 = B B^T: G_B = 2 G_S B
+                const float Gs[9] = {GS.xx, GS.xy, GS.xz, GS.xy, GS.yy, GS.yz, GS.xz, GS.yz, GS.zz};
+                float GB[12];
+    #pragma unroll
+                for (int r = 0; r < 3; ++r)
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        GB[r * 4 + k] = 2.f * (Gs[r * 3 + 0] * B[0 * 4 + k] + Gs[r * 3 + 1] * B[1 * 4 + k] +
+                                               Gs[r * 3 + 2] * B[2 * 4 + k]);
+                // B = M_x - (M_x u) u^T
+                float GBu[3];
+    #pragma unroll
+                for (int r = 0; r < 3; ++r) GBu[r] = GB[r * 4 + 0] * u[0] + GB[r * 4 + 1] * u[1] + GB[r * 4 + 2] * u[2] + GB[r * 4 + 3] * u[3];
+                float GM[16];
+    #pragma unroll
+                for (int r = 0; r < 3; ++r)
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) GM[r * 4 + k] = GB[r * 4 + k] - GBu[r] * u[k];
+                float gu[4];
+    #pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    gu[k] = -(M[0 * 4 + k] * GBu[0] + M[1 * 4 + k] * GBu[1] + M[2 * 4 + k] * GBu[2]) -
+                            (GB[0 * 4 + k] * vx[0] + GB[1 * 4 + k] * vx[1] + GB[2 * 4 + k] * vx[2]);
+                // mu3 = mu_x + M_x m_t dt / n2 (summed over views through gmu_dt)
+                const float a_b = gmu_dt[0] * b[0] + gmu_dt[1] * b[1] + gmu_dt[2] * b[2];
+                float gmt[4];
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+    #pragma unroll
+                    for (int r = 0; r < 3; ++r) GM[r * 4 + k] += gmu_dt[r] * mt[k] * in2;
+                    gmt[k] = (M[0 * 4 + k] * gmu_dt[0] + M[1 * 4 + k] * gmu_dt[1] + M[2 * 4 + k] * gmu_dt[2]) * in2;
+                }
+                float gn2 = -a_b * in2 * in2 + gp_dt2 * in2 * in2;
+                const float gmu_t = -(gmu_sum[0] * b[0] + gmu_sum[1] * b[1] + gmu_sum[2] * b[2]) * in2 + gp_dt * in2;
+                // u = m_t / |m_t|
+                const float ugu = u[0] * gu[0] + u[1] * gu[1] + u[2] * gu[2] + u[3] * gu[3];
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) gmt[k] += (gu[k] - u[k] * ugu) * in + 2.f * mt[k] * gn2;
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) GM[12 + k] = gmt[k];
+                // M = R diag(s)
+                float GR[16], gls[4];
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float acc = 0.f;
+    #pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        GR[r * 4 + k] = GM[r * 4 + k] * s[k];
+                        acc += GM[r * 4 + k] * R[r * 4 + k];
+                    }
+                    gls[k] = acc * s[k];
+                }
+                // R = L Rr:  G_L = G_R Rr^T,  G_Rr = L^T G_R
+                const float a = qln[0], bb = qln[1], c = qln[2], dd = qln[3];
+                const float p = qrn[0], q = qrn[1], rr = qrn[2], ss = qrn[3];
+                const float Lm[16] = {a, -bb, -c, -dd, bb, a, -dd, c, c, dd, a, -bb, dd, -c, bb, a};
+                const float Q[16] = {p, -q, -rr, -ss, q, p, ss, -rr, rr, -ss, p, q, ss, rr, -q, p};
+                float GL[16], GQ[16];
+    #pragma unroll
+                for (int r = 0; r < 4; ++r)
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        GL[r * 4 + k] = GR[r * 4 + 0] * Q[k * 4 + 0] + GR[r * 4 + 1] * Q[k * 4 + 1] +
+                                        GR[r * 4 + 2] * Q[k * 4 + 2] + GR[r * 4 + 3] * Q[k * 4 + 3];
+                        GQ[r * 4 + k] = Lm[0 * 4 + r] * GR[0 * 4 + k] + Lm[1 * 4 + r] * GR[1 * 4 + k] +
+                                        Lm[2 * 4 + r] * GR[2 * 4 + k] + Lm[3 * 4 + r] * GR[3 * 4 + k];
+                    }
+                const float gan[4] = {GL[0] + GL[5] + GL[10] + GL[15], -GL[1] + GL[4] - GL[11] + GL[14],
+                                      -GL[2] + GL[7] + GL[8] - GL[13], -GL[3] - GL[6] + GL[9] + GL[12]};
+                const float gbn[4] = {GQ[0] + GQ[5] + GQ[10] + GQ[15], -GQ[1] + GQ[4] + GQ[11] - GQ[14],
+                                      -GQ[2] - GQ[7] + GQ[8] + GQ[13], -GQ[3] + GQ[6] - GQ[9] + GQ[12]};
+                float gql[4], gqr[4];
+                normalise_backward(ql, gan, gql);
+                normalise_backward(qr, gbn, gqr);
+                const float sg = sigmoidf_(o);
+                ((float4*)dg4.mean)[i] = make_float4(gmu_sum[0], gmu_sum[1], gmu_sum[2], gmu_t);
+                ((float4*)dg4.log_scale)[i] = make_float4(gls[0], gls[1], gls[2], gls[3]);
+                ((float4*)dg4.ql)[i] = make_float4(gql[0], gql[1], gql[2], gql[3]);
+                ((float4*)dg4.qr)[i] = make_float4(gqr[0], gqr[1], gqr[2], gqr[3]);
+                dg4.opacity[i] = gal * sg * (1.f - sg);
+        } else {
+                const int64_t j = i - n4;
+                float q[4], ls[3];
+                load4<DT>(g3.quat, j, q);
+                load3<DT>(g3.log_scale, j, ls);
+                const float o = load1<DT>(g3.opacity, j);
+                const float iq = inv_norm4(q);
+                const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
+                float R[9], s[3], M[9];
+                quat_to_rot(w, x, y, z, R);
+    #pragma unroll
+                for (int k = 0; k < 3; ++k) s[k] = expf(ls[k]);
+    #pragma unroll
+                for (int r = 0; r < 3; ++r)
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) M[r * 3 + k] = R[r * 3 + k] * s[k];
+                const float Gs[9] = {GS.xx, GS.xy, GS.xz, GS.xy, GS.yy, GS.yz, GS.xz, GS.yz, GS.zz};
+                float GR[9], gls[3];
+    #pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float acc = 0.f;
+    #pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        const float gm = 2.f * (Gs[r * 3 + 0] * M[0 * 3 + k] + Gs[r * 3 + 1] * M[1 * 3 + k] +
+                                                Gs[r * 3 + 2] * M[2 * 3 + k]);
+                        GR[r * 3 + k] = gm * s[k];
+                        acc += gm * R[r * 3 + k];
+                    }
+                    gls[k] = acc * s[k];
+                }
+                float g4v[4];
+                g4v[0] = GR[1] * (-2.f * z) + GR[2] * (2.f * y) + GR[3] * (2.f * z) + GR[5] * (-2.f * x) + GR[6] * (-2.f * y) + GR[7] * (2.f * x);
+                g4v[1] = GR[1] * (2.f * y) + GR[2] * (2.f * z) + GR[3] * (2.f * y) + GR[4] * (-4.f * x) + GR[5] * (-2.f * w) + GR[6] * (2.f * z) + GR[7] * (2.f * w) + GR[8] * (-4.f * x);
+                g4v[2] = GR[0] * (-4.f * y) + GR[1] * (2.f * x) + GR[2] * (2.f * w) + GR[3] * (2.f * x) + GR[5] * (2.f * z) + GR[6] * (-2.f * w) + GR[7] * (2.f * z) + GR[8] * (-4.f * y);
+                g4v[3] = GR[0] * (-4.f * z) + GR[1] * (-2.f * w) + GR[2] * (2.f * x) + GR[3] * (2.f * w) + GR[4] * (-4.f * z) + GR[5] * (2.f * y) + GR[6] * (2.f * x) + GR[7] * (2.f * y);
+                float gq[4];
+                normalise_backward(q, g4v, gq);
+                const float sg = sigmoidf_(o);
+                float* dm = dg3.mean + j * 3;
+                dm[0] = gmu_sum[0]; dm[1] = gmu_sum[1]; dm[2] = gmu_sum[2];
+                float* dl = dg3.log_scale + j * 3;
+                dl[0] = gls[0]; dl[1] = gls[1]; dl[2] = gls[2];
+                ((float4*)dg3.quat)[j] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+                dg3.opacity[j] = gal * sg * (1.f - sg);
         }
+        }
+        __syncwarp();  // sums are rewritten by the next chunk
     }
 }
 
@@ -696,20 +802,43 @@ cudaError_t launch_slice_project(const splat_g3& g3, const splat_g4& g4, const V
     return cudaGetLastError();
 }
 
+template <int DT, int L>
+static void adjoint_launch(int blocks, cudaStream_t st, const splat_g3& g3, const splat_g4& g4, const ViewBatch& vb,
+                           const splat_proj& proj, const float* dproj, const splat_grads3& dg3,
+                           const splat_grads4& dg4, int32_t* status)
+{
+    k_adjoint<DT, L><<<blocks, kAdjThreads, 0, st>>>(g3, g4, vb, proj, dproj, dg3, dg4, status);
+}
+
+template <int DT>
+static void adjoint_lanes(int V, int64_t N, int num_sms, cudaStream_t st, const splat_g3& g3, const splat_g4& g4,
+                          const ViewBatch& vb, const splat_proj& proj, const float* dproj, const splat_grads3& dg3,
+                          const splat_grads4& dg4, int32_t* status)
+{
+    // lanes per Gaussian: the view count rounded up to a power of two
+    const int L = V <= 1 ? 1 : V <= 2 ? 2 : V <= 4 ? 4 : V <= 8 ? 8 : 16;
+    const int64_t want = (N + kAdjThreads - 1) / kAdjThreads;
+    const int blocks = (int)(want < (int64_t)num_sms * 64 ? want : (int64_t)num_sms * 64);
+    switch (L) {
+    case 1: adjoint_launch<DT, 1>(blocks, st, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    case 2: adjoint_launch<DT, 2>(blocks, st, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    case 4: adjoint_launch<DT, 4>(blocks, st, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    case 8: adjoint_launch<DT, 8>(blocks, st, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    default: adjoint_launch<DT, 16>(blocks, st, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    }
+}
+
 cudaError_t launch_adjoint(const splat_g3& g3, const splat_g4& g4, const ViewBatch& vb, const splat_proj& proj,
                            const float* dproj, const splat_grads3& dg3, const splat_grads4& dg4, int32_t* status,
                            int dtype, const LaunchCtx& ctx)
 {
     const int64_t N = proj.n;
     if (N == 0) return cudaSuccess;
-    const int threads = kAdjThreads;
-    const int64_t want = (N + threads - 1) / threads;
-    const int blocks = (int)(want < (int64_t)ctx.num_sms * 64 ? want : (int64_t)ctx.num_sms * 64);
     count_launch();
     switch (dtype) {
-    case SPLAT_F32: k_adjoint<SPLAT_F32><<<blocks, threads, 0, ctx.stream>>>(g3, g4, vb, proj, dproj, dg3, dg4, status); break;
-    case SPLAT_BF16: k_adjoint<SPLAT_BF16><<<blocks, threads, 0, ctx.stream>>>(g3, g4, vb, proj, dproj, dg3, dg4, status); break;
-    default: k_adjoint<SPLAT_F16><<<blocks, threads, 0, ctx.stream>>>(g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    case SPLAT_F32: adjoint_lanes<SPLAT_F32>(vb.V, N, ctx.num_sms, ctx.stream, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    case SPLAT_BF16: adjoint_lanes<SPLAT_BF16>(vb.V, N, ctx.num_sms, ctx.stream, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
+    default: adjoint_lanes<SPLAT_F16>(vb.V, N, ctx.num_sms, ctx.stream, g3, g4, vb, proj, dproj, dg3, dg4, status); break;
     }
     return cudaGetLastError();
 }

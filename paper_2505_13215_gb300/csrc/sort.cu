@@ -1694,8 +1694,6 @@ __global__ void __launch_bounds__(32) k_bin_scatter(BinArgs a)
 // Host side
 // ---------------------------------------------------------------------------
 
-static int g_tile_sort_mode = 0;  // 0 auto, 1 radix passes, 2 binned
-static int g_tile_cull = 1;       // binned path: drop tiles the opacity footprint cannot reach
 
 struct SortLayout {
     int64_t n_rows, capacity;
@@ -1724,7 +1722,7 @@ static uint32_t bin_chunk(int64_t capacity)
     return (uint32_t)std::min<int64_t>(std::max<int64_t>(c, 1024), 1 << 20);
 }
 
-SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY)
+SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY, int tile_sort)
 {
     SortLayout L{};
     L.n_rows = n_rows;
@@ -1740,7 +1738,7 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     }
     L.tmax = (tmax + 3) & ~3;
     L.smax = (smax + 3) & ~3;
-    L.binned = g_tile_sort_mode == 2 || (g_tile_sort_mode == 0 && tmax <= kBinMaxTiles);
+    L.binned = tile_sort == 2 || (tile_sort == 0 && tmax <= kBinMaxTiles);
     L.chunk = bin_chunk(capacity);
     L.max_chunks = (capacity + L.chunk - 1) / L.chunk + V;
     L.parts_d = (n_rows + kSortPart - 1) / kSortPart;
@@ -1818,7 +1816,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         TXs[v] = vb.v[v].TX;
         TYs[v] = vb.v[v].TY;
     }
-    const SortLayout L = sort_layout(n_rows, bins.capacity, vb.V, TXs, TYs);
+    const SortLayout L = sort_layout(n_rows, bins.capacity, vb.V, TXs, TYs, ctx.tile_sort);
     if (!L.binned && bins.capacity > 0 && !bins.keys) return cudaErrorInvalidValue;
     char* w = (char*)ws;
     auto U = [&](size_t off) { return (uint32_t*)(w + off); };
@@ -1923,7 +1921,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.vals_out = bins.vals;
         t.keys_out = bins.keys;
         t.status = status;
-        t.cull = g_tile_cull;
+        t.cull = ctx.tile_cull;
         t.seg_base = U(L.off_segbase);
         t.seg_cnt = U(L.off_segcnt);
         t.seg_super = U(L.off_segsuper);
@@ -2075,13 +2073,9 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);
 }
 
-size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY)
+size_t bin_sort_workspace(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY, int tile_sort)
 {
-    return sort_layout(n_rows, capacity, V, TX, TY).bytes;
+    return sort_layout(n_rows, capacity, V, TX, TY, tile_sort).bytes;
 }
-
-void set_tile_sort_mode(int mode) { g_tile_sort_mode = (mode >= 0 && mode <= 2) ? mode : 0; }
-
-void set_tile_cull(int on) { g_tile_cull = on ? 1 : 0; }
 
 }  // namespace splat

@@ -287,12 +287,19 @@ struct L1Fuse {
     float* loss;
 };
 
+// Per-call launch context: the stream, the device's SM count and the tuning
+// of this call (the library-wide splat_set_* settings, or a caller's
+// splat_options).
 struct LaunchCtx {
     cudaStream_t stream;
     int num_sms;
     int64_t spin_limit;
+    int tile_sort;   // 0 automatic, 1 radix passes, 2 binned partition
+    int tile_cull;   // binned path: footprint culling and the saturation cut
+    int ppl_fwd, ppl_bwd;
+    unsigned long long* stats;
 };
-LaunchCtx launch_ctx(void* stream);
+LaunchCtx launch_ctx(void* stream, const splat_options* opt = nullptr);
 
 // Host-side argument checks shared by the entry points that take the same
 // arguments (splat_bin_sort and its allocation-free variant reject the same

@@ -129,6 +129,9 @@ class Rasterizer:
     def __init__(self, n3: int, n4: int, views: Sequence, device="cuda", capacity: Optional[int] = None,
                  headroom: float = 1.25, keep_keys: bool = True, sh_time: int = 0):
         self.keep_keys = keep_keys
+        # this rasterizer's tuning (splat_options): unset fields follow the
+        # library-wide splat_set_* defaults; see set_options
+        self.options = abi.options()
         self.n3, self.n4 = int(n3), int(n4)
         self.N = self.n3 + self.n4
         self.views = list(views)
@@ -207,11 +210,35 @@ class Rasterizer:
         self.cbins = abi.splat_bins(capacity, self.keys.data_ptr() if self.keep_keys else None, self.vals.data_ptr(),
                                     self.ranges.data_ptr(), self.n_instances.data_ptr(), self.tile_order.data_ptr(),
                                     self.n_needed.data_ptr())
-        ws = abi.splat_workspace_size(abi.SPLAT_OP_ALL, self.n3, self.n4, self.W, self.H, capacity)
+        ws = abi.splat_workspace_size_opts(abi.SPLAT_OP_ALL, self.n3, self.n4, self.W, self.H, capacity,
+                                           C.byref(self.options))
         if ws == 0:
             raise ValueError("invalid sizes for the workspace")
         self.ws_bytes = int(ws)
         self.ws = torch.empty((self.ws_bytes,), dtype=torch.uint8, device=self.device)
+
+    def set_options(self, ppl_fwd=None, ppl_bwd=None, tile_sort=None, tile_cull=None, spin_limit=None,
+                    stats=False):
+        """This rasterizer's tuning, independent of other rasterizers in the
+        process: pixels per lane of the compositing kernels (2, 4, 8; 0 = the
+        library default), tile sort mode and footprint culling of the sort (-1 =
+        the library default), the bounded waits' spin limit (-1 = default) and
+        the pair-count statistics (a device pointer, or None for the default).
+        Arguments left out keep their current value."""
+        o = self.options
+        if ppl_fwd is not None:
+            o.pixels_per_lane_fwd = int(ppl_fwd)
+        if ppl_bwd is not None:
+            o.pixels_per_lane_bwd = int(ppl_bwd)
+        if spin_limit is not None:
+            o.spin_limit = int(spin_limit)
+        if stats is not False:
+            o.stats = stats
+        if tile_cull is not None:
+            o.tile_cull = int(tile_cull)
+        if tile_sort is not None and int(tile_sort) != o.tile_sort:
+            o.tile_sort = int(tile_sort)
+            self.set_capacity(self.capacity)  # the sort's workspace depends on the mode
 
     # -- stages -------------------------------------------------------------
     def slice_project(self, G: Gaussians, stream=None):
@@ -224,13 +251,14 @@ class Rasterizer:
                                           _ptr(self.status), _stream(stream)), "splat_slice_project")
 
     def bin_sort(self, stream=None):
-        abi.check(abi.splat_bin_sort(C.byref(self.cproj), self.cviews, self.V, C.byref(self.cbins), _ptr(self.status),
-                                     _ptr(self.ws), self.ws_bytes, _stream(stream)), "splat_bin_sort")
+        abi.check(abi.splat_bin_sort_opts(C.byref(self.cproj), self.cviews, self.V, C.byref(self.cbins),
+                                          _ptr(self.status), _ptr(self.ws), self.ws_bytes, C.byref(self.options),
+                                          _stream(stream)), "splat_bin_sort")
 
     def composite(self, stream=None):
-        abi.check(abi.splat_composite_fwd(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
-                                          C.byref(self.cimg), _ptr(self.status), _stream(stream)),
-                  "splat_composite_fwd")
+        abi.check(abi.splat_composite_fwd_opts(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
+                                               C.byref(self.cimg), _ptr(self.status), C.byref(self.options),
+                                               _stream(stream)), "splat_composite_fwd")
 
     def forward(self, G: Gaussians, stream=None):
         """Slice/project, bin/sort and composite all views (asynchronous)."""
@@ -241,11 +269,11 @@ class Rasterizer:
 
     def _bwd(self, G: Gaussians, dL_drgb: Optional[torch.Tensor], flags: int, stream=None):
         g3, g4 = G.c_g3(), G.c_g4()
-        abi.check(abi.splat_composite_bwd(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
-                                          C.byref(self.cimg), _ptr(dL_drgb), C.byref(g3), C.byref(g4),
-                                          C.byref(self.cg3), C.byref(self.cg4), _ptr(self.dproj), flags,
-                                          _ptr(self.status), _ptr(self.ws), self.ws_bytes, _stream(stream)),
-                  "splat_composite_bwd")
+        abi.check(abi.splat_composite_bwd_opts(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
+                                               C.byref(self.cimg), _ptr(dL_drgb), C.byref(g3), C.byref(g4),
+                                               C.byref(self.cg3), C.byref(self.cg4), _ptr(self.dproj), flags,
+                                               _ptr(self.status), _ptr(self.ws), self.ws_bytes, C.byref(self.options),
+                                               _stream(stream)), "splat_composite_bwd")
 
     def backward(self, G: Gaussians, dL_drgb: torch.Tensor, stream=None, stop_2d: bool = False):
         """Gradients of all parameters for pixel gradient dL_drgb (asynchronous);
@@ -269,10 +297,10 @@ class Rasterizer:
         """Composite all views with the L1 loss fused in (the same image, loss and
         pixel gradient as composite() followed by l1_loss(); asynchronous)."""
         n = self.rgb.numel()
-        abi.check(abi.splat_composite_fwd_l1(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
-                                             C.byref(self.cimg), _ptr(target), 1.0 / max(1, n), _ptr(self.dL),
-                                             _ptr(self.loss), _ptr(self.status), _stream(stream)),
-                  "splat_composite_fwd_l1")
+        abi.check(abi.splat_composite_fwd_l1_opts(C.byref(self.cproj), C.byref(self.cbins), self.cviews, self.V,
+                                                  C.byref(self.cimg), _ptr(target), 1.0 / max(1, n), _ptr(self.dL),
+                                                  _ptr(self.loss), _ptr(self.status), C.byref(self.options),
+                                                  _stream(stream)), "splat_composite_fwd_l1")
         return self.loss
 
     STAGES = ("slice_project", "bin_sort", "composite_fwd", "loss", "composite_bwd", "adjoint")

@@ -135,3 +135,35 @@ def test_both_bin_sorts_reject_misaligned_bins(lib):
     v[0].fx = 0.0
     bins = abi.splat_bins(1024, 4096, 4096, 4096, 4096)
     assert abi.splat_bin_sort_noalloc(C.byref(proj), v, 1, C.byref(bins), st, None) == abi.SPLAT_ERR_INVALID_ARG
+
+
+def test_invalid_options_rejected_before_any_device_work(lib):
+    """Per-call options (splat_options): out-of-range fields are rejected on the
+    host; a NULL pointer or the library-default values are accepted."""
+    W, H = [64], [64]
+    base = abi.splat_workspace_size(abi.SPLAT_OP_BIN_SORT, 10, 10, W, H, 1000)
+    assert abi.splat_workspace_size_opts(abi.SPLAT_OP_BIN_SORT, 10, 10, W, H, 1000, None) == base
+    assert abi.splat_workspace_size_opts(abi.SPLAT_OP_BIN_SORT, 10, 10, W, H, 1000, C.byref(abi.options())) == base
+    # the radix mode lays out its own workspace
+    assert abi.splat_workspace_size_opts(abi.SPLAT_OP_BIN_SORT, 10, 10, W, H, 1000,
+                                         C.byref(abi.options(tile_sort=1))) not in (0, base)
+    for bad in (abi.options(ppl_fwd=3), abi.options(ppl_bwd=16), abi.options(tile_sort=3),
+                abi.options(tile_cull=2), abi.options(spin_limit=-2)):
+        assert abi.splat_workspace_size_opts(abi.SPLAT_OP_BIN_SORT, 10, 10, W, H, 1000, C.byref(bad)) == 0
+    v = (abi.splat_view * 1)()
+    v[0].W, v[0].H, v[0].fx, v[0].fy, v[0].z_near = 64, 64, 50.0, 50.0, 0.2
+    proj = abi.splat_proj(10, 1, 0, 4096, 4096, 4096, 4096, 4096, 4096)
+    bins = abi.splat_bins(1024, 4096, 4096, 4096, 4096)
+    img = abi.splat_image(4096, 4096, 4096)
+    st = C.c_void_p(4096)
+    bad = abi.options(ppl_fwd=5)
+    assert abi.splat_bin_sort_opts(C.byref(proj), v, 1, C.byref(bins), st, C.c_void_p(4096), 1 << 30,
+                                   C.byref(abi.options(tile_sort=7)), None) == abi.SPLAT_ERR_INVALID_ARG
+    assert abi.splat_composite_fwd_opts(C.byref(proj), C.byref(bins), v, 1, C.byref(img), st, C.byref(bad),
+                                        None) == abi.SPLAT_ERR_INVALID_ARG
+    assert abi.splat_composite_fwd_l1_opts(C.byref(proj), C.byref(bins), v, 1, C.byref(img), C.c_void_p(4096), 1.0,
+                                           C.c_void_p(4096), C.c_void_p(4096), st, C.byref(bad),
+                                           None) == abi.SPLAT_ERR_INVALID_ARG
+    assert abi.splat_composite_bwd_opts(C.byref(proj), C.byref(bins), v, 1, C.byref(img), C.c_void_p(4096), None,
+                                        None, None, None, None, abi.SPLAT_BWD_STOP_2D, st, C.c_void_p(4096), 1 << 30,
+                                        C.byref(abi.options(ppl_bwd=1)), None) == abi.SPLAT_ERR_INVALID_ARG

@@ -8,6 +8,9 @@ import pytest
 from paper_2505_13215_gb300 import abi, autotune
 
 
+APPLIED = []  # (fwd, bwd) pixels per lane applied to the tuned rasterizer, in order
+
+
 class FakeR:
     W, H, V = [64, 32], [48, 16], 2
     capacity = 1000
@@ -15,13 +18,17 @@ class FakeR:
     def autotune_capacity(self, G):
         return 777
 
+    def set_options(self, ppl_fwd=None, ppl_bwd=None, **kw):
+        APPLIED.append((ppl_fwd, ppl_bwd))
+
 
 @pytest.fixture
 def fake(monkeypatch, tmp_path):
-    applied = []
-    monkeypatch.setattr(abi, "splat_set_pixels_per_lane", lambda f, b: applied.append((f, b)))
+    APPLIED.clear()
+    # the library-wide setting must not be touched: the choice goes to the rasterizer
+    monkeypatch.setattr(abi, "splat_set_pixels_per_lane", lambda f, b: pytest.fail("global knob changed"))
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
-    return applied
+    return APPLIED
 
 
 def scripted(monkeypatch, applied, times):
