@@ -94,8 +94,16 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// all but the most recently committed group have landed
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ void gather_rows(const splat_proj& proj, uint32_t row, RawRows& raw, int lane)
 {
@@ -268,6 +276,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     constexpr int BANDS = 8 / PPL, NP = PPL / 2;
     __shared__ float4 s_feat[kCompWarps][32][kFeat];
     __shared__ RawRows s_raw[kCompWarps];
+    __shared__ float s_target[kCompWarps][3 * PPL][32];  // the fused loss's target at the lane's pixels
     if (status_failed(status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * kCompWarps + warp;
@@ -282,6 +291,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     const int u = tx * kTile + (lane & 15);
     const int y0 = ty * kTile + band * (2 * PPL) + (lane >> 4);
     const float2 nu = make_float2(-(float)u, -(float)u);
+    const int64_t HW = (int64_t)vp.W * vp.H;
     // pair p holds pixels k = 2p, 2p + 1 (rows y0 + 4p, y0 + 4p + 2).  nrow:
     // minus the row, -kOffRow once the pixel is done (outside the image or
     // saturated).  nC: minus the accumulated colour.
@@ -310,14 +320,30 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
     float4* sf = &s_feat[warp][0][0];
     RawRows& raw = s_raw[warp];
     unsigned n_eval = 0, n_blend = 0;
-    // the rows of batch 0 in flight, the list entries of batch 1 in a register
+    // the rows of batch 0 in flight, the list entries of batch 1 in a register;
+    // then the fused loss's target at the lane's pixels, which lands in shared
+    // memory during the walk (a group of its own, committed after batch 0's:
+    // groups complete in order, so batch 0 need not wait for it)
     if (rg.x + lane < rg.y) gather_rows(proj, vals[rg.x + lane], raw, lane);
+    cp_async_commit();
+    if (l1.target) {  // same for every lane
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            const int y = y0 + 2 * k;
+            if (u < vp.W && y < vp.H) {
+                const int64_t q = 3 * vp.pix_base + (int64_t)y * vp.W + u;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) cp_async4(&s_target[warp][3 * k + ch][lane], l1.target + q + ch * HW);
+            }
+        }
+    }
     cp_async_commit();
     uint32_t next_row = rg.x + 32 + lane < rg.y ? vals[rg.x + 32 + lane] : 0u;
     for (uint32_t b = rg.x; b < rg.y; b += 32) {
         if (__all_sync(0xffffffffu, done == all_done)) break;
         const uint32_t idx = b + lane;
-        cp_async_wait_all();
+        if (b == rg.x) cp_async_wait_one();  // batch 0's rows (the target may still be in flight)
+        else cp_async_wait_all();
         if (idx < rg.y) stage_feat(raw, lane, sf + lane * kFeat);
         __syncwarp();
         // the next batch's rows land while this one is composited
@@ -348,7 +374,6 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
             atomicAdd(stats + 1, (unsigned long long)bl);
         }
     }
-    const int64_t HW = (int64_t)vp.W * vp.H;
     float* rgb = img.rgb + 3 * vp.pix_base;
     float l1sum = 0.f;  // the lane's share of the fused L1 loss
 #pragma unroll
@@ -369,7 +394,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
             const int64_t q = 3 * vp.pix_base + p;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                const float d = out[ch] - l1.target[q + ch * HW];
+                const float d = out[ch] - s_target[warp][3 * k + ch][lane];
                 l1sum += fabsf(d);
                 l1.dL[q + ch * HW] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * l1.scale;
             }
@@ -553,6 +578,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     // Q starts at <G, bg>.  Pixels in pairs as in the forward; nQ = -Q.  A pixel's
     // row enters nrow (as minus the row) only once the walk reaches its last
     // contributor; before that nrow is -kOffRow and every test fails.
+    const uint2 rg = ranges[tile];  // loaded with the pixels' state, not after it
     float2 T[NP], nQ[NP], G[NP][3], nrow[NP];
     int last[PPL];
     int maxlast = 0;
@@ -587,7 +613,6 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
     // act: the list position (0-based) at or below which one of the warp's
     // pixels still has to switch on (its last contributor), -1 when none is left
     int act = maxlast - 1;
-    const uint2 rg = ranges[tile];
     float4* sf = &s_feat[warp][0][0];
     float4* red = &s_red[warp][0][0];
     // entries walked: [rg.x, end); batches 0 .. nb - 2 are full
