@@ -456,7 +456,9 @@ struct ShPart {
 };
 
 // View-parallel adjoint.  A warp takes 32 consecutive Gaussians at a time.
-// First, in L sub-batches of 32 / L Gaussians, a group of L lanes (L: the
+// Each lane computes one Gaussian's view-independent geometry (Eq. 2 / Eq. 4
+// and the projector form of Eq. 6) into shared memory.  Then, in L sub-batches
+// of 32 / L Gaussians, a group of L lanes (L: the
 // view count rounded up to a power of two) per Gaussian, lane q chaining view
 // q's 2D gradients through the colour and the EWA projection; the group sums
 // its views -- the 15 view-summed quantities by shuffles, the SH gradient from
@@ -475,6 +477,7 @@ __global__ void __launch_bounds__(kAdjThreads, 5) k_adjoint(splat_g3 g3, splat_g
     constexpr int GPS = 32 / L;  // Gaussians per sub-batch of a warp
     __shared__ ShPart s_part[kAdjThreads];
     __shared__ float s_sum[kAdjThreads / 32][15][32];  // per warp: the 15 view sums of its 32 Gaussians
+    __shared__ float s_geo[kAdjThreads / 32][15][32];  // per warp: the view-independent geometry (Geo)
     __shared__ ViewParams s_view[SPLAT_MAX_VIEWS];  // lanes of one warp read different views
     if (status_failed(status)) return;
     for (int v = threadIdx.x; v < vb.V; v += blockDim.x) s_view[v] = vb.v[v];
@@ -484,9 +487,23 @@ __global__ void __launch_bounds__(kAdjThreads, 5) k_adjoint(splat_g3 g3, splat_g
     const int lane = threadIdx.x & 31, q = threadIdx.x % L, warp = threadIdx.x >> 5;
     const int gbase = threadIdx.x - q;  // first lane of the group
     float (*sums)[32] = s_sum[warp];
+    float (*geo)[32] = s_geo[warp];
     // every lane of a warp takes the same number of trips (the group sums are warp collectives)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + warp * 32; c0 < N; c0 += stride) {
+      {
+        // the geometry of Gaussian c0 + lane, once (the view lanes below share it)
+        const int64_t i = c0 + lane;
+        if (i < N) {
+            Geo G;
+            load_geo<DT>(g3, g4, i, i < n4, G);
+            const float g15[15] = {G.mu[0], G.mu[1], G.mu[2], G.S.xx, G.S.xy, G.S.xz, G.S.yy, G.S.yz, G.S.zz,
+                                   G.op, G.mu_t, G.inv_n2, G.b[0], G.b[1], G.b[2]};
+#pragma unroll
+            for (int e = 0; e < 15; ++e) geo[e][lane] = g15[e];
+        }
+        __syncwarp();
+      }
       for (int sb = 0; sb < L; ++sb) {
         const int slot = sb * GPS + lane / L;  // the Gaussian's lane in the chain phase
         const int64_t i = c0 + slot;
@@ -506,7 +523,10 @@ __global__ void __launch_bounds__(kAdjThreads, 5) k_adjoint(splat_g3 g3, splat_g
         const int v = q;
         const int64_t row = (int64_t)v * N + i;
         if (valid && v < vb.V && proj.radius[row] != 0) {
-            load_geo<DT>(g3, g4, i, is4, G);
+            G.mu[0] = geo[0][slot]; G.mu[1] = geo[1][slot]; G.mu[2] = geo[2][slot];
+            G.S = {geo[3][slot], geo[4][slot], geo[5][slot], geo[6][slot], geo[7][slot], geo[8][slot]};
+            G.op = geo[9][slot]; G.mu_t = geo[10][slot]; G.inv_n2 = geo[11][slot];
+            G.b[0] = geo[12][slot]; G.b[1] = geo[13][slot]; G.b[2] = geo[14][slot];
             const typename Storage<DT>::T* shp =
                 (const typename Storage<DT>::T*)(is4 ? g4.sh : g3.sh) + (is4 ? i : i - n4) * 48 * (Tn + 1);
             const ViewParams& vp = s_view[v];
@@ -777,7 +797,7 @@ __global__ void __launch_bounds__(kAdjThreads, 5) k_adjoint(splat_g3 g3, splat_g
                 dg3.opacity[j] = gal * sg * (1.f - sg);
         }
         }
-        __syncwarp();  // sums are rewritten by the next chunk
+        __syncwarp();  // sums and geometry are rewritten by the next chunk
     }
 }
 
