@@ -468,7 +468,7 @@ struct ShPart {
 // gradients.  No atomics; the views' memory requests are independent of one
 // another, and the heavy view-independent chain runs on full warps.
 template <int DT, int L>
-__global__ void __launch_bounds__(kAdjThreads, 5) k_adjoint(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj proj,
+__global__ void __launch_bounds__(kAdjThreads, 6) k_adjoint(splat_g3 g3, splat_g4 g4, ViewBatch vb, splat_proj proj,
                                                  const float* __restrict__ dproj, splat_grads3 dg3,
                                                  splat_grads4 dg4, int32_t* status)
 {

@@ -949,13 +949,14 @@ struct TileArgs {
     uint32_t* keys_out;               // may be null
     int cull;                         // drop tiles the opacity footprint cannot reach
     int W[SPLAT_MAX_VIEWS], H[SPLAT_MAX_VIEWS];
-    uint32_t* n_head;                 // [total_super] rows of each list the head pass went through
+    uint32_t* n_head8;                // [total_super][8] entries each tile row's head count went through
+    uint32_t* n_head;                 // [total_super] entries of each list the head pass went through
     uint2* sat_head;                  // [total_super] tiles (bit 8 r + c) whose lists ended in the head
     uint32_t* seg_base;               // [total_super + 1] first tail segment of each super-tile
     uint32_t* seg_super;              // [segments] super-tile of each tail segment
     uint32_t* seg_cnt;                // [segments][64] per-segment tile counts, then offsets
     uint2* mask;                      // per super-tile list entry: byte w = its tile columns in tile row w
-    uint32_t* ticket;                 // [4] tickets of the tail write / count and head write / count passes (zeroed)
+    uint32_t* ticket;                 // [3] tickets of the tail write / count and head write passes (zeroed)
     int32_t* status;
 };
 
@@ -1025,7 +1026,8 @@ __device__ __forceinline__ uint32_t sat_weight(const SatRow& r, float xlo, float
 constexpr int kFilterSeg = 1024;  // list entries per tail segment (one CTA)
 constexpr int kHeadChunks = 2;    // 256-row chunks of each list the head pass takes in order
 
-// one block: tail segments per super-tile list, exclusive scan -> seg_base
+// one block: head length of each super-tile list (its longest tile row's),
+// tail segments per list, exclusive scan -> seg_base
 __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
 {
     __shared__ uint32_t s_tmp[8];
@@ -1036,7 +1038,10 @@ __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
         uint32_t c = 0;
         if (gs < a.total_super) {  // the tail: what the head pass left, unless every list ended in it
             const uint2 rg = a.sranges[gs], sat = a.sat_head[gs];
-            const uint32_t rest = (sat.x & sat.y) == 0xffffffffu ? 0u : rg.y - rg.x - a.n_head[gs];
+            const uint4 h0 = ((const uint4*)a.n_head8)[2 * gs], h1 = ((const uint4*)a.n_head8)[2 * gs + 1];
+            const uint32_t nh = max(max(max(h0.x, h0.y), max(h0.z, h0.w)), max(max(h1.x, h1.y), max(h1.z, h1.w)));
+            a.n_head[gs] = nh;
+            const uint32_t rest = (sat.x & sat.y) == 0xffffffffu ? 0u : rg.y - rg.x - nh;
             c = (rest + kFilterSeg - 1) / kFilterSeg;
         }
         uint32_t tot;
@@ -1144,234 +1149,241 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
     return true;
 }
 
-// Head pass: one CTA per super-tile (8x8 tiles), taken from a ticket counter:
-// it streams the first kHeadChunks x 256 rows of the super-tile's row list in
-// depth order through shared memory, 256 rows at a time; warp w serves tile
-// row w (8 tiles).
-// COUNT: warp w keeps a row for the tiles of its rectangle in tile row w that
-// its opacity footprint reaches (the footprint enlarged by a margin that covers
-// FP32 rounding, so no pixel result changes), records them as byte w of the
-// entry's coverage word (bit k: tile column k of the super-tile), counts per
-// tile and, with culling on, ends each tile's list once the tile saturates;
-// the CTA stops when all its tiles have.  The tail pass takes the rest of the
-// lists of the tiles that did not saturate.  Write pass: each tile's list
-// starts at the tile's range start, driven by the coverage words of the rows
-// the count pass went through.
-template <bool COUNT>
-__global__ void __launch_bounds__(256) k_tile_head(TileArgs a)
+// Head pass, counting: one CTA per (super-tile, tile row), warp c serving
+// tile column c.  The CTA streams the first kHeadChunks x 256 entries of the
+// super-tile's list in depth order, 256 at a time.  Thread t takes entry t of
+// the chunk: the entry joins the tile row's queue (in order) when its
+// rectangle covers the row, and then gets its columns in the row (the
+// rectangle's, narrowed with culling on to the opacity footprint enlarged by a
+// margin that covers FP32 rounding, so no pixel result changes) and the terms
+// of its saturation bound for the row.  Warp c goes through the queue in
+// batches of 32, counts the entries listed in tile c and, with culling on,
+// sums their saturation weights; tile c's list ends after the batch that takes
+// the sum past the threshold.  Every entry up to the head's end gets its
+// coverage byte for this tile row (bit c: listed in tile c), zero once the
+// row's lists have all ended, so that the write pass runs on the bytes alone.
+// Per row the CTA leaves the entries it went through (n_head8: up to the end
+// of the chunk in which its last open list ended) and the ended columns (byte
+// w of sat_head); k_seg_plan takes the super-tile's head length as the
+// largest row's.
+__global__ void __launch_bounds__(256) k_head_count(TileArgs a)
 {
-    // COUNT: rectangle relative to the super-tile, clamped to [0, 8], one byte
-    // per bound (x0, y0, x1, y1); footprint constants; conic and alpha_max
-    // (0 when the row does not enter the saturation bound)
-    __shared__ uint32_t s_rect[COUNT ? 256 : 1];
-    __shared__ float4 s_g0[COUNT ? 256 : 1], s_g1[COUNT ? 256 : 1], s_co[COUNT ? 256 : 1];
-    __shared__ uint32_t s_row[COUNT ? 1 : 256];
-    __shared__ uint2 s_mask[256];
-    __shared__ unsigned char s_queue[8][256];  // per tile row: entries of the chunk it has work for
-    // COUNT: coverage byte -> four words of two 16-bit column counters (columns 2q, 2q + 1),
-    // so that four warp reductions count all eight columns of 32 entries
-    __shared__ uint4 s_spread[COUNT ? 256 : 1];
-    __shared__ uint32_t s_gs;
-    __shared__ uint32_t s_sat[8];
-    __shared__ uint32_t s_w[COUNT ? 8 : 1][8][32];  // COUNT: per tile row, saturation weights [column][lane]
+    __shared__ unsigned char s_m[256];       // columns of each entry of the chunk in this tile row
+    __shared__ unsigned char s_queue[256];   // the chunk's entries queued by the row, in order
+    __shared__ float4 s_sr0[256], s_sr1[256];  // saturation terms (a, B0, B1, C0), (C1, Bm, Cm, px)
+    __shared__ float s_amax[256];            // alpha_max, 0 when the entry does not enter the bound
+    __shared__ uint32_t s_wn[8], s_keep[8];
+    __shared__ uint32_t s_sat;
     if (status_failed(a.status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    if (COUNT) {
-        const unsigned b = threadIdx.x;
-        s_spread[b] = make_uint4((b & 1u) | ((b >> 1 & 1u) << 16), (b >> 2 & 1u) | ((b >> 3 & 1u) << 16),
-                                 (b >> 4 & 1u) | ((b >> 5 & 1u) << 16), (b >> 6 & 1u) | ((b >> 7 & 1u) << 16));
+    const int gs = (int)(blockIdx.x >> 3), w = (int)(blockIdx.x & 7);
+    if (gs >= a.total_super) return;
+    int v = 0;
+    for (int q = 1; q < a.V; ++q)
+        if (gs >= a.super_base[q]) v = q;
+    const int ls = gs - a.super_base[v];
+    const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
+    const int TX = a.TX[v], TY = a.TY[v];
+    const int ty = sy * 8 + w, tx0 = sx * 8;
+    const float vlo = (float)(ty * kTile), vhi = vlo + (float)(kTile - 1);
+    const float vhi_img = fminf(vhi, (float)(a.H[v] - 1)), xmax_img = (float)(a.W[v] - 1);
+    const float xlo = (float)((tx0 + warp) * kTile), xhi = fminf(xlo + (float)(kTile - 1), xmax_img);
+    // column state of this warp (warp-uniform): columns outside the grid have ended from the start
+    bool sat = !(ty < TY && tx0 + warp < TX);
+    uint32_t cnt = 0u, wsum = 0u;
+    if (threadIdx.x == 0) s_sat = 0u;
+    const uint2 rgs = a.sranges[gs];
+    const uint32_t end = min(rgs.y, rgs.x + (uint32_t)(kHeadChunks * 256));
+    uint32_t row_end = rgs.x;
+    int done = __syncthreads_and(sat);  // block-uniform: every list of the row has ended
+    for (uint32_t b = rgs.x; b < end; b += 256) {
+        if (!done) row_end = min(b + 256u, end);
+        const uint32_t j = b + threadIdx.x;
+        uint32_t m = 0u;
+        bool cov = false;
+        if (!done && j < end) {
+            const uint32_t row = a.list[j];
+            const int4 rc = ((const int4*)a.proj.rect)[row];
+            auto rel = [](int c, int o) { return min(max(c - o, 0), 8); };
+            cov = rel(rc.y, sy * 8) <= w && w < rel(rc.w, sy * 8);
+            if (cov) {
+                int lo = rel(rc.x, tx0), hi = rel(rc.z, tx0);
+                if (a.cull) {
+                    const float2 xy = ((const float2*)a.proj.xy)[row];
+                    const float4 co = ((const float4*)a.proj.conic_opacity)[row];
+                    // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
+                    const float R2 = -2.f * __logf(__fdividef(kAlphaMin, co.w)) * 1.0001f + 2e-3f;
+                    float4 g0, g1;
+                    ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1);
+                    float ul, ur;
+                    if (!ellipse_band_extent(g0, g1, vlo, vhi, ul, ur)) {
+                        hi = lo;
+                    } else {
+                        // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
+                        const float fl = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
+                        const float fh = floorf(ur * (1.f / kTile));
+                        lo = max(lo, (int)fminf(fmaxf(fl, -1.f), 1.0e6f) - tx0);
+                        hi = min(hi, (int)fminf(fmaxf(fh, -2.f), 1.0e6f) + 1 - tx0);
+                    }
+                    // the saturation bound needs a*c - b^2 >= 1e-3 a c: the
+                    // relative rounding of the power stays far below its size
+                    const bool ok = co.x > 0.f && co.z > 0.f && co.x * co.z - co.y * co.y >= 1e-3f * co.x * co.z &&
+                                    co.w <= 1.f;
+                    const SatRow sr = sat_row(co, xy.x, xy.y, vlo, vhi_img);
+                    s_sr0[threadIdx.x] = make_float4(sr.a, sr.B0, sr.B1, sr.C0);
+                    s_sr1[threadIdx.x] = make_float4(sr.C1, sr.Bm, sr.Cm, sr.px);
+                    s_amax[threadIdx.x] = ok ? co.w : 0.f;
+                }
+                if (hi > lo) m = (1u << hi) - (1u << lo);
+            }
+        }
+        // the row's queue: stable compaction of the covering entries
+        const unsigned bal = __ballot_sync(0xffffffffu, cov);
+        if (lane == 0) s_wn[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t qi = __popc(bal & lt), nq = 0u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t x = s_wn[q];
+            qi += q < warp ? x : 0u;
+            nq += x;
+        }
+        if (cov) s_queue[qi] = (unsigned char)threadIdx.x;
+        s_m[threadIdx.x] = (unsigned char)m;
+        __syncthreads();
+        // warp c: tile c of the row, the queue in batches of 32 while its list is open
+        uint32_t keep = 0u;  // queue entries listed in tile c
+        if (!sat) {
+            keep = nq;
+            for (uint32_t sb = 0; sb < nq; sb += 32) {
+                const uint32_t q = sb + lane;
+                bool bit = false;
+                uint32_t wt = 0u;
+                if (q < nq) {
+                    const int e = s_queue[q];
+                    bit = (s_m[e] >> warp) & 1u;
+                    if (a.cull && bit) {
+                        const float am = s_amax[e];
+                        if (am > 0.f) {
+                            const float4 p0 = s_sr0[e], p1 = s_sr1[e];
+                            SatRow sr;
+                            sr.a = p0.x; sr.B0 = p0.y; sr.B1 = p0.z; sr.C0 = p0.w;
+                            sr.C1 = p1.x; sr.Bm = p1.y; sr.Cm = p1.z; sr.px = p1.w;
+                            sr.amax = am;
+                            wt = sat_weight(sr, xlo, xhi);
+                        }
+                    }
+                }
+                cnt += __popc(__ballot_sync(0xffffffffu, bit));
+                if (a.cull) {
+                    wsum += __reduce_add_sync(0xffffffffu, wt);
+                    if (wsum >= kSatThreshold) {  // the list ends after this batch
+                        sat = true;
+                        keep = min(sb + 32u, nq);
+                        break;
+                    }
+                }
+            }
+        }
+        if (lane == 0) s_keep[warp] = keep;
+        __syncthreads();
+        if (j < end) {  // coverage byte of this tile row
+            uint32_t byte = 0u;
+            if (cov) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (qi < s_keep[c]) byte |= m & (1u << c);
+            }
+            reinterpret_cast<unsigned char*>(a.mask + j)[w] = (unsigned char)byte;
+        }
+        done = __syncthreads_and(sat);
     }
+    if (lane == 0) {
+        if (ty < TY && tx0 + warp < TX) a.tile_total[a.tile_base[v] + ty * TX + tx0 + warp] = cnt;
+        if (sat) atomicOr(&s_sat, 1u << warp);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.n_head8[8 * gs + w] = row_end - rgs.x;
+        reinterpret_cast<unsigned char*>(a.sat_head + gs)[w] = (unsigned char)s_sat;
+    }
+}
+
+// Head pass, writing: one CTA per super-tile, taken from a ticket counter;
+// warp w serves tile row w.  Each tile's list starts at the tile's range start
+// and takes, in order, the entries of the head whose coverage byte for the
+// tile row lists them in the tile.
+__global__ void __launch_bounds__(256) k_head_write(TileArgs a)
+{
+    __shared__ uint32_t s_row[256];
+    __shared__ uint2 s_mask[256];
+    __shared__ unsigned char s_queue[8][256];  // per tile row: entries of the chunk it has work for
+    __shared__ uint32_t s_gs;
+    if (status_failed(a.status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
     for (;;) {
-        if (threadIdx.x == 0) s_gs = atomicAdd(a.ticket + (COUNT ? 3 : 2), 1u);
+        if (threadIdx.x == 0) s_gs = atomicAdd(a.ticket + 2, 1u);
         __syncthreads();
         const uint32_t gs = s_gs;
         if (gs >= (uint32_t)a.total_super) break;
         int v = 0;
-        for (int w = 1; w < a.V; ++w)
-            if ((int)gs >= a.super_base[w]) v = w;
+        for (int q = 1; q < a.V; ++q)
+            if ((int)gs >= a.super_base[q]) v = q;
         const int ls = (int)gs - a.super_base[v];
         const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
         const int TX = a.TX[v], TY = a.TY[v];
         const int ty = sy * 8 + warp;
         const int tx0 = sx * 8;
-        const float vlo = (float)(ty * kTile), vhi = vlo + (float)(kTile - 1);
-        const float vhi_img = fminf(vhi, (float)(a.H[v] - 1)), xmax_img = (float)(a.W[v] - 1);
         const uint2 rgs = a.sranges[gs];
-        // COUNT: sat = columns whose list has ended (warp-uniform; columns and
-        // rows outside the grid from the start); lane k < 8 holds tile k's
-        // count and saturation sum
-        uint32_t sat = 0u, cnt = 0u, wsum = 0u;
-        uint32_t cur[8];  // write pass: next slot of each tile's list
-        uint32_t end = min(rgs.y, rgs.x + (uint32_t)(kHeadChunks * 256));
+        uint32_t cur[8];  // next slot of each tile's list
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const bool ok = ty < TY && tx0 + k < TX;
-            if (!ok) sat |= 1u << k;
-            cur[k] = (!COUNT && ok) ? a.ranges[a.tile_base[v] + ty * TX + tx0 + k].x : 0u;
+            cur[k] = ok ? a.ranges[a.tile_base[v] + ty * TX + tx0 + k].x : 0u;
         }
-        if (!COUNT) end = rgs.x + a.n_head[gs];
-        uint32_t b = rgs.x;
-        for (; b < end; b += 256) {
+        const uint32_t end = rgs.x + a.n_head[gs];
+        for (uint32_t b = rgs.x; b < end; b += 256) {
             __syncthreads();
             const uint32_t j = b + threadIdx.x;
             if (j < end) {
-                const uint32_t row = a.list[j];
-                if (COUNT) {
-                    const int4 rc = ((const int4*)a.proj.rect)[row];
-                    auto rel = [](int c, int o) { return (uint32_t)min(max(c - o, 0), 8); };
-                    s_rect[threadIdx.x] = rel(rc.x, tx0) | rel(rc.y, sy * 8) << 8 | rel(rc.z, tx0) << 16 |
-                                          rel(rc.w, sy * 8) << 24;
-                    s_mask[threadIdx.x] = make_uint2(0u, 0u);
-                    if (a.cull) {
-                        const float2 xy = ((const float2*)a.proj.xy)[row];
-                        const float4 co = ((const float4*)a.proj.conic_opacity)[row];
-                        // the compositing kernels skip power < log(1/(255 alpha_max)); cull with a margin
-                        const float R2 = -2.f * __logf(__fdividef(kAlphaMin, co.w)) * 1.0001f + 2e-3f;
-                        float4 g0, g1;
-                        ellipse_consts(xy.x, xy.y, co.x, co.y, co.z, R2, g0, g1);
-                        s_g0[threadIdx.x] = g0;
-                        s_g1[threadIdx.x] = g1;
-                        // the saturation bound needs a*c - b^2 >= 1e-3 a c: the
-                        // relative rounding of the power stays far below its size
-                        const bool ok = co.x > 0.f && co.z > 0.f && co.x * co.z - co.y * co.y >= 1e-3f * co.x * co.z &&
-                                        co.w <= 1.f;
-                        s_co[threadIdx.x] = make_float4(co.x, co.y, co.z, ok ? co.w : 0.f);
-                    }
-                } else {
-                    s_row[threadIdx.x] = row;
-                    s_mask[threadIdx.x] = a.mask[j];
-                }
+                s_row[threadIdx.x] = a.list[j];
+                s_mask[threadIdx.x] = a.mask[j];
             }
             __syncthreads();
-            if (!COUNT || sat != 0xffu) {
-                const int n = (int)min(256u, end - b);
-                // the entries this tile row has work for (COUNT: rectangle covers the
-                // row; write pass: listed in some tile of the row), queued in order
-                // so that the work below runs on full warps
-                int nq = 0;
-                if (ty < TY) {
-                    for (int sb = 0; sb < n; sb += 32) {
-                        const int e = sb + lane;
-                        bool take = false;
-                        if (e < n) {
-                            if (COUNT) {
-                                const uint32_t rc = s_rect[e];
-                                take = (int)(rc >> 8 & 0xffu) <= warp && warp < (int)(rc >> 24);
-                            } else {
-                                take = ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) &
-                                        0xffu) != 0u;
-                            }
-                        }
-                        const unsigned bal = __ballot_sync(0xffffffffu, take);
-                        if (take) s_queue[warp][nq + __popc(bal & lt)] = (unsigned char)e;
-                        nq += __popc(bal);
-                    }
-                }
-                __syncwarp();
-                uint32_t packed[4] = {0u, 0u, 0u, 0u};  // COUNT: column counters of this chunk, two per word
-                for (int sb = 0; sb < nq; sb += 32) {
-                    if (COUNT && sat == 0xffu) break;  // warp-uniform: the row's lists have all ended
-                    const int qi = sb + lane;
-                    const int e = qi < nq ? s_queue[warp][qi] : 0;
-                    unsigned m = 0;  // tile columns of this tile row the entry is listed in
-                    if (qi < nq) {
-                        if (COUNT) {
-                            const uint32_t rc = s_rect[e];
-                            int lo = (int)(rc & 0xffu), hi = (int)(rc >> 16 & 0xffu);  // columns of the super-tile
-                            if (a.cull) {
-                                float ul, ur;
-                                if (!ellipse_band_extent(s_g0[e], s_g1[e], vlo, vhi, ul, ur)) {
-                                    hi = lo;
-                                } else {
-                                    // tiles [16 tx, 16 tx + 15] meeting [ul, ur]
-                                    const float fl = ceilf((ul - (float)(kTile - 1)) * (1.f / kTile));
-                                    const float fh = floorf(ur * (1.f / kTile));
-                                    lo = max(lo, (int)fminf(fmaxf(fl, -1.f), 1.0e6f) - tx0);
-                                    hi = min(hi, (int)fminf(fmaxf(fh, -2.f), 1.0e6f) + 1 - tx0);
-                                }
-                            }
-                            if (hi > lo) m = ((1u << hi) - (1u << lo)) & ~sat;
-                            reinterpret_cast<unsigned char*>(&s_mask[e])[warp] = (unsigned char)m;
-                        } else {
-                            m = (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu;
-                        }
-                    }
-                    if (COUNT) {
-                        const uint4 w = s_spread[m];
-                        packed[0] += __reduce_add_sync(0xffffffffu, w.x);
-                        packed[1] += __reduce_add_sync(0xffffffffu, w.y);
-                        packed[2] += __reduce_add_sync(0xffffffffu, w.z);
-                        packed[3] += __reduce_add_sync(0xffffffffu, w.w);
-                        if (a.cull) {
-                            // saturation sums of this batch: each lane weighs its own
-                            // columns into shared memory, then one warp sum per column
-                            const float4 co = s_co[e];
-                            unsigned mine = co.w > 0.f ? m : 0u;
-                            const unsigned cols = __reduce_or_sync(0xffffffffu, mine);
-                            if (cols) {
-                                uint32_t* sw = &s_w[warp][0][lane];  // [column][lane]
-#pragma unroll
-                                for (int k = 0; k < 8; ++k) sw[32 * k] = 0u;
-                                if (mine) {
-                                    const SatRow sr = sat_row(co, s_g0[e].x, s_g0[e].y, vlo, vhi_img);
-                                    do {
-                                        const int k = __ffs(mine) - 1;
-                                        mine &= mine - 1;
-                                        const float xlo = (float)((tx0 + k) * kTile);
-                                        sw[32 * k] = sat_weight(sr, xlo, fminf(xlo + (float)(kTile - 1), xmax_img));
-                                    } while (mine);
-                                }
-                                __syncwarp();
-                                unsigned left = cols;
-                                while (left) {
-                                    const int k = __ffs(left) - 1;
-                                    left &= left - 1;
-                                    const uint32_t r = __reduce_add_sync(0xffffffffu, sw[32 * k]);
-                                    if (lane == k) wsum += r;
-                                }
-                                __syncwarp();
-                                sat |= __ballot_sync(0xffffffffu, lane < 8 && wsum >= kSatThreshold) & 0xffu;
-                            }
-                        }
-                    } else {
-                        const uint32_t row = s_row[e];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const bool cov = (m >> k) & 1u;
-                            const unsigned bal = __ballot_sync(0xffffffffu, cov);
-                            if (cov) {
-                                const uint32_t pos = cur[k] + __popc(bal & lt);
-                                a.vals_out[pos] = row;
-                                if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
-                            }
-                            cur[k] += __popc(bal);
-                        }
-                    }
-                }
-                if (COUNT) {  // at most 256 rows per chunk: the 16-bit counters do not overflow
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (lane == k) cnt += (packed[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+            const int n = (int)min(256u, end - b);
+            // the entries listed in some tile of this row, queued in order so
+            // that the writes below run on full warps
+            int nq = 0;
+            if (ty < TY) {
+                for (int sb = 0; sb < n; sb += 32) {
+                    const int e = sb + lane;
+                    const bool take = e < n && ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) &
+                                                0xffu) != 0u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, take);
+                    if (take) s_queue[warp][nq + __popc(bal & lt)] = (unsigned char)e;
+                    nq += __popc(bal);
                 }
             }
-            if (COUNT) {
-                __syncthreads();
-                if (j < end) a.mask[j] = s_mask[threadIdx.x];
-                if (__syncthreads_and(sat == 0xffu)) {  // every list of the super-tile has ended
-                    b += 256;
-                    break;
+            __syncwarp();
+            for (int sb = 0; sb < nq; sb += 32) {
+                const int qi = sb + lane;
+                const int e = qi < nq ? s_queue[warp][qi] : 0;
+                const unsigned m =
+                    qi < nq ? (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu : 0u;
+                const uint32_t row = s_row[e];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const bool cov = (m >> k) & 1u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, cov);
+                    if (cov) {
+                        const uint32_t pos = cur[k] + __popc(bal & lt);
+                        a.vals_out[pos] = row;
+                        if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
+                    }
+                    cur[k] += __popc(bal);
                 }
-            }
-        }
-        if (COUNT) {
-            if (lane == 0) s_sat[warp] = sat;
-            if (lane < 8 && ty < TY && tx0 + lane < TX) a.tile_total[a.tile_base[v] + ty * TX + tx0 + lane] = cnt;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                a.n_head[gs] = min(b, end) - rgs.x;
-                a.sat_head[gs] = make_uint2(s_sat[0] | s_sat[1] << 8 | s_sat[2] << 16 | s_sat[3] << 24,
-                                            s_sat[4] | s_sat[5] << 8 | s_sat[6] << 16 | s_sat[7] << 24);
             }
         }
         __syncthreads();
@@ -1706,7 +1718,7 @@ struct SortLayout {
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
         off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
     size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_segsuper, off_nhead, off_sathead,
-        off_mask, off_tord;
+        off_nhead8, off_mask, off_tord;
     int64_t max_segs;
     size_t bytes;
 };
@@ -1772,6 +1784,7 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.off_segsuper = take(L.binned ? 4 * (size_t)L.max_segs : 4);
     L.off_nhead = take(4 * (size_t)std::max<int64_t>(L.total_super, 1));
     L.off_sathead = take(8 * (size_t)std::max<int64_t>(L.total_super, 1));
+    L.off_nhead8 = take(32 * (size_t)std::max<int64_t>(L.total_super, 1));
     L.off_mask = take(L.binned ? 8 * (size_t)capacity : 4);
     L.off_tord = take(66 * 4);  // tile-order class counts and cursors
     L.bytes = o;
@@ -1926,6 +1939,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.seg_cnt = U(L.off_segcnt);
         t.seg_super = U(L.off_segsuper);
         t.n_head = U(L.off_nhead);
+        t.n_head8 = U(L.off_nhead8);
         t.sat_head = (uint2*)(w + L.off_sathead);
         t.mask = (uint2*)(w + L.off_mask);
         t.ticket = tickets + 10;
@@ -1997,17 +2011,17 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         // written; one wave of resident CTAs per pass, which take super-tiles or
         // segments from ticket counters
         static const int per_sm_f[2] = {ctas_per_sm(k_tile_filter<false>, 256), ctas_per_sm(k_tile_filter<true>, 256)};
-        static const int per_sm_h[2] = {ctas_per_sm(k_tile_head<false>, 256), ctas_per_sm(k_tile_head<true>, 256)};
+        static const int per_sm_hw = ctas_per_sm(k_head_write, 256);
         auto blocks_f = [&](int c) { return (int)std::min<int64_t>(L.max_segs, (int64_t)ctx.num_sms * per_sm_f[c]); };
-        auto blocks_h = [&](int c) { return (int)std::min<int64_t>(sb, (int64_t)ctx.num_sms * per_sm_h[c]); };
+        const int blocks_hw = (int)std::min<int64_t>(sb, (int64_t)ctx.num_sms * per_sm_hw);
         count_launch(7);
-        k_tile_head<true><<<blocks_h(1), 256, 0, s>>>(t);
+        k_head_count<<<8 * sb, 256, 0, s>>>(t);
         k_seg_plan<<<1, 256, 0, s>>>(t);
         k_tile_filter<true><<<blocks_f(1), 256, 0, s>>>(t);
         k_seg_prefix<<<(int)(((int64_t)sb * 64 + 255) / 256), 256, 0, s>>>(t);
         k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity, (const int64_t*)(w + L.off_ninst1),
                                        bins.n_needed);
-        k_tile_head<false><<<blocks_h(0), 256, 0, s>>>(t);
+        k_head_write<<<blocks_hw, 256, 0, s>>>(t);
         k_tile_filter<false><<<blocks_f(0), 256, 0, s>>>(t);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);
