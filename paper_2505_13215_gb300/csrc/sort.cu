@@ -11,10 +11,13 @@
 // key in emission order.
 //
 // Radix passes are single-pass "onesweep"-style: one 8-bit digit per pass,
-// partitions of 3840 keys taken in ticket order by persistent CTAs, local
+// partitions of 4096 keys taken in ticket order by persistent CTAs, local
 // ranking of the keys of a warp (digit-bit ballots or a match instruction)
 // with shared-memory counters, and a decoupled look-back across partitions
-// whose waits are bounded (SPLAT_ERR_TIMEOUT on expiry).
+// whose waits are bounded (SPLAT_ERR_TIMEOUT on expiry).  On the binned path
+// the depth passes sort each view's rows in place (partitions stay inside a
+// view, digit counts and look-back are per view), so four passes give the
+// (view, depth) order.
 //
 // The binned path (the default up to 40960 tiles per view) orders by tile
 // without tile-digit passes: the depth-ordered rows are partitioned stably by
@@ -95,24 +98,22 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_t
 // Depth keys of the projected rows + histograms of their 4 digits
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int64_t n_rows, uint32_t* keys, uint32_t* vals,
-                                                    uint32_t* hist /*[9][256]*/, uint32_t* zero_a, int64_t n_zero_a,
+__global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int V, int blocks_per_view, uint32_t* keys,
+                                                    uint32_t* vals, uint32_t* dhist /*[4][V][256]*/,
+                                                    uint32_t* view_rows /*[V]*/, uint32_t* zero_a, int64_t n_zero_a,
                                                     unsigned long long* zero_b, int64_t n_zero_b)
 {
     __shared__ uint32_t s_hist[4][kRadix];
-    __shared__ uint32_t s_view[SPLAT_MAX_VIEWS];
+    __shared__ uint32_t s_rows;
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
-    if (threadIdx.x < SPLAT_MAX_VIEWS) s_view[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_rows = 0;
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int v = 0;  // view of row r, advanced with r (no division in the loop)
-    int64_t vend = proj.n;
-    if (r0 < n_rows) {
-        v = (int)(r0 / proj.n);
-        vend = (int64_t)(v + 1) * proj.n;
-    }
-    for (int64_t r = r0; r < n_rows; r += stride) {
+    // block b serves view b / blocks_per_view: its digit counts are that view's
+    const int v = (int)(blockIdx.x / blocks_per_view), bi = (int)(blockIdx.x - v * blocks_per_view);
+    const int64_t n = proj.n, r_base = (int64_t)v * n;
+    uint32_t mine = 0;
+    for (int64_t i = bi * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)blocks_per_view * blockDim.x) {
+        const int64_t r = r_base + i;
         const uint32_t nt = proj.n_tiles[r];
         const float depth = ((const float4*)proj.rgb_depth)[r].w;
         const uint32_t k = nt > 0 ? __float_as_uint(depth) : 0xffffffffu;
@@ -120,20 +121,20 @@ __global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int64_t n_r
         vals[r] = (uint32_t)r;
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xff], 1u);
-        while (r >= vend) {
-            ++v;
-            vend += proj.n;
-        }
-        atomicAdd(&s_view[v], 1u);
+        ++mine;
     }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_a; i += stride) zero_a[i] = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_b; i += stride) zero_b[i] = 0;
+    mine = __reduce_add_sync(0xffffffffu, mine);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_rows, mine);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
         const uint32_t c = (&s_hist[0][0])[i];
-        if (c) atomicAdd(&hist[i], c);
+        const int p = i / kRadix, d = i - p * kRadix;
+        if (c) atomicAdd(&dhist[((size_t)p * V + v) * kRadix + d], c);
     }
-    if (threadIdx.x < SPLAT_MAX_VIEWS && s_view[threadIdx.x]) atomicAdd(&hist[8 * kRadix + threadIdx.x], s_view[threadIdx.x]);
+    if (threadIdx.x == 0 && s_rows) atomicAdd(&view_rows[v], s_rows);
 }
 
 // ---------------------------------------------------------------------------
@@ -148,7 +149,7 @@ struct PassArgs {
     const int64_t* n_dev;  // element count on the device (null: n_host)
     int64_t n_host;
     int64_t cap;
-    const uint32_t* hist;  // [256] digit counts of this pass
+    const uint32_t* hist;  // [segments][256] digit counts of this pass
     uint32_t* lb;          // [parts][256] look-back words of this pass (zeroed)
     uint32_t* lb_next;     // [parts][256] zeroed here for the next pass (may be null)
     uint32_t* ticket;
@@ -156,7 +157,9 @@ struct PassArgs {
     int stage;
     int shift;
     int64_t spin_limit;
-    int64_t view_div;      // > 0: write keys_out = value / view_div (the row's view) instead of the key
+    int64_t seg_len;       // > 0: the keys form segments of seg_len keys (the views' rows), each sorted on
+                           // its own in place, with hist holding [segments][256] counts; 0: one segment
+    int hist_sum;          // one segment: the digit counts are the sum of hist_sum [256] arrays
     int ballot_rank;       // rank by digit-bit ballots (many distinct digits per warp) instead of match
 };
 
@@ -165,7 +168,6 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
     __shared__ uint32_t s_keys[kSortPart];
     __shared__ uint32_t s_vals[kSortPart];
     __shared__ uint32_t s_whist[kSortWarps][kRadix];
-    __shared__ uint32_t s_gofs[kRadix];
     __shared__ uint32_t s_dstart[kRadix];
     __shared__ uint32_t s_base[kRadix];
     __shared__ uint32_t s_tmp[8];
@@ -174,10 +176,15 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
     if (status_failed(a.status)) return;
     const int64_t n = a.n_dev ? min(*a.n_dev, a.cap) : a.n_host;
     if (n <= 0) return;
-    const int64_t parts = (n + kSortPart - 1) / kSortPart;
+    // segments of seg keys, pps partitions each; a partition never crosses a
+    // segment boundary, and its look-back stops at its segment's first one
+    const int64_t seg = a.seg_len > 0 ? a.seg_len : n;
+    const int64_t pps = (seg + kSortPart - 1) / kSortPart;
+    const int64_t parts = pps * ((n + seg - 1) / seg);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = lanemask_lt();
-    s_gofs[tid] = block_excl_scan256(a.hist[tid], s_tmp, nullptr);
+    int64_t cur_seg = -1;
+    uint32_t gofs = 0;  // first output position of digit tid in the current segment
 
     for (;;) {
         if (tid == 0) s_ticket = atomicAdd(a.ticket, 1u);
@@ -186,14 +193,26 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
         __syncthreads();
         const int64_t ticket = s_ticket;
         if (ticket >= parts) break;
-        const int64_t base = ticket * kSortPart;
+        const int64_t sg = ticket / pps, lp = ticket - sg * pps, first = sg * pps;
+        if (sg != cur_seg) {  // block-uniform
+            cur_seg = sg;
+            uint32_t h = 0;
+            if (a.seg_len > 0) {
+                h = a.hist[sg * kRadix + tid];
+            } else {
+                for (int q = 0; q < a.hist_sum; ++q) h += a.hist[q * kRadix + tid];
+            }
+            gofs = (uint32_t)(sg * seg) + block_excl_scan256(h, s_tmp, nullptr);
+        }
+        const int64_t seg_end = min(n, (sg + 1) * seg);
+        const int64_t base = sg * seg + lp * kSortPart;
         const int64_t wbase = base + (int64_t)warp * 32 * kSortItems;
 
         uint32_t k[kSortItems], v[kSortItems], r[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const int64_t idx = wbase + j * 32 + lane;
-            const bool ok = idx < n;
+            const bool ok = idx < seg_end;
             k[j] = ok ? a.keys_in[idx] : 0u;
             v[j] = ok ? a.vals_in[idx] : 0u;
         }
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const int64_t idx = wbase + j * 32 + lane;
-            const bool ok = idx < n;
+            const bool ok = idx < seg_end;
             const uint32_t dj = (k[j] >> a.shift) & 0xff;
             const unsigned valid = __ballot_sync(0xffffffffu, ok);
             unsigned same = valid;
@@ -241,7 +260,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
             cnt += c;
         }
         uint32_t* my = a.lb + ticket * kRadix + d;
-        st_relaxed(my, (ticket == 0 ? kFlagPrefix : kFlagAgg) | cnt);
+        st_relaxed(my, (lp == 0 ? kFlagPrefix : kFlagAgg) | cnt);
         if (a.lb_next) a.lb_next[ticket * kRadix + d] = 0;
         s_dstart[d] = block_excl_scan256(cnt, s_tmp, nullptr);
         // decoupled look-back for digit d, kLookWindow predecessors per step
@@ -249,14 +268,14 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
         // so a walk of one predecessor per L2 round trip would make the last
         // partition wait for about half the partition count of round trips
         uint32_t excl = 0;
-        if (ticket > 0) {
+        if (lp > 0) {
             int64_t j = ticket - 1;  // nearest predecessor not yet added
             int64_t spins = 0;
             for (;;) {
                 uint32_t w[kLookWindow];
 #pragma unroll
                 for (int q = 0; q < kLookWindow; ++q)
-                    w[q] = j - q >= 0 ? ld_relaxed(a.lb + (j - q) * kRadix + d) : kFlagPrefix;
+                    w[q] = j - q >= first ? ld_relaxed(a.lb + (j - q) * kRadix + d) : kFlagPrefix;
                 // add the published words from the nearest one back, up to and
                 // including the first inclusive prefix, or up to the first word
                 // not yet published
@@ -283,13 +302,13 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
             }
             st_relaxed(my, kFlagPrefix | ((excl + cnt) & kValMask));
         }
-        s_base[d] = s_gofs[d] + excl - s_dstart[d];
+        s_base[d] = gofs + excl - s_dstart[d];
         __syncthreads();
         // local scatter into digit order
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const int64_t idx = wbase + j * 32 + lane;
-            if (idx < n) {
+            if (idx < seg_end) {
                 const uint32_t dd = (k[j] >> a.shift) & 0xff;
                 const uint32_t pos = s_dstart[dd] + s_whist[warp][dd] + r[j];
                 s_keys[pos] = k[j];
@@ -297,13 +316,13 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
             }
         }
         __syncthreads();
-        const int nvalid = (int)min((int64_t)kSortPart, n - base);
+        const int nvalid = (int)min((int64_t)kSortPart, seg_end - base);
         for (int i = tid; i < nvalid; i += kSortThreads) {
             const uint32_t key = s_keys[i];
             const uint32_t out = s_base[(key >> a.shift) & 0xff] + i;
             if (out >= (uint64_t)n) continue;  // only after a timed-out look-back
             const uint32_t val = s_vals[i];
-            if (a.keys_out) a.keys_out[out] = a.view_div ? (uint32_t)(val / a.view_div) : key;
+            if (a.keys_out) a.keys_out[out] = key;
             a.vals_out[out] = val;
         }
         __syncthreads();
@@ -1716,7 +1735,7 @@ struct SortLayout {
     int64_t parts_d, parts_t, parts_scan, n_chunks;
     int64_t total_tiles, total_super;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
-        off_tvals, off_hist, off_tickets, off_plan, off_counts, off_first, off_total;
+        off_tvals, off_hist, off_dhist, off_tickets, off_plan, off_counts, off_first, off_total;
     size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_segsuper, off_nhead, off_sathead,
         off_nhead8, off_mask, off_tord;
     int64_t max_segs;
@@ -1753,7 +1772,7 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.binned = tile_sort == 2 || (tile_sort == 0 && tmax <= kBinMaxTiles);
     L.chunk = bin_chunk(capacity);
     L.max_chunks = (capacity + L.chunk - 1) / L.chunk + V;
-    L.parts_d = (n_rows + kSortPart - 1) / kSortPart;
+    L.parts_d = V > 0 ? (int64_t)V * ((n_rows / V + kSortPart - 1) / kSortPart) : 0;  // partitions within views
     L.parts_t = L.binned ? 0 : (capacity + kSortPart - 1) / kSortPart;
     L.parts_scan = (n_rows + kScanPart - 1) / kScanPart;
     L.n_chunks = L.binned ? 1 : (capacity + kDupChunk - 1) / kDupChunk + 1;
@@ -1769,6 +1788,7 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.off_tkeys = take(L.binned ? 4 : 4 * (size_t)capacity);
     L.off_tvals = take(L.binned ? 4 : 4 * (size_t)capacity);
     L.off_hist = take(4 * (size_t)kRadix * 9);
+    L.off_dhist = take(4 * (size_t)kRadix * 4 * std::max(V, 1));  // depth digits per view (zeroed with hist)
     L.off_tickets = take(4 * 16);
     L.off_plan = take(sizeof(BinPlan));
     L.off_counts = take(L.binned ? 4 * (size_t)L.max_chunks * L.smax : 4);
@@ -1844,20 +1864,24 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     uint32_t* hist = U(L.off_hist);
     uint32_t* tickets = U(L.off_tickets);
     const int resident = ctx.num_sms * sort_ctas_per_sm();
-    const bool by_view = L.binned && vb.V > 1;
 
-    // 1. depth keys + digit histograms (+ rows per view); zero the first depth look-back buffer and the scan's
+    // 1. depth keys + per-view digit histograms (+ rows per view); zero the first depth look-back buffer and the
+    // scan's
+    uint32_t* dhist = U(L.off_dhist);
     {
         static const int per_sm = ctas_per_sm(k_depth_keys, 256);
-        const int blocks = (int)std::min<int64_t>((n_rows + 255) / 256, (int64_t)ctx.num_sms * per_sm);
+        const int per_view = (int)std::max<int64_t>(
+            1, std::min<int64_t>((proj.n + 255) / 256, (int64_t)ctx.num_sms * per_sm / vb.V));
         count_launch();
-        k_depth_keys<<<blocks, 256, 0, s>>>(proj, n_rows, U(L.off_dkeys[0]), U(L.off_dvals[0]), hist,
-                                            U(L.off_dlb[0]), L.parts_d * kRadix,
-                                            (unsigned long long*)(w + L.off_scan_lb), L.parts_scan);
+        k_depth_keys<<<vb.V * per_view, 256, 0, s>>>(proj, vb.V, per_view, U(L.off_dkeys[0]), U(L.off_dvals[0]), dhist,
+                                                     hist + 8 * kRadix, U(L.off_dlb[0]), L.parts_d * kRadix,
+                                                     (unsigned long long*)(w + L.off_scan_lb), L.parts_scan);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    // 2. depth passes (buffers 0 -> 1 -> 0 -> 1 -> 0), then (binned, V > 1) a stable pass on the view
-    const int passes = by_view ? 5 : 4;
+    // 2. depth passes (buffers 0 -> 1 -> 0 -> 1 -> 0).  Binned: each view's rows sorted in place, giving the
+    // (view, depth) order the super-tile partition takes.  Radix path: one sort of all rows by depth, so that
+    // the rows without tiles come last (the duplication's chunks assume no such row between listed ones)
+    const int passes = 4;
     for (int p = 0; p < passes; ++p) {
         PassArgs a{};
         a.keys_in = U(L.off_dkeys[p & 1]);
@@ -1867,16 +1891,17 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.n_dev = nullptr;
         a.n_host = n_rows;
         a.cap = n_rows;
-        a.hist = hist + (p < 4 ? p : 8) * kRadix;
+        a.hist = dhist + (size_t)p * vb.V * kRadix;
         a.lb = U(L.off_dlb[p & 1]);
         a.lb_next = p + 1 < passes ? U(L.off_dlb[(p + 1) & 1]) : nullptr;
-        a.ticket = tickets + (p < 4 ? p : 9);
+        a.ticket = tickets + p;
         a.status = status;
         a.stage = SPLAT_STAGE_DEPTH_SORT;
         a.shift = p < 4 ? 8 * p : 0;
         a.spin_limit = ctx.spin_limit;
-        a.view_div = (by_view && p == 3) ? proj.n : 0;
-        a.ballot_rank = p < 3;  // the low depth digits take many values in a warp, the top one and the view few
+        a.seg_len = L.binned ? proj.n : 0;
+        a.hist_sum = vb.V;
+        a.ballot_rank = p < 3;  // the low depth digits take many values in a warp, the top one few
         if ((err = run_pass(a, L.parts_d, resident, s)) != cudaSuccess) return err;
     }
     const uint32_t* rows = U(L.off_dvals[passes & 1]);
@@ -2068,6 +2093,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.n_host = 0;
         a.cap = bins.capacity;
         a.hist = hist + (4 + p) * kRadix;
+        a.hist_sum = 1;
         a.lb = U(L.off_tlb[p & 1]);
         a.lb_next = p + 1 < tile_passes ? U(L.off_tlb[(p + 1) & 1]) : nullptr;
         a.ticket = tickets + 5 + p;
