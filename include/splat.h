@@ -552,10 +552,12 @@ int64_t splat_launch_count(void);
 /*
  * Selects how splat_bin_sort orders the instances by tile (the result is the
  * same):  0 = automatic (default), 1 = tile-digit radix passes over the
- * instance list, 2 = binned partition with per-tile shared-memory counters
- * (used automatically when every view has at most 40960 tiles).  Host-side
- * global (the library default of splat_options.tile_sort); splat_workspace_size
- * depends on it.
+ * instance list, 2 = binned partition: the rows split by 8x8-tile super-tile,
+ * then each super-tile's list filtered into its tiles' lists (used
+ * automatically when every view has at most 40960 tiles; never for a view of
+ * more than 1023 super-tiles in x or y or more than about 5000 in all, which
+ * take the radix passes).  Host-side global (the library default of
+ * splat_options.tile_sort); splat_workspace_size depends on it.
  */
 void splat_set_tile_sort(int mode);
 

@@ -98,43 +98,91 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_t
 // Depth keys of the projected rows + histograms of their 4 digits
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_depth_keys(splat_proj proj, int V, int blocks_per_view, uint32_t* keys,
-                                                    uint32_t* vals, uint32_t* dhist /*[4][V][256]*/,
-                                                    uint32_t* view_rows /*[V]*/, uint32_t* zero_a, int64_t n_zero_a,
-                                                    unsigned long long* zero_b, int64_t n_zero_b)
+struct DepthArgs {
+    splat_proj proj;
+    int V, blocks_per_view;
+    uint32_t* keys;
+    uint32_t* vals;
+    uint32_t* dhist;        // [4][V][256] digit counts per view
+    uint32_t* super_total;  // [total_super] entries of each super-tile list (binned path), or null
+    int super_base[SPLAT_MAX_VIEWS];
+    int STX[SPLAT_MAX_VIEWS], STY[SPLAT_MAX_VIEWS];
+    uint32_t* zero_a;
+    int64_t n_zero_a;
+    unsigned long long* zero_b;
+    int64_t n_zero_b;
+    unsigned long long* zero_c;
+    int64_t n_zero_c;
+};
+
+// Block b serves view b / blocks_per_view.  The super-tile list sizes (binned
+// path) are counted through a 2D difference array of the view's super-tile
+// grid in dynamic shared memory ((STX + 1) x (STY + 1) words): a row adds its
+// super-rectangle with four corner updates, and the block's prefix sums over
+// x then y give its counts per super-tile.
+__global__ void __launch_bounds__(256) k_depth_keys(DepthArgs a)
 {
+    extern __shared__ uint32_t s_diff[];
     __shared__ uint32_t s_hist[4][kRadix];
-    __shared__ uint32_t s_rows;
+    const int v = (int)(blockIdx.x / a.blocks_per_view), bi = (int)(blockIdx.x - v * a.blocks_per_view);
+    const int SX = a.super_total ? a.STX[v] + 1 : 0, SY = a.super_total ? a.STY[v] + 1 : 0;
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
-    if (threadIdx.x == 0) s_rows = 0;
+    for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) s_diff[i] = 0;
     __syncthreads();
-    // block b serves view b / blocks_per_view: its digit counts are that view's
-    const int v = (int)(blockIdx.x / blocks_per_view), bi = (int)(blockIdx.x - v * blocks_per_view);
-    const int64_t n = proj.n, r_base = (int64_t)v * n;
-    uint32_t mine = 0;
-    for (int64_t i = bi * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)blocks_per_view * blockDim.x) {
+    const int64_t n = a.proj.n, r_base = (int64_t)v * n;
+    for (int64_t i = bi * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)a.blocks_per_view * blockDim.x) {
         const int64_t r = r_base + i;
-        const uint32_t nt = proj.n_tiles[r];
-        const float depth = ((const float4*)proj.rgb_depth)[r].w;
+        const uint32_t nt = a.proj.n_tiles[r];
+        const float depth = ((const float4*)a.proj.rgb_depth)[r].w;
         const uint32_t k = nt > 0 ? __float_as_uint(depth) : 0xffffffffu;
-        keys[r] = k;
-        vals[r] = (uint32_t)r;
+        a.keys[r] = k;
+        a.vals[r] = (uint32_t)r;
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xff], 1u);
-        ++mine;
+        if (nt > 0 && SX) {  // the super-rectangle [sx0, sx1) x [sy0, sy1) of the row's tile rectangle
+            const int4 rc = ((const int4*)a.proj.rect)[r];
+            const int sx0 = rc.x >> 3, sy0 = rc.y >> 3, sx1 = (rc.z + 7) >> 3, sy1 = (rc.w + 7) >> 3;
+            atomicAdd(&s_diff[sy0 * SX + sx0], 1u);
+            atomicAdd(&s_diff[sy0 * SX + sx1], 0xffffffffu);
+            atomicAdd(&s_diff[sy1 * SX + sx0], 0xffffffffu);
+            atomicAdd(&s_diff[sy1 * SX + sx1], 1u);
+        }
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_a; i += stride) zero_a[i] = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_zero_b; i += stride) zero_b[i] = 0;
-    mine = __reduce_add_sync(0xffffffffu, mine);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_rows, mine);
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t i = gt; i < a.n_zero_a; i += stride) a.zero_a[i] = 0;
+    for (int64_t i = gt; i < a.n_zero_b; i += stride) a.zero_b[i] = 0;
+    for (int64_t i = gt; i < a.n_zero_c; i += stride) a.zero_c[i] = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
         const uint32_t c = (&s_hist[0][0])[i];
         const int p = i / kRadix, d = i - p * kRadix;
-        if (c) atomicAdd(&dhist[((size_t)p * V + v) * kRadix + d], c);
+        if (c) atomicAdd(&a.dhist[((size_t)p * a.V + v) * kRadix + d], c);
     }
-    if (threadIdx.x == 0 && s_rows) atomicAdd(&view_rows[v], s_rows);
+    if (SX) {
+        for (int y = threadIdx.x; y < SY; y += blockDim.x) {  // prefix along x
+            uint32_t run = 0;
+            for (int x = 0; x < SX; ++x) {
+                run += s_diff[y * SX + x];
+                s_diff[y * SX + x] = run;
+            }
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < SX; x += blockDim.x) {  // then along y
+            uint32_t run = 0;
+            for (int y = 0; y < SY; ++y) {
+                run += s_diff[y * SX + x];
+                s_diff[y * SX + x] = run;
+            }
+        }
+        __syncthreads();
+        const int STX = SX - 1, nsup = STX * (SY - 1);
+        for (int i = threadIdx.x; i < nsup; i += blockDim.x) {
+            const int y = i / STX, x = i - y * STX;
+            const uint32_t c = s_diff[y * SX + x];
+            if (c) atomicAdd(&a.super_total[a.super_base[v] + i], c);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -575,250 +623,336 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* keys, const int6
 }
 
 // ---------------------------------------------------------------------------
-// Binned tile partition (replaces the tile-digit radix passes when one view's
-// tile counters fit in shared memory).  Rows are sorted by (view, depth); the
-// instance stream of each view is cut into chunks of consecutive slots.
-//   count:   per chunk, instances per tile (shared-memory counters)
-//   prefix:  per tile, exclusive sum over the view's chunks + tile total
-//   ranges:  exclusive sum of the tile totals -> [start, end) of every tile
-//   scatter: per chunk, rows in order, each tile's slot = its cursor++ ; the
-//            result is the stable sort of the instances by tile.
+// Super-tile lists (level 1 of the binned path): a stable multi-split of the
+// (view, depth)-ordered visible rows by 8x8-tile super-tile.  A row enters
+// the list of every super-tile its tile rectangle meets, in raster order of
+// its super-rectangle, and the scan of the rows' super-tile counts gives every
+// row its first slot in that order (the slots of a view are contiguous).  The
+// lists' sizes come from the depth-key pass; one onesweep-style pass over
+// equal runs of slots then ranks each run's entries per super-tile in slot
+// order, finds every super-tile's offset from the runs before it by decoupled
+// look-back, and writes the entries in a second sweep over the same slots.
 // ---------------------------------------------------------------------------
 
-constexpr int kBinThreads = 256;
-constexpr int64_t kBinMaxTiles = 40960;  // per view, shared-memory counters
+constexpr int64_t kBinMaxTiles = 40960;  // per view: the binned path's default range
+constexpr int kSplitSlots = 4096;        // list slots per split partition (512 per warp)
+constexpr int kSplitWarpSlots = kSplitSlots / 8;
+constexpr int kSplitMaxSmem = 200 * 1024;  // shared memory the split's counters and grids may take
+constexpr unsigned long long kSplitAgg = 1ull << 62, kSplitPrefix = 2ull << 62, kSplitMask = (1ull << 62) - 1;
 
-struct BinPlan {
-    uint32_t S[SPLAT_MAX_VIEWS + 1];      // first slot of each view
-    uint32_t R[SPLAT_MAX_VIEWS + 1];      // first (view, depth)-sorted row of each view
-    uint32_t cbase[SPLAT_MAX_VIEWS + 1];  // first chunk of each view; cbase[V] = chunk count
-};
-
-struct BinArgs {
+struct SplitArgs {
     splat_proj proj;
-    int shift;                  // level: 0 tiles, 3 super-tiles of 8x8 tiles
-    const uint32_t* rows;
-    const uint32_t* offsets;
-    const uint32_t* view_hist;  // [V] rows per view
-    BinPlan* plan;
+    const uint32_t* rows;          // [V * n] rows, each view's in depth order, its visible ones first
+    const uint32_t* offsets;       // [V * n] first list slot of each of those rows
+    const uint32_t* super_total;   // [total_super] entries of each super-tile list
+    const int64_t* n_instances;    // K1, the slot count (checked against the capacity by the scan)
     int V;
-    int64_t n_rows;
-    uint32_t chunk;
-    int tmax;                   // row stride of counts
-    int total_tiles;
-    int tile_base[SPLAT_MAX_VIEWS + 1];
-    int TX[SPLAT_MAX_VIEWS];
-    uint32_t* counts;           // [chunks][tmax]
-    uint32_t* first_row;        // [chunks]
-    uint32_t* tile_total;       // [total_tiles]
-    uint2* ranges;
-    uint32_t* vals_out;
-    uint32_t* keys_out;         // may be null
-    const int64_t* n_instances;
-    int64_t capacity;
+    int64_t n;                     // rows per view
+    int smax;                      // row stride of the per-warp counters (>= every view's super-tile count)
+    int sdiff;                     // row stride of the per-warp difference grids (>= (STX + 1) (STY + 1))
+    int total_super;
+    int super_base[SPLAT_MAX_VIEWS + 1];
+    int STX[SPLAT_MAX_VIEWS], STY[SPLAT_MAX_VIEWS];
+    unsigned long long* lb;        // [max_parts][smax] look-back words (zeroed)
+    int64_t max_parts;
+    uint32_t* ticket;
+    uint32_t* list;                // out: the super-tile lists, K1 entries
+    uint2* sranges;                // out: [total_super] [start, end) of each list, (0, 0) when empty
     int32_t* status;
+    int64_t spin_limit;
 };
 
-// the row's rectangle at this level and its cell count
-__device__ __forceinline__ int4 level_rect(const BinArgs& a, uint32_t row, uint32_t& n)
+// Last position p in [lo, hi) with offsets[p] <= s, given offsets[lo] <= s
+// (the warp probes 32 positions per step).
+__device__ __forceinline__ int64_t warp_search(const uint32_t* offsets, int64_t lo, int64_t hi, uint32_t s, int lane)
 {
-    const int4 rc = shifted_rect(((const int4*)a.proj.rect)[row], a.shift);
-    n = a.proj.n_tiles[row] ? (uint32_t)((rc.z - rc.x) * (rc.w - rc.y)) : 0u;
-    return rc;
-}
-
-__global__ void k_bin_plan(BinArgs a)
-{
-    if (threadIdx.x != 0 || status_failed(a.status)) return;
-    const int64_t K = min(*a.n_instances, a.capacity);
-    BinPlan P;
-    P.R[0] = 0;
-    for (int v = 0; v < a.V; ++v) P.R[v + 1] = P.R[v] + (a.V > 1 ? a.view_hist[v] : (uint32_t)a.n_rows);
-    for (int v = 0; v < a.V; ++v) P.S[v] = P.R[v] < (uint32_t)a.n_rows ? a.offsets[P.R[v]] : (uint32_t)K;
-    P.S[a.V] = (uint32_t)K;
-    P.cbase[0] = 0;
-    for (int v = 0; v < a.V; ++v) P.cbase[v + 1] = P.cbase[v] + (P.S[v + 1] - P.S[v] + a.chunk - 1) / a.chunk;
-    *a.plan = P;
-}
-
-struct ChunkGeo {
-    int v;
-    uint32_t cs, ce;   // slot range
-};
-
-__device__ __forceinline__ ChunkGeo chunk_geo(const BinPlan& P, int V, uint32_t chunk, uint32_t g)
-{
-    ChunkGeo c;
-    c.v = 0;
-    for (int w = 1; w < V; ++w)
-        if (g >= P.cbase[w]) c.v = w;
-    c.cs = P.S[c.v] + (g - P.cbase[c.v]) * chunk;
-    c.ce = min(c.cs + chunk, P.S[c.v + 1]);
-    return c;
-}
-
-// Last row r in [lo, hi) with offsets[r] <= s (offsets[lo] <= s), by one warp.
-__device__ __forceinline__ uint32_t warp_search(const uint32_t* offsets, uint32_t lo, uint32_t hi, uint32_t s)
-{
-    const int lane = threadIdx.x & 31;
     while (hi - lo > 1) {
-        const uint32_t step = (hi - lo + 31) / 32;
-        const uint32_t p = lo + lane * step;
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t p = lo + lane * step;
         const bool ok = p < hi && offsets[p] <= s;
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        const int L = 31 - __clz(m);
-        const uint32_t nlo = lo + L * step;
+        const unsigned m = __ballot_sync(0xffffffffu, ok) | 1u;
+        const int64_t nlo = lo + (31 - __clz(m)) * step;
         hi = min(hi, nlo + step);
         lo = nlo;
     }
     return lo;
 }
 
-// Adds +1 on the tiles of the rectangle [x0,x1) x [y0,y1) to a 2D difference
-// array of (TX+1) x (TY+1) entries.
-__device__ __forceinline__ void diff_rect(int* d, int TXp, int x0, int y0, int x1, int y1)
+// One warp's slots [sa, sb) of view v, from its row j0 on, in rounds of 32
+// rows: each row's entries whose slot lies in the range, in slot order, ranked
+// per super-tile by ballots over the bits of the super-tile index
+// (depth-ordered rows are scattered over the image, so a round holds many
+// distinct super-tiles, for which a match instruction is slow); the warp's
+// counter of each super-tile advances by its entries.  WRITE: the counters
+// hold the warp's first list slot of every super-tile and each entry is
+// written there.
+template <bool WRITE>
+__device__ __forceinline__ void split_sweep(const SplitArgs& a, int v, int nbits, int64_t j0, uint32_t sa,
+                                            uint32_t sb, uint32_t* cnt, int lane, unsigned lt)
 {
-    if (x1 <= x0 || y1 <= y0) return;
-    atomicAdd(&d[y0 * TXp + x0], 1);
-    atomicAdd(&d[y0 * TXp + x1], -1);
-    atomicAdd(&d[y1 * TXp + x0], -1);
-    atomicAdd(&d[y1 * TXp + x1], 1);
-}
-
-// Per chunk: instances per tile.  Each row's slots inside the chunk are a run of
-// its row-major tile sequence, i.e. at most three rectangles, recorded in a 2D
-// difference array whose 2D prefix sum gives the per-tile counts.
-__global__ void __launch_bounds__(kBinThreads) k_bin_count(BinArgs a)
-{
-    extern __shared__ int dsm[];  // [(TY+1) * (TX+1)] of the largest view
-    __shared__ uint32_t s_first;
-    __shared__ BinPlan P;
-    if (status_failed(a.status)) return;
-    if (threadIdx.x == 0) P = *a.plan;
-    __syncthreads();
-    const uint32_t nchunks = P.cbase[a.V];
-    for (uint32_t g = blockIdx.x; g < nchunks; g += gridDim.x) {
-        const ChunkGeo c = chunk_geo(P, a.V, a.chunk, g);
-        const int TX = a.TX[c.v];
-        const int T = a.tile_base[c.v + 1] - a.tile_base[c.v];
-        const int TY = T / TX;
-        const int TXp = TX + 1;
-        const int nd = TXp * (TY + 1);
-        for (int i = threadIdx.x; i < nd; i += kBinThreads) dsm[i] = 0;
-        if (threadIdx.x < 32) {
-            const uint32_t r0 = warp_search(a.offsets, P.R[c.v], P.R[c.v + 1], c.cs);
-            if (threadIdx.x == 0) {
-                s_first = r0;
-                a.first_row[g] = r0;
-            }
+    const int STX = a.STX[v];
+    const int64_t vend = (int64_t)(v + 1) * a.n;
+    auto emit = [&](bool ok, uint32_t d, uint32_t row) {
+        unsigned peers = __ballot_sync(0xffffffffu, ok);
+        for (int b = 0; b < nbits; ++b) {  // warp-uniform
+            const bool bit = (d >> b) & 1u;
+            const unsigned bb = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bb : ~bb;
         }
-        __syncthreads();
-        const uint32_t r0 = s_first, rend = P.R[c.v + 1];
-        // rows r0 .. while offsets < ce, row-parallel
-        for (uint32_t j = r0 + threadIdx.x;; j += kBinThreads) {
-            const bool in = j < rend && a.offsets[j] < c.ce;
-            if (__syncthreads_or(in) == 0) break;
-            if (!in) continue;
+        if (ok) {
+            const int leader = __ffs(peers) - 1;
+            uint32_t prev = 0;
+            if (lane == leader) {
+                prev = cnt[d];
+                cnt[d] = prev + __popc(peers);
+            }
+            prev = __shfl_sync(peers, prev, leader);
+            if (WRITE) a.list[prev + __popc(peers & lt)] = row;
+        }
+        __syncwarp();
+    };
+    for (int64_t jb = j0;; jb += 32) {
+        const int64_t j = jb + lane;
+        // c entries of row j from its entry kl on fall inside [sa, sb); pk: the
+        // super-rectangle's origin x | y << 10 | width << 20
+        uint32_t row = 0, c = 0, kl = 0, pk = 0;
+        bool past = true;
+        if (j < vend) {
             const uint32_t off = a.offsets[j];
-            const uint32_t row = a.rows[j];
-            uint32_t n;
-            const int4 rc = level_rect(a, row, n);
-            const int w = rc.z - rc.x;
-            const uint32_t lo = max(off, c.cs) - off, hi = min(off + n, c.ce) - off;  // [lo, hi) of the row's tiles
-            const int ylo = (int)(lo / w), xlo = (int)(lo - ylo * w);
-            const int yhi = (int)((hi - 1) / w), xhi = (int)(hi - 1 - yhi * w);       // last tile, inclusive
-            if (ylo == yhi) {
-                diff_rect(dsm, TXp, rc.x + xlo, rc.y + ylo, rc.x + xhi + 1, rc.y + ylo + 1);
-            } else {
-                diff_rect(dsm, TXp, rc.x + xlo, rc.y + ylo, rc.z, rc.y + ylo + 1);
-                diff_rect(dsm, TXp, rc.x, rc.y + ylo + 1, rc.z, rc.y + yhi);
-                diff_rect(dsm, TXp, rc.x, rc.y + yhi, rc.x + xhi + 1, rc.y + yhi + 1);
+            past = off >= sb;
+            if (!past) {
+                row = a.rows[j];
+                const int4 rc = ((const int4*)a.proj.rect)[row];
+                const int sx0 = rc.x >> 3, sy0 = rc.y >> 3, sx1 = (rc.z + 7) >> 3, sy1 = (rc.w + 7) >> 3;
+                if (sx1 > sx0 && sy1 > sy0) {
+                    const uint32_t cr = (uint32_t)((sx1 - sx0) * (sy1 - sy0));
+                    kl = off < sa ? sa - off : 0u;
+                    const uint32_t kh = min(cr, sb - off);
+                    c = kh > kl ? kh - kl : 0u;
+                    pk = (uint32_t)sx0 | (uint32_t)sy0 << 10 | (uint32_t)(sx1 - sx0) << 20;
+                }
             }
         }
-        __syncthreads();
-        // 2D inclusive prefix sum: along x per row, then along y per column
-        for (int y = threadIdx.x; y < TY; y += kBinThreads) {
-            int run = 0;
-            for (int x = 0; x < TX; ++x) {
-                run += dsm[y * TXp + x];
-                dsm[y * TXp + x] = run;
+        if (__all_sync(0xffffffffu, c <= 1u && kl == 0u)) {  // the common case: a row's first entry at most
+            emit(c == 1u, (pk >> 10 & 1023u) * STX + (pk & 1023u), row);
+        } else {
+            // entry slots of the round in order: lane l owns [e, e + c)
+            uint32_t e = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, e, o);
+                if (lane >= o) e += y;
+            }
+            const uint32_t E = __shfl_sync(0xffffffffu, e, 31);
+            e -= c;
+            for (uint32_t s0 = 0; s0 < E; s0 += 32) {
+                const uint32_t sl = s0 + lane;
+                // the row of slot sl: the last lane whose first slot is at or before it
+                int src = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(0xffffffffu, e, src + step) <= sl) src += step;
+                const uint32_t srow = __shfl_sync(0xffffffffu, row, src), spk = __shfl_sync(0xffffffffu, pk, src);
+                const uint32_t k = sl - __shfl_sync(0xffffffffu, e, src) + __shfl_sync(0xffffffffu, kl, src);
+                const int w = (int)(spk >> 20);
+                // k / w: an approximate quotient of (k + 1/2) / w (off by at most one), then corrected
+                int ky = w ? (int)__fdividef((float)k + 0.5f, (float)w) : 0, kx = (int)k - ky * w;
+                if (kx < 0) {
+                    --ky;
+                    kx += w;
+                } else if (kx >= w && w) {
+                    ++ky;
+                    kx -= w;
+                }
+                emit(sl < E, ((spk >> 10 & 1023u) + (uint32_t)ky) * STX + (spk & 1023u) + (uint32_t)kx, srow);
             }
         }
-        __syncthreads();
-        for (int x = threadIdx.x; x < TX; x += kBinThreads) {
-            int run = 0;
-            for (int y = 0; y < TY; ++y) {
-                run += dsm[y * TXp + x];
-                dsm[y * TXp + x] = run;
-            }
-        }
-        __syncthreads();
-        uint32_t* dst = a.counts + (size_t)g * a.tmax;
-        for (int t = threadIdx.x; t < T; t += kBinThreads) {
-            const int y = t / TX, x = t - y * TX;
-            dst[t] = (uint32_t)dsm[y * TXp + x];
-        }
-        __syncthreads();
+        if (__any_sync(0xffffffffu, past)) break;  // offsets grow with j: the later rows are past sb too
     }
 }
 
-// Per-tile sums over the view's chunks.  A block covers 32 tiles (lanes,
-// coalesced) x kPrefixSegs segments of chunks (warps).  Pass 0 writes the tile
-// totals; pass 1 (after k_bin_ranges turned the totals into tile starts)
-// rewrites every count as the absolute first slot of that (chunk, tile).
-constexpr int kPrefixSegs = 32;
-
-template <int PASS>
-__global__ void __launch_bounds__(32 * kPrefixSegs) k_bin_prefix(BinArgs a)
+// Counting pass of one warp's slots [sa, sb) of view v, from its row j0 on:
+// a row whose entries all fall inside the range adds its super-rectangle to
+// the warp's 2D difference grid diff ((STX + 1) x (STY + 1), zeroed) with four
+// corner updates; the first and last rows of the range, which may fall in it
+// only in part, add their entries inside it to cnt one by one.  The grid's
+// prefix sums are then added to cnt.
+__device__ __forceinline__ void split_count(const SplitArgs& a, int v, int64_t j0, uint32_t sa, uint32_t sb,
+                                            uint32_t* cnt, uint32_t* diff, int lane)
 {
-    __shared__ uint32_t s_seg[kPrefixSegs][33];
-    if (status_failed(a.status)) return;
-    const BinPlan& P = *a.plan;
-    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
-    const int gt = blockIdx.x * 32 + lane;
-    const bool ok = gt < a.total_tiles;
-    int v = 0;
-    for (int w = 1; w < a.V; ++w)
-        if (gt >= a.tile_base[w]) v = w;
-    const int tl = gt - a.tile_base[v];
-    const uint32_t cb = P.cbase[v], ce = P.cbase[v + 1];
-    const uint32_t per = (ce - cb + kPrefixSegs - 1) / kPrefixSegs;
-    const uint32_t g0 = min(cb + seg * per, ce), g1 = min(g0 + per, ce);
-    uint32_t* col = a.counts + tl;
-    uint32_t sum = 0;
-    if (ok) {
-        uint32_t g = g0;
-        for (; g + 4 <= g1; g += 4) {
-            const uint32_t c0 = col[(size_t)g * a.tmax], c1 = col[(size_t)(g + 1) * a.tmax];
-            const uint32_t c2 = col[(size_t)(g + 2) * a.tmax], c3 = col[(size_t)(g + 3) * a.tmax];
-            sum += c0 + c1 + c2 + c3;
+    const int STX = a.STX[v], SX = STX + 1, SY = a.STY[v] + 1;
+    const int64_t vend = (int64_t)(v + 1) * a.n;
+    for (int64_t jb = j0;; jb += 32) {
+        const int64_t j = jb + lane;
+        bool past = true;
+        if (j < vend) {
+            const uint32_t off = a.offsets[j];
+            past = off >= sb;
+            if (!past) {
+                const int4 rc = ((const int4*)a.proj.rect)[a.rows[j]];
+                const int sx0 = rc.x >> 3, sy0 = rc.y >> 3, sx1 = (rc.z + 7) >> 3, sy1 = (rc.w + 7) >> 3;
+                if (sx1 > sx0 && sy1 > sy0) {
+                    const uint32_t w = (uint32_t)(sx1 - sx0), cr = w * (uint32_t)(sy1 - sy0);
+                    if (off >= sa && cr <= sb - off) {
+                        atomicAdd(&diff[sy0 * SX + sx0], 1u);
+                        atomicAdd(&diff[sy0 * SX + sx1], 0xffffffffu);
+                        atomicAdd(&diff[sy1 * SX + sx0], 0xffffffffu);
+                        atomicAdd(&diff[sy1 * SX + sx1], 1u);
+                    } else {
+                        const uint32_t kh = min(cr, sb - off);
+                        for (uint32_t k = off < sa ? sa - off : 0u; k < kh; ++k) {
+                            const uint32_t ky = k / w;
+                            atomicAdd(&cnt[(sy0 + ky) * STX + sx0 + (k - ky * w)], 1u);
+                        }
+                    }
+                }
+            }
         }
-        for (; g < g1; ++g) sum += col[(size_t)g * a.tmax];
+        if (__any_sync(0xffffffffu, past)) break;  // offsets grow with j: the later rows are past sb too
     }
-    s_seg[seg][lane] = sum;
+    __syncwarp();
+    for (int y = lane; y < SY; y += 32) {  // prefix along x
+        uint32_t run = 0;
+        for (int x = 0; x < SX; ++x) {
+            run += diff[y * SX + x];
+            diff[y * SX + x] = run;
+        }
+    }
+    __syncwarp();
+    for (int x = lane; x < SX; x += 32) {  // then along y
+        uint32_t run = 0;
+        for (int y = 0; y < SY; ++y) {
+            run += diff[y * SX + x];
+            diff[y * SX + x] = run;
+        }
+    }
+    __syncwarp();
+    for (int d = lane; d < STX * (SY - 1); d += 32) {
+        const int y = d / STX;
+        cnt[d] += diff[y * SX + (d - y * STX)];
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) k_super_split(SplitArgs a)
+{
+    extern __shared__ uint32_t s_dyn[];
+    uint32_t* s_cnt = s_dyn;                 // [8][smax] per-warp counters, then the warps' first slots
+    uint32_t* s_start = s_dyn + 8 * a.smax;  // [smax] first list slot of each super-tile of the view
+    uint32_t* s_diff = s_start + a.smax;     // [8][sdiff] per-warp difference grids of the counting pass
+    __shared__ uint32_t s_S[SPLAT_MAX_VIEWS + 1];   // first slot of each view
+    __shared__ uint32_t s_cb[SPLAT_MAX_VIEWS + 1];  // first partition of each view
+    __shared__ unsigned long long s_tmp64[8];
+    __shared__ int64_t s_ticket;
+    if (status_failed(a.status)) return;  // includes K1 above the capacity
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = lanemask_lt();
+    if (tid == 0) {
+        const uint32_t K1 = (uint32_t)*a.n_instances;
+        uint32_t cb = 0;
+        for (int v = 0; v < a.V; ++v) s_S[v] = a.offsets[(int64_t)v * a.n];
+        s_S[a.V] = K1;
+        for (int v = 0; v < a.V; ++v) {  // every view takes a partition, if only to write its ranges
+            s_cb[v] = cb;
+            cb += max(1u, (s_S[v + 1] - s_S[v] + kSplitSlots - 1) / kSplitSlots);
+        }
+        s_cb[a.V] = cb;
+    }
     __syncthreads();
-    uint32_t base = 0, tot = 0;
-#pragma unroll 8
-    for (int k = 0; k < kPrefixSegs; ++k) {
-        const uint32_t x = s_seg[k][lane];
-        if (k < seg) base += x;
-        tot += x;
-    }
-    if (!ok) return;
-    if (PASS == 0) {
-        if (seg == 0) a.tile_total[gt] = tot;
-        return;
-    }
-    uint32_t run = a.tile_total[gt] + base;  // tile start (after k_bin_ranges) + earlier segments
-    for (uint32_t g = g0; g < g1; g += 8) {
-        uint32_t c[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = g + k < g1 ? col[(size_t)(g + k) * a.tmax] : 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (g + k < g1) col[(size_t)(g + k) * a.tmax] = run;
-            run += c[k];
+    const int64_t parts = min((int64_t)s_cb[a.V], a.max_parts);
+    int cur_v = -1;
+    for (;;) {
+        if (tid == 0) s_ticket = atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        const int64_t ticket = s_ticket;
+        if (ticket >= parts) break;
+        int v = 0;
+        for (int q = 1; q < a.V; ++q)
+            if (ticket >= (int64_t)s_cb[q]) v = q;
+        const int64_t first = s_cb[v], lp = ticket - first;
+        const int nsup = a.STX[v] * a.STY[v];
+        const int nbits = 32 - __clz(max(nsup - 1, 1));  // bits of a super-tile index of the view
+        const int sbase = a.super_base[v];
+        if (v != cur_v) {  // block-uniform: the first list slot of each of the view's super-tiles
+            cur_v = v;
+            unsigned long long before = s_S[v];
+            for (int d0 = 0; d0 < nsup; d0 += 256) {
+                const int d = d0 + tid;
+                const uint32_t c = d < nsup ? a.super_total[sbase + d] : 0u;
+                unsigned long long tot;
+                const unsigned long long ex = block_excl_scan256_u64(c, s_tmp64, &tot);
+                if (d < nsup) s_start[d] = (uint32_t)(before + ex);
+                before += tot;
+            }
+            __syncthreads();
         }
+        if (lp == 0) {
+            for (int d = tid; d < nsup; d += 256) {
+                const uint32_t c = a.super_total[sbase + d], st = s_start[d];
+                a.sranges[sbase + d] = c ? make_uint2(st, st + c) : make_uint2(0u, 0u);
+            }
+        }
+        // this partition's slots and this warp's share of them
+        const uint32_t s0 = s_S[v] + (uint32_t)lp * kSplitSlots, s1 = min(s_S[v + 1], s0 + kSplitSlots);
+        const uint32_t wa = min(s1, s0 + warp * kSplitWarpSlots), wb = min(s1, wa + kSplitWarpSlots);
+        int64_t j0 = 0;
+        if (wa < wb) j0 = warp_search(a.offsets, (int64_t)v * a.n, (int64_t)(v + 1) * a.n, wa, lane);
+        uint32_t* cnt = s_cnt + warp * a.smax;
+        uint32_t* diff = s_diff + warp * a.sdiff;
+        for (int d = lane; d < nsup; d += 32) cnt[d] = 0u;
+        for (int d = lane; d < (a.STX[v] + 1) * (a.STY[v] + 1); d += 32) diff[d] = 0u;
+        __syncwarp();
+        if (wa < wb) split_count(a, v, j0, wa, wb, cnt, diff, lane);
+        __syncthreads();
+        // per super-tile: prefix over the warps, the partition's count, look-back
+        for (int d = tid; d < nsup; d += 256) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t c = s_cnt[w * a.smax + d];
+                s_cnt[w * a.smax + d] = run;
+                run += c;
+            }
+            unsigned long long* my = a.lb + ticket * a.smax + d;
+            st_relaxed64(my, (lp == 0 ? kSplitPrefix : kSplitAgg) | run);
+            unsigned long long excl = 0;
+            if (lp > 0) {
+                int64_t j = ticket - 1, spins = 0;  // nearest predecessor not yet added
+                for (;;) {
+                    unsigned long long wd[kLookWindow];
+#pragma unroll
+                    for (int q = 0; q < kLookWindow; ++q)
+                        wd[q] = j - q >= first ? ld_relaxed64(a.lb + (j - q) * a.smax + d) : kSplitPrefix;
+                    int q = 0;
+                    bool found = false;
+#pragma unroll
+                    for (int t = 0; t < kLookWindow; ++t) {
+                        if (found || q < t) continue;  // stopped at an earlier word
+                        const unsigned long long flag = wd[t] & ~kSplitMask;
+                        if (flag == 0) continue;       // not yet published: q stays at t
+                        excl += wd[t] & kSplitMask;
+                        q = t + 1;
+                        found = flag == kSplitPrefix;
+                    }
+                    if (found) break;
+                    j -= q;
+                    if (q == 0) {
+                        if (++spins > a.spin_limit) {
+                            set_status(a.status, SPLAT_ERR_TIMEOUT, SPLAT_STAGE_SCAN, ticket);
+                            break;
+                        }
+                        if (spins > 64) __nanosleep(64);
+                    }
+                }
+                st_relaxed64(my, kSplitPrefix | ((excl + run) & kSplitMask));
+            }
+            const uint32_t base = s_start[d] + (uint32_t)excl;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s_cnt[w * a.smax + d] += base;
+        }
+        __syncthreads();
+        if (wa < wb && !status_failed(a.status)) split_sweep<true>(a, v, nbits, j0, wa, wb, cnt, lane, lt);
+        __syncthreads();
     }
 }
 
@@ -832,7 +966,14 @@ constexpr int kRangeRound = 256 * kRangeItems;
 
 __device__ __forceinline__ int range_pad(int i) { return i + (i >> 5); }  // conflict-free strided reads
 
-__global__ void __launch_bounds__(256) k_bin_ranges(BinArgs a, int64_t* K_out, int64_t capacity,
+struct RangeArgs {
+    int total_tiles;
+    uint32_t* tile_total;  // [total_tiles] counts in, list starts out
+    uint2* ranges;         // out: [start, end) of each list, (0, 0) when empty
+    int32_t* status;
+};
+
+__global__ void __launch_bounds__(256) k_bin_ranges(RangeArgs a, int64_t* K_out, int64_t capacity,
                                                     const int64_t* K_super = nullptr, int64_t* needed = nullptr)
 {
     __shared__ uint32_t s_c[kRangeRound + kRangeRound / 32], s_st[kRangeRound + kRangeRound / 32];
@@ -1600,127 +1741,6 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
     }
 }
 
-constexpr int kScatterStage = 512;  // rows staged by the scatter warp
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-// One warp per chunk.  Slots are taken 32 at a time in order, across row
-// boundaries; lanes holding the same tile (found by ballots over the tile
-// index bits) are ordered by lane (= slot order), and the group's lowest lane
-// advances the tile's cursor.
-__global__ void __launch_bounds__(32) k_bin_scatter(BinArgs a)
-{
-    extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ BinPlan P;
-    __shared__ uint32_t s_off[kScatterStage + 1], s_base[kScatterStage], s_w[kScatterStage], s_row[kScatterStage];
-    if (status_failed(a.status)) return;
-    const int lane = threadIdx.x;
-    if (lane == 0) P = *a.plan;
-    __syncwarp();
-    uint32_t* s_cur = smem;
-    const unsigned lt = lanemask_lt();
-    const uint32_t nchunks = P.cbase[a.V];
-    for (uint32_t g = blockIdx.x; g < nchunks; g += gridDim.x) {
-        const ChunkGeo c = chunk_geo(P, a.V, a.chunk, g);
-        const int tb = a.tile_base[c.v];
-        const int T = a.tile_base[c.v + 1] - tb;
-        const int TX = a.TX[c.v];
-        const int tbits = 32 - __clz(max(T - 1, 1));  // bits of a tile index of this view
-        // absolute cursors of this chunk: one burst of 16-byte async copies (tmax % 4 == 0)
-        const uint32_t* cnt = a.counts + (size_t)g * a.tmax;
-        for (int t = lane * 4; t < T; t += 128) cp_async16(s_cur + t, cnt + t);
-        cp_async_wait_all();
-        __syncwarp();
-        const uint32_t rend = P.R[c.v + 1];
-        uint32_t rbase = a.first_row[g];  // first staged row
-        int qcur = 0;                      // staged row holding slot s0 - 1 (s0 at the start)
-        int nst = 0;
-        bool more = true;                  // rows of the chunk beyond the staged ones may exist
-        for (uint32_t s0 = c.cs; s0 < c.ce; s0 += 32) {
-            if (more && qcur + 33 > nst) {  // (re)stage rows from the current one
-                rbase += qcur;
-                qcur = 0;
-                __syncwarp();
-                nst = 0;
-                constexpr int PER = kScatterStage / 32;
-                uint32_t offv[PER], rowv[PER];
-                bool inv[PER];
-#pragma unroll
-                for (int i = 0; i < PER; ++i) {
-                    const uint32_t j = rbase + lane + 32 * i;
-                    offv[i] = j < rend ? a.offsets[j] : c.ce;
-                }
-#pragma unroll
-                for (int i = 0; i < PER; ++i) {
-                    inv[i] = offv[i] < c.ce;
-                    rowv[i] = inv[i] ? a.rows[rbase + lane + 32 * i] : 0u;
-                }
-#pragma unroll
-                for (int i = 0; i < PER; ++i) {
-                    const int q = lane + 32 * i;
-                    if (inv[i]) {
-                        uint32_t n_;
-                        const int4 rc = level_rect(a, rowv[i], n_);
-                        s_off[q] = offv[i];
-                        s_base[q] = (uint32_t)(rc.y * TX + rc.x);
-                        s_w[q] = (uint32_t)max(rc.z - rc.x, 1);
-                        s_row[q] = rowv[i];
-                    }
-                    nst += __popc(__ballot_sync(0xffffffffu, inv[i]));
-                }
-                more = nst == kScatterStage;
-                if (lane == 0) s_off[nst] = c.ce;  // sentinel, read only when every row is staged
-                __syncwarp();
-            }
-            // rows starting inside [s0, s0 + 31] (a row starting at s0 follows qcur)
-            const int k = qcur + 1 + lane;
-            const uint32_t ok_ = k <= nst ? s_off[k] : c.ce;
-            const uint32_t p = ok_ - s0;  // >= 0 for rows after qcur
-            const unsigned M = __reduce_or_sync(0xffffffffu, p < 32u ? (1u << p) : 0u);
-            const int q = qcur + __popc(M & ((2u << lane) - 1u));
-            const uint32_t s = s0 + lane;
-            const bool act = s < c.ce;
-            uint32_t tl = 0xffffffffu;
-            if (act) {
-                const uint32_t l = s - s_off[q], w = s_w[q];
-                const uint32_t ty = l / w;
-                tl = s_base[q] + ty * TX + (l - ty * w);
-            }
-            // lanes holding the same tile: one ballot per bit of the view's
-            // tile index (constant cost; a warp holds many distinct tiles)
-            const unsigned actm = __ballot_sync(0xffffffffu, act);
-            unsigned peers = act ? actm : ~actm;
-            for (int bit = 0; bit < tbits; ++bit) {
-                const unsigned bb = __ballot_sync(0xffffffffu, (tl >> bit) & 1u);
-                peers &= ((tl >> bit) & 1u) ? bb : ~bb;
-            }
-            const int leader = __ffs(peers) - 1;
-            uint32_t pos = 0;
-            if (lane == leader && act) {
-                pos = s_cur[tl];
-                s_cur[tl] = pos + __popc(peers);
-            }
-            pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lt);
-            if (act) {
-                a.vals_out[pos] = s_row[q];
-                if (a.keys_out) a.keys_out[pos] = (uint32_t)tb + tl;
-            }
-            qcur += __popc(M);
-            __syncwarp();
-        }
-        __syncwarp();
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -1730,13 +1750,12 @@ struct SortLayout {
     int64_t n_rows, capacity;
     int V, tmax, smax;
     bool binned;
-    uint32_t chunk;
-    int64_t max_chunks;
     int64_t parts_d, parts_t, parts_scan, n_chunks;
     int64_t total_tiles, total_super;
+    int64_t parts_split;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
-        off_tvals, off_hist, off_dhist, off_tickets, off_plan, off_counts, off_first, off_total;
-    size_t off_vals1, off_sranges, off_stotal, off_ninst1, off_segbase, off_segcnt, off_segsuper, off_nhead, off_sathead,
+        off_tvals, off_hist, off_dhist, off_suptot, off_tickets, off_split_lb, off_total;
+    size_t off_vals1, off_sranges, off_ninst1, off_segbase, off_segcnt, off_segsuper, off_nhead, off_sathead,
         off_nhead8, off_mask, off_tord;
     int64_t max_segs;
     size_t bytes;
@@ -1745,13 +1764,6 @@ struct SortLayout {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kSuperShift = 3;  // super-tiles of 8 x 8 tiles
-
-// level-1 (row, super-tile) slots per chunk: about 64k chunks at full capacity
-static uint32_t bin_chunk(int64_t capacity)
-{
-    int64_t c = (capacity / 65536 + 255) / 256 * 256;
-    return (uint32_t)std::min<int64_t>(std::max<int64_t>(c, 1024), 1 << 20);
-}
 
 SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, const int* TY, int tile_sort)
 {
@@ -1769,12 +1781,21 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     }
     L.tmax = (tmax + 3) & ~3;
     L.smax = (smax + 3) & ~3;
-    L.binned = tile_sort == 2 || (tile_sort == 0 && tmax <= kBinMaxTiles);
-    L.chunk = bin_chunk(capacity);
-    L.max_chunks = (capacity + L.chunk - 1) / L.chunk + V;
+    // the split packs super-tile coordinates in 10 bits and keeps 9 counters per super-tile and 8 difference
+    // grids in shared memory
+    int sdiff = 0;
+    bool split_ok = true;
+    for (int v = 0; v < V; ++v) {
+        const int sx = (TX[v] + 7) >> kSuperShift, sy = (TY[v] + 7) >> kSuperShift;
+        split_ok = split_ok && sx < 1024 && sy < 1024;
+        sdiff = std::max(sdiff, (sx + 1) * (sy + 1));
+    }
+    split_ok = split_ok && 4 * (9 * (int64_t)L.smax + 8 * (int64_t)sdiff) <= kSplitMaxSmem;
+    L.binned = split_ok && (tile_sort == 2 || (tile_sort == 0 && tmax <= kBinMaxTiles));
     L.parts_d = V > 0 ? (int64_t)V * ((n_rows / V + kSortPart - 1) / kSortPart) : 0;  // partitions within views
     L.parts_t = L.binned ? 0 : (capacity + kSortPart - 1) / kSortPart;
     L.parts_scan = (n_rows + kScanPart - 1) / kScanPart;
+    L.parts_split = L.binned ? (capacity + kSplitSlots - 1) / kSplitSlots + V : 0;
     L.n_chunks = L.binned ? 1 : (capacity + kDupChunk - 1) / kDupChunk + 1;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align256(o + std::max<size_t>(bytes, 4)); return r; };
@@ -1788,15 +1809,14 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.off_tkeys = take(L.binned ? 4 : 4 * (size_t)capacity);
     L.off_tvals = take(L.binned ? 4 : 4 * (size_t)capacity);
     L.off_hist = take(4 * (size_t)kRadix * 9);
-    L.off_dhist = take(4 * (size_t)kRadix * 4 * std::max(V, 1));  // depth digits per view (zeroed with hist)
+    // zeroed together with hist: the depth digits per view and the super-tile list sizes
+    L.off_dhist = take(4 * (size_t)kRadix * 4 * std::max(V, 1));
+    L.off_suptot = take(L.binned ? 4 * (size_t)L.total_super : 4);
     L.off_tickets = take(4 * 16);
-    L.off_plan = take(sizeof(BinPlan));
-    L.off_counts = take(L.binned ? 4 * (size_t)L.max_chunks * L.smax : 4);
-    L.off_first = take(L.binned ? 4 * (size_t)L.max_chunks : 4);
+    L.off_split_lb = take(L.binned ? 8 * (size_t)L.smax * std::max<int64_t>(L.parts_split, 1) : 4);
     L.off_total = take(L.binned ? 4 * (size_t)L.total_tiles : 4);
     L.off_vals1 = take(L.binned ? 4 * (size_t)capacity : 4);
     L.off_sranges = take(L.binned ? 8 * (size_t)L.total_super : 4);
-    L.off_stotal = take(L.binned ? 4 * (size_t)L.total_super : 4);
     L.off_ninst1 = take(8);
     L.max_segs = L.binned ? (capacity + kFilterSeg - 1) / kFilterSeg + L.total_super : 1;
     L.off_segbase = take(4 * (size_t)(L.total_super + 1));
@@ -1865,21 +1885,61 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
     uint32_t* tickets = U(L.off_tickets);
     const int resident = ctx.num_sms * sort_ctas_per_sm();
 
-    // 1. depth keys + per-view digit histograms (+ rows per view); zero the first depth look-back buffer and the
-    // scan's
+    // super-tile grids (binned path)
+    int super_base[SPLAT_MAX_VIEWS + 1], STX[SPLAT_MAX_VIEWS], STY[SPLAT_MAX_VIEWS];
+    int sb = 0;
+    for (int v = 0; v < vb.V; ++v) {
+        super_base[v] = sb;
+        STX[v] = (vb.v[v].TX + 7) >> kSuperShift;
+        STY[v] = (vb.v[v].TY + 7) >> kSuperShift;
+        sb += STX[v] * STY[v];
+    }
+    super_base[vb.V] = sb;
+    int sdiff = 0;  // words of the largest view's super-tile difference grid
+    for (int v = 0; v < vb.V; ++v) sdiff = std::max(sdiff, (STX[v] + 1) * (STY[v] + 1));
+    // 1. depth keys + per-view digit counts and (binned) the super-tile list sizes; zero the first depth
+    // look-back buffer, the scan's and the split's
     uint32_t* dhist = U(L.off_dhist);
+    uint32_t* suptot = U(L.off_suptot);
     {
-        static const int per_sm = ctas_per_sm(k_depth_keys, 256);
-        const int per_view = (int)std::max<int64_t>(
+        DepthArgs a{};
+        a.proj = proj;
+        a.V = vb.V;
+        a.keys = U(L.off_dkeys[0]);
+        a.vals = U(L.off_dvals[0]);
+        a.dhist = dhist;
+        a.super_total = L.binned ? suptot : nullptr;
+        for (int v = 0; v < vb.V; ++v) {
+            a.super_base[v] = super_base[v];
+            a.STX[v] = STX[v];
+            a.STY[v] = STY[v];
+        }
+        a.zero_a = U(L.off_dlb[0]);
+        a.n_zero_a = L.parts_d * kRadix;
+        a.zero_b = (unsigned long long*)(w + L.off_scan_lb);
+        a.n_zero_b = L.parts_scan;
+        a.zero_c = (unsigned long long*)(w + L.off_split_lb);
+        a.n_zero_c = L.binned ? L.parts_split * L.smax : 0;
+        const size_t smem = L.binned ? 4 * (size_t)sdiff : 0;
+        static size_t smem_set = 0;
+        if (smem > smem_set) {
+            if ((err = cudaFuncSetAttribute(k_depth_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return err;
+            smem_set = smem;
+        }
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_depth_keys, 256, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        a.blocks_per_view = (int)std::max<int64_t>(
             1, std::min<int64_t>((proj.n + 255) / 256, (int64_t)ctx.num_sms * per_sm / vb.V));
         count_launch();
-        k_depth_keys<<<vb.V * per_view, 256, 0, s>>>(proj, vb.V, per_view, U(L.off_dkeys[0]), U(L.off_dvals[0]), dhist,
-                                                     hist + 8 * kRadix, U(L.off_dlb[0]), L.parts_d * kRadix,
-                                                     (unsigned long long*)(w + L.off_scan_lb), L.parts_scan);
+        k_depth_keys<<<vb.V * a.blocks_per_view, 256, smem, s>>>(a);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     // 2. depth passes (buffers 0 -> 1 -> 0 -> 1 -> 0).  Binned: each view's rows sorted in place, giving the
-    // (view, depth) order the super-tile partition takes.  Radix path: one sort of all rows by depth, so that
+    // (view, depth) order the super-tile split takes.  Radix path: one sort of all rows by depth, so that
     // the rows without tiles come last (the duplication's chunks assume no such row between listed ones)
     const int passes = 4;
     for (int p = 0; p < passes; ++p) {
@@ -1897,7 +1957,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         a.ticket = tickets + p;
         a.status = status;
         a.stage = SPLAT_STAGE_DEPTH_SORT;
-        a.shift = p < 4 ? 8 * p : 0;
+        a.shift = 8 * p;
         a.spin_limit = ctx.spin_limit;
         a.seg_len = L.binned ? proj.n : 0;
         a.hist_sum = vb.V;
@@ -1905,49 +1965,88 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         if ((err = run_pass(a, L.parts_d, resident, s)) != cudaSuccess) return err;
     }
     const uint32_t* rows = U(L.off_dvals[passes & 1]);
-    // 3. scan of the per-row counts in that order: tiles (radix path) or super-tiles (binned path)
-    {
-        ScanArgs a{};
-        a.rows = rows;
-        a.n_tiles = proj.n_tiles;
-        a.rect = (const int4*)proj.rect;
-        a.shift = L.binned ? kSuperShift : 0;
-        a.n_rows = n_rows;
-        a.offsets = U(L.off_offsets);
-        a.chunk_row = U(L.off_chunk);
-        a.n_chunks_max = L.binned ? 0 : L.n_chunks;
-        a.lb = (unsigned long long*)(w + L.off_scan_lb);
-        a.ticket = tickets + 4;
-        a.n_instances = L.binned ? (int64_t*)(w + L.off_ninst1) : bins.n_instances;
-        a.n_needed = L.binned ? nullptr : bins.n_needed;
-        // binned: the super-tile list (K1 entries) lives in a capacity-sized
-        // buffer, so K1 is checked here, before anything is written; K itself is
-        // checked by the tile ranges once the lists are counted
-        a.capacity = bins.capacity;
-        a.status = status;
-        a.spin_limit = ctx.spin_limit;
-        const int blocks = (int)std::min<int64_t>(L.parts_scan, (int64_t)ctx.num_sms * 4);
-        count_launch();
-        k_scan_tiles<<<blocks, kScanThreads, 0, s>>>(a);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
     if (L.binned) {
-        // tile level: per-super-tile lists filtered into per-tile lists (see below)
+        // 3. super-tile lists.  The scan of the rows' super-tile counts gives each row its first slot and K1;
+        // the lists (K1 entries) live in a capacity-sized buffer, so K1 is checked there, before anything is
+        // written (K itself is checked by the tile ranges once the tile lists are counted).  Then the stable
+        // split of the slots by super-tile.
+        {
+            ScanArgs a{};
+            a.rows = rows;
+            a.n_tiles = proj.n_tiles;
+            a.rect = (const int4*)proj.rect;
+            a.shift = kSuperShift;
+            a.n_rows = n_rows;
+            a.offsets = U(L.off_offsets);
+            a.chunk_row = U(L.off_chunk);
+            a.n_chunks_max = 0;
+            a.lb = (unsigned long long*)(w + L.off_scan_lb);
+            a.ticket = tickets + 4;
+            a.n_instances = (int64_t*)(w + L.off_ninst1);
+            a.n_needed = nullptr;
+            a.capacity = bins.capacity;
+            a.status = status;
+            a.spin_limit = ctx.spin_limit;
+            const int blocks = (int)std::min<int64_t>(L.parts_scan, (int64_t)ctx.num_sms * 4);
+            count_launch();
+            k_scan_tiles<<<blocks, kScanThreads, 0, s>>>(a);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        }
+        {
+            SplitArgs a{};
+            a.proj = proj;
+            a.rows = rows;
+            a.offsets = U(L.off_offsets);
+            a.super_total = suptot;
+            a.n_instances = (const int64_t*)(w + L.off_ninst1);
+            a.V = vb.V;
+            a.n = proj.n;
+            a.smax = L.smax;
+            a.sdiff = sdiff;
+            a.total_super = sb;
+            for (int v = 0; v <= vb.V; ++v) a.super_base[v] = super_base[v];
+            for (int v = 0; v < vb.V; ++v) {
+                a.STX[v] = STX[v];
+                a.STY[v] = STY[v];
+            }
+            a.lb = (unsigned long long*)(w + L.off_split_lb);
+            a.max_parts = L.parts_split;
+            a.ticket = tickets + 9;
+            a.list = U(L.off_vals1);
+            a.sranges = (uint2*)(w + L.off_sranges);
+            a.status = status;
+            a.spin_limit = ctx.spin_limit;
+            const size_t smem = 4 * ((size_t)L.smax * 9 + 8 * (size_t)sdiff);
+            static size_t smem_set = 0;
+            if (smem > smem_set) {
+                if ((err = cudaFuncSetAttribute(k_super_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem)) != cudaSuccess)
+                    return err;
+                smem_set = smem;
+            }
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_super_split, 256, smem) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(L.parts_split, (int64_t)ctx.num_sms * per_sm));
+            count_launch();
+            k_super_split<<<blocks, 256, smem, s>>>(a);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        }
+        // 4. tile level: per-super-tile lists filtered into per-tile lists (see above)
         TileArgs t{};
         t.proj = proj;
         t.V = vb.V;
         t.n_rows = n_rows;
         t.total_tiles = vb.total_tiles;
-        int sb = 0;
         for (int v = 0; v < vb.V; ++v) {
             t.tile_base[v] = vb.v[v].tile_base;
             t.TX[v] = vb.v[v].TX;
             t.TY[v] = vb.v[v].TY;
             t.W[v] = vb.v[v].W;
             t.H[v] = vb.v[v].H;
-            t.super_base[v] = sb;
-            t.STX[v] = (vb.v[v].TX + 7) >> kSuperShift;
-            sb += t.STX[v] * ((vb.v[v].TY + 7) >> kSuperShift);
+            t.super_base[v] = super_base[v];
+            t.STX[v] = STX[v];
         }
         t.tile_base[vb.V] = vb.total_tiles;
         t.super_base[vb.V] = sb;
@@ -1968,73 +2067,14 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.sat_head = (uint2*)(w + L.off_sathead);
         t.mask = (uint2*)(w + L.off_mask);
         t.ticket = tickets + 10;
-        BinArgs tr{};
+        RangeArgs tr{};
         tr.total_tiles = vb.total_tiles;
         tr.tile_total = U(L.off_total);
         tr.ranges = (uint2*)bins.ranges;
         tr.status = status;
-        // super-tile level: stable partition of the (view, depth)-ordered rows by super-tile
-        BinArgs a{};
-        a.proj = proj;
-        a.shift = kSuperShift;
-        a.rows = rows;
-        a.offsets = U(L.off_offsets);
-        a.view_hist = hist + 8 * kRadix;
-        a.plan = (BinPlan*)(w + L.off_plan);
-        a.V = vb.V;
-        a.n_rows = n_rows;
-        a.chunk = L.chunk;
-        a.tmax = L.smax;
-        a.total_tiles = sb;
-        for (int v = 0; v < vb.V; ++v) {
-            a.tile_base[v] = t.super_base[v];
-            a.TX[v] = t.STX[v];
-        }
-        a.tile_base[vb.V] = sb;
-        a.counts = U(L.off_counts);
-        a.first_row = U(L.off_first);
-        a.tile_total = U(L.off_stotal);
-        a.ranges = (uint2*)(w + L.off_sranges);
-        a.vals_out = U(L.off_vals1);
-        a.keys_out = nullptr;
-        a.n_instances = (const int64_t*)(w + L.off_ninst1);
-        a.capacity = bins.capacity;
-        a.status = status;
-        int dmax = 1;
-        for (int v = 0; v < vb.V; ++v)
-            dmax = std::max(dmax, (t.STX[v] + 1) * (((vb.v[v].TY + 7) >> kSuperShift) + 1));
-        const size_t smem_count = 4 * (size_t)dmax;
-        const size_t smem_scatter = 4 * (size_t)L.smax;
-        static size_t set_count = 0, set_scatter = 0;
-        if (smem_count > set_count) {
-            if ((err = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem_count)) != cudaSuccess)
-                return err;
-            set_count = smem_count;
-        }
-        if (smem_scatter > set_scatter) {
-            if ((err = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem_scatter)) != cudaSuccess)
-                return err;
-            set_scatter = smem_scatter;
-        }
-        int per_sm_c = 0, per_sm_s = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, k_bin_count, kBinThreads, smem_count);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_bin_scatter, 32, smem_scatter);
-        const int blocks_c = (int)std::min<int64_t>(L.max_chunks, (int64_t)ctx.num_sms * std::max(1, per_sm_c));
-        const int blocks_s = (int)std::min<int64_t>(L.max_chunks, (int64_t)ctx.num_sms * std::max(1, per_sm_s));
-        count_launch(7);
-        k_bin_plan<<<1, 32, 0, s>>>(a);
-        k_bin_count<<<blocks_c, kBinThreads, smem_count, s>>>(a);
-        k_bin_prefix<0><<<(sb + 31) / 32, 32 * kPrefixSegs, 0, s>>>(a);
-        k_bin_ranges<<<1, 256, 0, s>>>(a, nullptr, 0);
-        k_bin_prefix<1><<<(sb + 31) / 32, 32 * kPrefixSegs, 0, s>>>(a);
-        k_bin_scatter<<<blocks_s, 32, smem_scatter, s>>>(a);
-        // tile level: the head of each super-tile list in order (each tile's list
-        // up to its saturation), the tail in parallel segments, the prefix over
-        // head and segments, ranges + K + capacity check, then the lists are
-        // written; one wave of resident CTAs per pass, which take super-tiles or
-        // segments from ticket counters
+        // the head of each super-tile list in order (each tile's list up to its
+        // saturation), the tail in parallel segments, the prefix over head and
+        // segments, ranges + K + capacity check, then the lists are written
         static const int per_sm_f[2] = {ctas_per_sm(k_tile_filter<false>, 256), ctas_per_sm(k_tile_filter<true>, 256)};
         static const int per_sm_hw = ctas_per_sm(k_head_write, 256);
         auto blocks_f = [&](int c) { return (int)std::min<int64_t>(L.max_segs, (int64_t)ctx.num_sms * per_sm_f[c]); };
@@ -2050,6 +2090,29 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         k_tile_filter<false><<<blocks_f(0), 256, 0, s>>>(t);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);
+    }
+    // 3. radix path: scan of the per-row tile counts in depth order
+    {
+        ScanArgs a{};
+        a.rows = rows;
+        a.n_tiles = proj.n_tiles;
+        a.rect = (const int4*)proj.rect;
+        a.shift = 0;
+        a.n_rows = n_rows;
+        a.offsets = U(L.off_offsets);
+        a.chunk_row = U(L.off_chunk);
+        a.n_chunks_max = L.n_chunks;
+        a.lb = (unsigned long long*)(w + L.off_scan_lb);
+        a.ticket = tickets + 4;
+        a.n_instances = bins.n_instances;
+        a.n_needed = bins.n_needed;
+        a.capacity = bins.capacity;
+        a.status = status;
+        a.spin_limit = ctx.spin_limit;
+        const int blocks = (int)std::min<int64_t>(L.parts_scan, (int64_t)ctx.num_sms * 4);
+        count_launch();
+        k_scan_tiles<<<blocks, kScanThreads, 0, s>>>(a);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     // 4. radix path: duplicate, tile-digit passes, ranges
     int bits = 1;
