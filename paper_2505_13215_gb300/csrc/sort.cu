@@ -956,74 +956,6 @@ __global__ void __launch_bounds__(256) k_super_split(SplitArgs a)
     }
 }
 
-// one block: ranges[t] = [start, start + total); tile_total becomes the start.
-// With K_out, also the instance count K and the capacity check.  Each round
-// stages 256 x kRangeItems tile totals in shared memory with coalesced loads;
-// thread i then scans its kRangeItems consecutive tiles (one block scan per
-// round) and the starts and ranges go back out coalesced.
-constexpr int kRangeItems = 16;
-constexpr int kRangeRound = 256 * kRangeItems;
-
-__device__ __forceinline__ int range_pad(int i) { return i + (i >> 5); }  // conflict-free strided reads
-
-struct RangeArgs {
-    int total_tiles;
-    uint32_t* tile_total;  // [total_tiles] counts in, list starts out
-    uint2* ranges;         // out: [start, end) of each list, (0, 0) when empty
-    int32_t* status;
-};
-
-__global__ void __launch_bounds__(256) k_bin_ranges(RangeArgs a, int64_t* K_out, int64_t capacity,
-                                                    const int64_t* K_super = nullptr, int64_t* needed = nullptr)
-{
-    __shared__ uint32_t s_c[kRangeRound + kRangeRound / 32], s_st[kRangeRound + kRangeRound / 32];
-    __shared__ unsigned long long s_tmp64[8];
-    if (status_failed(a.status)) return;
-    unsigned long long carry = 0;
-    const int n = a.total_tiles;
-    for (int base = 0; base < n; base += kRangeRound) {
-#pragma unroll
-        for (int q = 0; q < kRangeItems; ++q) {
-            const int i = q * 256 + threadIdx.x;
-            s_c[range_pad(i)] = base + i < n ? a.tile_total[base + i] : 0u;
-        }
-        __syncthreads();
-        uint32_t c[kRangeItems];
-        unsigned long long sum = 0;
-#pragma unroll
-        for (int k = 0; k < kRangeItems; ++k) {
-            c[k] = s_c[range_pad(threadIdx.x * kRangeItems + k)];
-            sum += c[k];
-        }
-        unsigned long long tot;
-        // slots past 2^32 only arise with K beyond any capacity: the check below reports them
-        uint32_t st = (uint32_t)(carry + block_excl_scan256_u64(sum, s_tmp64, &tot));
-#pragma unroll
-        for (int k = 0; k < kRangeItems; ++k) {
-            s_st[range_pad(threadIdx.x * kRangeItems + k)] = st;
-            st += c[k];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kRangeItems; ++q) {
-            const int i = q * 256 + threadIdx.x;
-            if (base + i < n) {
-                const uint32_t ci = s_c[range_pad(i)], si = s_st[range_pad(i)];
-                a.ranges[base + i] = ci ? make_uint2(si, si + ci) : make_uint2(0u, 0u);
-                a.tile_total[base + i] = si;
-            }
-        }
-        carry += tot;
-        __syncthreads();
-    }
-    if (K_out && threadIdx.x == 0) {
-        *K_out = (int64_t)carry;
-        if ((int64_t)carry > capacity) set_status(a.status, SPLAT_ERR_CAPACITY, SPLAT_STAGE_DUPLICATE, (int64_t)carry);
-        // the capacity the call needed: the super-tile lists share the buffers' size
-        if (needed) *needed = K_super ? max((int64_t)carry, *K_super) : (int64_t)carry;
-    }
-}
-
 // Tiles in decreasing order of list length for the compositing kernels'
 // scheduling (the longest first, so that the last wave of warps is short):
 // classes of powers of two, a counting sort over the classes in two grid-wide
@@ -1070,24 +1002,29 @@ __global__ void __launch_bounds__(256) k_tile_order(const uint2* ranges, int n, 
     }
 }
 
+// counted: the class counts cls[0..32] are already in place (and the cursors
+// zero), from the binned path's tile ranges
 static cudaError_t launch_tile_order(const splat_bins& bins, int64_t total_tiles, uint32_t* cls, int32_t* status,
-                                     const LaunchCtx& ctx)
+                                     const LaunchCtx& ctx, bool counted = false)
 {
     if (!bins.tile_order || total_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(cls, 0, 66 * sizeof(uint32_t), ctx.stream);
-    if (e != cudaSuccess) return e;
     const int n = (int)total_tiles;
     const int blocks = (int)std::min<int64_t>((total_tiles + 255) / 256, (int64_t)ctx.num_sms * 4);
-    count_launch(2);
-    k_tile_order<false><<<blocks, 256, 0, ctx.stream>>>((const uint2*)bins.ranges, n, cls, bins.tile_order, status);
+    if (!counted) {
+        cudaError_t e = cudaMemsetAsync(cls, 0, 66 * sizeof(uint32_t), ctx.stream);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        k_tile_order<false><<<blocks, 256, 0, ctx.stream>>>((const uint2*)bins.ranges, n, cls, bins.tile_order, status);
+    }
+    count_launch();
     k_tile_order<true><<<blocks, 256, 0, ctx.stream>>>((const uint2*)bins.ranges, n, cls, bins.tile_order, status);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Tile level.  A counting pass of the per-super-tile filter gives every tile's
-// total, k_bin_ranges scans them into ranges (and K), and the writing pass of
-// the same filter emits the lists.
+// Tile level.  Counting passes over each super-tile's list (the head in order,
+// the tail in segments) give every tile's counts, k_tile_ranges turns them
+// into ranges (and K), and the writing passes emit the lists.
 // ---------------------------------------------------------------------------
 
 struct TileArgs {
@@ -1116,7 +1053,8 @@ struct TileArgs {
     uint32_t* seg_super;              // [segments] super-tile of each tail segment
     uint32_t* seg_cnt;                // [segments][64] per-segment tile counts, then offsets
     uint2* mask;                      // per super-tile list entry: byte w = its tile columns in tile row w
-    uint32_t* ticket;                 // [3] tickets of the tail write / count and head write passes (zeroed)
+    uint32_t* ticket;                 // [3] tickets of the writing and tail counting passes, head count
+                                      // CTAs done (zeroed)
     int32_t* status;
 };
 
@@ -1186,12 +1124,10 @@ __device__ __forceinline__ uint32_t sat_weight(const SatRow& r, float xlo, float
 constexpr int kFilterSeg = 1024;  // list entries per tail segment (one CTA)
 constexpr int kHeadChunks = 2;    // 256-row chunks of each list the head pass takes in order
 
-// one block: head length of each super-tile list (its longest tile row's),
-// tail segments per list, exclusive scan -> seg_base
-__global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
+// one block (the last of the head count): head length of each super-tile list
+// (its longest tile row's), tail segments per list, exclusive scan -> seg_base
+__device__ __forceinline__ void seg_plan(const TileArgs& a, uint32_t* s_tmp)
 {
-    __shared__ uint32_t s_tmp[8];
-    if (status_failed(a.status)) return;
     uint32_t carry = 0;
     for (int base = 0; base < a.total_super; base += 256) {
         const int gs = base + threadIdx.x;
@@ -1215,30 +1151,131 @@ __global__ void __launch_bounds__(256) k_seg_plan(TileArgs a)
     if (threadIdx.x == 0) a.seg_base[a.total_super] = carry;
 }
 
-// thread per (super-tile, tile of its 8x8 block): exclusive sum of the tile's
-// counts over the head and the super-tile's tail segments; the tile's total
-__global__ void __launch_bounds__(256) k_seg_prefix(TileArgs a)
+// Tile totals, offsets and ranges in one pass over the tiles in global order,
+// kRangeTiles per block taken in ticket order, kRangeTiles / 256 consecutive
+// tiles per thread.  A tile's total is its head count plus its counts in the
+// tail segments of its super-tile, whose entries become the tile-relative
+// offsets of the segments; the exclusive scan of the totals across blocks
+// (decoupled look-back) gives every tile's range [start, start + total) and
+// leaves the start in tile_total.  The last block also writes K, checks it
+// against the capacity and reports the capacity the call needed.
+constexpr int kRangeTileItems = 1;
+constexpr int kRangeTiles = 256 * kRangeTileItems;
+
+struct TileRangeArgs {
+    unsigned long long* lb;  // [blocks] look-back words (zeroed)
+    uint32_t* ticket;        // (zeroed)
+    uint2* ranges;
+    int64_t* K_out;
+    int64_t capacity;
+    const int64_t* K_super;  // entries of the super-tile lists, which share the capacity
+    int64_t* needed;         // may be null
+    uint32_t* cls;           // [33] tiles per list-length class for the tile order (zeroed), or null
+    int64_t spin_limit;
+};
+
+__global__ void __launch_bounds__(256) k_tile_ranges(TileArgs a, TileRangeArgs r)
 {
+    __shared__ unsigned long long s_tmp64[8];
+    __shared__ unsigned long long s_excl;
+    __shared__ int64_t s_ticket;
+    __shared__ uint32_t s_cls[33];
+    constexpr unsigned long long kA = 1ull << 62, kP = 2ull << 62, kM = (1ull << 62) - 1;
     if (status_failed(a.status)) return;
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)a.total_super * 64) return;
-    const int gs = (int)(idx >> 6), lt = (int)(idx & 63);
-    int v = 0;
-    for (int w = 1; w < a.V; ++w)
-        if (gs >= a.super_base[w]) v = w;
-    const int ls = gs - a.super_base[v];
-    const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
-    const int ty = sy * 8 + (lt >> 3), tx = sx * 8 + (lt & 7);
-    if (ty >= a.TY[v] || tx >= a.TX[v]) return;
-    uint32_t* total = a.tile_total + a.tile_base[v] + ty * a.TX[v] + tx;
-    uint32_t run = *total;  // the head's count: the tail segments follow it
-    for (uint32_t g = a.seg_base[gs]; g < a.seg_base[gs + 1]; ++g) {
-        uint32_t* p = a.seg_cnt + (size_t)g * 64 + lt;
-        const uint32_t c = *p;
-        *p = run;
-        run += c;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_ticket = atomicAdd(r.ticket, 1u);
+    if (tid < 33) s_cls[tid] = 0u;
+    __syncthreads();
+    const int64_t blk = s_ticket, nblk = ((int64_t)a.total_tiles + kRangeTiles - 1) / kRangeTiles;
+    if (blk >= nblk) return;
+    const int64_t t0 = blk * kRangeTiles + (int64_t)tid * kRangeTileItems;
+    uint32_t cnt[kRangeTileItems];
+    unsigned long long tsum = 0;
+#pragma unroll
+    for (int q = 0; q < kRangeTileItems; ++q) {
+        const int64_t t = t0 + q;
+        uint32_t run = 0;
+        if (t < a.total_tiles) {
+            int v = 0;
+            for (int w = 1; w < a.V; ++w)
+                if (t >= a.tile_base[w]) v = w;
+            const int local = (int)(t - a.tile_base[v]);
+            const int ty = local / a.TX[v], tx = local - ty * a.TX[v];
+            const int gs = a.super_base[v] + (ty >> 3) * a.STX[v] + (tx >> 3), lt = (ty & 7) * 8 + (tx & 7);
+            run = a.tile_total[t];  // the head's count: the tail segments follow it
+            // the segments' counts, four loads in flight at a time, become their offsets
+            const uint32_t g1 = a.seg_base[gs + 1];
+            for (uint32_t g = a.seg_base[gs]; g < g1; g += 4) {
+                uint32_t c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) c[u] = g + u < g1 ? a.seg_cnt[(size_t)(g + u) * 64 + lt] : 0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (g + u < g1) a.seg_cnt[(size_t)(g + u) * 64 + lt] = run;
+                    run += c[u];
+                }
+            }
+        }
+        cnt[q] = run;
+        tsum += run;
+        if (r.cls && t < a.total_tiles) atomicAdd(&s_cls[run ? 32u - __clz(run) : 0u], 1u);  // as tile_class
     }
-    *total = run;
+    unsigned long long agg;
+    const unsigned long long texcl = block_excl_scan256_u64(tsum, s_tmp64, &agg);
+    if (tid < 32) {  // decoupled look-back by one warp, 32 predecessors per round trip
+        const int lane = tid;
+        unsigned long long excl = 0;
+        if (lane == 0) st_relaxed64(r.lb + blk, (blk == 0 ? kP : kA) | agg);
+        if (blk > 0) {
+            int64_t j = blk - 1, spins = 0;
+            for (;;) {
+                const unsigned long long w = j - lane >= 0 ? ld_relaxed64(r.lb + (j - lane)) : kP;
+                const unsigned long long flag = w & ~kM;
+                const unsigned pend = __ballot_sync(0xffffffffu, flag == 0);
+                const unsigned pref = __ballot_sync(0xffffffffu, flag == kP);
+                const int first_pend = pend ? __ffs(pend) - 1 : 32;
+                const int first_pref = pref ? __ffs(pref) - 1 : 32;
+                const bool found = first_pref < first_pend;
+                const int take = found ? first_pref + 1 : first_pend;
+                unsigned long long x = lane < take ? (w & kM) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                excl += x;
+                if (found) break;
+                j -= take;
+                if (take == 0) {
+                    if (++spins > r.spin_limit) {
+                        if (lane == 0) set_status(a.status, SPLAT_ERR_TIMEOUT, SPLAT_STAGE_DUPLICATE, blk);
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(64);
+                }
+            }
+            if (lane == 0) st_relaxed64(r.lb + blk, kP | ((excl + agg) & kM));
+        }
+        if (lane == 0) {
+            s_excl = excl;
+            if (blk == nblk - 1) {
+                const int64_t K = (int64_t)(excl + agg);
+                *r.K_out = K;
+                if (K > r.capacity) set_status(a.status, SPLAT_ERR_CAPACITY, SPLAT_STAGE_DUPLICATE, K);
+                if (r.needed) *r.needed = max(K, *r.K_super);
+            }
+        }
+    }
+    __syncthreads();
+    if (r.cls && tid < 33 && s_cls[tid]) atomicAdd(&r.cls[tid], s_cls[tid]);
+    // slots past 2^32 only arise with K beyond any capacity: the check above reports them
+    uint32_t st = (uint32_t)(s_excl + texcl);
+#pragma unroll
+    for (int q = 0; q < kRangeTileItems; ++q) {
+        const int64_t t = t0 + q;
+        if (t < a.total_tiles) {
+            r.ranges[t] = cnt[q] ? make_uint2(st, st + cnt[q]) : make_uint2(0u, 0u);
+            a.tile_total[t] = st;
+        }
+        st += cnt[q];
+    }
 }
 
 // Opacity footprint of one projected Gaussian: the ellipse {power >= pcut},
@@ -1324,8 +1361,8 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
 // row's lists have all ended, so that the write pass runs on the bytes alone.
 // Per row the CTA leaves the entries it went through (n_head8: up to the end
 // of the chunk in which its last open list ended) and the ended columns (byte
-// w of sat_head); k_seg_plan takes the super-tile's head length as the
-// largest row's.
+// w of sat_head); the last CTA to finish then takes each super-tile's head
+// length as its largest row's and plans the tail segments (seg_plan).
 __global__ void __launch_bounds__(256) k_head_count(TileArgs a)
 {
     __shared__ unsigned char s_m[256];       // columns of each entry of the chunk in this tile row
@@ -1334,6 +1371,7 @@ __global__ void __launch_bounds__(256) k_head_count(TileArgs a)
     __shared__ float s_amax[256];            // alpha_max, 0 when the entry does not enter the bound
     __shared__ uint32_t s_wn[8], s_keep[8];
     __shared__ uint32_t s_sat;
+    __shared__ bool s_last;
     if (status_failed(a.status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
@@ -1467,88 +1505,85 @@ __global__ void __launch_bounds__(256) k_head_count(TileArgs a)
     if (threadIdx.x == 0) {
         a.n_head8[8 * gs + w] = row_end - rgs.x;
         reinterpret_cast<unsigned char*>(a.sat_head + gs)[w] = (unsigned char)s_sat;
+        // the last CTA to finish plans the tail from every CTA's results
+        __threadfence();
+        s_last = atomicAdd(a.ticket + 2, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        seg_plan(a, s_wn);
     }
 }
 
-// Head pass, writing: one CTA per super-tile, taken from a ticket counter;
-// warp w serves tile row w.  Each tile's list starts at the tile's range start
-// and takes, in order, the entries of the head whose coverage byte for the
-// tile row lists them in the tile.
-__global__ void __launch_bounds__(256) k_head_write(TileArgs a)
+// Head pass, writing, of super-tile gs (a CTA of 256 threads, warp w serving
+// tile row w): each tile's list starts at the tile's range start and takes, in
+// order, the entries of the head whose coverage byte for the tile row lists
+// them in the tile.  Runs in the tail pass's writing kernel (k_tile_filter).
+__device__ __forceinline__ void head_write(const TileArgs& a, uint32_t gs, uint32_t* s_row, uint2* s_mask,
+                                           unsigned char (*s_queue)[256], int lane, int warp, unsigned lt)
 {
-    __shared__ uint32_t s_row[256];
-    __shared__ uint2 s_mask[256];
-    __shared__ unsigned char s_queue[8][256];  // per tile row: entries of the chunk it has work for
-    __shared__ uint32_t s_gs;
-    if (status_failed(a.status)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
-    for (;;) {
-        if (threadIdx.x == 0) s_gs = atomicAdd(a.ticket + 2, 1u);
-        __syncthreads();
-        const uint32_t gs = s_gs;
-        if (gs >= (uint32_t)a.total_super) break;
-        int v = 0;
-        for (int q = 1; q < a.V; ++q)
-            if ((int)gs >= a.super_base[q]) v = q;
-        const int ls = (int)gs - a.super_base[v];
-        const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
-        const int TX = a.TX[v], TY = a.TY[v];
-        const int ty = sy * 8 + warp;
-        const int tx0 = sx * 8;
-        const uint2 rgs = a.sranges[gs];
-        uint32_t cur[8];  // next slot of each tile's list
+    int v = 0;
+    for (int q = 1; q < a.V; ++q)
+        if ((int)gs >= a.super_base[q]) v = q;
+    const int ls = (int)gs - a.super_base[v];
+    const int sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
+    const int TX = a.TX[v], TY = a.TY[v];
+    const int ty = sy * 8 + warp;
+    const int tx0 = sx * 8;
+    const uint2 rgs = a.sranges[gs];
+    uint32_t cur[8];  // next slot of each tile's list
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const bool ok = ty < TY && tx0 + k < TX;
-            cur[k] = ok ? a.ranges[a.tile_base[v] + ty * TX + tx0 + k].x : 0u;
-        }
-        const uint32_t end = rgs.x + a.n_head[gs];
-        for (uint32_t b = rgs.x; b < end; b += 256) {
-            __syncthreads();
-            const uint32_t j = b + threadIdx.x;
-            if (j < end) {
-                s_row[threadIdx.x] = a.list[j];
-                s_mask[threadIdx.x] = a.mask[j];
-            }
-            __syncthreads();
-            const int n = (int)min(256u, end - b);
-            // the entries listed in some tile of this row, queued in order so
-            // that the writes below run on full warps
-            int nq = 0;
-            if (ty < TY) {
-                for (int sb = 0; sb < n; sb += 32) {
-                    const int e = sb + lane;
-                    const bool take = e < n && ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) &
-                                                0xffu) != 0u;
-                    const unsigned bal = __ballot_sync(0xffffffffu, take);
-                    if (take) s_queue[warp][nq + __popc(bal & lt)] = (unsigned char)e;
-                    nq += __popc(bal);
-                }
-            }
-            __syncwarp();
-            for (int sb = 0; sb < nq; sb += 32) {
-                const int qi = sb + lane;
-                const int e = qi < nq ? s_queue[warp][qi] : 0;
-                const unsigned m =
-                    qi < nq ? (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu : 0u;
-                const uint32_t row = s_row[e];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const bool cov = (m >> k) & 1u;
-                    const unsigned bal = __ballot_sync(0xffffffffu, cov);
-                    if (cov) {
-                        const uint32_t pos = cur[k] + __popc(bal & lt);
-                        a.vals_out[pos] = row;
-                        if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
-                    }
-                    cur[k] += __popc(bal);
-                }
-            }
-        }
-        __syncthreads();
+    for (int k = 0; k < 8; ++k) {
+        const bool ok = ty < TY && tx0 + k < TX;
+        cur[k] = ok ? a.ranges[a.tile_base[v] + ty * TX + tx0 + k].x : 0u;
     }
+    const uint32_t end = rgs.x + a.n_head[gs];
+    for (uint32_t b = rgs.x; b < end; b += 256) {
+        __syncthreads();
+        const uint32_t j = b + threadIdx.x;
+        if (j < end) {
+            s_row[threadIdx.x] = a.list[j];
+            s_mask[threadIdx.x] = a.mask[j];
+        }
+        __syncthreads();
+        const int n = (int)min(256u, end - b);
+        // the entries listed in some tile of this row, queued in order so
+        // that the writes below run on full warps
+        int nq = 0;
+        if (ty < TY) {
+            for (int sb = 0; sb < n; sb += 32) {
+                const int e = sb + lane;
+                const bool take = e < n && ((warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) &
+                                            0xffu) != 0u;
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                if (take) s_queue[warp][nq + __popc(bal & lt)] = (unsigned char)e;
+                nq += __popc(bal);
+            }
+        }
+        __syncwarp();
+        for (int sb = 0; sb < nq; sb += 32) {
+            const int qi = sb + lane;
+            const int e = qi < nq ? s_queue[warp][qi] : 0;
+            const unsigned m =
+                qi < nq ? (warp < 4 ? s_mask[e].x >> (8 * warp) : s_mask[e].y >> (8 * (warp - 4))) & 0xffu : 0u;
+            const uint32_t row = s_row[e];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const bool cov = (m >> k) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, cov);
+                if (cov) {
+                    const uint32_t pos = cur[k] + __popc(bal & lt);
+                    a.vals_out[pos] = row;
+                    if (a.keys_out) a.keys_out[pos] = (uint32_t)(a.tile_base[v] + ty * TX + tx0 + k);
+                }
+                cur[k] += __popc(bal);
+            }
+        }
+    }
+    __syncthreads();
 }
+
 
 // Tail pass: one CTA per segment (kFilterSeg entries) of what the head pass
 // left of a super-tile's row list (8x8 tiles): it streams the rows in depth
@@ -1579,6 +1614,8 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const uint32_t nseg = a.seg_base[a.total_super];
+    // writing pass: the heads' writes (one ticket per super-tile) come first, then the segments
+    const uint32_t nhead = COUNT ? 0u : (uint32_t)a.total_super;
     if (COUNT) {
         const unsigned b = threadIdx.x;
         s_spread[b] = make_uint4((b & 1u) | ((b >> 1 & 1u) << 16), (b >> 2 & 1u) | ((b >> 3 & 1u) << 16),
@@ -1589,13 +1626,19 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
         // segments are taken from a ticket counter: their costs differ, so a
         // fixed assignment leaves SMs idle while others finish
         if (threadIdx.x == 0) {
-            const uint32_t g = atomicAdd(a.ticket + (COUNT ? 1 : 0), 1u);
-            s_g = g;
-            if (g < nseg) s_gs = (int)a.seg_super[g];  // super-tile of segment g
+            const uint32_t tk = atomicAdd(a.ticket + (COUNT ? 1 : 0), 1u);
+            s_g = tk;
+            const uint32_t sg = tk - nhead;  // wraps below the heads' tickets
+            if ((COUNT || tk >= nhead) && sg < nseg) s_gs = (int)a.seg_super[sg];  // super-tile of the segment
         }
         __syncthreads();
-        const uint32_t g = s_g;
-        if (g >= nseg) break;
+        const uint32_t tk = s_g;
+        if (tk >= nhead + nseg) break;
+        if (!COUNT && tk < nhead) {
+            head_write(a, tk, s_row, s_mask, s_queue, lane, warp, lt);
+            continue;
+        }
+        const uint32_t g = tk - nhead;
         const int gs = s_gs;
         int v = 0;
         for (int w = 1; w < a.V; ++w)
@@ -1611,7 +1654,7 @@ __global__ void __launch_bounds__(256) k_tile_filter(TileArgs a)
         // columns whose lists ended in the head (none are added to them here)
         const uint2 sat = a.sat_head[gs];
         const uint32_t done = ((warp < 4 ? sat.x >> (8 * warp) : sat.y >> (8 * (warp - 4))) & 0xffu);
-        const uint32_t* off = a.seg_cnt + (size_t)g * 64 + warp * 8;  // (after k_seg_prefix) segment offsets
+        const uint32_t* off = a.seg_cnt + (size_t)g * 64 + warp * 8;  // (after k_tile_ranges) segment offsets
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const bool ok = ty < TY && tx0 + k < TX;
@@ -1754,7 +1797,7 @@ struct SortLayout {
     int64_t total_tiles, total_super;
     int64_t parts_split;
     size_t off_dkeys[2], off_dvals[2], off_offsets, off_chunk, off_scan_lb, off_dlb[2], off_tlb[2], off_tkeys,
-        off_tvals, off_hist, off_dhist, off_suptot, off_tickets, off_split_lb, off_total;
+        off_tvals, off_hist, off_dhist, off_suptot, off_rlb, off_tickets, off_split_lb, off_total;
     size_t off_vals1, off_sranges, off_ninst1, off_segbase, off_segcnt, off_segsuper, off_nhead, off_sathead,
         off_nhead8, off_mask, off_tord;
     int64_t max_segs;
@@ -1812,6 +1855,8 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     // zeroed together with hist: the depth digits per view and the super-tile list sizes
     L.off_dhist = take(4 * (size_t)kRadix * 4 * std::max(V, 1));
     L.off_suptot = take(L.binned ? 4 * (size_t)L.total_super : 4);
+    L.off_rlb = take(8 * (size_t)((L.total_tiles + kRangeTiles - 1) / kRangeTiles + 1));  // tile ranges' look-back
+    L.off_tord = take(66 * 4);  // tile-order class counts and cursors
     L.off_tickets = take(4 * 16);
     L.off_split_lb = take(L.binned ? 8 * (size_t)L.smax * std::max<int64_t>(L.parts_split, 1) : 4);
     L.off_total = take(L.binned ? 4 * (size_t)L.total_tiles : 4);
@@ -1826,7 +1871,6 @@ SortLayout sort_layout(int64_t n_rows, int64_t capacity, int V, const int* TX, c
     L.off_sathead = take(8 * (size_t)std::max<int64_t>(L.total_super, 1));
     L.off_nhead8 = take(32 * (size_t)std::max<int64_t>(L.total_super, 1));
     L.off_mask = take(L.binned ? 8 * (size_t)capacity : 4);
-    L.off_tord = take(66 * 4);  // tile-order class counts and cursors
     L.bytes = o;
     return L;
 }
@@ -2067,29 +2111,31 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.sat_head = (uint2*)(w + L.off_sathead);
         t.mask = (uint2*)(w + L.off_mask);
         t.ticket = tickets + 10;
-        RangeArgs tr{};
-        tr.total_tiles = vb.total_tiles;
-        tr.tile_total = U(L.off_total);
+        TileRangeArgs tr{};
+        tr.lb = (unsigned long long*)(w + L.off_rlb);
+        tr.ticket = tickets + 13;
         tr.ranges = (uint2*)bins.ranges;
-        tr.status = status;
+        tr.K_out = bins.n_instances;
+        tr.capacity = bins.capacity;
+        tr.K_super = (const int64_t*)(w + L.off_ninst1);
+        tr.needed = bins.n_needed;
+        tr.cls = bins.tile_order ? U(L.off_tord) : nullptr;
+        tr.spin_limit = ctx.spin_limit;
         // the head of each super-tile list in order (each tile's list up to its
         // saturation), the tail in parallel segments, the prefix over head and
-        // segments, ranges + K + capacity check, then the lists are written
+        // segments with the ranges, K and the capacity check, then the heads'
+        // and segments' writes in one pass
         static const int per_sm_f[2] = {ctas_per_sm(k_tile_filter<false>, 256), ctas_per_sm(k_tile_filter<true>, 256)};
-        static const int per_sm_hw = ctas_per_sm(k_head_write, 256);
-        auto blocks_f = [&](int c) { return (int)std::min<int64_t>(L.max_segs, (int64_t)ctx.num_sms * per_sm_f[c]); };
-        const int blocks_hw = (int)std::min<int64_t>(sb, (int64_t)ctx.num_sms * per_sm_hw);
-        count_launch(7);
+        auto blocks_f = [&](int c) {
+            return (int)std::min<int64_t>(L.max_segs + (c ? 0 : sb), (int64_t)ctx.num_sms * per_sm_f[c]);
+        };
+        count_launch(4);
         k_head_count<<<8 * sb, 256, 0, s>>>(t);
-        k_seg_plan<<<1, 256, 0, s>>>(t);
         k_tile_filter<true><<<blocks_f(1), 256, 0, s>>>(t);
-        k_seg_prefix<<<(int)(((int64_t)sb * 64 + 255) / 256), 256, 0, s>>>(t);
-        k_bin_ranges<<<1, 256, 0, s>>>(tr, bins.n_instances, bins.capacity, (const int64_t*)(w + L.off_ninst1),
-                                       bins.n_needed);
-        k_head_write<<<blocks_hw, 256, 0, s>>>(t);
+        k_tile_ranges<<<(int)((vb.total_tiles + kRangeTiles - 1) / kRangeTiles), 256, 0, s>>>(t, tr);
         k_tile_filter<false><<<blocks_f(0), 256, 0, s>>>(t);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx);
+        return launch_tile_order(bins, L.total_tiles, U(L.off_tord), status, ctx, true);
     }
     // 3. radix path: scan of the per-row tile counts in depth order
     {
