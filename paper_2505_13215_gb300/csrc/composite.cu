@@ -432,7 +432,7 @@ struct BwdOccupancy {
 
 // Reduction of a group of consecutive staged Gaussians j0, j0 - 1, ..,
 // j0 - nq + 1 held in slots 0 .. nq - 1; slot q is added to dproj when bit q of
-// `used` is set (some pixel of the warp blended that Gaussian).
+// `used` is set.
 __device__ __forceinline__ void flush_group(const float4* red, int nq, unsigned used, int j0, const float4* sf,
                                             const uint32_t* srow, float* dproj, int lane)
 {
@@ -487,9 +487,11 @@ struct BwdSums {
 };
 
 // The backward's work for one staged Gaussian on all pixel pairs of the lane,
-// in straight-line code (a skipped pixel with alpha = 0, no effect); returns
-// whether any lane of the warp blended it (one vote, after the work: few
-// listed Gaussians reach no pixel, and the block keeps the pairs independent).
+// in straight-line code (a skipped pixel with alpha = 0, no effect).  Returns
+// whether the Gaussian's sums are to be added to dproj: with STATS, whether
+// any lane of the warp blended it (one vote); otherwise always, as the sums of
+// a Gaussian no pixel blended are exactly zero, and few listed Gaussians reach
+// no pixel, so a vote per Gaussian costs more than the atomics it saves.
 template <int NP, bool CLAMP, bool STATS>
 __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, float2 (&T)[NP], float2 (&nQ)[NP],
                                              const float2 (&G)[NP][3], const float2 (&nrow)[NP], BwdSums& S,
@@ -497,15 +499,16 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
 {
     const float2 one = make_float2(1.f, 1.f);
     bool anyv = false;
-    S.W0 = S.W1 = S.W2 = S.r = S.g = S.b = make_float2(0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const float2 dy = add2(f.py, nrow[p]);
         const float2 np2 = pair_npower(f, ct, dy);
         // the forward's skip, bit for bit, on the pixels that reached this Gaussian
         const bool ox = __float_as_uint(np2.x) <= f.lim, oy = __float_as_uint(np2.y) <= f.lim;
-        anyv |= ox | oy;
-        if (STATS) n_blend += ox + oy;
+        if (STATS) {
+            anyv |= ox | oy;
+            n_blend += ox + oy;
+        }
         const float2 nraw = pair_alpha_raw(f, np2);
         float2 na = nraw;  // -alpha, 0 for a skipped pixel of the pair
         if (CLAMP) {
@@ -519,9 +522,10 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
         // pixel multiplies T by the reciprocal of exactly 1)
         const float2 Tj = mul2(T[p], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
         const float2 nw = mul2(na, Tj);  // -alpha T_j
-        S.r = fma2(nw, G[p][0], S.r);
-        S.g = fma2(nw, G[p][1], S.g);
-        S.b = fma2(nw, G[p][2], S.b);
+        // the sums start at the first pair's terms
+        S.r = p ? fma2(nw, G[p][0], S.r) : mul2(nw, G[p][0]);
+        S.g = p ? fma2(nw, G[p][1], S.g) : mul2(nw, G[p][1]);
+        S.b = p ? fma2(nw, G[p][2], S.b) : mul2(nw, G[p][2]);
         float2 d = fma2(G[p][0], f.r, nQ[p]);  // <G, c_j> - Q
         d = fma2(G[p][1], f.g, d);
         d = fma2(G[p][2], f.bl, d);
@@ -534,11 +538,11 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
             dp.y = nraw.y > -kAlphaClamp ? dp.y : 0.f;
         }
         const float2 dpy = mul2(dp, dy);
-        S.W0 = add2(S.W0, dp);
-        S.W1 = add2(S.W1, dpy);
-        S.W2 = fma2(dpy, dy, S.W2);
+        S.W0 = p ? add2(S.W0, dp) : dp;
+        S.W1 = p ? add2(S.W1, dpy) : dpy;
+        S.W2 = p ? fma2(dpy, dy, S.W2) : mul2(dpy, dy);
     }
-    return __any_sync(0xffffffffu, anyv);
+    return STATS ? __any_sync(0xffffffffu, anyv) : true;
 }
 
 // STATS: also count the pairs evaluated and blended into stats[2..3].
