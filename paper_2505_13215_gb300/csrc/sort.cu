@@ -211,6 +211,7 @@ struct PassArgs {
     int ballot_rank;       // rank by digit-bit ballots (many distinct digits per warp) instead of match
 };
 
+template <bool BALLOT>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
 {
     __shared__ uint32_t s_keys[kSortPart];
@@ -255,27 +256,30 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
         const int64_t seg_end = min(n, (sg + 1) * seg);
         const int64_t base = sg * seg + lp * kSortPart;
         const int64_t wbase = base + (int64_t)warp * 32 * kSortItems;
+        // keys of this warp's share of the partition: its items j * 32 + lane < wrem
+        const int64_t wr = seg_end - wbase;
+        const int wrem = wr <= 0 ? 0 : (wr >= 32 * kSortItems ? 32 * kSortItems : (int)wr);
+        const uint32_t* kin = a.keys_in + wbase;
+        const uint32_t* vin = a.vals_in + wbase;
 
         uint32_t k[kSortItems], v[kSortItems], r[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            const int64_t idx = wbase + j * 32 + lane;
-            const bool ok = idx < seg_end;
-            k[j] = ok ? a.keys_in[idx] : 0u;
-            v[j] = ok ? a.vals_in[idx] : 0u;
+            const bool ok = j * 32 + lane < wrem;
+            k[j] = ok ? kin[j * 32 + lane] : 0u;
+            v[j] = ok ? vin[j * 32 + lane] : 0u;
         }
         // warp-level stable ranking, items in (j, lane) order.  The lanes holding
-        // the same digit: with ballot_rank, one ballot per digit bit (a constant
+        // the same digit: with BALLOT, one ballot per digit bit (a constant
         // cost, for digits that take many values in a warp); otherwise a match
         // instruction (fast when the warp holds few distinct digits, slow with many)
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            const int64_t idx = wbase + j * 32 + lane;
-            const bool ok = idx < seg_end;
+            const bool ok = j * 32 + lane < wrem;
             const uint32_t dj = (k[j] >> a.shift) & 0xff;
             const unsigned valid = __ballot_sync(0xffffffffu, ok);
             unsigned same = valid;
-            if (a.ballot_rank) {  // same for every thread
+            if (BALLOT) {
 #pragma unroll
                 for (int bit = 0; bit < 8; ++bit) {
                     const unsigned bb = __ballot_sync(0xffffffffu, (dj >> bit) & 1u);
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
             r[j] = 0;
             if (ok) {
                 const uint32_t d = dj;
-                const unsigned peers = a.ballot_rank ? same : __match_any_sync(valid, d);
+                const unsigned peers = BALLOT ? same : __match_any_sync(valid, d);
                 const int leader = __ffs(peers) - 1;
                 uint32_t prev = 0;
                 if (lane == leader) {
@@ -355,8 +359,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a)
         // local scatter into digit order
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            const int64_t idx = wbase + j * 32 + lane;
-            if (idx < seg_end) {
+            if (j * 32 + lane < wrem) {
                 const uint32_t dd = (k[j] >> a.shift) & 0xff;
                 const uint32_t pos = s_dstart[dd] + s_whist[warp][dd] + r[j];
                 s_keys[pos] = k[j];
@@ -1888,9 +1891,10 @@ static int sort_ctas_per_sm()
 {
     static int cached = 0;
     if (!cached) {
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_onesweep, kSortThreads, 0) != cudaSuccess || n < 1) n = 1;
-        cached = n;
+        int n0 = 0, n1 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_onesweep<false>, kSortThreads, 0) != cudaSuccess) n0 = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_onesweep<true>, kSortThreads, 0) != cudaSuccess) n1 = 1;
+        cached = std::max(1, std::min(n0, n1));
     }
     return cached;
 }
@@ -1900,7 +1904,10 @@ static cudaError_t run_pass(const PassArgs& a, int64_t parts, int resident, cuda
 {
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(parts, resident));
     count_launch();
-    k_onesweep<<<blocks, kSortThreads, 0, s>>>(a);
+    if (a.ballot_rank)
+        k_onesweep<true><<<blocks, kSortThreads, 0, s>>>(a);
+    else
+        k_onesweep<false><<<blocks, kSortThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
