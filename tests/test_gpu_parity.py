@@ -181,6 +181,31 @@ def test_bin_sort_ties_and_multiview(tile_sort_mode):
     np.testing.assert_array_equal(ranges, expected_ranges(ok, T))
 
 
+def test_bin_sort_bitexact_at_scale(tile_sort_mode):
+    """Three views of different sizes (704x528, 512x400, 880x300) of a frustum
+    scene of 18k Gaussians at depths 1-20, the near ones covering many tiles:
+    several super-tiles per view, super-tile lists of several runs of 4096 slots
+    with rows cut across runs, and more tiles than one block of the tile
+    ranges takes.  Lists, ranges and K bit-exact against the oracle's stable
+    sort of the same keys."""
+    import dataclasses
+    scene, base = scenes.video_scene(seed=5, n3=12000, n4=6000, W=704, H=528, f=760.0)
+    jit = scenes.jittered_views(base[0], 3, seed=11)
+    views = [jit[0], dataclasses.replace(jit[1], W=512, H=400, cx=256.0, cy=200.0),
+             dataclasses.replace(jit[2], W=880, H=300, cx=440.0, cy=150.0)]
+    Ps = [O.project(scene, v) for v in views]
+    # the split's work at this size: super-tile entries per view, tiles in all
+    for P in Ps:
+        r = P["rect"][P["visible"] == 1].astype(np.int64)
+        k1 = (((r[:, 2] + 7) >> 3) - (r[:, 0] >> 3)) * (((r[:, 3] + 7) >> 3) - (r[:, 1] >> 3))
+        assert k1.sum() > 3 * 4096 and k1.max() >= 16
+    gk, gv, ok, ov, ranges, T = staged_sort(views, Ps, scene.n)
+    assert T > 2 * 1024
+    np.testing.assert_array_equal(gk, ok)
+    np.testing.assert_array_equal(gv, ov)
+    np.testing.assert_array_equal(ranges, expected_ranges(ok, T))
+
+
 def test_bin_sort_end_to_end_lists(small):
     """The GPU's own keys: per tile the same Gaussians, in non-decreasing oracle depth."""
     scene, views, G, R0, P, ref = small
