@@ -181,6 +181,26 @@ def test_bin_sort_ties_and_multiview(tile_sort_mode):
     np.testing.assert_array_equal(ranges, expected_ranges(ok, T))
 
 
+def test_bin_sort_crowded_depths(tile_sort_mode):
+    """Two thirds of 6000 rows per view at one of two depths (as BF16-rounded
+    means produce in dense depth ranges): thousands of exact depth ties per
+    view, broken in emission order, the lists bit-exact in both tile-sort modes."""
+    scene, _ = scenes.small_scene(seed=4, n3=4200, n4=1800)
+    views = [scenes.identity_view(160, 128, 150.0, 0.3), scenes.identity_view(96, 80, 90.0, 0.7)]
+    Ps = [O.project(scene, v) for v in views]
+    rng = np.random.default_rng(5)
+    deps = []
+    for _ in views:
+        d = rng.uniform(1.5, 6.0, scene.n).astype(np.float32)
+        crowd = rng.random(scene.n) < 2.0 / 3.0
+        d[crowd] = rng.choice(np.array([2.5, 4.0], np.float32), size=int(crowd.sum()))
+        deps.append(d)
+    gk, gv, ok, ov, ranges, T = staged_sort(views, Ps, scene.n, depth_override=deps)
+    np.testing.assert_array_equal(gk, ok)
+    np.testing.assert_array_equal(gv, ov)
+    np.testing.assert_array_equal(ranges, expected_ranges(ok, T))
+
+
 def test_bin_sort_bitexact_at_scale(tile_sort_mode):
     """Three views of different sizes (704x528, 512x400, 880x300) of a frustum
     scene of 18k Gaussians at depths 1-20, the near ones covering many tiles:
