@@ -150,6 +150,79 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+class NvmlSampler:
+    """SM clock, power and clock-event reasons read through NVML (the driver's
+    management library, read only) about every millisecond from a thread, so
+    that a timed region of tens of milliseconds still holds dozens of samples.
+    The GPU is matched by its PCI address."""
+    SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL = 0x4, 0x8, 0x20, 0x40
+    CLOCK_SM = 1
+
+    def __init__(self, dev):
+        import ctypes
+        import threading
+
+        import torch
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        props = torch.cuda.get_device_properties(dev)
+        bus = b"%08X:%02X:%02X.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML device at " + bus.decode())
+        mx = ctypes.c_uint()
+        self.max_mhz = mx.value if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.CLOCK_SM, ctypes.byref(mx)) == 0 \
+            else None
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples = []
+        self.done = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 2.0:
+            time.sleep(0.001)
+
+    def _run(self):
+        ct = self.ct
+        c, r, pw = ct.c_uint(), ct.c_ulonglong(), ct.c_uint()
+        while not self.done.is_set():
+            sm = c.value if self.lib.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, ct.byref(c)) == 0 else None
+            rs = r.value if self.reasons_fn(self.h, ct.byref(r)) == 0 else None
+            w = pw.value / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(pw)) == 0 else None
+            self.samples.append((sm, rs, w))
+            time.sleep(0.001)
+
+    def stop(self):
+        self.done.set()
+        self.thread.join(timeout=5)
+        rows = list(self.samples)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"], "source": "nvml"}
+        sm = sorted(x[0] for x in rows if x[0] is not None)
+        bits = 0
+        for x in rows:
+            bits |= x[1] or 0
+        names = ((self.HW_SLOWDOWN, "hw_slowdown"), (self.HW_THERMAL, "hw_thermal_slowdown"),
+                 (self.SW_THERMAL, "sw_thermal_slowdown"), (self.SW_POWER_CAP, "sw_power_cap"))
+        pw = [x[2] for x in rows if x[2] is not None]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": [n for b, n in names if bits & b], "samples": len(rows),
+                "power_w_max": max(pw) if pw else None, "source": "nvml"}
+
+
+def clock_sampler(dev, index):
+    """Clocks during a timed region: NVML when the driver's library loads, else nvidia-smi."""
+    try:
+        return NvmlSampler(dev)
+    except (OSError, AttributeError, RuntimeError):
+        return ClockSampler(index)
+
+
 # ---------------------------------------------------------------------------
 # roofline model
 # ---------------------------------------------------------------------------
@@ -253,7 +326,7 @@ def measure_pipe_peaks(dev, local, reps=12):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     res = {}
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(dev, local)
     for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ex2"), (3, "rcp")):
         for _ in range(2):
             abi.splat_peak_probe(kind, blocks, PROBE_ITERS[kind], out.data_ptr(), sp)
@@ -333,7 +406,7 @@ def run_ours(args, rank, local, world):
     torch.cuda.synchronize()
     R.check("warm-up")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(dev, local)
     barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
