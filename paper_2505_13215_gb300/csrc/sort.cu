@@ -20,11 +20,16 @@
 // (view, depth) order.
 //
 // The binned path (the default up to 40960 tiles per view) orders by tile
-// without tile-digit passes: the depth-ordered rows are partitioned stably by
-// 8x8-tile super-tile, then each super-tile's rows are filtered into its
-// tiles' lists in order.  With culling on, a list holds only the tiles the
-// opacity footprint reaches and ends where every pixel of the tile has
-// certainly saturated (tile saturation, below); neither changes a result.
+// without tile-digit passes: the depth-ordered rows are split stably by
+// 8x8-tile super-tile in one onesweep-style pass over equal runs of list
+// slots (k_super_split), then each super-tile's list is filtered into its
+// tiles' lists in order: the first 512 entries by a saturation head
+// (k_head_count, a CTA per tile row), the rest in parallel segments
+// (k_tile_filter), the counts turned into ranges by one look-back pass
+// (k_tile_ranges) and the lists written by one pass.  With culling on, a list
+// holds only the tiles the opacity footprint reaches and ends where every
+// pixel of the tile has certainly saturated (tile saturation, below); neither
+// changes a result.  12 launches for any number of views.
 #include <algorithm>
 
 #include "splat_internal.cuh"
