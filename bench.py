@@ -262,13 +262,13 @@ def algorithmic_bytes(stage, n3, n4, V, pix, K, elem, K_super=0):
 
 # FP32 operations per pixel-Gaussian pair on each path of the compositing
 # kernels, counted from their source (FMA = 2, exp2 and reciprocal 1, compares
-# and selects 0): evaluating the power (dy and two FMA) costs 5; a blended pair
-# costs those 5 plus 10 in the forward (exp2, alpha, alpha T, transmittance,
-# three colour FMA) and plus 26 in the backward (exp2, alpha, 1 - alpha,
-# reciprocal, replayed T by one multiply, alpha T, three colour-gradient FMA,
-# three FMA for <dL/dC, c> - Q, the Q update, dL/dpower and its three moments).
+# and selects 0): evaluating -log2(alpha) (dy and two FMA) costs 5; a blended
+# pair costs those 5 plus 9 in the forward (exp2, alpha T, transmittance, three
+# colour FMA) and plus 25 in the backward (exp2, 1 - alpha, reciprocal,
+# replayed T by one multiply, alpha T, three colour-gradient FMA, three FMA for
+# <dL/dC, c> - Q, the Q update, dL/dpower and its three moments).
 FLOPS_EVAL = 5
-FLOPS_BLEND = {"composite_fwd": 5 + 10, "composite_bwd": 5 + 26}
+FLOPS_BLEND = {"composite_fwd": 5 + 9, "composite_bwd": 5 + 25}
 # the round per-pair figures of the method's cost model: about 15 FP32
 # operations and one exponential per evaluated pair forward, about 60 backward
 SURVEY_OPS = {"composite_fwd": 15, "composite_bwd": 60}

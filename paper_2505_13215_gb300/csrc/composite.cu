@@ -41,21 +41,21 @@ __device__ __forceinline__ float ex2_approx(float x)
 
 // Projected features of one Gaussian as staged in shared memory, every value
 // duplicated for the packed pixel-pair arithmetic (five float4):
-//   (px, px, py, py) (na2, na2, nb2, nb2) (nc2, nc2, -op, -op) (r, r, g, g) (b, b, lim, op)
-// The conic is staged scaled by log2(e)/2 (na2, nc2) and log2(e) (nb2), so that
-// np2 = na2 dx^2 + nb2 dx dy + nc2 dy^2 is minus the power in base 2 and
-// alpha = alpha_max 2^-np2 needs no extra multiply.  The skip tests power > 0
-// and alpha < 1/255 become 0 <= np2 <= -pcut2 with pcut2 = log2(1/(255 alpha_max)),
-// evaluated as one unsigned compare of the bits of np2 with lim, the bits of
-// 0 - pcut2 (non-negative floats order like their bit patterns; a NaN or a
-// negative np2 is above every lim).  np2 is +0, never -0, where the power
-// vanishes (dx = px - u is +0 there, and every product and sum of the
-// evaluation then gives +0).  Forward and backward take every decision (the
-// skip, the clamp, the stop) on the same values.
+//   (px, px, py, py) (na2, na2, nb2, nb2) (nc2, nc2, ml, ml) (r, r, g, g) (b, b, 0, op)
+// The conic is staged scaled by log2(e)/2 (na2, nc2) and log2(e) (nb2), and
+// ml = -log2(alpha_max) >= 0 joins the x-only term, so that
+// np2 = ml + na2 dx^2 + nb2 dx dy + nc2 dy^2 is minus the base-2 logarithm of
+// alpha = alpha_max exp(power): alpha = 2^-np2, one exponential and no
+// multiply.  The skip test alpha < 1/255 becomes np2 > log2(255), evaluated as
+// one unsigned compare of the bits of np2 with the bits of log2(255)
+// (non-negative floats order like their bit patterns; a NaN or a negative np2,
+// which needs power > -ml, i.e. alpha above alpha_max, is above the limit).
+// Forward and backward take every decision (the skip, the clamp, the stop) on
+// the same values.
 constexpr int kFeat = 5;  // float4 per staged Gaussian
+constexpr uint32_t kLimBits = 0x40ffd1beu;  // bits of log2(255) rounded to FP32 (7.9943533)
 struct Feat {
-    float2 px, py, na2, nb2, nc2, nop, r, g, bl;
-    uint32_t lim;
+    float2 px, py, na2, nb2, nc2, ml, r, g, bl;
     float op;
 };
 
@@ -64,10 +64,9 @@ __device__ __forceinline__ void load_feat(const float4* s, Feat& f)
     const float4 f0 = s[0], f1 = s[1], f2 = s[2], f3 = s[3], f4 = s[4];
     f.px = make_float2(f0.x, f0.y); f.py = make_float2(f0.z, f0.w);
     f.na2 = make_float2(f1.x, f1.y); f.nb2 = make_float2(f1.z, f1.w);
-    f.nc2 = make_float2(f2.x, f2.y); f.nop = make_float2(f2.z, f2.w);
+    f.nc2 = make_float2(f2.x, f2.y); f.ml = make_float2(f2.z, f2.w);
     f.r = make_float2(f3.x, f3.y); f.g = make_float2(f3.z, f3.w);
     f.bl = make_float2(f4.x, f4.y);
-    f.lim = __float_as_uint(f4.z);
     f.op = f4.w;
 }
 
@@ -119,17 +118,16 @@ __device__ __forceinline__ void stage_feat(const RawRows& raw, int lane, float4*
     const float2 xy = raw.xy[lane];
     const float4 co = raw.co[lane];
     const float4 rd = raw.rd[lane];
-    const float pcut2 = __log2f(kAlphaMin / co.w);
-    // alpha_max >= 1/255 for every listed Gaussian, so pcut2 <= 0; should the
-    // approximate logarithm round above 0, a NaN mean makes every test fail,
-    // as pcut2 <= p2 <= 0 would
-    const float px = pcut2 <= 0.f ? xy.x : __int_as_float(0x7fc00000);
+    // alpha_max <= 1 (a sigmoid times a temporal factor), so ml >= 0; a
+    // Gaussian with alpha_max < 1/255 (none is listed) has ml > log2(255) and
+    // fails every skip test
+    const float ml = 0.f - __log2f(co.w);
     const float na2 = 0.5f * kLog2e * co.x, nb2 = kLog2e * co.y, nc2 = 0.5f * kLog2e * co.z;
-    s[0] = make_float4(px, px, xy.y, xy.y);
+    s[0] = make_float4(xy.x, xy.x, xy.y, xy.y);
     s[1] = make_float4(na2, na2, nb2, nb2);
-    s[2] = make_float4(nc2, nc2, -co.w, -co.w);
+    s[2] = make_float4(nc2, nc2, ml, ml);
     s[3] = make_float4(rd.x, rd.x, rd.y, rd.y);
-    s[4] = make_float4(rd.z, rd.z, 0.f - pcut2, co.w);
+    s[4] = make_float4(rd.z, rd.z, 0.f, co.w);
 }
 
 __device__ __forceinline__ int find_view(const ViewBatch& vb, int tile)
@@ -155,8 +153,8 @@ __device__ __forceinline__ float rcp_approx(float x)
 }
 
 // One Gaussian seen from one lane's pixel column (-u in nu): the x-only terms
-// of minus the power for the pixel pairs.  Forward and backward build them
-// with the same operations, so both evaluate bit-identical powers.
+// of np2 (with ml) for the pixel pairs.  Forward and backward build them with
+// the same operations, so both evaluate bit-identical values.
 struct ColTerms {
     float2 nA2, nBx2, dx;
 };
@@ -165,7 +163,7 @@ __device__ __forceinline__ ColTerms col_terms(const Feat& f, float2 nu)
 {
     ColTerms c;
     c.dx = add2(f.px, nu);
-    c.nA2 = mul2(mul2(f.na2, c.dx), c.dx);
+    c.nA2 = fma2(mul2(f.na2, c.dx), c.dx, f.ml);
     c.nBx2 = mul2(f.nb2, c.dx);
     return c;
 }
@@ -176,21 +174,22 @@ __device__ __forceinline__ ColTerms col_terms(const Feat& f, float2 nu)
 // (dL/dpower = 0 times dy) stay 0.
 constexpr float kOffRow = 1e30f;
 
-// minus the base-2 power at a pixel pair whose rows are -nrow:
+// np2 = -log2(alpha) at a pixel pair whose rows are -nrow:
 // nA2 + dy (nBx2 + nc2 dy), dy = py - row.
 __device__ __forceinline__ float2 pair_npower(const Feat& f, const ColTerms& c, float2 dy)
 {
     return fma2(dy, fma2(f.nc2, dy, c.nBx2), c.nA2);
 }
 
-__device__ __forceinline__ float2 pair_alpha_raw(const Feat& f, float2 np2)
+__device__ __forceinline__ float2 pair_alpha(float2 np2)
 {
-    return mul2(f.nop, make_float2(ex2_approx(-np2.x), ex2_approx(-np2.y)));  // -alpha_max 2^p2
+    return make_float2(ex2_approx(-np2.x), ex2_approx(-np2.y));  // alpha = 2^-np2
 }
 
-// A Gaussian with alpha_max below this never reaches the 0.99 clamp (p2 <= 0
-// makes 2^p2 <= 1, and ex2.approx overshoots 1 by far less than the margin),
-// so the clamp and its zero derivative are evaluated only above it.
+// A Gaussian with alpha_max below this never reaches the 0.99 clamp (np2 >= ml
+// up to rounding, so 2^-np2 <= alpha_max, and the logarithm, the rounding and
+// ex2.approx move that by far less than the margin), so the clamp and its zero
+// derivative are evaluated only above it.
 constexpr float kClampFree = 0.989f;
 
 // The forward's work for one staged Gaussian (list position pos, 1-based) on
@@ -219,14 +218,14 @@ __device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, 
     bool stop = false;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        float2 na = pair_alpha_raw(f, np2[p]);  // -alpha, 0 for a skipped pixel
+        float2 a = pair_alpha(np2[p]);  // alpha, 0 for a skipped pixel
         if (CLAMP) {
-            na.x = fmaxf(na.x, -kAlphaClamp);
-            na.y = fmaxf(na.y, -kAlphaClamp);
+            a.x = fminf(a.x, kAlphaClamp);
+            a.y = fminf(a.y, kAlphaClamp);
         }
-        na.x = __float_as_uint(np2[p].x) <= f.lim ? na.x : 0.f;
-        na.y = __float_as_uint(np2[p].y) <= f.lim ? na.y : 0.f;
-        nw[p] = mul2(na, T[p]);     // -alpha T: nonzero exactly for the blended pixels
+        a.x = __float_as_uint(np2[p].x) <= kLimBits ? a.x : 0.f;
+        a.y = __float_as_uint(np2[p].y) <= kLimBits ? a.y : 0.f;
+        nw[p] = mul2(make_float2(-a.x, -a.y), T[p]);  // -alpha T: nonzero exactly for the blended pixels
         tT[p] = add2(T[p], nw[p]);  // T (1 - alpha); T itself for a skipped pixel (T >= 1e-4)
         stop |= (tT[p].x < kTMin) | (tT[p].y < kTMin);
     }
@@ -462,12 +461,13 @@ __device__ __forceinline__ void flush_group(const float4* red, int nq, unsigned 
         const uint32_t row = srow[jv];
         if (h == 0) {
             const float4 f1 = sf[jv * kFeat + 1], f2 = sf[jv * kFeat + 2];
+            const float nop = -sf[jv * kFeat + 4].w;
             float4 out;
             if ((gi & 1) == 0) {
                 const float ca = kLn2x2 * f1.x, cb = 0.5f * kLn2x2 * f1.z, cc = kLn2x2 * f2.x;
                 out = make_float4(ca * s0.x + cb * s0.y, cc * s0.y + cb * s0.x, 0.5f * s1.x, s1.y);
             } else {
-                out = make_float4(0.5f * s0.x, s0.y / f2.z, -s1.x, -s1.y);
+                out = make_float4(0.5f * s0.x, s0.y / nop, -s1.x, -s1.y);
             }
             atomicAdd((float4*)(dproj + (int64_t)row * 12) + (gi & 1), out);
         } else {
@@ -504,19 +504,20 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
         const float2 dy = add2(f.py, nrow[p]);
         const float2 np2 = pair_npower(f, ct, dy);
         // the forward's skip, bit for bit, on the pixels that reached this Gaussian
-        const bool ox = __float_as_uint(np2.x) <= f.lim, oy = __float_as_uint(np2.y) <= f.lim;
+        const bool ox = __float_as_uint(np2.x) <= kLimBits, oy = __float_as_uint(np2.y) <= kLimBits;
         if (STATS) {
             anyv |= ox | oy;
             n_blend += ox + oy;
         }
-        const float2 nraw = pair_alpha_raw(f, np2);
-        float2 na = nraw;  // -alpha, 0 for a skipped pixel of the pair
+        const float2 araw = pair_alpha(np2);
+        float2 a = araw;  // alpha, 0 for a skipped pixel of the pair
         if (CLAMP) {
-            na.x = fmaxf(na.x, -kAlphaClamp);
-            na.y = fmaxf(na.y, -kAlphaClamp);
+            a.x = fminf(a.x, kAlphaClamp);
+            a.y = fminf(a.y, kAlphaClamp);
         }
-        na.x = ox ? na.x : 0.f;
-        na.y = oy ? na.y : 0.f;
+        a.x = ox ? a.x : 0.f;
+        a.y = oy ? a.y : 0.f;
+        const float2 na = make_float2(-a.x, -a.y);  // -alpha
         const float2 om = add2(one, na);  // 1 - alpha >= 0.01
         // T_j = T / (1 - alpha), one reciprocal and one multiply (a skipped
         // pixel multiplies T by the reciprocal of exactly 1)
@@ -534,8 +535,8 @@ __device__ __forceinline__ bool bwd_gaussian(const Feat& f, const ColTerms& ct, 
         // dL/dpower = dL/dalpha * alpha = w d where alpha is not clamped
         float2 dp = mul2(nw, d);
         if (CLAMP) {
-            dp.x = nraw.x > -kAlphaClamp ? dp.x : 0.f;
-            dp.y = nraw.y > -kAlphaClamp ? dp.y : 0.f;
+            dp.x = araw.x < kAlphaClamp ? dp.x : 0.f;
+            dp.y = araw.y < kAlphaClamp ? dp.y : 0.f;
         }
         const float2 dpy = mul2(dp, dy);
         S.W0 = p ? add2(S.W0, dp) : dp;
