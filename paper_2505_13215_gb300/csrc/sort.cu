@@ -1371,7 +1371,10 @@ __device__ __forceinline__ bool ellipse_band_extent(const float4& g0, const floa
 // of the chunk in which its last open list ended) and the ended columns (byte
 // w of sat_head); the last CTA to finish then takes each super-tile's head
 // length as its largest row's and plans the tail segments (seg_plan).
-__global__ void __launch_bounds__(256) k_head_count(TileArgs a)
+// compiled for 8 resident CTAs per SM (32 registers; 6 at 39 registers measured
+// 1.5 us slower per 4-view step, while the split and the tail passes measured
+// slower when held to 32 registers)
+__global__ void __launch_bounds__(256, 8) k_head_count(TileArgs a)
 {
     __shared__ unsigned char s_m[256];       // columns of each entry of the chunk in this tile row
     __shared__ unsigned char s_queue[256];   // the chunk's entries queued by the row, in order
