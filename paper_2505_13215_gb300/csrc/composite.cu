@@ -39,9 +39,10 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Projected features of one Gaussian as staged in shared memory, every value
-// duplicated for the packed pixel-pair arithmetic (five float4):
-//   (px, px, py, py) (na2, na2, nb2, nb2) (nc2, nc2, ml, ml) (r, r, g, g) (b, b, 0, op)
+// Projected features of one Gaussian as staged in shared memory (four float4),
+// the values the pixel pairs use duplicated for the packed arithmetic, the
+// column terms' inputs once:
+//   (py, py, nc2, nc2) (r, r, g, g) (b, b, px, op) (na2, nb2, ml, 0)
 // The conic is staged scaled by log2(e)/2 (na2, nc2) and log2(e) (nb2), and
 // ml = -log2(alpha_max) >= 0 joins the x-only term, so that
 // np2 = ml + na2 dx^2 + nb2 dx dy + nc2 dy^2 is minus the base-2 logarithm of
@@ -52,22 +53,21 @@ __device__ __forceinline__ float ex2_approx(float x)
 // which needs power > -ml, i.e. alpha above alpha_max, is above the limit).
 // Forward and backward take every decision (the skip, the clamp, the stop) on
 // the same values.
-constexpr int kFeat = 5;  // float4 per staged Gaussian
+constexpr int kFeat = 4;  // float4 per staged Gaussian
 constexpr uint32_t kLimBits = 0x40ffd1beu;  // bits of log2(255) rounded to FP32 (7.9943533)
 struct Feat {
-    float2 px, py, na2, nb2, nc2, ml, r, g, bl;
-    float op;
+    float2 py, nc2, r, g, bl;
+    float px, op, na2, nb2, ml;
 };
 
 __device__ __forceinline__ void load_feat(const float4* s, Feat& f)
 {
-    const float4 f0 = s[0], f1 = s[1], f2 = s[2], f3 = s[3], f4 = s[4];
-    f.px = make_float2(f0.x, f0.y); f.py = make_float2(f0.z, f0.w);
-    f.na2 = make_float2(f1.x, f1.y); f.nb2 = make_float2(f1.z, f1.w);
-    f.nc2 = make_float2(f2.x, f2.y); f.ml = make_float2(f2.z, f2.w);
-    f.r = make_float2(f3.x, f3.y); f.g = make_float2(f3.z, f3.w);
-    f.bl = make_float2(f4.x, f4.y);
-    f.op = f4.w;
+    const float4 f0 = s[0], f1 = s[1], f2 = s[2], f3 = s[3];
+    f.py = make_float2(f0.x, f0.y); f.nc2 = make_float2(f0.z, f0.w);
+    f.r = make_float2(f1.x, f1.y); f.g = make_float2(f1.z, f1.w);
+    f.bl = make_float2(f2.x, f2.y);
+    f.px = f2.z; f.op = f2.w;
+    f.na2 = f3.x; f.nb2 = f3.y; f.ml = f3.z;
 }
 
 // The projected rows of the next batch are gathered while the current batch
@@ -123,11 +123,10 @@ __device__ __forceinline__ void stage_feat(const RawRows& raw, int lane, float4*
     // fails every skip test
     const float ml = 0.f - __log2f(co.w);
     const float na2 = 0.5f * kLog2e * co.x, nb2 = kLog2e * co.y, nc2 = 0.5f * kLog2e * co.z;
-    s[0] = make_float4(xy.x, xy.x, xy.y, xy.y);
-    s[1] = make_float4(na2, na2, nb2, nb2);
-    s[2] = make_float4(nc2, nc2, ml, ml);
-    s[3] = make_float4(rd.x, rd.x, rd.y, rd.y);
-    s[4] = make_float4(rd.z, rd.z, 0.f, co.w);
+    s[0] = make_float4(xy.y, xy.y, nc2, nc2);
+    s[1] = make_float4(rd.x, rd.x, rd.y, rd.y);
+    s[2] = make_float4(rd.z, rd.z, xy.x, co.w);
+    s[3] = make_float4(na2, nb2, ml, 0.f);
 }
 
 __device__ __forceinline__ int find_view(const ViewBatch& vb, int tile)
@@ -156,15 +155,20 @@ __device__ __forceinline__ float rcp_approx(float x)
 // of np2 (with ml) for the pixel pairs.  Forward and backward build them with
 // the same operations, so both evaluate bit-identical values.
 struct ColTerms {
-    float2 nA2, nBx2, dx;
+    float2 nA2, nBx2;
+    float dx;
 };
 
+// Both halves of a pair share the column, so the terms are computed once in
+// scalar arithmetic (a packed operation on equal halves costs the FMA pipe
+// twice as much) and then duplicated.
 __device__ __forceinline__ ColTerms col_terms(const Feat& f, float2 nu)
 {
     ColTerms c;
-    c.dx = add2(f.px, nu);
-    c.nA2 = fma2(mul2(f.na2, c.dx), c.dx, f.ml);
-    c.nBx2 = mul2(f.nb2, c.dx);
+    c.dx = f.px + nu.x;
+    const float a = fmaf(f.na2 * c.dx, c.dx, f.ml), b = f.nb2 * c.dx;
+    c.nA2 = make_float2(a, a);
+    c.nBx2 = make_float2(b, b);
     return c;
 }
 
@@ -460,11 +464,11 @@ __device__ __forceinline__ void flush_group(const float4* red, int nq, unsigned 
         const int jv = j0 - q;
         const uint32_t row = srow[jv];
         if (h == 0) {
-            const float4 f1 = sf[jv * kFeat + 1], f2 = sf[jv * kFeat + 2];
-            const float nop = -sf[jv * kFeat + 4].w;
+            const float4 f3 = sf[jv * kFeat + 3];
+            const float nc2 = sf[jv * kFeat].z, nop = -sf[jv * kFeat + 2].w;
             float4 out;
             if ((gi & 1) == 0) {
-                const float ca = kLn2x2 * f1.x, cb = 0.5f * kLn2x2 * f1.z, cc = kLn2x2 * f2.x;
+                const float ca = kLn2x2 * f3.x, cb = 0.5f * kLn2x2 * f3.y, cc = kLn2x2 * nc2;
                 out = make_float4(ca * s0.x + cb * s0.y, cc * s0.y + cb * s0.x, 0.5f * s1.x, s1.y);
             } else {
                 out = make_float4(0.5f * s0.x, s0.y / nop, -s1.x, -s1.y);
@@ -655,7 +659,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
         if (bi >= 2) next_row = vals[b - 64u + lane];
         const int n = (int)min(32u, end - b);
         // one vote per batch: does any staged Gaussian reach the 0.99 clamp
-        const bool clamp_batch = __any_sync(0xffffffffu, lane < n && sf[lane * kFeat + 4].w >= kClampFree);
+        const bool clamp_batch = __any_sync(0xffffffffu, lane < n && sf[lane * kFeat + 2].w >= kClampFree);
         auto walk = [&](auto clamp_tag) {
             constexpr bool CL = decltype(clamp_tag)::value;
             // groups of kRedBatch consecutive Gaussians, back to front; Gaussian
@@ -694,7 +698,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, BwdOccupancy<PPL>::kMinBlocks
                     used |= (unsigned)any << q;
                     const float W0 = S.W0.x + S.W0.y, W1 = S.W1.x + S.W1.y;
                     float4* slot = red + 2 * q * 32 + lane;
-                    const float dx = ct.dx.x, dxW0 = dx * W0;
+                    const float dx = ct.dx, dxW0 = dx * W0;
                     slot[0] = make_float4(dxW0, W1, dx * dxW0, dx * W1);
                     slot[32] = make_float4(S.W2.x + S.W2.y, W0, S.r.x + S.r.y, S.g.x + S.g.y);
                     ((float*)(red + (14 + (q >> 2)) * 32 + lane))[q & 3] = S.b.x + S.b.y;
