@@ -266,10 +266,20 @@ __device__ __forceinline__ bool fwd_gaussian(const Feat& f, const ColTerms& ct, 
     return finished;
 }
 
+// Resident one-warp CTAs per SM the forward is compiled for.  The register
+// file is split among the four schedulers, so occupancy moves in steps of four
+// warps: PPL = 8 at 24 (80 registers, 8 bytes spilled) measured 0.329 ->
+// 0.317 ms per 4-view step against 20 at 92 registers (28 at 72 registers:
+// 0.321, 32 at 64: 0.337); the smaller variants fit 32 in 64 registers.
+template <int PPL>
+struct FwdOccupancy {
+    static constexpr int kMinBlocks = PPL >= 8 ? 24 : 32;
+};
+
 // STATS: also count, per warp, the pixel-Gaussian pairs evaluated (power
 // computed) and blended, into stats[0..1] (diagnostic instantiation only).
 template <int PPL, bool STATS>
-__global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj proj, const uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(kCompWarps * 32, FwdOccupancy<PPL>::kMinBlocks) k_composite_fwd(splat_proj proj, const uint32_t* __restrict__ vals,
                                                                    const uint2* __restrict__ ranges,
                                                                    const uint32_t* __restrict__ order, ViewBatch vb,
                                                                    splat_image img, L1Fuse l1, int32_t* status,
@@ -426,8 +436,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite_fwd(splat_proj pr
 constexpr int kRedBatch = 7;
 constexpr int kRedGroups = 16;
 // resident one-warp CTAs per SM the backward is compiled for: 16 leave
-// PPL = 8 its 128 registers (fewer registers spill in the loop and measured
-// slower), 20 give the smaller variants 96
+// PPL = 8 its 128 registers (20, at 96 registers, spill in the loop and
+// measured slower: 0.615 -> 0.641 ms per 4-view step), 20 give the smaller
+// variants 96
 template <int PPL>
 struct BwdOccupancy {
     static constexpr int kMinBlocks = PPL >= 8 ? 16 : 20;
