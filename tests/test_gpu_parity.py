@@ -885,9 +885,10 @@ def test_max_batch_sixteen_views_mixed_sizes():
 
 
 def test_tile_order_longest_first_changes_nothing(small):
-    """splat_bin_sort writes the tiles longest list first (classes of powers of
-    two); the compositing kernels take them in that order.  The order is a
-    permutation of the tiles, non-increasing by class, and rendering with it or
+    """splat_bin_sort writes the tiles longest list first (classes of eight per
+    power of two: the exponent and the next three bits of the length); the
+    compositing kernels take them in that order.  The order is a permutation of
+    the tiles, non-increasing by class, and rendering with it or
     in raster order (NULL) gives the same images, T and ends of walks (gradients
     up to the order of their float atomics)."""
     scene, views = scenes.arc_scene(seed=5, n=20000, frac4=0.3, n_views=3, full=(256, 192, 280.0),
@@ -911,8 +912,14 @@ def test_tile_order_longest_first_changes_nothing(small):
     T = R.total_tiles
     assert np.array_equal(np.sort(order[:T]), np.arange(T))
     length = rg[order[:T], 1] - rg[order[:T], 0]
-    cls = np.where(length > 0, np.floor(np.log2(np.maximum(length, 1))).astype(np.int64) + 1, 0)
+    e = np.floor(np.log2(np.maximum(length, 1))).astype(np.int64)
+    frac = np.floor((np.maximum(length, 1) / 2.0 ** e - 1.0) * 8).astype(np.int64)
+    cls = np.where(length > 0, 1 + 8 * e + frac, 0)
     assert np.all(np.diff(cls) <= 0) and cls[0] > cls[-1]
+    # each class spans less than a factor 9/8 of lengths
+    for c in np.unique(cls[cls > 0]):
+        sel = length[cls == c]
+        assert sel.max() < sel.min() * 9 / 8 + 1
     (rgb0, T0, l0, g0), (rgb1, T1, l1, g1) = out
     assert torch.equal(rgb0, rgb1) and torch.equal(T0, T1) and torch.equal(l0, l1)
     for k in g0:
