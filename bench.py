@@ -534,7 +534,12 @@ def run_ours(args, rank, local, world):
 
     # ---- roofline of the dominant stage ----
     pix = int(sum(R.pix))
-    dom = max(stages, key=lambda s: stages[s])
+    # every stage interval carries one in-graph event, whose cost the empty
+    # "loss" interval (the loss is computed inside the forward) measures; the
+    # rooflines take the stages' kernel time as the interval less that cost
+    ev_over = stages.get("loss", 0.0) if (marks_ok and raster.Rasterizer.fuse_loss) else 0.0
+    net = {s: max(1e-6, ms - ev_over) for s, ms in stages.items() if not (s == "loss" and ev_over > 0.0)}
+    dom = max(net, key=lambda s: net[s])
     pipes = measure_pipe_peaks(dev, local)
     fp32_peak = pipes["fp32_peak_tflops"]
     # operation counts per pair: the kernels' own source (FLOPS_EVAL / FLOPS_BLEND)
@@ -558,12 +563,12 @@ def run_ours(args, rank, local, world):
                 "mufu_frac": round(mufu_s / (ms / 1e3), 4)}
 
     if dom in flops:
-        roofline = dict(alu_entry(dom, stages[dom]), kernel=dom, traffic=measured_traffic(dom, V),
+        roofline = dict(alu_entry(dom, net[dom]), kernel=dom, traffic=measured_traffic(dom, V),
                         peak_source="measured: splat_peak_probe, max of fma.rn.f32 and fma.rn.f32x2 chains",
                         algorithmic_flops=flops[dom], algorithmic_flops_survey_count=survey_flops[dom])
     else:
         alg = algorithmic_bytes(dom, G.n3, G.n4, V, pix, K_inst, 2)
-        ach = alg / (stages[dom] / 1e3) / 1e9
+        ach = alg / (net[dom] / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(ach / hbm_peak, 4), "traffic": measured_traffic(dom, V),
                     "peak_source": peak_src + " (copy bandwidth)", "algorithmic_bytes": alg}
@@ -573,7 +578,7 @@ def run_ours(args, rank, local, world):
     # HBM bytes (inputs read once, outputs written once) against the measured
     # copy bandwidth
     stage_roof = {}
-    for st, ms in stages.items():
+    for st, ms in net.items():
         if ms <= 0:
             continue
         if st == "loss" and raster.Rasterizer.fuse_loss:
@@ -586,6 +591,8 @@ def run_ours(args, rank, local, world):
             a = alg / (ms / 1e3) / 1e9
             stage_roof[st] = {"bound": "hbm", "achieved": round(a, 1), "unit": "GB/s", "frac": round(a / hbm_peak, 4),
                               "algorithmic_bytes": int(alg)}
+    if raster.Rasterizer.fuse_loss and "loss" not in stage_roof:
+        stage_roof["loss"] = {"fused": "computed inside composite_fwd's pixel epilogue (splat_composite_fwd_l1)"}
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -600,6 +607,7 @@ def run_ours(args, rank, local, world):
         "plain_fp32": {"value": round(plain_value, 2), "unit": UNIT, "path": "per-view launches, FP32 storage, eager",
                        "autotune": {k: plain_tune[k] for k in ("ppl_fwd", "ppl_bwd")}},
         "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+        "stage_event_ms": round(ev_over, 4),
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
                 "pipeline": "pinned host parameters and targets copied on a second stream one step ahead; "
                             "loss and status read back after every step"},
