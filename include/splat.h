@@ -167,8 +167,10 @@ typedef struct {
                               on SPLAT_ERR_CAPACITY the count that was needed    */
     uint32_t *tile_order;  /* optional (may be NULL), [total_tiles]: written by
                               splat_bin_sort with the tiles in decreasing
-                              order of list length (powers of two; order inside
-                              a class unspecified); the compositing kernels
+                              order of list length (classes of eight per power
+                              of two: the exponent and the next three bits;
+                              order inside a class unspecified); the
+                              compositing kernels
                               take tiles in this order, the longest first, so
                               that the last wave of warps is short.  Results
                               do not depend on it.  NULL: raster order.      */
