@@ -170,10 +170,10 @@ typedef struct {
                               order of list length (classes of eight per power
                               of two: the exponent and the next three bits;
                               order inside a class unspecified); the
-                              compositing kernels
-                              take tiles in this order, the longest first, so
-                              that the last wave of warps is short.  Results
-                              do not depend on it.  NULL: raster order.      */
+                              compositing kernels take tiles in this order,
+                              the longest first, so that the last wave of
+                              warps is short.  Results do not depend on it.
+                              NULL: raster order.                            */
     int64_t *n_needed;     /* optional (may be NULL), [1]: the capacity the call
                               needed, K or, on the binned path, the larger of K
                               and the super-tile list length (which shares the
