@@ -520,7 +520,7 @@ def run_ours(args, rank, local, world):
     e2e_value = aggregate(V * args.steps, e2e_s, dev)[0]
 
     # ---- pair counts of the compositing kernels (one instrumented step, untimed) ----
-    counters = torch.zeros(4, dtype=torch.int64, device=dev)
+    counters = torch.zeros(8, dtype=torch.int64, device=dev)
     R.set_options(stats=counters.data_ptr())
     try:
         R.step(G, target)

@@ -498,7 +498,7 @@ typedef struct {
     int32_t tile_sort;            /* 0 automatic, 1 radix, 2 binned; -1: splat_set_tile_sort */
     int32_t tile_cull;            /* 0 off, 1 on; -1: splat_set_tile_cull                    */
     int64_t spin_limit;           /* >= 0; -1: splat_set_spin_limit                          */
-    unsigned long long *stats;    /* device uint64[4] (see splat_set_stats); NULL: library default */
+    unsigned long long *stats;    /* device uint64[8] (see splat_set_stats); NULL: library default */
 } splat_options;
 
 /* splat_workspace_size for a call made with the given options (the sort's
@@ -583,12 +583,15 @@ void splat_set_tile_sort(int mode);
 void splat_set_tile_cull(int on);
 
 /*
- * Diagnostic: when dev_counters (device uint64[4]) is not NULL, later
+ * Diagnostic: when dev_counters (device uint64[8]) is not NULL, later
  * compositing launches use an instrumented variant that adds the numbers of
  * pixel-Gaussian pairs evaluated (power computed) and blended by the forward
- * (counters 0, 1) and by the backward (2, 3).  NULL (default) turns it off.
- * Host-side global (the library default of splat_options.stats); the caller
- * zeroes the counters.
+ * (counters 0, 1) and by the backward (2, 3), and splat_bin_sort on the
+ * binned path with culling adds the number of super-tiles whose lists ended
+ * in the saturation head for some of their tiles while others continue in
+ * tail segments (4) and the number of tail segments (5); 6 and 7 are
+ * reserved.  NULL (default) turns it off.  Host-side global (the library
+ * default of splat_options.stats); the caller zeroes the counters.
  */
 void splat_set_stats(unsigned long long *dev_counters);
 

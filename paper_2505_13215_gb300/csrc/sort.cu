@@ -1078,6 +1078,9 @@ struct TileArgs {
     uint32_t* ticket;                 // [3] tickets of the writing and tail counting passes, head count
                                       // CTAs done (zeroed)
     int32_t* status;
+    unsigned long long* stats;        // diagnostic (may be null): [4] super-tiles whose lists ended in
+                                      // the head for some tiles and continue in tail segments for others,
+                                      // [5] tail segments
 };
 
 // Tile saturation.  Every pixel of a tile stops its walk before the first
@@ -1167,10 +1170,29 @@ __device__ __forceinline__ void seg_plan(const TileArgs& a, uint32_t* s_tmp)
         if (gs < a.total_super) {
             a.seg_base[gs] = carry + ex;
             for (uint32_t q = 0; q < c; ++q) a.seg_super[carry + ex + q] = (uint32_t)gs;
+            if (a.stats && c > 0) {  // some of its tiles closed in the head, others open in the tail
+                int v = 0;
+                for (int q = 1; q < a.V; ++q)
+                    if (gs >= a.super_base[q]) v = q;
+                const int ls = gs - a.super_base[v], sy = ls / a.STX[v], sx = ls - sy * a.STX[v];
+                const int nx = min(8, a.TX[v] - 8 * sx), ny = min(8, a.TY[v] - 8 * sy);
+                const uint32_t in_grid = (1u << nx) - 1u;
+                const uint2 sat = a.sat_head[gs];
+                bool closed = false, open = false;
+                for (int r = 0; r < ny; ++r) {
+                    const uint32_t b = ((r < 4 ? sat.x >> (8 * r) : sat.y >> (8 * (r - 4))) & 0xffu) & in_grid;
+                    closed |= b != 0u;
+                    open |= b != in_grid;
+                }
+                if (closed && open) atomicAdd(a.stats + 4, 1ull);
+            }
         }
         carry += tot;
     }
-    if (threadIdx.x == 0) a.seg_base[a.total_super] = carry;
+    if (threadIdx.x == 0) {
+        a.seg_base[a.total_super] = carry;
+        if (a.stats) atomicAdd(a.stats + 5, (unsigned long long)carry);
+    }
 }
 
 // Tile totals, offsets and ranges in one pass over the tiles in global order,
@@ -2133,6 +2155,7 @@ cudaError_t launch_bin_sort(const splat_proj& proj, const ViewBatch& vb, const s
         t.vals_out = bins.vals;
         t.keys_out = bins.keys;
         t.status = status;
+        t.stats = ctx.stats;
         t.cull = ctx.tile_cull;
         t.seg_base = U(L.off_segbase);
         t.seg_cnt = U(L.off_segcnt);

@@ -27,8 +27,8 @@ def test_two_rasterizers_with_their_own_options():
                         device="cuda")
     Ra = raster.Rasterizer(G.n3, G.n4, views)
     Rb = raster.Rasterizer(G.n3, G.n4, views)
-    ca = torch.zeros(4, dtype=torch.int64, device="cuda")
-    cb = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ca = torch.zeros(8, dtype=torch.int64, device="cuda")
+    cb = torch.zeros(8, dtype=torch.int64, device="cuda")
     Ra.set_options(ppl_fwd=2, ppl_bwd=4, tile_sort=1, tile_cull=0, stats=ca.data_ptr())
     Rb.set_options(ppl_fwd=8, ppl_bwd=8, tile_sort=2, tile_cull=1, stats=cb.data_ptr())
     # library-wide defaults that neither rasterizer should follow
@@ -52,6 +52,8 @@ def test_two_rasterizers_with_their_own_options():
         # the pair counters of each rasterizer's own calls (two steps each)
         fa, fb = ca.cpu().numpy(), cb.cpu().numpy()
         assert fa[0] > 0 and fb[0] > 0 and fa[2] > 0 and fb[2] > 0
+        # the sort's counters: only the binned, culled path has tail segments to count
+        assert fa[4] == 0 and fa[5] == 0
         # the result does not depend on the tuning
         assert torch.equal(Ra.rgb, Rb.rgb) and torch.equal(Ra.final_T, Rb.final_T)
         for k in raster.FIELDS3 + raster.FIELDS4:

@@ -317,7 +317,8 @@ def test_saturation_cut_changes_nothing_but_the_lists():
     (the bench's camera batch): with culling on, each tile's list ends once the
     alpha lower bounds certify T < 1e-4 at every pixel of the tile -- in the
     base view every super-tile saturates within the head pass, the turned view
-    sees sparse regions whose tiles continue in the tail -- so the lists shrink
+    sees sparse regions whose tiles continue in the tail, and some super-tiles
+    hold both (the sort's diagnostic counters show it) -- so the lists shrink
     to a fraction of the rectangle lists, while the images, the transmittance
     and the gradients are those of the full lists, and every pixel's walk stops
     at the same Gaussian (or at the end of its list in both runs)."""
@@ -345,10 +346,14 @@ def test_saturation_cut_changes_nothing_but_the_lists():
         return res
 
     out = []
+    counters = torch.zeros(8, dtype=torch.int64, device="cuda")
     for on in (False, True):
         with tile_cull(on):
             R = raster.Rasterizer(G.n3, G.n4, views)
             R.autotune_capacity(G)
+            if on:  # the sort's diagnostic counters of the culled step (the images do not change)
+                R.set_options(stats=counters.data_ptr())
+                counters.zero_()
             R.step(G, target)
             torch.cuda.synchronize()
             R.check()
@@ -357,6 +362,11 @@ def test_saturation_cut_changes_nothing_but_the_lists():
             del R
     (k0, n0, st0, rgb0, T0, g0), (k1, n1, st1, rgb1, T1, g1) = out
     assert k1 < 0.5 * k0, (k0, k1)
+    # the case where the head's cut and the tail's 'done' mask both matter: a
+    # super-tile some of whose tiles' lists ended in the head while others
+    # continued in its tail segments
+    c = counters.cpu().numpy()
+    assert c[4] > 0 and c[5] > 0, c
     assert n1 >= k1 and n0 == k0
     assert torch.equal(rgb0, rgb1) and torch.equal(T0, T1)
     for k in g0:
