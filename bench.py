@@ -271,7 +271,7 @@ FLOPS_EVAL = 5
 FLOPS_BLEND = {"composite_fwd": 5 + 9, "composite_bwd": 5 + 25}
 # the round per-pair figures of the method's cost model: about 15 FP32
 # operations and one exponential per evaluated pair forward, about 60 backward
-SURVEY_OPS = {"composite_fwd": 15, "composite_bwd": 60}
+COST_MODEL_OPS = {"composite_fwd": 15, "composite_bwd": 60}
 KERNEL_SOURCES = {"composite_fwd": ["composite.cu", "splat_internal.cuh"],
                   "composite_bwd": ["composite.cu", "splat_internal.cuh"],
                   "slice_project": ["project.cu", "splat_internal.cuh"],
@@ -543,9 +543,9 @@ def run_ours(args, rank, local, world):
     pipes = measure_pipe_peaks(dev, local)
     fp32_peak = pipes["fp32_peak_tflops"]
     # operation counts per pair: the kernels' own source (FLOPS_EVAL / FLOPS_BLEND)
-    # and the survey's round figures (about 15 FP32 operations per evaluated pair
+    # and the method's cost model in round figures (about 15 FP32 operations per evaluated pair
     # in the forward, about 60 in the backward)
-    survey_flops = {"composite_fwd": SURVEY_OPS["composite_fwd"] * fe, "composite_bwd": SURVEY_OPS["composite_bwd"] * be}
+    model_flops = {"composite_fwd": COST_MODEL_OPS["composite_fwd"] * fe, "composite_bwd": COST_MODEL_OPS["composite_bwd"] * be}
     # MUFU work: one base-2 exponential per evaluated pair in both kernels, plus
     # one reciprocal per evaluated pair in the backward, each at its own
     # measured rate; mufu_frac is the share of the kernel's time the unit needs
@@ -553,19 +553,19 @@ def run_ours(args, rank, local, world):
 
     def alu_entry(st, ms):
         a = flops[st] / (ms / 1e3) / 1e12
-        a_s = survey_flops[st] / (ms / 1e3) / 1e12
+        a_s = model_flops[st] / (ms / 1e3) / 1e12
         n_ex2, n_rcp = mufu_ops[st]
         mufu_s = n_ex2 / (pipes["ex2"] * 1e12) + n_rcp / (pipes["rcp"] * 1e12)
         return {"bound": "alu", "achieved": round(a, 2), "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": round(a / fp32_peak, 4), "achieved_survey_count": round(a_s, 2),
-                "frac_survey_count": round(a_s / fp32_peak, 4),
+                "frac": round(a / fp32_peak, 4), "achieved_cost_model": round(a_s, 2),
+                "frac_cost_model": round(a_s / fp32_peak, 4),
                 "mufu_tops": round((n_ex2 + n_rcp) / (ms / 1e3) / 1e12, 3),
                 "mufu_frac": round(mufu_s / (ms / 1e3), 4)}
 
     if dom in flops:
         roofline = dict(alu_entry(dom, net[dom]), kernel=dom, traffic=measured_traffic(dom, V),
                         peak_source="measured: splat_peak_probe, max of fma.rn.f32 and fma.rn.f32x2 chains",
-                        algorithmic_flops=flops[dom], algorithmic_flops_survey_count=survey_flops[dom])
+                        algorithmic_flops=flops[dom], algorithmic_flops_cost_model=model_flops[dom])
     else:
         alg = algorithmic_bytes(dom, G.n3, G.n4, V, pix, K_inst, 2)
         ach = alg / (net[dom] / 1e3) / 1e9
